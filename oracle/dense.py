@@ -1,0 +1,84 @@
+"""Dense small-grid reference: the plain definition the QTT scheme approximates.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The same discrete scheme as the QTT method, with no tensor network and no
+truncation: fields are dense N x N arrays (axis 0 = x1, axis 1 = x2), the
+central difference is a periodic stencil (Eq. "fdm"), products are
+element-wise, and the penalty projection (I + mu h^2 G^T G) v = w with
+G = [D_1 D_2] is solved exactly per Fourier mode.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def d(F: np.ndarray, axis: int, dx: float) -> np.ndarray:
+    """(F(x+1) - F(x-1)) / (2 dx) along axis 1 (x1) or 2 (x2), periodic."""
+    ax = axis - 1
+    return (np.roll(F, -1, axis=ax) - np.roll(F, 1, axis=ax)) / (2.0 * dx)
+
+
+def convection(u, dx):
+    """Skew-symmetric convection 1/2 sum_j (u_j D_j u_i + D_j(u_j u_i)) (App. B)."""
+    out = []
+    for i in range(2):
+        acc = np.zeros_like(u[i])
+        for j in range(2):
+            acc += 0.5 * (u[j] * d(u[i], j + 1, dx) + d(u[j] * u[i], j + 1, dx))
+        out.append(acc)
+    return out
+
+
+def rhs_B(u, nu, dx):
+    """B_i = convection_i - nu sum_j D_j D_j u_i (App. B, Eq. for B_i)."""
+    conv = convection(u, dx)
+    return [conv[i] - nu * sum(d(d(u[i], j, dx), j, dx) for j in (1, 2)) for i in range(2)]
+
+
+def symbols(N: int, dx: float):
+    """Fourier symbols g_j = i sin(2 pi m_j / N) / dx of D_j (axis 0, 1)."""
+    m = np.fft.fftfreq(N) * N
+    g = 1j * np.sin(2.0 * np.pi * m / N) / dx
+    return g[:, None] * np.ones((1, N)), np.ones((N, 1)) * g[None, :]
+
+
+def project(w, h: float, mu: float, dx: float):
+    """Exact minimiser of mu |D1 v1 + D2 v2|^2 + |v - w|^2 / h^2.
+
+    Per Fourier mode the normal matrix is I + c conj(g) g^T (c = mu h^2;
+    D_j^T = -D_j has symbol conj(g_j)); Sherman-Morrison gives
+    v = w - c conj(g) (g^T w) / (1 + c |g|^2).
+    """
+    N = w[0].shape[0]
+    g1, g2 = symbols(N, dx)
+    c = mu * h * h
+    W1, W2 = np.fft.fft2(w[0]), np.fft.fft2(w[1])
+    gw = g1 * W1 + g2 * W2
+    den = 1.0 + c * (np.abs(g1) ** 2 + np.abs(g2) ** 2)
+    V1 = W1 - c * np.conj(g1) * gw / den
+    V2 = W2 - c * np.conj(g2) * gw / den
+    return [np.real(np.fft.ifft2(V1)), np.real(np.fft.ifft2(V2))]
+
+
+def divergence(u, dx):
+    return d(u[0], 1, dx) + d(u[1], 2, dx)
+
+
+RK4_H = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
+RK4_B = (None, (3.0, 0.25), (1.5, 0.625), (3.0, 0.25))
+
+
+def rk4_step(u, dt, nu, mu, dx):
+    """Four projected Euler stages (App. B, Table RK4, Eqs. U1-U4)."""
+    U = []
+    b = u
+    for s in range(4):
+        if s > 0:
+            c1, c2 = RK4_B[s]
+            b = [c1 * U[s - 1][i] + c2 * u[i] for i in range(2)]
+        h = RK4_H[s] * dt
+        B = rhs_B(b, nu, dx)
+        w = [0.25 * u[i] - h * B[i] for i in range(2)]
+        U.append(project(w, h, mu, dx))
+    return [U[0][i] + U[1][i] + U[2][i] + U[3][i] for i in range(2)]

@@ -1,0 +1,634 @@
+"""QTT / MPS oracle: the paper's algorithm in plain numpy FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Conventions (paper Sec. II.B, "quantics" encoding and Eq. for the MPS):
+  * a velocity component on the periodic N x N grid, N = 2**n, is the array
+    F[x1, x2] (x1 slow); bit k of x_i (k = 1 most significant) is x_i^k;
+  * site k carries the physical index omega_k = 2 * x1^k + x2^k (dim 4);
+  * an MPS is a list of n cores, core k of shape (D_{k-1}, 4, D_k),
+    D_0 = D_n = 1;
+  * an MPO is a list of n cores W[p, s_out, s_in, q] of shape
+    (w_{k-1}, 4, 4, w_k) with the boundary vectors folded in (w_0 = w_n = 1);
+    applied to a state it maps the coefficient at s_in to s_out.
+
+Where the paper is silent or ambiguous, the docstring of the function
+concerned states the reading it implements.
+
+parity: pinned by tests/test_oracle_*.py (carry table of App. A, dense
+stencils, Fourier-space projection, closed forms and invariants).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+D_PHYS = 4
+
+
+def _c(spec, *ops):
+    """Tensor contraction (numpy einsum with pairwise BLAS contractions)."""
+    return np.einsum(spec, *ops, optimize=True)
+
+
+# --------------------------------------------------------------------------
+# Encoding (Sec. II.B, quantics representation)
+# --------------------------------------------------------------------------
+def dense_to_tensor(F: np.ndarray) -> np.ndarray:
+    """Reorder F[x1, x2] into the tensor U[omega_1, ..., omega_n].
+
+    omega_k = (x1^k x2^k)_2, site 1 holding the most significant bits
+    (Sec. II.B).
+    """
+    N = F.shape[0]
+    n = int(round(math.log2(N)))
+    assert F.shape == (N, N) and 2 ** n == N
+    T = F.reshape((2,) * n + (2,) * n)  # x1^1..x1^n, x2^1..x2^n
+    perm = [ax for k in range(n) for ax in (k, n + k)]
+    return T.transpose(perm).reshape((D_PHYS,) * n)
+
+
+def tensor_to_dense(T: np.ndarray, n: int) -> np.ndarray:
+    """Inverse of :func:`dense_to_tensor`."""
+    T = np.asarray(T).reshape((2, 2) * n)  # x1^1, x2^1, x1^2, x2^2, ...
+    perm = list(range(0, 2 * n, 2)) + list(range(1, 2 * n, 2))
+    return T.transpose(perm).reshape(2 ** n, 2 ** n)
+
+
+def trunc_rank(s: np.ndarray, eps: float, chi_max: int) -> int:
+    """Rank kept at one bond (Sec. III.E, Eq. for epsilon).
+
+    The paper defines epsilon for a whole state only; here it is applied
+    per bond, relative to that bond's own weight: the smallest r >= 1 whose
+    discarded weight sum_{j>r} s_j^2 is at most eps^2 * sum_j s_j^2, then
+    capped at chi_max.  s is sorted descending.  An all-zero spectrum keeps
+    rank 1.
+    """
+    s2 = np.asarray(s, dtype=np.float64) ** 2
+    m = s2.shape[0]
+    total = float(s2.sum())
+    if total == 0.0 or m == 0:
+        return 1
+    # tail[j] = sum_{i >= j} s2[i], summed from the small end
+    tail = np.zeros(m + 1)
+    for j in range(m - 1, -1, -1):
+        tail[j] = tail[j + 1] + s2[j]
+    thr = eps * eps * total
+    r = m
+    for cand in range(1, m + 1):
+        if tail[cand] <= thr:
+            r = cand
+            break
+    return max(1, min(r, chi_max))
+
+
+def from_dense(F: np.ndarray, eps: float, chi_max: int) -> list:
+    """TT-SVD of a dense field into a QTT (Sec. II.B; truncation of Sec. III.E).
+
+    Left to right: at each bond the unfolding is split by an SVD, the rank
+    is chosen by :func:`trunc_rank`, U becomes the core and S V^T carries on.
+    """
+    n = int(round(math.log2(F.shape[0])))
+    M = dense_to_tensor(np.asarray(F, dtype=np.float64)).reshape(1, -1)
+    cores = []
+    r = 1
+    for _ in range(n - 1):
+        M = M.reshape(r * D_PHYS, -1)
+        U, S, Vt = np.linalg.svd(M, full_matrices=False)
+        rk = trunc_rank(S, eps, chi_max)
+        cores.append(U[:, :rk].reshape(r, D_PHYS, rk).copy())
+        M = S[:rk, None] * Vt[:rk]
+        r = rk
+    cores.append(M.reshape(r, D_PHYS, 1).copy())
+    return cores
+
+
+def to_dense(cores: list) -> np.ndarray:
+    """Contract the cores left to right and undo the interleaving."""
+    n = len(cores)
+    T = np.ones((1, 1))
+    for A in cores:
+        T = np.tensordot(T, A, axes=(1, 0)).reshape(-1, A.shape[2])
+    return tensor_to_dense(T.reshape(-1), n)
+
+
+def bond_dims(cores: list) -> list:
+    return [1] + [int(A.shape[2]) for A in cores]
+
+
+def inner(A: list, B: list) -> float:
+    """<a|b> by transfer matrices."""
+    E = np.ones((1, 1))
+    for a, b in zip(A, B):
+        E = _c("ab,asc,bsd->cd", E, a, b)
+    return float(E[0, 0])
+
+
+def norm2(A: list) -> float:
+    return inner(A, A)
+
+
+# --------------------------------------------------------------------------
+# MPOs (Sec. II.B and App. A, Table "diff_mpo")
+# --------------------------------------------------------------------------
+def carry_core(axis: int) -> np.ndarray:
+    """Central rank-4 tensor C[alpha_m, omega_m, omega'_m, alpha_{m+1}].
+
+    App. A: alpha_{m+1} is the request coming from the less significant
+    bits (0: keep, 1: add 1, 2: subtract 1) applied to the x-bit (axis 1)
+    or, "using the same logic" (Sec. II.B), to the y-bit (axis 2) of
+    omega_m; alpha_m is the carry / borrow passed to the more significant
+    site.  The table is read with omega_m as the output index and omega'_m
+    as the input index, so that the assembled operator computes
+    (U(x+1) - U(x-1)) / (2 dx); tests pin this against the dense stencil.
+    """
+    assert axis in (1, 2)
+    C = np.zeros((3, D_PHYS, D_PHYS, 3))
+    for q in range(3):
+        for s_out in range(D_PHYS):
+            x, y = s_out >> 1, s_out & 1
+            bit = x if axis == 1 else y
+            if q == 0:
+                nb, p = bit, 0
+            elif q == 1:
+                nb = bit + 1
+                p = 1 if nb == 2 else 0
+                nb %= 2
+            else:
+                nb = bit - 1
+                p = 2 if nb == -1 else 0
+                nb %= 2
+            s_in = (nb << 1 | y) if axis == 1 else (x << 1 | nb)
+            C[p, s_out, s_in, q] = 1.0
+    return C
+
+
+def mpo_diff(n: int, axis: int, dx: float) -> list:
+    """Central-difference MPO D_axis (App. A).
+
+    L = (1, 1, 1) on the most significant side drops the final carry
+    (periodic wrap), R = (0, 1, -1) / (2 dx) on the least significant side
+    starts the +1 / -1 branches.  The grid is periodic, so the spacing is
+    dx = L_domain / N (the paper's 1/(N-1) would not close the period).
+    """
+    C = carry_core(axis)
+    L = np.ones(3)
+    R = np.array([0.0, 1.0, -1.0]) / (2.0 * dx)
+    W = [C.copy() for _ in range(n)]
+    W[0] = np.einsum("p,pstq->stq", L, W[0])[None]
+    W[-1] = np.einsum("pstq,q->pst", W[-1], R)[..., None]
+    return W
+
+
+def mpo_transpose(W: list) -> list:
+    return [w.transpose(0, 2, 1, 3).copy() for w in W]
+
+
+def mpo_product(A: list, B: list) -> list:
+    """The MPO of A.B (B acts first): sum over the shared physical index."""
+    out = []
+    for a, b in zip(A, B):
+        t = np.einsum("pxtq,rtys->prxyqs", a, b)
+        pa, pb, _, _, qa, qb = t.shape
+        out.append(t.reshape(pa * pb, D_PHYS, D_PHYS, qa * qb))
+    return out
+
+
+def mpo_sum(A: list, B: list) -> list:
+    """Block-diagonal sum of two MPOs (bonds add)."""
+    n = len(A)
+    out = []
+    for k, (a, b) in enumerate(zip(A, B)):
+        if n == 1:
+            out.append(a + b)
+        elif k == 0:
+            out.append(np.concatenate([a, b], axis=3))
+        elif k == n - 1:
+            out.append(np.concatenate([a, b], axis=0))
+        else:
+            pa, _, _, qa = a.shape
+            pb, _, _, qb = b.shape
+            t = np.zeros((pa + pb, D_PHYS, D_PHYS, qa + qb))
+            t[:pa, :, :, :qa] = a
+            t[pa:, :, :, qa:] = b
+            out.append(t)
+    return out
+
+
+def mpo_compress(W: list, rel_tol: float = 1e-13) -> list:
+    """Exact (up to rounding) bond reduction of an MPO by the MPS sweep.
+
+    The MPO is read as an MPS with physical dimension 16; singular values
+    below rel_tol times the largest at that bond are dropped.
+    """
+    A = [w.reshape(w.shape[0], D_PHYS * D_PHYS, w.shape[3]) for w in W]
+    n = len(A)
+    for k in range(n - 1):
+        Dl, d, Dr = A[k].shape
+        Q, R = np.linalg.qr(A[k].reshape(Dl * d, Dr))
+        A[k] = Q.reshape(Dl, d, -1)
+        A[k + 1] = np.tensordot(R, A[k + 1], axes=(1, 0))
+    for k in range(n - 1, 0, -1):
+        Dl, d, Dr = A[k].shape
+        U, S, Vt = np.linalg.svd(A[k].reshape(Dl, d * Dr), full_matrices=False)
+        r = max(1, int(np.sum(S > rel_tol * S[0]))) if S[0] > 0 else 1
+        A[k] = Vt[:r].reshape(r, d, Dr)
+        A[k - 1] = np.tensordot(A[k - 1], U[:, :r] * S[:r], axes=(2, 0))
+    return [a.reshape(a.shape[0], D_PHYS, D_PHYS, a.shape[2]) for a in A]
+
+
+def tensor_index(x1: int, x2: int, n: int) -> int:
+    """Flat omega-ordered index of grid point (x1, x2)."""
+    idx = 0
+    for k in range(n):
+        b1 = (x1 >> (n - 1 - k)) & 1
+        b2 = (x2 >> (n - 1 - k)) & 1
+        idx = idx * D_PHYS + (2 * b1 + b2)
+    return idx
+
+
+def mpo_to_dense(W: list) -> np.ndarray:
+    """Dense N^2 x N^2 matrix of an MPO in grid order (x1, x2): brute force,
+    small n only."""
+    n = len(W)
+    T = np.ones((1, 1, 1))  # (out, in, bond)
+    for w in W:
+        T = np.einsum("abp,pxyq->axbyq", T, w)
+        o, _, i, _, q = T.shape
+        T = T.reshape(o * D_PHYS, i * D_PHYS, q)
+    M = T[:, :, 0]
+    N = 2 ** n
+    perm = np.array([tensor_index(x1, x2, n) for x1 in range(N) for x2 in range(N)])
+    return M[np.ix_(perm, perm)]
+
+
+@dataclasses.dataclass
+class Operators:
+    """The MPOs one time step needs, built once (App. A, App. B)."""
+    n: int
+    dx: float
+    D: list            # [D_1, D_2]
+    lap: list          # D_1 D_1 + D_2 D_2, the literal square of the central difference
+    K: dict            # (i, j) -> D_i^T D_j, the blocks of the projection system
+
+
+def build_operators(n: int, dx: float) -> Operators:
+    D1 = mpo_diff(n, 1, dx)
+    D2 = mpo_diff(n, 2, dx)
+    lap = mpo_compress(mpo_sum(mpo_compress(mpo_product(D1, D1)),
+                               mpo_compress(mpo_product(D2, D2))))
+    D = [D1, D2]
+    K = {}
+    for i in range(2):
+        for j in range(2):
+            K[(i, j)] = mpo_compress(mpo_product(mpo_transpose(D[i]), D[j]))
+    return Operators(n=n, dx=dx, D=D, lap=lap, K=K)
+
+
+# --------------------------------------------------------------------------
+# MPS algebra (Sec. II.B-II.C)
+# --------------------------------------------------------------------------
+def compress(cores: list, eps: float, chi_max: int) -> list:
+    """Compression sweep to (eps, chi_max) (Sec. II.C, "repeated SVDs").
+
+    Left to right: QR of the (D_{k-1}*4) x D_k unfolding, R pushed into the
+    next core.  Right to left: SVD of the D_{k-1} x (4*D_k) unfolding, rank
+    by :func:`trunc_rank`, V^T kept as the core and U*S pushed into the
+    previous core.  The result has its centre at site 1 (sites 2..n are
+    right isometries).
+    """
+    A = [np.array(c, dtype=np.float64, copy=True) for c in cores]
+    n = len(A)
+    for k in range(n - 1):
+        Dl, d, Dr = A[k].shape
+        Q, R = np.linalg.qr(A[k].reshape(Dl * d, Dr))
+        A[k] = Q.reshape(Dl, d, Q.shape[1])
+        A[k + 1] = np.tensordot(R, A[k + 1], axes=(1, 0))
+    for k in range(n - 1, 0, -1):
+        Dl, d, Dr = A[k].shape
+        U, S, Vt = np.linalg.svd(A[k].reshape(Dl, d * Dr), full_matrices=False)
+        r = trunc_rank(S, eps, chi_max)
+        A[k] = Vt[:r].reshape(r, d, Dr)
+        A[k - 1] = np.tensordot(A[k - 1], U[:, :r] * S[:r], axes=(2, 0))
+    return A
+
+
+def apply_mpo_exact(W: list, A: list) -> list:
+    """MPO x MPS site by site: out[(a,p), s', (b,q)] = sum_s W[p,s',s,q] A[a,s,b].
+
+    Bonds multiply by the MPO bond (Sec. II.B: MPOs act by contracting the
+    physical indices).
+    """
+    out = []
+    for w, a in zip(W, A):
+        t = np.einsum("pxsq,asb->apxbq", w, a)
+        da, pw, _, db, qw = t.shape
+        out.append(t.reshape(da * pw, D_PHYS, db * qw))
+    return out
+
+
+def apply_mpo(W, A, eps, chi_max):
+    return compress(apply_mpo_exact(W, A), eps, chi_max)
+
+
+def add_exact(coefs, terms) -> list:
+    """Block-diagonal MPS sum sum_t c_t |t> (Sec. II.C "addition step").
+
+    The coefficients scale the first core; bonds add.
+    """
+    n = len(terms[0])
+    out = []
+    for k in range(n):
+        blocks = [t[k] for t in terms]
+        if k == 0:
+            blocks = [c * b for c, b in zip(coefs, blocks)]
+        if n == 1:
+            out.append(sum(blocks))
+        elif k == 0:
+            out.append(np.concatenate(blocks, axis=2))
+        elif k == n - 1:
+            out.append(np.concatenate(blocks, axis=0))
+        else:
+            Dl = sum(b.shape[0] for b in blocks)
+            Dr = sum(b.shape[2] for b in blocks)
+            t = np.zeros((Dl, D_PHYS, Dr))
+            i0 = j0 = 0
+            for b in blocks:
+                t[i0:i0 + b.shape[0], :, j0:j0 + b.shape[2]] = b
+                i0 += b.shape[0]
+                j0 += b.shape[2]
+            out.append(t)
+    return out
+
+
+def add(coefs, terms, eps, chi_max):
+    return compress(add_exact(coefs, terms), eps, chi_max)
+
+
+def hadamard_exact(A, B) -> list:
+    """Element-wise product |a> (.) |b> with bond Da*Db (Sec. II.B, copy
+    tensors delta_{omega omega omega})."""
+    out = []
+    for a, b in zip(A, B):
+        t = np.einsum("asc,bsd->abscd", a, b)
+        da, db, _, dc, dd = t.shape
+        out.append(t.reshape(da * db, D_PHYS, dc * dd))
+    return out
+
+
+def hadamard(A, B, eps, chi_max) -> list:
+    """Hadamard product by zip-up, then a compression sweep (Sec. II.B).
+
+    The chi^2 product bond is never formed.  A carry R[r, a, b] runs left
+    to right; at site k the contraction
+    T[r, s, a', b'] = sum_{a,b} R[r,a,b] A_k[a,s,a'] B_k[b,s,b'] is split
+    by an SVD of its (r*4) x (a'*b') unfolding, keeping
+    min(4r, a'b', chi_max) directions (a cap only: the eps decision is left
+    to the final sweep, whose environments are orthonormal), U becoming the
+    core and S V^T the new carry.  A full compress(eps, chi_max) follows.
+    """
+    n = len(A)
+    R = np.ones((1, 1, 1))
+    C = []
+    for k in range(n):
+        T = _c("rab,asc,bsd->rscd", R, A[k], B[k])
+        r = T.shape[0]
+        if k == n - 1:
+            C.append(T.reshape(r, D_PHYS, 1))
+            break
+        dc, dd = T.shape[2], T.shape[3]
+        M = T.reshape(r * D_PHYS, dc * dd)
+        U, S, Vt = np.linalg.svd(M, full_matrices=False)
+        rk = max(1, min(S.shape[0], chi_max))
+        C.append(U[:, :rk].reshape(r, D_PHYS, rk))
+        R = (S[:rk, None] * Vt[:rk]).reshape(rk, dc, dd)
+    return compress(C, eps, chi_max)
+
+
+# --------------------------------------------------------------------------
+# Variational projection (App. B, Eqs. "first", "second", "big_LS")
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class Params:
+    """Solver parameters; defaults are the paper's (Sec. II.C, App. B)."""
+    eps: float = 1e-8
+    chi_max: int = 64
+    mu: float = 2.5e5
+    cg_tol: float = 1e-5
+    cg_maxit: int = 100
+    sweep_tol: float = 1e-5
+    max_sweeps: int = 20
+
+
+def right_canonicalize(A: list) -> list:
+    """Right-to-left QR sweep: sites 2..n become right isometries."""
+    A = [a.copy() for a in A]
+    for k in range(len(A) - 1, 0, -1):
+        Dl, d, Dr = A[k].shape
+        Q, R = np.linalg.qr(A[k].reshape(Dl, d * Dr).T)
+        A[k] = Q.T.reshape(Q.shape[1], d, Dr)
+        A[k - 1] = np.tensordot(A[k - 1], R.T, axes=(2, 0))
+    return A
+
+
+@dataclasses.dataclass
+class ProjectInfo:
+    sweeps: int = 0
+    cg_iters: int = 0
+    converged: bool = False
+
+
+def project(w: list, h: float, params: Params, ops: Operators):
+    """Minimise mu |D1 v1 + D2 v2|^2 + |v - w|^2 / h^2 over MPS pairs v.
+
+    This is the cost Theta of App. B with w_i = a_i - h B_i formed
+    explicitly as an MPS and the cost multiplied by h^2; its stationarity
+    condition is the coupled system "big_LS",
+    (1 + mu h^2 sum_j D_i^T D_j) C = <basis|w> (Eqs. "first"/"second"
+    with D^T = -D).  DMRG-like single-site sweeps (Sec. II.C): both
+    components share the centre site d; the local system is solved by CG
+    with the operator kept factored (Sec. II.D); the centre moves by QR
+    (QR and SVD give the same state when no bond is truncated).  One
+    sweep = sites 1..n-1 left to right, then n..2 right to left, so the
+    centre returns to site 1; sweeps stop when the relative change of
+    sum_i <v_i|v_i> over one sweep is <= sweep_tol.  Initial guess: w
+    itself, brought to right-canonical form (the paper starts from the
+    previous time step; w is already rank-adapted by its compression).
+    """
+    n = ops.n
+    c = params.mu * h * h
+    V = [right_canonicalize(w[0]), right_canonicalize(w[1])]
+    W = [w[0], w[1]]
+    blocks = [(i, j) for i in range(2) for j in range(2)]
+
+    one3 = np.ones((1, 1, 1))
+    one2 = np.ones((1, 1))
+    LE = {b: [None] * (n + 1) for b in blocks}
+    RE = {b: [None] * (n + 1) for b in blocks}
+    LW = [[None] * (n + 1) for _ in range(2)]
+    RW = [[None] * (n + 1) for _ in range(2)]
+    for b in blocks:
+        LE[b][0] = one3
+        RE[b][n] = one3
+    for i in range(2):
+        LW[i][0] = one2
+        RW[i][n] = one2
+
+    def build_right(k):
+        """Environments of sites k..n-1 (0-based), stored at index k."""
+        for (i, j) in blocks:
+            RE[(i, j)][k] = _c("asb,pstq,xtz,bqz->apx", V[i][k], ops.K[(i, j)][k],
+                               V[j][k], RE[(i, j)][k + 1])
+        for i in range(2):
+            RW[i][k] = _c("asb,csd,bd->ac", V[i][k], W[i][k], RW[i][k + 1])
+
+    def build_left(k):
+        """Environments of sites 0..k-1 (0-based), stored at index k."""
+        for (i, j) in blocks:
+            LE[(i, j)][k] = _c("apx,asb,pstq,xtz->bqz", LE[(i, j)][k - 1], V[i][k - 1],
+                               ops.K[(i, j)][k - 1], V[j][k - 1])
+        for i in range(2):
+            LW[i][k] = _c("ac,asb,csd->bd", LW[i][k - 1], V[i][k - 1], W[i][k - 1])
+
+    for k in range(n - 1, 0, -1):
+        build_right(k)
+
+    info = ProjectInfo()
+
+    def matvec(d, X):
+        Y = [X[0].copy(), X[1].copy()]
+        for (i, j) in blocks:
+            Y[i] += c * _c("apx,pstq,xtz,bqz->asb", LE[(i, j)][d],
+                           ops.K[(i, j)][d], X[j], RE[(i, j)][d + 1])
+        return Y
+
+    def solve(d):
+        rhs = [_c("ac,csd,bd->asb", LW[i][d], W[i][d], RW[i][d + 1]) for i in range(2)]
+        x = [V[0][d].copy(), V[1][d].copy()]
+        its = conjugate_gradient(lambda X: matvec(d, X), rhs, x, params.cg_tol, params.cg_maxit)
+        info.cg_iters += its
+        V[0][d], V[1][d] = x
+
+    def norm_total():
+        return float(sum(np.sum(V[i][0] ** 2) for i in range(2)))
+
+    n_prev = norm_total()
+    for sweep in range(params.max_sweeps):
+        for d in range(0, n - 1):
+            solve(d)
+            for i in range(2):
+                Dl, dd, Dr = V[i][d].shape
+                Q, R = np.linalg.qr(V[i][d].reshape(Dl * dd, Dr))
+                V[i][d] = Q.reshape(Dl, dd, Q.shape[1])
+                V[i][d + 1] = np.tensordot(R, V[i][d + 1], axes=(1, 0))
+            build_left(d + 1)
+        for d in range(n - 1, 0, -1):
+            solve(d)
+            for i in range(2):
+                Dl, dd, Dr = V[i][d].shape
+                Q, R = np.linalg.qr(V[i][d].reshape(Dl, dd * Dr).T)
+                V[i][d] = Q.T.reshape(Q.shape[1], dd, Dr)
+                V[i][d - 1] = np.tensordot(V[i][d - 1], R.T, axes=(2, 0))
+            build_right(d)
+        info.sweeps = sweep + 1
+        n_new = norm_total()
+        if n_new == 0.0 or abs(n_new - n_prev) <= params.sweep_tol * n_new:
+            info.converged = True
+            break
+        n_prev = n_new
+    return V, info
+
+
+def conjugate_gradient(matvec, b, x, tol, maxit) -> int:
+    """Plain CG on a list-of-arrays vector, in place on x (App. B).
+
+    Stops when |r| <= tol * |b| (relative residual) or after maxit
+    iterations; returns the iteration count.
+    """
+    def dot(u, v):
+        return float(sum(np.vdot(a, b_) for a, b_ in zip(u, v)))
+
+    bnorm = math.sqrt(dot(b, b))
+    if bnorm == 0.0:
+        for a in x:
+            a[...] = 0.0
+        return 0
+    Ax = matvec(x)
+    r = [bi - ai for bi, ai in zip(b, Ax)]
+    p = [ri.copy() for ri in r]
+    rs = dot(r, r)
+    it = 0
+    while it < maxit and math.sqrt(rs) > tol * bnorm:
+        Ap = matvec(p)
+        alpha = rs / dot(p, Ap)
+        for xi, pi in zip(x, p):
+            xi += alpha * pi
+        for ri, api in zip(r, Ap):
+            ri -= alpha * api
+        rs_new = dot(r, r)
+        beta = rs_new / rs
+        p = [ri + beta * pi for ri, pi in zip(r, p)]
+        rs = rs_new
+        it += 1
+    return it
+
+
+# --------------------------------------------------------------------------
+# Right-hand side and RK4 (App. B, Eq. for B_i, Table RK4, Eqs. U1-U4)
+# --------------------------------------------------------------------------
+def stage_w(u, b, h, nu, params: Params, ops: Operators):
+    """w_i = u_i / 4 - h B_i(b) with the skew-symmetric convection term
+    B_i = sum_j 1/2 (b_j (.) D_j b_i + D_j (b_j (.) b_i)) - nu D_j^2 b_i
+    (App. B, Eq. for B_i).  Every intermediate is compressed to
+    (eps, chi_max); the sums are taken pairwise in the order below.
+    """
+    eps, chi = params.eps, params.chi_max
+    Db = {(j, i): apply_mpo(ops.D[j], b[i], eps, chi) for i in range(2) for j in range(2)}
+    P = {(j, i): hadamard(b[j], Db[(j, i)], eps, chi) for i in range(2) for j in range(2)}
+    Q = {}
+    for j in range(2):
+        for i in range(j, 2):
+            Q[(j, i)] = hadamard(b[j], b[i], eps, chi)
+    Q[(1, 0)] = Q[(0, 1)]
+    DQ = {(j, i): apply_mpo(ops.D[j], Q[(j, i)], eps, chi) for i in range(2) for j in range(2)}
+    Lb = [apply_mpo(ops.lap, b[i], eps, chi) for i in range(2)]
+    w = []
+    for i in range(2):
+        ca = add([1.0, 1.0], [P[(0, i)], P[(1, i)]], eps, chi)
+        cb = add([1.0, 1.0], [DQ[(0, i)], DQ[(1, i)]], eps, chi)
+        conv = add([0.5, 0.5], [ca, cb], eps, chi)
+        B = add([1.0, -nu], [conv, Lb[i]], eps, chi)
+        w.append(add([0.25, -h], [u[i], B], eps, chi))
+    return w
+
+
+RK4_H = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)        # h_s / dt, Eqs. U1-U4
+RK4_B = (None, (3.0, 0.25), (1.5, 0.625), (3.0, 0.25))      # Table RK4
+
+
+def rk4_step(u, dt: float, nu: float, params: Params, ops: Operators, stats=None):
+    """One RK4 step as four penalised Euler minimisations (App. B, Eq.
+    "4euler", Table RK4, Eqs. U1-U4); u^{s+1} = U1 + U2 + U3 + U4, summed
+    left to right with a compression after each addition."""
+    eps, chi = params.eps, params.chi_max
+    U = []
+    b = u
+    for s in range(4):
+        if s > 0:
+            c1, c2 = RK4_B[s]
+            b = [add([c1, c2], [U[s - 1][i], u[i]], eps, chi) for i in range(2)]
+        h = RK4_H[s] * dt
+        w = stage_w(u, b, h, nu, params, ops)
+        v, info = project(w, h, params, ops)
+        if stats is not None:
+            stats.append(info)
+        U.append(v)
+    out = []
+    for i in range(2):
+        acc = add([1.0, 1.0], [U[0][i], U[1][i]], eps, chi)
+        acc = add([1.0, 1.0], [acc, U[2][i]], eps, chi)
+        acc = add([1.0, 1.0], [acc, U[3][i]], eps, chi)
+        out.append(acc)
+    return out
