@@ -10,7 +10,7 @@ Modules
 -------
 ``oracle.qtt``    the QTT/MPS algorithm of the paper (Sec. II.B-II.C,
                   App. A-B) written out step by step with numpy FP64
-                  (numpy's QR / SVD / einsum serve as library primitives).
+                  (numpy's QR / SVD / tensordot serve as library primitives).
 ``oracle.dense``  the plain definition the QTT method approximates: the same
                   finite-difference scheme on the dense 2^n x 2^n grid, with
                   the penalty projection solved exactly in Fourier space.

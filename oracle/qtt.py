@@ -28,9 +28,45 @@ import numpy as np
 D_PHYS = 4
 
 
-def _c(spec, *ops):
-    """Tensor contraction (numpy einsum with pairwise BLAS contractions)."""
-    return np.einsum(spec, *ops, optimize=True)
+td = np.tensordot   # pairwise contractions below are plain matrix products
+
+
+def env_left(E, vi, K, vj):
+    """E'[b,q,z] = sum E[a,p,x] vi[a,s,b] K[p,s,t,q] vj[x,t,z]."""
+    t = td(E, vj, ([2], [0]))              # a p t z
+    t = td(t, K, ([1, 2], [0, 2]))         # a z s q
+    t = td(t, vi, ([0, 2], [0, 1]))        # z q b
+    return t.transpose(2, 1, 0)
+
+
+def env_right(E, vi, K, vj):
+    """E'[a,p,x] = sum vi[a,s,b] K[p,s,t,q] vj[x,t,z] E[b,q,z]."""
+    t = td(vj, E, ([2], [2]))              # x t b q
+    t = td(t, K, ([1, 3], [2, 3]))         # x b p s
+    t = td(t, vi, ([1, 3], [2, 1]))        # x p a
+    return t.transpose(2, 1, 0)
+
+
+def local_apply(LE, K, X, RE):
+    """Y[a,s,b] = sum LE[a,p,x] K[p,s,t,q] X[x,t,z] RE[b,q,z]."""
+    t = td(LE, X, ([2], [0]))              # a p t z
+    t = td(t, K, ([1, 2], [0, 2]))         # a z s q
+    return td(t, RE, ([1, 3], [2, 1]))     # a s b
+
+
+def ovl_left(E, vi, wi):
+    """E'[b,d] = sum E[a,c] vi[a,s,b] wi[c,s,d]."""
+    return td(vi, td(E, wi, ([1], [0])), ([0, 1], [0, 1]))
+
+
+def ovl_right(E, vi, wi):
+    """E'[a,c] = sum vi[a,s,b] wi[c,s,d] E[b,d]."""
+    return td(vi, td(wi, E, ([2], [1])), ([1, 2], [1, 2]))
+
+
+def local_rhs(LW, wi, RW):
+    """b[a,s,b] = sum LW[a,c] wi[c,s,d] RW[b,d]."""
+    return td(td(LW, wi, ([1], [0])), RW, ([2], [1]))
 
 
 # --------------------------------------------------------------------------
@@ -122,7 +158,7 @@ def inner(A: list, B: list) -> float:
     """<a|b> by transfer matrices."""
     E = np.ones((1, 1))
     for a, b in zip(A, B):
-        E = _c("ab,asc,bsd->cd", E, a, b)
+        E = ovl_left(E, a, b)
     return float(E[0, 0])
 
 
@@ -393,7 +429,8 @@ def hadamard(A, B, eps, chi_max) -> list:
     R = np.ones((1, 1, 1))
     C = []
     for k in range(n):
-        T = _c("rab,asc,bsd->rscd", R, A[k], B[k])
+        T = np.stack([td(td(R, A[k][:, s, :], ([1], [0])), B[k][:, s, :], ([1], [0]))
+                      for s in range(D_PHYS)], axis=1)      # r s a' b'
         r = T.shape[0]
         if k == n - 1:
             C.append(T.reshape(r, D_PHYS, 1))
@@ -479,18 +516,17 @@ def project(w: list, h: float, params: Params, ops: Operators):
     def build_right(k):
         """Environments of sites k..n-1 (0-based), stored at index k."""
         for (i, j) in blocks:
-            RE[(i, j)][k] = _c("asb,pstq,xtz,bqz->apx", V[i][k], ops.K[(i, j)][k],
-                               V[j][k], RE[(i, j)][k + 1])
+            RE[(i, j)][k] = env_right(RE[(i, j)][k + 1], V[i][k], ops.K[(i, j)][k], V[j][k])
         for i in range(2):
-            RW[i][k] = _c("asb,csd,bd->ac", V[i][k], W[i][k], RW[i][k + 1])
+            RW[i][k] = ovl_right(RW[i][k + 1], V[i][k], W[i][k])
 
     def build_left(k):
         """Environments of sites 0..k-1 (0-based), stored at index k."""
         for (i, j) in blocks:
-            LE[(i, j)][k] = _c("apx,asb,pstq,xtz->bqz", LE[(i, j)][k - 1], V[i][k - 1],
-                               ops.K[(i, j)][k - 1], V[j][k - 1])
+            LE[(i, j)][k] = env_left(LE[(i, j)][k - 1], V[i][k - 1], ops.K[(i, j)][k - 1],
+                                     V[j][k - 1])
         for i in range(2):
-            LW[i][k] = _c("ac,asb,csd->bd", LW[i][k - 1], V[i][k - 1], W[i][k - 1])
+            LW[i][k] = ovl_left(LW[i][k - 1], V[i][k - 1], W[i][k - 1])
 
     for k in range(n - 1, 0, -1):
         build_right(k)
@@ -500,12 +536,11 @@ def project(w: list, h: float, params: Params, ops: Operators):
     def matvec(d, X):
         Y = [X[0].copy(), X[1].copy()]
         for (i, j) in blocks:
-            Y[i] += c * _c("apx,pstq,xtz,bqz->asb", LE[(i, j)][d],
-                           ops.K[(i, j)][d], X[j], RE[(i, j)][d + 1])
+            Y[i] += c * local_apply(LE[(i, j)][d], ops.K[(i, j)][d], X[j], RE[(i, j)][d + 1])
         return Y
 
     def solve(d):
-        rhs = [_c("ac,csd,bd->asb", LW[i][d], W[i][d], RW[i][d + 1]) for i in range(2)]
+        rhs = [local_rhs(LW[i][d], W[i][d], RW[i][d + 1]) for i in range(2)]
         x = [V[0][d].copy(), V[1][d].copy()]
         its = conjugate_gradient(lambda X: matvec(d, X), rhs, x, params.cg_tol, params.cg_maxit)
         info.cg_iters += its
