@@ -1,0 +1,151 @@
+/*
+ * qtt.h -- C ABI of the QTT / MPS Navier-Stokes time step on one B300 GPU.
+ *
+ * The operations follow the problem statement of arXiv 2406.17823
+ * ("quantum-inspired" incompressible 2-D Navier-Stokes): velocity
+ * components are quantics tensor trains (MPS with interleaved x1/x2 bits,
+ * Sec. II.B), derivatives are MPOs (App. A), the convection term uses
+ * Hadamard products (Sec. II.B), and one time step is RK4 written as four
+ * penalised Euler minimisations solved by DMRG-like sweeps (Sec. II.C,
+ * App. B).  Every call below enqueues work on the context's CUDA stream
+ * and returns without waiting, except where stated.
+ *
+ * Conventions shared by all calls
+ *   - Grid: periodic, N = 2^n points per side over [0, L)^2, dx = L / N.
+ *     A dense field is N*N doubles, row-major, F[x1 * N + x2] (x1 slow).
+ *   - Site k = 1..n carries omega_k = 2 * x1^k + x2^k, site 1 the most
+ *     significant bits (Sec. II.B).
+ *   - An MPS with bond dimensions D_0 = 1, D_1, ..., D_n = 1 has cores of
+ *     shape (D_{k-1}, 4, D_k).  The "packed" layout is the n cores one
+ *     after the other, each contiguous and row-major.
+ *   - qtt_mps / qtt_mpo objects are owned by the library: every `out`
+ *     is newly allocated and must be released with qtt_free_mps /
+ *     qtt_free_mpo.  Device buffers passed in (d_*) belong to the caller
+ *     and are only read (or written, for outputs) by work on the context
+ *     stream; they must stay valid until that work has completed.
+ *   - Errors: every call returns a qtt_status.  Argument and shape errors
+ *     are reported at once.  Errors found on the device (a non-finite
+ *     value, a CG that did not converge) are recorded in the context and
+ *     returned by the next call that synchronises (qtt_sync,
+ *     qtt_to_dense, qtt_mps_info, qtt_mps_to_packed) or by
+ *     qtt_project / qtt_rk4_step, which synchronise internally.
+ *     qtt_last_error() gives a one-line description.
+ */
+#ifndef QTT_H_
+#define QTT_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qtt_ctx_s* qtt_ctx;
+typedef struct qtt_mps_s* qtt_mps;
+typedef struct qtt_mpo_s* qtt_mpo;
+
+typedef enum {
+  QTT_OK = 0,
+  QTT_ERR_ARG = 1,            /* invalid argument                         */
+  QTT_ERR_SHAPE = 2,          /* incompatible n / bond dimensions         */
+  QTT_ERR_ALLOC = 3,          /* device or host allocation failed         */
+  QTT_ERR_CUDA = 4,           /* a CUDA runtime call failed               */
+  QTT_ERR_NOT_CONVERGED = 5,  /* CG or sweep limit reached (result kept)  */
+  QTT_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up       */
+  QTT_ERR_NUMERIC = 7         /* NaN / Inf met on the device              */
+} qtt_status;
+
+typedef enum {
+  QTT_PREC_FP64 = 0,   /* every contraction and factorisation in FP64      */
+  QTT_PREC_MIXED = 1   /* tensor-core contractions, FP64 gauge / residual  */
+} qtt_precision;
+
+/* Solver parameters.  Paper defaults (Sec. II.C, App. B): mu = 2.5e5,
+ * cg_tol = 1e-5, cg_maxit = 100, sweep_tol = 1e-5. */
+typedef struct {
+  int n;              /* bits per axis, 1 <= n <= 16                      */
+  double L;           /* domain length (dx = L / 2^n)                     */
+  double eps;         /* relative truncation per bond (Sec. III.E)        */
+  int chi_max;        /* bond cap                                         */
+  double mu;          /* penalty of the divergence term (App. B)          */
+  double cg_tol;      /* CG stop: |r| <= cg_tol |b|                       */
+  int cg_maxit;       /* CG iteration cap per local solve                 */
+  double sweep_tol;   /* sweep stop: relative change of sum_i <v_i|v_i>   */
+  int max_sweeps;     /* sweep cap per projection                         */
+  int precision;      /* qtt_precision                                    */
+} qtt_params;
+
+/* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,
+ * NULL = the legacy default stream).  Builds the MPOs D_1, D_2, the
+ * Laplacian D_1 D_1 + D_2 D_2 and the projection blocks D_i^T D_j for
+ * dx = L / 2^n (App. A).  Returns QTT_ERR_ARG for invalid parameters. */
+qtt_status qtt_create(qtt_ctx* out, int device, void* cuda_stream, const qtt_params* params);
+qtt_status qtt_destroy(qtt_ctx ctx);
+/* Replace the solver parameters (n and L must not change). */
+qtt_status qtt_set_params(qtt_ctx ctx, const qtt_params* params);
+/* Wait for all work on the context stream; returns a deferred error. */
+qtt_status qtt_sync(qtt_ctx ctx);
+const char* qtt_last_error(qtt_ctx ctx);
+
+/* Dense field (device, N*N doubles) -> QTT by a left-to-right TT-SVD with
+ * per-bond truncation (eps, chi_max) (Sec. II.B, Sec. III.E). */
+qtt_status qtt_from_dense(qtt_ctx ctx, const double* d_field, double eps, int chi_max,
+                          qtt_mps* out);
+/* QTT -> dense field (device, N*N doubles).  Synchronises. */
+qtt_status qtt_to_dense(qtt_ctx ctx, qtt_mps mps, double* d_field_out);
+
+/* Build an MPS from packed cores (see conventions).  `cores_are_device`
+ * selects whether `cores` is a device or a host pointer; bonds[0..n]. */
+qtt_status qtt_mps_from_packed(qtt_ctx ctx, const double* cores, int cores_are_device,
+                               const int* bonds, qtt_mps* out);
+/* Copy an MPS out in packed layout.  Synchronises; writes bonds[0..n] and
+ * at most `capacity` doubles to `cores` (device or host). */
+qtt_status qtt_mps_to_packed(qtt_ctx ctx, qtt_mps mps, double* cores, int cores_are_device,
+                             size_t capacity, int* bonds);
+/* n and the current bonds[0..n].  Synchronises. */
+qtt_status qtt_mps_info(qtt_mps mps, int* n, int* bonds);
+void qtt_free_mps(qtt_mps mps);
+
+/* The context's operators: which = 1 (D_1), 2 (D_2), 3 (Laplacian),
+ * 4 + 2i + j (the projection block D_i^T D_j, i, j in {0, 1}).  The handle
+ * is a new reference owned by the caller. */
+qtt_status qtt_mpo_get(qtt_ctx ctx, int which, qtt_mpo* out);
+void qtt_free_mpo(qtt_mpo mpo);
+
+/* out = compress(W |in>, eps, chi_max): site-wise MPO x MPS contraction
+ * (Sec. II.B) followed by the compression sweep (Sec. II.C). */
+qtt_status qtt_apply_mpo(qtt_ctx ctx, qtt_mpo mpo, qtt_mps in, double eps, int chi_max,
+                         qtt_mps* out);
+/* out = compress(sum_t coef[t] |terms[t]>, eps, chi_max), k >= 1 terms
+ * (block-diagonal MPS sum, Sec. II.C "addition step"). */
+qtt_status qtt_add(qtt_ctx ctx, int k, const double* coef, const qtt_mps* terms, double eps,
+                   int chi_max, qtt_mps* out);
+/* out ~ |a> (.) |b>, the element-wise product (Sec. II.B), by a
+ * left-to-right zip-up capped at chi_max then compress(eps, chi_max). */
+qtt_status qtt_hadamard(qtt_ctx ctx, qtt_mps a, qtt_mps b, double eps, int chi_max,
+                        qtt_mps* out);
+/* In-place compression sweep: left-to-right QR, right-to-left truncated
+ * SVD keeping per bond the smallest rank whose discarded weight is at most
+ * eps^2 of the bond's weight, capped at chi_max (Sec. II.C, Sec. III.E). */
+qtt_status qtt_compress(qtt_ctx ctx, qtt_mps inout, double eps, int chi_max);
+/* (v1, v2) = argmin mu |D_1 v1 + D_2 v2|^2 + |v - w|^2 / h^2 by DMRG-like
+ * single-site sweeps with CG local solves (App. B, Eqs. "first", "second",
+ * "big_LS"; Sec. II.C).  Initial guess w; bonds of w are kept.
+ * Synchronises; cg_iters / sweeps may be NULL.  Returns
+ * QTT_ERR_NOT_CONVERGED (results still written) when a cap was hit. */
+qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1,
+                       qtt_mps* v2, int* cg_iters, int* sweeps);
+/* One RK4 step (App. B, Eq. "4euler", Table RK4, Eqs. U1-U4) in place:
+ * *u1, *u2 are replaced by new handles (the old ones are released).
+ * nu = 1 / Re.  Synchronises (the projections do). */
+qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu);
+
+/* Counters of the last qtt_project / qtt_rk4_step: total CG iterations,
+ * sweeps, kernel launches enqueued by the library since context creation. */
+qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps,
+                     long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTT_H_ */

@@ -1,0 +1,7 @@
+"""B300-native QTT / MPS time step for 2-D incompressible Navier-Stokes.
+
+The compute path is the CUDA library libqtt_b300.so (C ABI in
+include/qtt.h); :mod:`paper_2406_17823_b300.qtt` is its Python binding.
+"""
+from .qtt import (PREC_FP64, PREC_MIXED, Context, MPS, Params, QttError,  # noqa: F401
+                  EXPORTS, lib)

@@ -1,0 +1,92 @@
+// Shared types of the QTT library: device-side dimension references, matrix
+// views over capacity-padded storage, error handling and launch helpers.
+//
+// Storage model.  Every tensor (MPS core, environment, carry) lives in a
+// buffer sized for its CAPACITY along each index; the ACTUAL extents (bond
+// dimensions chosen by truncation on the device) are ints in device memory,
+// and everything outside the actual extents is kept exactly zero.  Dense
+// contractions therefore run over capacities without reading the actual
+// dims (zeros contribute nothing), and only factorisations, which must see
+// the true shape, read them.  No host synchronisation is needed to enqueue
+// an operation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "qtt.h"
+
+#define QTT_MAX_N 20
+
+// value = (p ? *p : 1) * c
+struct DimRef {
+  const int* p;
+  int c;
+};
+static inline DimRef dconst(int c) { return DimRef{nullptr, c}; }
+static inline DimRef dref(const int* p, int c = 1) { return DimRef{p, c}; }
+__device__ __forceinline__ int dval(const DimRef& d) { return d.p ? (*d.p) * d.c : d.c; }
+
+// One matrix index made of (hi, lo) with storage index hi * lcap + lo; the
+// actual entries are hi < hact, lo < lact.  Compact index jc maps to
+// (jc / lact) * lcap + jc % lact.
+struct Axis {
+  int hcap, lcap;
+  DimRef hact, lact;
+};
+static inline Axis axis_prefix(int cap, DimRef act) { return Axis{cap, 1, act, dconst(1)}; }
+static inline Axis axis_pair(int hcap, DimRef hact, int lcap, DimRef lact) {
+  return Axis{hcap, lcap, hact, lact};
+}
+__device__ __forceinline__ int axis_len(const Axis& a) { return dval(a.hact) * dval(a.lact); }
+__device__ __forceinline__ int axis_full(const Axis& a, int jc, int lact) {
+  return (jc / lact) * a.lcap + (jc % lact);
+}
+__device__ __forceinline__ bool axis_actual(const Axis& a, int j, int hact, int lact) {
+  return (j / a.lcap) < hact && (j % a.lcap) < lact;
+}
+
+// Row-major matrix over capacity storage: element (i, j) at ptr[i * ld + j].
+struct MatView {
+  double* ptr;
+  int ld;
+  Axis rows, cols;
+};
+
+// Device-side error flags (bit mask), read at synchronisation points.
+enum : int {
+  QTT_DEVERR_NUMERIC = 1,
+  QTT_DEVERR_SHAPE = 2,
+  QTT_DEVERR_TIMEOUT = 4,
+};
+
+struct LaunchCounter {
+  long long n = 0;
+};
+extern thread_local LaunchCounter* g_launch_counter;
+static inline void count_launch() {
+  if (g_launch_counter) g_launch_counter->n++;
+}
+
+#define QTT_CUDA_CHECK(expr)                                   \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) throw CudaError(_e, #expr, __LINE__); \
+  } while (0)
+
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+  int line;
+  CudaError(cudaError_t e_, const char* w, int l) : e(e_), what(w), line(l) {}
+};
+
+struct QttError {
+  qtt_status st;
+  std::string msg;
+  QttError(qtt_status s, std::string m) : st(s), msg(std::move(m)) {}
+};
+
+static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

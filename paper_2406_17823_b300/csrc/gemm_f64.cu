@@ -1,0 +1,96 @@
+// Batched FP64 GEMM used for every dense contraction of the FP64 path:
+// C[z] = alpha * op(A[z]) * op(B[z]) + beta * C[z], row-major operands,
+// op = optional transpose, batch z = z1 * nb2 + z2 with two stride levels
+// (the site contractions of the zip-up batch over (carry row, omega)).
+//
+// Tiling: 64 x 64 output tile per 256-thread CTA, K staged 16 at a time in
+// shared memory, 4 x 4 register accumulators per thread.  FP64 on this GPU
+// runs on the CUDA-core DFMA pipe (no FP64 tensor-core rate worth using), so
+// the kernel is DFMA-bound once tiles are full.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
+  if (g.skip && *g.skip) return;
+  const int z = blockIdx.z;
+  const int z1 = z / g.nb2, z2 = z % g.nb2;
+  const double* A = g.A + z1 * g.sA1 + z2 * g.sA2;
+  const double* B = g.B + z1 * g.sB1 + z2 * g.sB2;
+  double* C = g.C + z1 * g.sC1 + z2 * g.sC2;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+    for (int t = 0; t < 4; t++) {
+      int idx = tid + t * 256;
+      int mm, kk;
+      if (!g.tA) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
+      int gm = m0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < g.M && gk < g.K) v = g.tA ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
+      As[kk][mm] = v;
+      int nn;
+      if (!g.tB) { kk = idx / BN; nn = idx % BN; } else { nn = idx / BK; kk = idx % BK; }
+      int gn = n0 + nn;
+      gk = k0 + kk;
+      double w = 0.0;
+      if (gn < g.N && gk < g.K) w = g.tB ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
+      Bs[kk][nn] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk++) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    int gm = m0 + ty + 16 * i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      int gn = n0 + tx + 16 * j;
+      if (gn >= g.N) continue;
+      double* c = C + (long long)gm * g.ldc + gn;
+      double v = g.alpha * acc[i][j];
+      if (g.beta != 0.0) v = fma(g.beta, *c, v);
+      *c = v;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_gemm_f64(const GemmF64& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.nb1 * g.nb2 <= 0) return;
+  if (g.K <= 0) {
+    // C = beta * C (alpha * empty product)
+    launch_scale(g, s);
+    return;
+  }
+  dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.nb1 * g.nb2);
+  k_gemm_f64<<<grid, 256, 0, s>>>(g);
+  count_launch();
+}

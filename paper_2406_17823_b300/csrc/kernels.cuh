@@ -1,0 +1,115 @@
+// Kernel argument structs and launchers (host-callable), FP64 path.
+#pragma once
+
+#include "common.cuh"
+
+// ---------------------------------------------------------------- GEMM
+struct GemmF64 {
+  const double* A;
+  const double* B;
+  double* C;
+  int M, N, K;
+  int lda, ldb, ldc;
+  long long sA1, sA2, sB1, sB2, sC1, sC2;  // batch strides, z = z1 * nb2 + z2
+  int nb1, nb2;
+  int tA, tB;  // op(A) = A^T when tA (A stored K x M), likewise B
+  double alpha, beta;
+  const int* skip;  // if non-null and *skip != 0 the launch does nothing
+};
+static inline GemmF64 gemm_plain(const double* A, const double* B, double* C, int M, int N,
+                                 int K, int lda, int ldb, int ldc) {
+  GemmF64 g{};
+  g.A = A; g.B = B; g.C = C;
+  g.M = M; g.N = N; g.K = K;
+  g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+  g.nb1 = 1; g.nb2 = 1;
+  g.alpha = 1.0; g.beta = 0.0;
+  return g;
+}
+void launch_gemm_f64(const GemmF64& g, cudaStream_t s);
+void launch_scale(const GemmF64& g, cudaStream_t s);  // C = beta C
+
+// ---------------------------------------------------------------- QR
+// Householder QR of F = A (or A^T when inT): F = Q R, Q (m x r) with
+// orthonormal columns, R (r x c) upper triangular, r = min(m, c).
+struct QrArgs {
+  MatView A;
+  int inT;
+  MatView Q;   // m x r  (or r x m when qT)
+  int qT;
+  MatView R;   // r x c  (or c x r when rT)
+  int rT;
+  int* r_out;  // receives r (may be null)
+  double* work;
+  const int* skip;
+  int* err;
+};
+size_t qr_work_doubles(int mcap, int ccap);
+void launch_qr_f64(const QrArgs& a, int mcap, int ccap, cudaStream_t s);
+
+// ---------------------------------------------------------------- SVD
+// SVD of M (m x N): Householder QR of the tall orientation, one-sided
+// Jacobi on the square factor, descending order, rank by the truncation
+// rule (eps >= 0) or by the cap alone (eps < 0).  Writes U*S (m x r) and
+// V^T (r x N) of F = M (or M^T when inT), each optionally transposed.
+struct SvdArgs {
+  MatView M;
+  int inT;     // factor M^T instead of M
+  MatView US;
+  int usT;     // write (U S)^T
+  MatView VT;
+  int vtT;     // write (V^T)^T
+  double eps;
+  int chi;
+  DimRef rank_limit;
+  int* r_out;
+  double* sv_out;   // optional, receives the c singular values
+  double* work;
+  const int* skip;
+  int* err;
+};
+size_t svd_work_doubles(int mcap, int ncap);
+void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);
+
+// ---------------------------------------------------------------- misc
+void launch_zero(double* p, size_t n, cudaStream_t s);
+void launch_copy(double* dst, const double* src, size_t n, cudaStream_t s);
+void launch_fill(double* p, size_t n, double v, cudaStream_t s);
+// out[(a,p), so, (b,q)] = sum_si W[p,so,si,q] A[a,si,b], capacities a<Ca, b<Cb
+void launch_mpo_expand(const double* W, int wl, int wr, const double* A, int Ca, int Cb,
+                       double* out, cudaStream_t s);
+// Block-diagonal placement of up to 8 cores (actual dims read on the device).
+struct AddTerm {
+  const double* core;
+  int capl, capr;
+  const int* dl;  // actual left dim (device)
+  const int* dr;  // actual right dim (device)
+  double coef;    // applied on the first site
+};
+void launch_add_assemble(const AddTerm* terms, int K, int first, int last, double* out,
+                         int capl_out, int capr_out, cudaStream_t s);
+// out[b][s][a] = in[a][s][b]   (capacities)
+void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaStream_t s);
+void launch_set_int(int* p, int v, cudaStream_t s);
+void launch_fill_int(int* p, int n, int v, cudaStream_t s);
+// out[b] = sum_t src[t][b] * mul[t][b] for 0 < b < nb-1, out[0] = out[nb-1] = 1
+void launch_dims(const int* const* src, const int (*mul)[QTT_MAX_N + 1], int K, int nb, int* out,
+                 cudaStream_t s);
+void launch_dense_to_omega(const double* F, double* T, int n, cudaStream_t s);
+void launch_omega_to_dense(const double* T, double* F, int n, cudaStream_t s);
+void launch_check_finite(const double* p, size_t n, int* err, cudaStream_t s);
+
+// CG on the two-component local vector (App. B).
+struct CgVec {
+  double* x[2];
+  double* r[2];
+  double* p[2];
+  double* ap[2];
+  long long len[2];
+};
+// scal: [0] r.r, [1] b.b, [2] tol^2 b.b ; ist: [0] done, [1] iterations
+void launch_cg_start(const CgVec& v, const double* b0, const double* b1, double* scal, int* ist,
+                     double tol, int* err, cudaStream_t s);
+void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err, cudaStream_t s);
+void launch_sumsq2(const double* a, long long na, const double* b, long long nb, double* out,
+                   cudaStream_t s);

@@ -1,0 +1,363 @@
+// Data-movement kernels of the QTT path: MPO x MPS site expansion
+// (Sec. II.B), block-diagonal MPS sums (Sec. II.C), core transposes,
+// dense <-> quantics reordering (Sec. II.B), and the CG vector updates
+// of the local solves (App. B).  The CG updates run in one CTA: the local
+// vectors are at most a few 10^4 doubles, and a single CTA gives a fixed,
+// reproducible summation order.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+__global__ void k_scale(double* C, int M, int N, int ldc, double beta) {
+  const long long tot = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    C[(long long)i * ldc + j] *= beta;
+  }
+}
+
+// out[(a,p), so, (b,q)] = sum_si W[p, so, si, q] * A[a, si, b]
+__global__ void k_mpo_expand(const double* __restrict__ W, int wl, int wr,
+                             const double* __restrict__ A, int Ca, int Cb, double* out) {
+  const long long tot = (long long)Ca * wl * 4 * Cb * wr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long t = e;
+    const int q = (int)(t % wr); t /= wr;
+    const int b = (int)(t % Cb); t /= Cb;
+    const int so = (int)(t % 4); t /= 4;
+    const int p = (int)(t % wl); t /= wl;
+    const int a = (int)t;
+    double acc = 0.0;
+#pragma unroll
+    for (int si = 0; si < 4; si++) {
+      const double w = W[((p * 4 + so) * 4 + si) * wr + q];
+      if (w != 0.0) acc = fma(w, A[((long long)a * 4 + si) * Cb + b], acc);
+    }
+    out[e] = acc;
+  }
+}
+
+struct AddArgs {
+  AddTerm t[8];
+  int K;
+  int first, last;
+  double* out;
+  int capl, capr;
+};
+
+__global__ void k_add_assemble(AddArgs g) {
+  int loff[9], roff[9];
+  loff[0] = roff[0] = 0;
+  for (int t = 0; t < g.K; t++) {
+    loff[t + 1] = loff[t] + (g.first ? 0 : *g.t[t].dl);
+    roff[t + 1] = roff[t] + (g.last ? 0 : *g.t[t].dr);
+  }
+  const long long tot = (long long)g.capl * 4 * g.capr;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % g.capr);
+    const int s = (int)((e / g.capr) % 4);
+    const int i = (int)(e / ((long long)g.capr * 4));
+    double v = 0.0;
+    for (int t = 0; t < g.K; t++) {
+      const int dl = *g.t[t].dl, dr = *g.t[t].dr;
+      const int ii = g.first ? i : i - loff[t];
+      const int jj = g.last ? j : j - roff[t];
+      if (ii >= 0 && ii < dl && jj >= 0 && jj < dr) {
+        const double x = g.t[t].core[((long long)ii * 4 + s) * g.t[t].capr + jj];
+        if (g.first && g.last) v += g.t[t].coef * x;
+        else if (g.first) v = g.t[t].coef * x;
+        else v = x;
+        if (!(g.first && g.last)) break;
+      }
+    }
+    g.out[e] = v;
+  }
+}
+
+__global__ void k_core_transpose(const double* __restrict__ in, int Ca, int Cb, double* out) {
+  const long long tot = (long long)Ca * 4 * Cb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(e % Ca);
+    const int s = (int)((e / Ca) % 4);
+    const int b = (int)(e / ((long long)Ca * 4));
+    out[e] = in[((long long)a * 4 + s) * Cb + b];  // out[b][s][a]
+  }
+}
+
+struct DimsArgs {
+  const int* src[8];
+  int mul[8][QTT_MAX_N + 1];
+  int K;
+  int nb;  // bonds 0..nb-1
+  int* out;
+};
+
+__global__ void k_dims(DimsArgs g) {
+  const int b = threadIdx.x;
+  if (b >= g.nb) return;
+  int v = 0;
+  for (int t = 0; t < g.K; t++) v += g.src[t][b] * g.mul[t][b];
+  if (b == 0 || b == g.nb - 1) v = 1;
+  g.out[b] = v;
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+__global__ void k_fill_int(int* p, int n, int v) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = v;
+}
+
+__device__ __forceinline__ long long omega_index(int x1, int x2, int n) {
+  long long idx = 0;
+  for (int k = 0; k < n; k++) {
+    const int b1 = (x1 >> (n - 1 - k)) & 1, b2 = (x2 >> (n - 1 - k)) & 1;
+    idx = idx * 4 + (2 * b1 + b2);
+  }
+  return idx;
+}
+
+__global__ void k_dense_to_omega(const double* F, double* T, int n) {
+  const long long N = 1LL << n, tot = N * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x)
+    T[omega_index((int)(e / N), (int)(e % N), n)] = F[e];
+}
+
+__global__ void k_omega_to_dense(const double* T, double* F, int n) {
+  const long long N = 1LL << n, tot = N * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x)
+    F[e] = T[omega_index((int)(e / N), (int)(e % N), n)];
+}
+
+__device__ double cta_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; i++) t += sh[i];
+  return t;
+}
+
+__global__ void k_check_finite(const double* p, size_t n, int* err) {
+  bool bad = false;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(p[e])) bad = true;
+  if (bad) atomicOr(err, QTT_DEVERR_NUMERIC);
+}
+
+// scal: [0] rs, [1] bb, [2] tol^2 * bb ; ist: [0] done, [1] iters
+__global__ void __launch_bounds__(1024) k_cg_start(CgVec v, const double* b0, const double* b1,
+                                                    double* scal, int* ist, double tol, int* err) {
+  __shared__ double sh[32];
+  double rr = 0.0, bb = 0.0;
+  for (int sgm = 0; sgm < 2; sgm++) {
+    const double* b = sgm ? b1 : b0;
+    for (long long e = threadIdx.x; e < v.len[sgm]; e += blockDim.x) {
+      const double be = b[e];
+      const double re = be - v.ap[sgm][e];
+      v.r[sgm][e] = re;
+      v.p[sgm][e] = re;
+      rr += re * re;
+      bb += be * be;
+    }
+  }
+  rr = cta_sum(rr, sh);
+  bb = cta_sum(bb, sh);
+  if (bb == 0.0) {
+    for (int sgm = 0; sgm < 2; sgm++)
+      for (long long e = threadIdx.x; e < v.len[sgm]; e += blockDim.x)
+        v.x[sgm][e] = v.r[sgm][e] = v.p[sgm][e] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    if (!isfinite(rr) || !isfinite(bb)) atomicOr(err, QTT_DEVERR_NUMERIC);
+    scal[0] = rr;
+    scal[1] = bb;
+    scal[2] = tol * tol * bb;
+    ist[0] = (bb == 0.0 || rr <= tol * tol * bb || !isfinite(rr)) ? 1 : 0;
+    ist[1] = 0;
+  }
+}
+
+// One CG iteration after ap = A p (App. B: the local system is solved by CG).
+__global__ void __launch_bounds__(1024) k_cg_step(CgVec v, double* scal, int* ist, int maxit,
+                                                   int* err) {
+  __shared__ double sh[32];
+  if (ist[0]) return;
+  double pap = 0.0;
+  for (int sgm = 0; sgm < 2; sgm++)
+    for (long long e = threadIdx.x; e < v.len[sgm]; e += blockDim.x) pap += v.p[sgm][e] * v.ap[sgm][e];
+  pap = cta_sum(pap, sh);
+  const double rs = scal[0];
+  if (!(pap > 0.0) || !isfinite(pap)) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      ist[0] = 1;
+      if (!isfinite(pap)) atomicOr(err, QTT_DEVERR_NUMERIC);
+    }
+    return;
+  }
+  const double alpha = rs / pap;
+  double rr = 0.0;
+  for (int sgm = 0; sgm < 2; sgm++)
+    for (long long e = threadIdx.x; e < v.len[sgm]; e += blockDim.x) {
+      v.x[sgm][e] = fma(alpha, v.p[sgm][e], v.x[sgm][e]);
+      const double re = fma(-alpha, v.ap[sgm][e], v.r[sgm][e]);
+      v.r[sgm][e] = re;
+      rr += re * re;
+    }
+  rr = cta_sum(rr, sh);
+  const double beta = rr / rs;
+  for (int sgm = 0; sgm < 2; sgm++)
+    for (long long e = threadIdx.x; e < v.len[sgm]; e += blockDim.x)
+      v.p[sgm][e] = fma(beta, v.p[sgm][e], v.r[sgm][e]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    scal[0] = rr;
+    const int it = ist[1] + 1;
+    ist[1] = it;
+    if (rr <= scal[2] || it >= maxit || !isfinite(rr)) ist[0] = 1;
+    if (!isfinite(rr)) atomicOr(err, QTT_DEVERR_NUMERIC);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_sumsq2(const double* a, long long na, const double* b,
+                                                  long long nb, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long e = threadIdx.x; e < na; e += blockDim.x) s += a[e] * a[e];
+  for (long long e = threadIdx.x; e < nb; e += blockDim.x) s += b[e] * b[e];
+  s = cta_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_fill(double* p, size_t n, double v) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x)
+    p[e] = v;
+}
+
+int grid_for(long long tot) {
+  long long g = (tot + 255) / 256;
+  if (g > 148 * 16) g = 148 * 16;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+void launch_scale(const GemmF64& g, cudaStream_t s) {
+  if (g.beta == 1.0) return;
+  for (int z = 0; z < g.nb1 * g.nb2; z++) {
+    const int z1 = z / g.nb2, z2 = z % g.nb2;
+    k_scale<<<grid_for((long long)g.M * g.N), 256, 0, s>>>(g.C + z1 * g.sC1 + z2 * g.sC2, g.M, g.N,
+                                                           g.ldc, g.beta);
+    count_launch();
+  }
+}
+
+void launch_zero(double* p, size_t n, cudaStream_t s) {
+  if (n) QTT_CUDA_CHECK(cudaMemsetAsync(p, 0, n * sizeof(double), s));
+}
+void launch_copy(double* dst, const double* src, size_t n, cudaStream_t s) {
+  if (n) QTT_CUDA_CHECK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+void launch_fill(double* p, size_t n, double v, cudaStream_t s) {
+  k_fill<<<grid_for((long long)n), 256, 0, s>>>(p, n, v);
+  count_launch();
+}
+
+void launch_mpo_expand(const double* W, int wl, int wr, const double* A, int Ca, int Cb,
+                       double* out, cudaStream_t s) {
+  const long long tot = (long long)Ca * wl * 4 * Cb * wr;
+  k_mpo_expand<<<grid_for(tot), 256, 0, s>>>(W, wl, wr, A, Ca, Cb, out);
+  count_launch();
+}
+
+void launch_add_assemble_args(const AddTerm* terms, int K, int first, int last, double* out,
+                              int capl, int capr, cudaStream_t s) {
+  AddArgs g{};
+  for (int t = 0; t < K; t++) g.t[t] = terms[t];
+  g.K = K;
+  g.first = first;
+  g.last = last;
+  g.out = out;
+  g.capl = capl;
+  g.capr = capr;
+  k_add_assemble<<<grid_for((long long)capl * 4 * capr), 256, 0, s>>>(g);
+  count_launch();
+}
+
+void launch_add_assemble(const AddTerm* terms, int K, int first, int last, double* out,
+                         int capl_out, int capr_out, cudaStream_t s) {
+  launch_add_assemble_args(terms, K, first, last, out, capl_out, capr_out, s);
+}
+
+void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaStream_t s) {
+  k_core_transpose<<<grid_for((long long)Ca * 4 * Cb), 256, 0, s>>>(in, Ca, Cb, out);
+  count_launch();
+}
+
+void launch_set_int(int* p, int v, cudaStream_t s) {
+  k_set_int<<<1, 1, 0, s>>>(p, v);
+  count_launch();
+}
+
+void launch_fill_int(int* p, int n, int v, cudaStream_t s) {
+  k_fill_int<<<1, 64, 0, s>>>(p, n, v);
+  count_launch();
+}
+
+void launch_dims(const int* const* src, const int (*mul)[QTT_MAX_N + 1], int K, int nb, int* out,
+                 cudaStream_t s) {
+  DimsArgs g{};
+  for (int t = 0; t < K; t++) {
+    g.src[t] = src[t];
+    for (int b = 0; b < nb; b++) g.mul[t][b] = mul[t][b];
+  }
+  g.K = K;
+  g.nb = nb;
+  g.out = out;
+  k_dims<<<1, 32, 0, s>>>(g);
+  count_launch();
+}
+
+void launch_dense_to_omega(const double* F, double* T, int n, cudaStream_t s) {
+  k_dense_to_omega<<<grid_for(1LL << (2 * n)), 256, 0, s>>>(F, T, n);
+  count_launch();
+}
+void launch_omega_to_dense(const double* T, double* F, int n, cudaStream_t s) {
+  k_omega_to_dense<<<grid_for(1LL << (2 * n)), 256, 0, s>>>(T, F, n);
+  count_launch();
+}
+
+void launch_check_finite(const double* p, size_t n, int* err, cudaStream_t s) {
+  k_check_finite<<<grid_for((long long)n), 256, 0, s>>>(p, n, err);
+  count_launch();
+}
+
+void launch_cg_start(const CgVec& v, const double* b0, const double* b1, double* scal, int* ist,
+                     double tol, int* err, cudaStream_t s) {
+  k_cg_start<<<1, 1024, 0, s>>>(v, b0, b1, scal, ist, tol, err);
+  count_launch();
+}
+void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err, cudaStream_t s) {
+  k_cg_step<<<1, 1024, 0, s>>>(v, scal, ist, maxit, err);
+  count_launch();
+}
+void launch_sumsq2(const double* a, long long na, const double* b, long long nb, double* out,
+                   cudaStream_t s) {
+  k_sumsq2<<<1, 1024, 0, s>>>(a, na, b, nb, out);
+  count_launch();
+}

@@ -1,0 +1,1428 @@
+// Host orchestration of the QTT time step and the C ABI of include/qtt.h.
+//
+// Every operation is a fixed sequence of kernel launches on the context
+// stream whose shapes are the host-known CAPACITIES; actual bond
+// dimensions are decided and read on the device (see common.cuh), so
+// nothing here waits for the GPU except the convergence tests of the
+// projection (CG every few iterations, and once per sweep).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+thread_local LaunchCounter* g_launch_counter = nullptr;
+
+
+// ------------------------------------------------------------------ objects
+struct qtt_mps_s {
+  qtt_ctx ctx = nullptr;
+  int n = 0;
+  std::vector<int> cap;     // n + 1
+  std::vector<size_t> off;  // n + 1, off[n] = total doubles
+  double* data = nullptr;   // device
+  int* dims = nullptr;      // device, n + 1
+  cudaStream_t stream = nullptr;
+  double* core(int k) const { return data + off[k]; }
+  size_t core_size(int k) const { return (size_t)cap[k] * 4 * cap[k + 1]; }
+};
+
+struct qtt_mpo_s {
+  int n = 0;
+  std::vector<int> w;                      // n + 1
+  std::vector<std::vector<double>> h;      // W[p][so][si][q]
+  double* dev = nullptr;                   // raw cores
+  double* dev_k2 = nullptr;                // [(s q)][(p t)]
+  double* dev_kr2 = nullptr;               // [(s p)][(q t)]
+  std::vector<size_t> off;                 // per core offset (same for all three)
+  int refs = 1;
+  double* raw(int k) const { return dev + off[k]; }
+  double* k2(int k) const { return dev_k2 + off[k]; }
+  double* kr2(int k) const { return dev_kr2 + off[k]; }
+};
+
+struct qtt_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  qtt_params p{};
+  double dx = 0.0;
+  std::string err;
+  int* d_err = nullptr;
+  qtt_mpo D[2] = {nullptr, nullptr};
+  qtt_mpo lap = nullptr;
+  qtt_mpo K[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  LaunchCounter launches;
+  long long cg_iters = 0, sweeps = 0;
+  int last_not_converged = 0;
+};
+
+namespace {
+
+struct CtxGuard {
+  LaunchCounter* prev;
+  explicit CtxGuard(qtt_ctx c) : prev(g_launch_counter) {
+    g_launch_counter = &c->launches;
+    cudaSetDevice(c->device);
+  }
+  ~CtxGuard() { g_launch_counter = prev; }
+};
+
+// Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DBuf() = default;
+  DBuf(size_t n_, cudaStream_t s_) : n(n_), s(s_) {
+    if (n) {
+      cudaError_t e = cudaMallocAsync((void**)&p, n * sizeof(T), s);
+      if (e != cudaSuccess) throw QttError(QTT_ERR_ALLOC, "cudaMallocAsync failed");
+    }
+  }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    release();
+    p = o.p; n = o.n; s = o.s; o.p = nullptr;
+    return *this;
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+  }
+  ~DBuf() { release(); }
+};
+
+long long natural_cap(int n, int b) {
+  long long a = 1, c = 1;
+  for (int i = 0; i < b && a < (1LL << 40); i++) a *= 4;
+  for (int i = 0; i < n - b && c < (1LL << 40); i++) c *= 4;
+  return std::min(a, c);
+}
+int clampi(long long v) { return (int)std::min<long long>(v, 1 << 30); }
+
+qtt_mps new_mps(qtt_ctx ctx, int n, const std::vector<int>& cap) {
+  auto m = new qtt_mps_s;
+  m->ctx = ctx;
+  m->n = n;
+  m->cap = cap;
+  m->off.resize(n + 1);
+  size_t o = 0;
+  for (int k = 0; k < n; k++) {
+    m->off[k] = o;
+    o += (size_t)cap[k] * 4 * cap[k + 1];
+  }
+  m->off[n] = o;
+  m->stream = ctx->stream;
+  if (cudaMallocAsync((void**)&m->data, o * sizeof(double), ctx->stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&m->dims, (n + 1) * sizeof(int), ctx->stream) != cudaSuccess) {
+    delete m;
+    throw QttError(QTT_ERR_ALLOC, "MPS allocation failed");
+  }
+  QTT_CUDA_CHECK(cudaMemsetAsync(m->data, 0, o * sizeof(double), ctx->stream));
+  return m;
+}
+
+void free_mps(qtt_mps m) {
+  if (!m) return;
+  if (m->data) cudaFreeAsync(m->data, m->stream);
+  if (m->dims) cudaFreeAsync(m->dims, m->stream);
+  delete m;
+}
+
+struct MpsPtr {
+  qtt_mps m = nullptr;
+  MpsPtr() = default;
+  explicit MpsPtr(qtt_mps x) : m(x) {}
+  MpsPtr(const MpsPtr&) = delete;
+  MpsPtr(MpsPtr&& o) noexcept : m(o.m) { o.m = nullptr; }
+  MpsPtr& operator=(MpsPtr&& o) noexcept {
+    if (m != o.m) free_mps(m);
+    m = o.m;
+    o.m = nullptr;
+    return *this;
+  }
+  ~MpsPtr() { free_mps(m); }
+  qtt_mps release() {
+    qtt_mps t = m;
+    m = nullptr;
+    return t;
+  }
+  qtt_mps get() const { return m; }
+  qtt_mps operator->() const { return m; }
+};
+
+void gemm(const GemmF64& g, cudaStream_t s) { launch_gemm_f64(g, s); }
+
+// --------------------------------------------------------------- MPO build
+// Carry tensor of App. A, Table "diff_mpo": C[p][so][si][q], p = alpha_m
+// (carry to the more significant site), q = alpha_{m+1} (request from the
+// less significant site: 0 keep, 1 add one, 2 subtract one), acting on the
+// x1 bit (axis 1) or the x2 bit (axis 2) of omega; so is the output index
+// and si the input index, so that the operator maps U to U(x +- 1).
+void carry_tensor(int axis, double C[3][4][4][3]) {
+  memset(C, 0, sizeof(double) * 3 * 4 * 4 * 3);
+  for (int q = 0; q < 3; q++)
+    for (int so = 0; so < 4; so++) {
+      const int x = so >> 1, y = so & 1;
+      const int bit = axis == 1 ? x : y;
+      int nb = bit, p = 0;
+      if (q == 1) { nb = bit + 1; if (nb == 2) { nb = 0; p = 1; } }
+      if (q == 2) { nb = bit - 1; if (nb == -1) { nb = 1; p = 2; } }
+      const int si = axis == 1 ? (nb << 1 | y) : (x << 1 | nb);
+      C[p][so][si][q] = 1.0;
+    }
+}
+
+// Generic host MPO: cores as flat vectors with bonds w.
+struct HostMpo {
+  int n;
+  std::vector<int> w;
+  std::vector<std::vector<double>> c;  // [p][so][si][q]
+};
+
+// A finite-state carry MPO for coef0 * I + sum_t coef_t * S_{axis_t}^{shift_t}
+// with shift_t in {-2, -1, +1, +2} and (S U)(x) = U(x + shift) along the
+// axis.  Bond states: 0 = idle, plus one state per (axis, sign) meaning
+// "add sign to this axis bit" requested by the less significant side; a
+// bit overflow passes the same state on as a carry (App. A, Table
+// "diff_mpo", generalised).  A shift by 2 leaves the least significant bit
+// unchanged and starts its request one site up.  The final carry out of
+// the most significant site is dropped (periodic grid).
+HostMpo shift_sum_mpo(int n, double coef0, const std::vector<int>& axes,
+                      const std::vector<int>& shifts, const std::vector<double>& coefs) {
+  std::vector<std::pair<int, int>> st{{0, 0}};
+  auto sid = [&](int axis, int sign) {
+    for (size_t i = 1; i < st.size(); i++)
+      if (st[i].first == axis && st[i].second == sign) return (int)i;
+    st.push_back({axis, sign});
+    return (int)st.size() - 1;
+  };
+  for (size_t t = 0; t < axes.size(); t++) sid(axes[t], shifts[t] > 0 ? 1 : -1);
+  const int S = (int)st.size();
+  // C[p][so][si][q]: request q applied to omega (so = output, si = input)
+  std::vector<double> C((size_t)S * 16 * S, 0.0);
+  for (int q = 0; q < S; q++)
+    for (int so = 0; so < 4; so++) {
+      const int x = so >> 1, y = so & 1;
+      int p = 0, si = so;
+      if (q != 0) {
+        const int axis = st[q].first, sign = st[q].second;
+        int nb = (axis == 1 ? x : y) + sign;
+        bool carry = false;
+        if (nb == 2) { nb = 0; carry = true; }
+        if (nb == -1) { nb = 1; carry = true; }
+        si = axis == 1 ? (nb << 1 | y) : (x << 1 | nb);
+        p = carry ? q : 0;
+      }
+      C[((size_t)(p * 4 + so) * 4 + si) * S + q] = 1.0;
+    }
+  std::vector<double> Rn(S, 0.0), Rn1(S, 0.0);  // requests entering site n / site n-1
+  Rn[0] = coef0;
+  for (size_t t = 0; t < axes.size(); t++) {
+    const int id = sid(axes[t], shifts[t] > 0 ? 1 : -1);
+    if (std::abs(shifts[t]) == 1) Rn[id] += coefs[t];
+    else Rn1[id] += coefs[t];
+  }
+  HostMpo m;
+  m.n = n;
+  m.w.assign(n + 1, S);
+  m.w[0] = 1;
+  m.w[n] = 1;
+  m.c.resize(n);
+  for (int k = 0; k < n; k++) {
+    const int wr = m.w[k + 1];
+    m.c[k].assign((size_t)m.w[k] * 16 * wr, 0.0);
+    for (int p = 0; p < S; p++)
+      for (int so = 0; so < 4; so++)
+        for (int si = 0; si < 4; si++) {
+          const int pi = (k == 0) ? 0 : p;  // L = all ones
+          if (k == n - 1) {
+            double v = 0.0;
+            for (int q = 0; q < S; q++) v += C[((size_t)(p * 4 + so) * 4 + si) * S + q] * Rn[q];
+            if (so == si && p > 0) v += Rn1[p];  // shift by 2: pass through, request upward
+            if (v != 0.0) m.c[k][((size_t)(pi * 4 + so) * 4 + si) * wr] += v;
+          } else {
+            for (int q = 0; q < S; q++) {
+              const double v = C[((size_t)(p * 4 + so) * 4 + si) * S + q];
+              if (v != 0.0) m.c[k][((size_t)(pi * 4 + so) * 4 + si) * wr + q] += v;
+            }
+          }
+        }
+  }
+  return m;
+}
+
+qtt_mpo upload_mpo(qtt_ctx ctx, const HostMpo& hm) {
+  auto m = new qtt_mpo_s;
+  m->n = hm.n;
+  m->w = hm.w;
+  m->h = hm.c;
+  m->off.resize(hm.n + 1);
+  size_t o = 0;
+  for (int k = 0; k < hm.n; k++) {
+    m->off[k] = o;
+    o += hm.c[k].size();
+  }
+  m->off[hm.n] = o;
+  std::vector<double> raw(o), k2(o), kr2(o);
+  for (int k = 0; k < hm.n; k++) {
+    const int wl = hm.w[k], wr = hm.w[k + 1];
+    for (int p = 0; p < wl; p++)
+      for (int s = 0; s < 4; s++)
+        for (int t = 0; t < 4; t++)
+          for (int q = 0; q < wr; q++) {
+            const double v = hm.c[k][((p * 4 + s) * 4 + t) * wr + q];
+            raw[m->off[k] + ((p * 4 + s) * 4 + t) * wr + q] = v;
+            // k2[(s q)][(p t)]
+            k2[m->off[k] + (size_t)(s * wr + q) * (wl * 4) + (p * 4 + t)] = v;
+            // kr2[(s p)][(q t)]
+            kr2[m->off[k] + (size_t)(s * wl + p) * (wr * 4) + (q * 4 + t)] = v;
+          }
+  }
+  cudaSetDevice(ctx->device);
+  if (cudaMalloc((void**)&m->dev, 3 * o * sizeof(double)) != cudaSuccess) {
+    delete m;
+    throw QttError(QTT_ERR_ALLOC, "MPO allocation failed");
+  }
+  m->dev_k2 = m->dev + o;
+  m->dev_kr2 = m->dev + 2 * o;
+  QTT_CUDA_CHECK(cudaMemcpy(m->dev, raw.data(), o * sizeof(double), cudaMemcpyHostToDevice));
+  QTT_CUDA_CHECK(cudaMemcpy(m->dev_k2, k2.data(), o * sizeof(double), cudaMemcpyHostToDevice));
+  QTT_CUDA_CHECK(cudaMemcpy(m->dev_kr2, kr2.data(), o * sizeof(double), cudaMemcpyHostToDevice));
+  return m;
+}
+
+void mpo_release(qtt_mpo m) {
+  if (!m) return;
+  if (--m->refs > 0) return;
+  if (m->dev) cudaFree(m->dev);
+  delete m;
+}
+
+// D_axis (App. A): L = (1,1,1), R = (0, 1, -1) / (2 dx), carry table.
+HostMpo diff_mpo(int n, int axis, double dx) {
+  double C[3][4][4][3];
+  carry_tensor(axis, C);
+  HostMpo m;
+  m.n = n;
+  m.w.assign(n + 1, 3);
+  m.w[0] = m.w[n] = 1;
+  m.c.resize(n);
+  const double R[3] = {0.0, 1.0 / (2.0 * dx), -1.0 / (2.0 * dx)};
+  for (int k = 0; k < n; k++) {
+    const int wl = m.w[k], wr = m.w[k + 1];
+    m.c[k].assign((size_t)wl * 16 * wr, 0.0);
+    for (int p = 0; p < 3; p++)
+      for (int so = 0; so < 4; so++)
+        for (int si = 0; si < 4; si++)
+          for (int q = 0; q < 3; q++) {
+            double v = C[p][so][si][q];
+            if (v == 0.0) continue;
+            if (k == n - 1) v *= R[q];
+            const int pi = (k == 0) ? 0 : p, qi = (k == n - 1) ? 0 : q;
+            m.c[k][((pi * 4 + so) * 4 + si) * wr + qi] += v;  // L = (1,1,1) sums p at k = 0
+          }
+  }
+  return m;
+}
+
+// Product of two host MPOs A.B (B acts first), bonds multiply.
+HostMpo mpo_mul(const HostMpo& A, const HostMpo& B) {
+  HostMpo m;
+  m.n = A.n;
+  m.w.resize(A.n + 1);
+  for (int b = 0; b <= A.n; b++) m.w[b] = A.w[b] * B.w[b];
+  m.c.resize(A.n);
+  for (int k = 0; k < A.n; k++) {
+    const int al = A.w[k], ar = A.w[k + 1], bl = B.w[k], br = B.w[k + 1];
+    const int wr = ar * br;
+    m.c[k].assign((size_t)al * bl * 16 * wr, 0.0);
+    for (int pa = 0; pa < al; pa++)
+      for (int pb = 0; pb < bl; pb++)
+        for (int so = 0; so < 4; so++)
+          for (int si = 0; si < 4; si++)
+            for (int qa = 0; qa < ar; qa++)
+              for (int qb = 0; qb < br; qb++) {
+                double v = 0.0;
+                for (int t = 0; t < 4; t++)
+                  v += A.c[k][((pa * 4 + so) * 4 + t) * ar + qa] *
+                       B.c[k][((pb * 4 + t) * 4 + si) * br + qb];
+                if (v == 0.0) continue;
+                m.c[k][(((pa * bl + pb) * 4 + so) * 4 + si) * wr + (qa * br + qb)] = v;
+              }
+  }
+  return m;
+}
+
+HostMpo mpo_scaled(HostMpo m, double s) {
+  for (double& v : m.c[0]) v *= s;
+  return m;
+}
+
+// ------------------------------------------------------------ compression
+// compress X -> new MPS with caps ocap; X unchanged.
+qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
+  const int n = X->n;
+  cudaStream_t s = ctx->stream;
+  const auto& cin = X->cap;
+  std::vector<int> qcap(n + 1, 1), ocap(n + 1, 1);
+  for (int b = 1; b < n; b++) qcap[b] = std::min(4 * qcap[b - 1], cin[b]);
+  for (int b = n - 1; b >= 1; b--)
+    ocap[b] = std::min({qcap[b], 4 * ocap[b + 1], chi, clampi(natural_cap(n, b))});
+  MpsPtr Y(new_mps(ctx, n, ocap));
+  launch_fill_int(Y->dims, n + 1, 1, s);  // interior bonds are written by the SVDs
+  if (n == 1) {
+    launch_copy(Y->core(0), X->core(0), 4, s);
+    return Y.release();
+  }
+  // workspace
+  size_t qcore_tot = 0;
+  std::vector<size_t> qoff(n);
+  for (int k = 0; k < n - 1; k++) {
+    qoff[k] = qcore_tot;
+    qcore_tot += (size_t)qcap[k] * 4 * qcap[k + 1];
+  }
+  size_t rmax = 1, tmax = 1, usmax = 1, mmax = 1, qrw = 1, svw = 1;
+  for (int b = 1; b < n; b++) rmax = std::max(rmax, (size_t)qcap[b] * cin[b]);
+  for (int k = 0; k < n; k++) tmax = std::max(tmax, (size_t)qcap[k] * 4 * cin[k + 1]);
+  for (int b = 1; b < n; b++) usmax = std::max(usmax, (size_t)qcap[b] * ocap[b]);
+  for (int k = 0; k < n; k++) mmax = std::max(mmax, (size_t)qcap[k] * 4 * ocap[k + 1]);
+  for (int k = 0; k < n - 1; k++) qrw = std::max(qrw, qr_work_doubles(4 * qcap[k], cin[k + 1]));
+  for (int k = 1; k < n; k++) svw = std::max(svw, svd_work_doubles(qcap[k], 4 * ocap[k + 1]));
+  DBuf<double> Qc(qcore_tot, s), Rb(rmax, s), Tb(tmax, s), USb(usmax, s), Mb(mmax, s),
+      W(std::max(qrw, svw), s);
+  DBuf<int> qD(n + 1, s);
+  launch_fill_int(qD.p, n + 1, 1, s);
+  // left-to-right QR
+  for (int k = 0; k < n - 1; k++) {
+    const double* Tp;
+    if (k == 0) {
+      Tp = X->core(0);
+    } else {
+      GemmF64 g = gemm_plain(Rb.p, X->core(k), Tb.p, qcap[k], 4 * cin[k + 1], cin[k], cin[k],
+                             4 * cin[k + 1], 4 * cin[k + 1]);
+      gemm(g, s);
+      Tp = Tb.p;
+    }
+    QrArgs a{};
+    a.A = MatView{const_cast<double*>(Tp), cin[k + 1], axis_pair(qcap[k], dref(qD.p + k), 4, dconst(4)),
+                  axis_prefix(cin[k + 1], dref(X->dims + k + 1))};
+    a.Q = MatView{Qc.p + qoff[k], qcap[k + 1], axis_pair(qcap[k], dref(qD.p + k), 4, dconst(4)),
+                  axis_prefix(qcap[k + 1], dconst(1))};
+    a.R = MatView{Rb.p, cin[k + 1], axis_prefix(qcap[k + 1], dconst(1)),
+                  axis_prefix(cin[k + 1], dref(X->dims + k + 1))};
+    a.r_out = qD.p + k + 1;
+    a.work = W.p;
+    a.err = ctx->d_err;
+    launch_qr_f64(a, 4 * qcap[k], cin[k + 1], s);
+  }
+  // last core after the sweep: T = R * X_{n-1}  (qcap[n-1] x 4)
+  {
+    GemmF64 g = gemm_plain(Rb.p, X->core(n - 1), Tb.p, qcap[n - 1], 4, cin[n - 1], cin[n - 1], 4, 4);
+    gemm(g, s);
+  }
+  // right-to-left truncated SVD
+  for (int k = n - 1; k >= 1; k--) {
+    const double* Mp;
+    if (k == n - 1) {
+      Mp = Tb.p;
+    } else {
+      // M = Qcore_k (4 qcap[k] x qcap[k+1]) * US (qcap[k+1] x ocap[k+1])
+      GemmF64 g = gemm_plain(Qc.p + qoff[k], USb.p, Mb.p, 4 * qcap[k], ocap[k + 1], qcap[k + 1],
+                             qcap[k + 1], ocap[k + 1], ocap[k + 1]);
+      gemm(g, s);
+      Mp = Mb.p;
+    }
+    SvdArgs a{};
+    a.M = MatView{const_cast<double*>(Mp), 4 * ocap[k + 1], axis_prefix(qcap[k], dref(qD.p + k)),
+                  axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
+    a.US = MatView{USb.p, ocap[k], axis_prefix(qcap[k], dref(qD.p + k)),
+                   axis_prefix(ocap[k], dconst(1))};
+    a.VT = MatView{Y->core(k), 4 * ocap[k + 1], axis_prefix(ocap[k], dconst(1)),
+                   axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
+    a.eps = eps;
+    a.chi = chi;
+    a.rank_limit = dconst(1 << 30);
+    a.r_out = Y->dims + k;
+    a.work = W.p;
+    a.err = ctx->d_err;
+    launch_svd_f64(a, qcap[k], 4 * ocap[k + 1], s);
+  }
+  // first core: Y_0 = Qcore_0 (4 x qcap[1]) * US (qcap[1] x ocap[1])
+  {
+    GemmF64 g = gemm_plain(Qc.p + qoff[0], USb.p, Y->core(0), 4, ocap[1], qcap[1], qcap[1],
+                           ocap[1], ocap[1]);
+    gemm(g, s);
+  }
+  return Y.release();
+}
+
+// ------------------------------------------------------------ apply / add
+qtt_mps expand_mpo(qtt_ctx ctx, qtt_mpo W, qtt_mps A) {
+  const int n = A->n;
+  cudaStream_t s = ctx->stream;
+  std::vector<int> cap(n + 1);
+  for (int b = 0; b <= n; b++) cap[b] = A->cap[b] * W->w[b];
+  MpsPtr X(new_mps(ctx, n, cap));
+  for (int k = 0; k < n; k++)
+    launch_mpo_expand(W->raw(k), W->w[k], W->w[k + 1], A->core(k), A->cap[k], A->cap[k + 1],
+                      X->core(k), s);
+  const int* src[1] = {A->dims};
+  int mul[1][QTT_MAX_N + 1];
+  for (int b = 0; b <= n; b++) mul[0][b] = W->w[b];
+  launch_dims(src, mul, 1, n + 1, X->dims, s);
+  return X.release();
+}
+
+qtt_mps add_exact(qtt_ctx ctx, int K, const double* coef, const qtt_mps* terms) {
+  const int n = terms[0]->n;
+  cudaStream_t s = ctx->stream;
+  std::vector<int> cap(n + 1, 0);
+  for (int b = 0; b <= n; b++)
+    for (int t = 0; t < K; t++) cap[b] += terms[t]->cap[b];
+  cap[0] = cap[n] = 1;
+  MpsPtr X(new_mps(ctx, n, cap));
+  for (int k = 0; k < n; k++) {
+    AddTerm tt[8];
+    for (int t = 0; t < K; t++)
+      tt[t] = AddTerm{terms[t]->core(k), terms[t]->cap[k], terms[t]->cap[k + 1],
+                      terms[t]->dims + k, terms[t]->dims + k + 1, coef[t]};
+    launch_add_assemble(tt, K, k == 0, k == n - 1, X->core(k), cap[k], cap[k + 1], s);
+  }
+  const int* src[8];
+  int mul[8][QTT_MAX_N + 1];
+  for (int t = 0; t < K; t++) {
+    src[t] = terms[t]->dims;
+    for (int b = 0; b <= n; b++) mul[t][b] = 1;
+  }
+  launch_dims(src, mul, K, n + 1, X->dims, s);
+  return X.release();
+}
+
+qtt_mps apply_impl(qtt_ctx ctx, qtt_mpo W, qtt_mps A, double eps, int chi) {
+  MpsPtr X(expand_mpo(ctx, W, A));
+  return compress_impl(ctx, X.get(), eps, chi);
+}
+
+qtt_mps add_impl(qtt_ctx ctx, int K, const double* coef, const qtt_mps* terms, double eps,
+                 int chi) {
+  if (K > 8) throw QttError(QTT_ERR_ARG, "qtt_add supports at most 8 terms");
+  MpsPtr X(add_exact(ctx, K, coef, terms));
+  return compress_impl(ctx, X.get(), eps, chi);
+}
+
+qtt_mps add2(qtt_ctx ctx, double c1, qtt_mps a, double c2, qtt_mps b) {
+  const double cf[2] = {c1, c2};
+  const qtt_mps t[2] = {a, b};
+  return add_impl(ctx, 2, cf, t, ctx->p.eps, ctx->p.chi_max);
+}
+
+// ------------------------------------------------------------ Hadamard
+qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
+  const int n = A->n;
+  cudaStream_t s = ctx->stream;
+  const auto& ca = A->cap;
+  const auto& cb = B->cap;
+  std::vector<int> rcap(n + 1, 1);
+  for (int b = 1; b < n; b++)
+    rcap[b] = std::min({4 * rcap[b - 1], clampi((long long)ca[b] * cb[b]), chi,
+                        clampi(natural_cap(n, b))});
+  MpsPtr C(new_mps(ctx, n, rcap));
+  launch_fill_int(C->dims, n + 1, 1, s);
+  size_t xmax = 1, tmax = 1, rmax = 1, svw = 1;
+  for (int k = 0; k < n; k++) {
+    xmax = std::max(xmax, (size_t)rcap[k] * cb[k] * 4 * ca[k + 1]);
+    tmax = std::max(tmax, (size_t)rcap[k] * 4 * ca[k + 1] * cb[k + 1]);
+    rmax = std::max(rmax, (size_t)rcap[k] * ca[k] * cb[k]);
+    if (k < n - 1)
+      svw = std::max(svw, svd_work_doubles(4 * rcap[k], ca[k + 1] * cb[k + 1]));
+  }
+  DBuf<double> R0(rmax, s), R1(rmax, s), Xb(xmax, s), Tb(tmax, s), W(svw, s);
+  launch_fill(R0.p, 1, 1.0, s);
+  double* Rc = R0.p;
+  double* Rn = R1.p;
+  for (int k = 0; k < n; k++) {
+    // X[r][b][s][a'] = sum_a R[r][a][b] A[a][s][a']
+    GemmF64 g1{};
+    g1.A = Rc; g1.B = A->core(k); g1.C = Xb.p;
+    g1.M = cb[k]; g1.N = 4 * ca[k + 1]; g1.K = ca[k];
+    g1.lda = cb[k]; g1.ldb = 4 * ca[k + 1]; g1.ldc = 4 * ca[k + 1];
+    g1.tA = 1;
+    g1.nb1 = rcap[k]; g1.nb2 = 1;
+    g1.sA1 = (long long)ca[k] * cb[k]; g1.sB1 = 0; g1.sC1 = (long long)cb[k] * 4 * ca[k + 1];
+    g1.alpha = 1.0; g1.beta = 0.0;
+    gemm(g1, s);
+    // T[r][s][a'][b'] = sum_b X[r][b][s][a'] B[b][s][b']
+    double* Tout = (k == n - 1) ? C->core(n - 1) : Tb.p;
+    GemmF64 g2{};
+    g2.A = Xb.p; g2.B = B->core(k); g2.C = Tout;
+    g2.M = ca[k + 1]; g2.N = cb[k + 1]; g2.K = cb[k];
+    g2.lda = 4 * ca[k + 1]; g2.ldb = 4 * cb[k + 1]; g2.ldc = cb[k + 1];
+    g2.tA = 1;
+    g2.nb1 = rcap[k]; g2.nb2 = 4;
+    g2.sA1 = (long long)cb[k] * 4 * ca[k + 1]; g2.sA2 = ca[k + 1];
+    g2.sB1 = 0; g2.sB2 = cb[k + 1];
+    g2.sC1 = (long long)4 * ca[k + 1] * cb[k + 1]; g2.sC2 = (long long)ca[k + 1] * cb[k + 1];
+    g2.alpha = 1.0; g2.beta = 0.0;
+    gemm(g2, s);
+    if (k == n - 1) break;
+    // zip-up split of T ((r,s) x (a',b')): core U, carry S V^T, cap only.
+    // Factor T^T so that U comes out of the orthonormal V^T side.
+    SvdArgs a{};
+    a.M = MatView{Tb.p, ca[k + 1] * cb[k + 1], axis_pair(rcap[k], dref(C->dims + k), 4, dconst(4)),
+                  axis_pair(ca[k + 1], dref(A->dims + k + 1), cb[k + 1], dref(B->dims + k + 1))};
+    a.inT = 1;
+    // US of T^T = V S  -> written transposed: carry (r' x (a',b'))
+    a.US = MatView{Rn, ca[k + 1] * cb[k + 1], axis_prefix(rcap[k + 1], dconst(1)),
+                   axis_pair(ca[k + 1], dref(A->dims + k + 1), cb[k + 1], dref(B->dims + k + 1))};
+    a.usT = 1;
+    // V^T of T^T = U^T -> written transposed: core ((r,s) x r')
+    a.VT = MatView{C->core(k), rcap[k + 1], axis_pair(rcap[k], dref(C->dims + k), 4, dconst(4)),
+                   axis_prefix(rcap[k + 1], dconst(1))};
+    a.vtT = 1;
+    a.eps = -1.0;
+    a.chi = chi;
+    a.rank_limit = dconst(1 << 30);
+    a.r_out = C->dims + k + 1;
+    a.work = W.p;
+    a.err = ctx->d_err;
+    launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+    std::swap(Rc, Rn);
+  }
+  return compress_impl(ctx, C.get(), eps, chi);
+}
+
+}  // namespace
+
+// ===================================================================== projection
+namespace {
+
+struct Env {
+  std::vector<DBuf<double>> b;  // per bond
+};
+
+struct Projector {
+  qtt_ctx ctx;
+  cudaStream_t s;
+  int n;
+  double c;  // mu h^2
+  qtt_mps V[2];
+  qtt_mps W[2];
+  qtt_mpo K[2][2];
+  // environments per block, per bond
+  std::vector<DBuf<double>> LE[2][2], RE[2][2], LW[2], RW[2];
+  DBuf<double> t1, t2, rb, tmp, work, vt_i, vt_j, wt;
+  DBuf<double> cg_r[2], cg_p[2], cg_ap[2], rhs[2];
+  DBuf<double> scal;
+  DBuf<int> ist;
+  size_t maxcore = 0;
+
+  const std::vector<int>& cap(int i) const { return V[i]->cap; }
+
+  void alloc() {
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++) {
+        LE[i][j].resize(n + 1);
+        RE[i][j].resize(n + 1);
+        for (int b = 0; b <= n; b++) {
+          const size_t sz = (size_t)cap(i)[b] * K[i][j]->w[b] * cap(j)[b];
+          LE[i][j][b] = DBuf<double>(sz, s);
+          RE[i][j][b] = DBuf<double>(sz, s);
+        }
+      }
+    for (int i = 0; i < 2; i++) {
+      LW[i].resize(n + 1);
+      RW[i].resize(n + 1);
+      for (int b = 0; b <= n; b++) {
+        LW[i][b] = DBuf<double>((size_t)cap(i)[b] * W[i]->cap[b], s);
+        RW[i][b] = DBuf<double>((size_t)cap(i)[b] * W[i]->cap[b], s);
+      }
+    }
+    size_t t1m = 1, t2m = 1, cm = 1, qrw = 1;
+    int wmax = 1;
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++)
+        for (int b = 0; b <= n; b++) wmax = std::max(wmax, K[i][j]->w[b]);
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++)
+        for (int k = 0; k < n; k++) {
+          const size_t ci = cap(i)[k], cj = cap(j)[k], ci1 = cap(i)[k + 1], cj1 = cap(j)[k + 1];
+          t1m = std::max(t1m, ci * wmax * 4 * cj1);          // left: a p t z
+          t1m = std::max(t1m, ci1 * wmax * 4 * cj);          // right: b q t x
+          t2m = std::max(t2m, ci * 4 * wmax * cj1);          // a s q z
+          t2m = std::max(t2m, ci1 * 4 * wmax * cj);          // b s p x
+          t1m = std::max(t1m, ci1 * 4 * (size_t)W[i]->cap[k]);
+          t1m = std::max(t1m, ci * 4 * (size_t)W[i]->cap[k + 1]);
+        }
+    for (int i = 0; i < 2; i++)
+      for (int k = 0; k < n; k++) {
+        cm = std::max(cm, V[i]->core_size(k));
+        cm = std::max(cm, W[i]->core_size(k));
+        qrw = std::max(qrw, qr_work_doubles(4 * cap(i)[k], cap(i)[k + 1]));
+        qrw = std::max(qrw, qr_work_doubles(4 * cap(i)[k + 1], cap(i)[k]));
+      }
+    maxcore = cm;
+    t1 = DBuf<double>(t1m, s);
+    t2 = DBuf<double>(t2m, s);
+    int cmax = 1;
+    for (int i = 0; i < 2; i++)
+      for (int b = 0; b <= n; b++) cmax = std::max(cmax, cap(i)[b]);
+    rb = DBuf<double>((size_t)cmax * cmax, s);
+    tmp = DBuf<double>(cm, s);
+    work = DBuf<double>(qrw, s);
+    vt_i = DBuf<double>(cm, s);
+    vt_j = DBuf<double>(cm, s);
+    wt = DBuf<double>(cm, s);
+    for (int i = 0; i < 2; i++) {
+      cg_r[i] = DBuf<double>(cm, s);
+      cg_p[i] = DBuf<double>(cm, s);
+      cg_ap[i] = DBuf<double>(cm, s);
+      rhs[i] = DBuf<double>(cm, s);
+    }
+    scal = DBuf<double>(8, s);
+    ist = DBuf<int>(4, s);
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++) {
+        launch_fill(LE[i][j][0].p, 1, 1.0, s);
+        launch_fill(RE[i][j][n].p, 1, 1.0, s);
+      }
+    for (int i = 0; i < 2; i++) {
+      launch_fill(LW[i][0].p, 1, 1.0, s);
+      launch_fill(RW[i][n].p, 1, 1.0, s);
+    }
+  }
+
+  // RE[b] from RE[b+1] and site b (sites b..n-1), all blocks + overlaps.
+  void build_right(int k) {
+    for (int j = 0; j < 2; j++) {
+      // transposed copy of V_j[k] ([b][s][a]) into vt_j; reused for every i
+      launch_core_transpose(V[j]->core(k), cap(j)[k], cap(j)[k + 1], j == 0 ? vt_i.p : vt_j.p, s);
+    }
+    for (int i = 0; i < 2; i++) {
+      const double* ViT = (i == 0) ? vt_i.p : vt_j.p;
+      for (int j = 0; j < 2; j++) {
+        const double* VjT = (j == 0) ? vt_i.p : vt_j.p;
+        qtt_mpo Kij = K[i][j];
+        const int wl = Kij->w[k], wr = Kij->w[k + 1];
+        const int ci = cap(i)[k], cj = cap(j)[k], ci1 = cap(i)[k + 1], cj1 = cap(j)[k + 1];
+        // T1[(b q)][(t x)] = RE[k+1][(b q)][z] * VjT[z][(t x)]
+        gemm(gemm_plain(RE[i][j][k + 1].p, VjT, t1.p, ci1 * wr, 4 * cj, cj1, cj1, 4 * cj, 4 * cj), s);
+        // T2[b][(s p)][x] = KR2[(s p)][(q t)] * T1[b][(q t)][x]
+        GemmF64 g{};
+        g.A = Kij->kr2(k); g.B = t1.p; g.C = t2.p;
+        g.M = 4 * wl; g.N = cj; g.K = wr * 4;
+        g.lda = wr * 4; g.ldb = cj; g.ldc = cj;
+        g.nb1 = ci1; g.nb2 = 1;
+        g.sA1 = 0; g.sB1 = (long long)wr * 4 * cj; g.sC1 = (long long)4 * wl * cj;
+        g.alpha = 1.0;
+        gemm(g, s);
+        // RE[k][a][(p x)] = ViT[(b s)][a]^T * T2[(b s)][(p x)]
+        GemmF64 g3 = gemm_plain(ViT, t2.p, RE[i][j][k].p, ci, wl * cj, ci1 * 4, ci, wl * cj, wl * cj);
+        g3.tA = 1;
+        gemm(g3, s);
+      }
+    }
+    for (int i = 0; i < 2; i++) {
+      const double* ViT = (i == 0) ? vt_i.p : vt_j.p;
+      const int ci = cap(i)[k], ci1 = cap(i)[k + 1];
+      const int cw = W[i]->cap[k], cw1 = W[i]->cap[k + 1];
+      launch_core_transpose(W[i]->core(k), cw, cw1, wt.p, s);
+      // T1[b][(s c)] = RW[k+1][b][d] * WiT[d][(s c)]
+      gemm(gemm_plain(RW[i][k + 1].p, wt.p, t1.p, ci1, 4 * cw, cw1, cw1, 4 * cw, 4 * cw), s);
+      // RW[k][a][c] = ViT[(b s)][a]^T * T1[(b s)][c]
+      GemmF64 g = gemm_plain(ViT, t1.p, RW[i][k].p, ci, cw, ci1 * 4, ci, cw, cw);
+      g.tA = 1;
+      gemm(g, s);
+    }
+  }
+
+  // LE[k+1] from LE[k] and site k.
+  void build_left(int k) {
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++) {
+        qtt_mpo Kij = K[i][j];
+        const int wl = Kij->w[k], wr = Kij->w[k + 1];
+        const int ci = cap(i)[k], cj = cap(j)[k], ci1 = cap(i)[k + 1], cj1 = cap(j)[k + 1];
+        // T1[(a p)][(t z)] = LE[k][(a p)][x] * Vj[k][x][(t z)]
+        gemm(gemm_plain(LE[i][j][k].p, V[j]->core(k), t1.p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1), s);
+        // T2[a][(s q)][z] = K2[(s q)][(p t)] * T1[a][(p t)][z]
+        GemmF64 g{};
+        g.A = Kij->k2(k); g.B = t1.p; g.C = t2.p;
+        g.M = 4 * wr; g.N = cj1; g.K = 4 * wl;
+        g.lda = 4 * wl; g.ldb = cj1; g.ldc = cj1;
+        g.nb1 = ci; g.nb2 = 1;
+        g.sA1 = 0; g.sB1 = (long long)wl * 4 * cj1; g.sC1 = (long long)4 * wr * cj1;
+        g.alpha = 1.0;
+        gemm(g, s);
+        // LE[k+1][b][(q z)] = Vi[(a s)][b]^T * T2[(a s)][(q z)]
+        GemmF64 g3 = gemm_plain(V[i]->core(k), t2.p, LE[i][j][k + 1].p, ci1, wr * cj1, 4 * ci, ci1,
+                                wr * cj1, wr * cj1);
+        g3.tA = 1;
+        gemm(g3, s);
+      }
+    for (int i = 0; i < 2; i++) {
+      const int ci = cap(i)[k], ci1 = cap(i)[k + 1];
+      const int cw = W[i]->cap[k], cw1 = W[i]->cap[k + 1];
+      // T1[a][(s d)] = LW[k][a][c] * Wi[c][(s d)]
+      gemm(gemm_plain(LW[i][k].p, W[i]->core(k), t1.p, ci, 4 * cw1, cw, cw, 4 * cw1, 4 * cw1), s);
+      // LW[k+1][b][d] = Vi[(a s)][b]^T * T1[(a s)][d]
+      GemmF64 g = gemm_plain(V[i]->core(k), t1.p, LW[i][k + 1].p, ci1, cw1, 4 * ci, ci1, cw1, cw1);
+      g.tA = 1;
+      gemm(g, s);
+    }
+  }
+
+  // Y = (1 + c sum_j K_ij) X at site d; X, Y two-component local tensors.
+  void matvec(int d, double* const X[2], double* const Y[2], const int* skip) {
+    for (int i = 0; i < 2; i++) {
+      launch_copy(Y[i], X[i], V[i]->core_size(d), s);
+      for (int j = 0; j < 2; j++) {
+        qtt_mpo Kij = K[i][j];
+        const int wl = Kij->w[d], wr = Kij->w[d + 1];
+        const int ci = cap(i)[d], cj = cap(j)[d], ci1 = cap(i)[d + 1], cj1 = cap(j)[d + 1];
+        GemmF64 g1 = gemm_plain(LE[i][j][d].p, X[j], t1.p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1);
+        g1.skip = skip;
+        gemm(g1, s);
+        GemmF64 g{};
+        g.A = Kij->k2(d); g.B = t1.p; g.C = t2.p;
+        g.M = 4 * wr; g.N = cj1; g.K = 4 * wl;
+        g.lda = 4 * wl; g.ldb = cj1; g.ldc = cj1;
+        g.nb1 = ci; g.nb2 = 1;
+        g.sA1 = 0; g.sB1 = (long long)wl * 4 * cj1; g.sC1 = (long long)4 * wr * cj1;
+        g.alpha = 1.0;
+        g.skip = skip;
+        gemm(g, s);
+        // Y[(a s)][b] += c * T2[(a s)][(q z)] * RE[d+1][b][(q z)]^T
+        GemmF64 g3 = gemm_plain(t2.p, RE[i][j][d + 1].p, Y[i], 4 * ci, ci1, wr * cj1, wr * cj1,
+                                wr * cj1, ci1);
+        g3.tB = 1;
+        g3.alpha = c;
+        g3.beta = 1.0;
+        g3.skip = skip;
+        gemm(g3, s);
+      }
+    }
+  }
+
+  void local_rhs(int d) {
+    for (int i = 0; i < 2; i++) {
+      const int ci = cap(i)[d], ci1 = cap(i)[d + 1];
+      const int cw = W[i]->cap[d], cw1 = W[i]->cap[d + 1];
+      gemm(gemm_plain(LW[i][d].p, W[i]->core(d), t1.p, ci, 4 * cw1, cw, cw, 4 * cw1, 4 * cw1), s);
+      GemmF64 g = gemm_plain(t1.p, RW[i][d + 1].p, rhs[i].p, 4 * ci, ci1, cw1, cw1, cw1, ci1);
+      g.tB = 1;
+      gemm(g, s);
+    }
+  }
+
+  int solve(int d) {
+    local_rhs(d);
+    CgVec v{};
+    double* X[2] = {V[0]->core(d), V[1]->core(d)};
+    double* AP[2] = {cg_ap[0].p, cg_ap[1].p};
+    double* P[2] = {cg_p[0].p, cg_p[1].p};
+    for (int i = 0; i < 2; i++) {
+      v.x[i] = X[i];
+      v.r[i] = cg_r[i].p;
+      v.p[i] = cg_p[i].p;
+      v.ap[i] = cg_ap[i].p;
+      v.len[i] = (long long)V[i]->core_size(d);
+    }
+    matvec(d, X, AP, nullptr);
+    launch_cg_start(v, rhs[0].p, rhs[1].p, scal.p, ist.p, ctx->p.cg_tol, ctx->d_err, s);
+    const int maxit = ctx->p.cg_maxit;
+    int done_iters = 0;
+    const int chunk = 8;
+    for (int it = 0; it < maxit; it += chunk) {
+      const int m = std::min(chunk, maxit - it);
+      for (int q = 0; q < m; q++) {
+        matvec(d, P, AP, ist.p);
+        launch_cg_step(v, scal.p, ist.p, maxit, ctx->d_err, s);
+      }
+      int h[2];
+      QTT_CUDA_CHECK(cudaMemcpyAsync(h, ist.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      QTT_CUDA_CHECK(cudaStreamSynchronize(s));
+      done_iters = h[1];
+      if (h[0]) break;
+    }
+    if (done_iters >= maxit) ctx->last_not_converged = 1;
+    return done_iters;
+  }
+
+  // centre moves right: V_i[d] = Q, V_i[d+1] = R V_i[d+1]
+  void shift_right(int d) {
+    for (int i = 0; i < 2; i++) {
+      const int cl = cap(i)[d], cr = cap(i)[d + 1], cr2 = cap(i)[d + 2];
+      QrArgs a{};
+      a.A = MatView{V[i]->core(d), cr, axis_pair(cl, dref(V[i]->dims + d), 4, dconst(4)),
+                    axis_prefix(cr, dref(V[i]->dims + d + 1))};
+      a.Q = MatView{V[i]->core(d), cr, axis_pair(cl, dref(V[i]->dims + d), 4, dconst(4)),
+                    axis_prefix(cr, dconst(1))};
+      a.R = MatView{rb.p, cr, axis_prefix(cr, dconst(1)), axis_prefix(cr, dref(V[i]->dims + d + 1))};
+      a.r_out = V[i]->dims + d + 1;
+      a.work = work.p;
+      a.err = ctx->d_err;
+      launch_qr_f64(a, 4 * cl, cr, s);
+      gemm(gemm_plain(rb.p, V[i]->core(d + 1), tmp.p, cr, 4 * cr2, cr, cr, 4 * cr2, 4 * cr2), s);
+      launch_copy(V[i]->core(d + 1), tmp.p, V[i]->core_size(d + 1), s);
+    }
+  }
+
+  // centre moves left: V_i[d] = Q^T (right isometry), V_i[d-1] = V_i[d-1] R^T
+  void shift_left(int d) {
+    for (int i = 0; i < 2; i++) {
+      const int cl = cap(i)[d], cr = cap(i)[d + 1], cl0 = cap(i)[d - 1];
+      QrArgs a{};
+      a.A = MatView{V[i]->core(d), 4 * cr, axis_prefix(cl, dref(V[i]->dims + d)),
+                    axis_pair(4, dconst(4), cr, dref(V[i]->dims + d + 1))};
+      a.inT = 1;
+      a.Q = MatView{V[i]->core(d), 4 * cr, axis_prefix(cl, dconst(1)),
+                    axis_pair(4, dconst(4), cr, dref(V[i]->dims + d + 1))};
+      a.qT = 1;
+      a.R = MatView{rb.p, cl, axis_prefix(cl, dref(V[i]->dims + d)), axis_prefix(cl, dconst(1))};
+      a.rT = 1;
+      a.r_out = V[i]->dims + d;
+      a.work = work.p;
+      a.err = ctx->d_err;
+      launch_qr_f64(a, 4 * cr, cl, s);
+      gemm(gemm_plain(V[i]->core(d - 1), rb.p, tmp.p, 4 * cl0, cl, cl, cl, cl, cl), s);
+      launch_copy(V[i]->core(d - 1), tmp.p, V[i]->core_size(d - 1), s);
+    }
+  }
+
+  double norm_total() {
+    launch_sumsq2(V[0]->core(0), (long long)V[0]->core_size(0), V[1]->core(0),
+                  (long long)V[1]->core_size(0), scal.p + 6, s);
+    double h;
+    QTT_CUDA_CHECK(cudaMemcpyAsync(&h, scal.p + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    QTT_CUDA_CHECK(cudaStreamSynchronize(s));
+    return h;
+  }
+};
+
+qtt_mps copy_mps(qtt_ctx ctx, qtt_mps A) {
+  MpsPtr X(new_mps(ctx, A->n, A->cap));
+  launch_copy(X->data, A->data, A->off[A->n], ctx->stream);
+  QTT_CUDA_CHECK(cudaMemcpyAsync(X->dims, A->dims, (A->n + 1) * sizeof(int),
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+  return X.release();
+}
+
+void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qtt_mps* v2,
+                  int* cg_out, int* sw_out) {
+  const int n = w1->n;
+  Projector P;
+  P.ctx = ctx;
+  P.s = ctx->stream;
+  P.n = n;
+  P.c = ctx->p.mu * h * h;
+  MpsPtr V0(copy_mps(ctx, w1)), V1(copy_mps(ctx, w2));
+  P.V[0] = V0.get();
+  P.V[1] = V1.get();
+  P.W[0] = w1;
+  P.W[1] = w2;
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
+  P.alloc();
+  // right-canonical initial guess (centre at site 1)
+  for (int d = n - 1; d >= 1; d--) P.shift_left(d);
+  for (int k = n - 1; k >= 1; k--) P.build_right(k);
+  long long cg = 0;
+  int sweeps = 0;
+  ctx->last_not_converged = 0;
+  double nprev = P.norm_total();
+  bool conv = false;
+  for (int sw = 0; sw < ctx->p.max_sweeps; sw++) {
+    for (int d = 0; d < n - 1; d++) {
+      cg += P.solve(d);
+      P.shift_right(d);
+      P.build_left(d);
+    }
+    for (int d = n - 1; d >= 1; d--) {
+      cg += P.solve(d);
+      P.shift_left(d);
+      P.build_right(d);
+    }
+    sweeps = sw + 1;
+    const double nn = P.norm_total();
+    if (nn == 0.0 || fabs(nn - nprev) <= ctx->p.sweep_tol * nn) {
+      conv = true;
+      break;
+    }
+    nprev = nn;
+  }
+  if (n == 1) conv = true;
+  if (!conv) ctx->last_not_converged = 1;
+  ctx->cg_iters += cg;
+  ctx->sweeps += sweeps;
+  if (cg_out) *cg_out = (int)cg;
+  if (sw_out) *sw_out = sweeps;
+  *v1 = V0.release();
+  *v2 = V1.release();
+}
+
+// ===================================================================== RK4
+void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2]) {
+  const double eps = ctx->p.eps;
+  const int chi = ctx->p.chi_max;
+  MpsPtr Db[2][2], P[2][2], Q[2][2], DQ[2][2], Lb[2];
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) Db[j][i] = MpsPtr(apply_impl(ctx, ctx->D[j], b[i], eps, chi));
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) P[j][i] = MpsPtr(hadamard_impl(ctx, b[j], Db[j][i].get(), eps, chi));
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) Db[j][i] = MpsPtr();
+  Q[0][0] = MpsPtr(hadamard_impl(ctx, b[0], b[0], eps, chi));
+  Q[0][1] = MpsPtr(hadamard_impl(ctx, b[0], b[1], eps, chi));
+  Q[1][1] = MpsPtr(hadamard_impl(ctx, b[1], b[1], eps, chi));
+  auto q = [&](int j, int i) { return (j == 1 && i == 0) ? Q[0][1].get() : Q[j][i].get(); };
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) DQ[j][i] = MpsPtr(apply_impl(ctx, ctx->D[j], q(j, i), eps, chi));
+  for (int i = 0; i < 2; i++) Lb[i] = MpsPtr(apply_impl(ctx, ctx->lap, b[i], eps, chi));
+  for (int i = 0; i < 2; i++) {
+    MpsPtr ca(add2(ctx, 1.0, P[0][i].get(), 1.0, P[1][i].get()));
+    MpsPtr cb(add2(ctx, 1.0, DQ[0][i].get(), 1.0, DQ[1][i].get()));
+    MpsPtr conv(add2(ctx, 0.5, ca.get(), 0.5, cb.get()));
+    MpsPtr B(add2(ctx, 1.0, conv.get(), -nu, Lb[i].get()));
+    w[i] = MpsPtr(add2(ctx, 0.25, u[i], -h, B.get()));
+  }
+}
+
+void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+  static const double HS[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  static const double BC[4][2] = {{0, 0}, {3.0, 0.25}, {1.5, 0.625}, {3.0, 0.25}};
+  qtt_mps u[2] = {*u1, *u2};
+  MpsPtr U[4][2];
+  long long cg_total = 0, sw_total = 0;
+  int nc = 0;
+  for (int st = 0; st < 4; st++) {
+    MpsPtr bown[2];
+    qtt_mps b[2] = {u[0], u[1]};
+    if (st > 0) {
+      for (int i = 0; i < 2; i++) {
+        bown[i] = MpsPtr(add2(ctx, BC[st][0], U[st - 1][i].get(), BC[st][1], u[i]));
+        b[i] = bown[i].get();
+      }
+    }
+    const double h = HS[st] * dt;
+    MpsPtr w[2];
+    stage_w(ctx, u, b, h, nu, w);
+    qtt_mps v1, v2;
+    int cg = 0, sw = 0;
+    project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+    nc |= ctx->last_not_converged;
+    cg_total += cg;
+    sw_total += sw;
+    U[st][0] = MpsPtr(v1);
+    U[st][1] = MpsPtr(v2);
+  }
+  MpsPtr out[2];
+  for (int i = 0; i < 2; i++) {
+    MpsPtr acc(add2(ctx, 1.0, U[0][i].get(), 1.0, U[1][i].get()));
+    acc = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[2][i].get()));
+    out[i] = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[3][i].get()));
+  }
+  free_mps(*u1);
+  free_mps(*u2);
+  *u1 = out[0].release();
+  *u2 = out[1].release();
+  ctx->last_not_converged = nc;
+  (void)cg_total;
+  (void)sw_total;
+}
+
+// ---------------------------------------------------------------- dense I/O
+qtt_mps from_dense_impl(qtt_ctx ctx, const double* F, double eps, int chi) {
+  const int n = ctx->p.n;
+  cudaStream_t s = ctx->stream;
+  std::vector<int> ocap(n + 1, 1);
+  for (int b = 1; b < n; b++) ocap[b] = std::min(chi, clampi(natural_cap(n, b)));
+  MpsPtr Y(new_mps(ctx, n, ocap));
+  launch_fill_int(Y->dims, n + 1, 1, s);
+  const size_t tot = (size_t)1 << (2 * n);
+  DBuf<double> T(tot, s);
+  launch_check_finite(F, tot, ctx->d_err, s);
+  launch_dense_to_omega(F, T.p, n, s);
+  if (n == 1) {
+    launch_copy(Y->core(0), T.p, 4, s);
+    return Y.release();
+  }
+  // right-to-left TT-SVD: carry C (4^k x ocap[k]) -> reshape (4^(k-1) x 4 ocap[k])
+  size_t cmax = 1, svw = 1;
+  for (int k = 1; k < n; k++) {
+    const size_t rows = (size_t)1 << (2 * k);  // 4^k
+    cmax = std::max(cmax, rows * ocap[k]);
+    svw = std::max(svw, svd_work_doubles(clampi(1LL << (2 * k)), 4 * ocap[k + 1]));
+  }
+  DBuf<double> C0(cmax, s), C1(cmax, s), W(svw, s);
+  const double* Mp = T.p;
+  double* Cn = C0.p;
+  double* Co = C1.p;
+  for (int k = n - 1; k >= 1; k--) {
+    const int rows = clampi(1LL << (2 * k));  // 4^k rows (sites 0..k-1)
+    SvdArgs a{};
+    a.M = MatView{const_cast<double*>(Mp), 4 * ocap[k + 1], axis_prefix(rows, dconst(rows)),
+                  axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
+    a.US = MatView{Cn, ocap[k], axis_prefix(rows, dconst(rows)), axis_prefix(ocap[k], dconst(1))};
+    a.VT = MatView{Y->core(k), 4 * ocap[k + 1], axis_prefix(ocap[k], dconst(1)),
+                   axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
+    a.eps = eps;
+    a.chi = chi;
+    a.rank_limit = dconst(1 << 30);
+    a.r_out = Y->dims + k;
+    a.work = W.p;
+    a.err = ctx->d_err;
+    launch_svd_f64(a, rows, 4 * ocap[k + 1], s);
+    Mp = Cn;
+    std::swap(Cn, Co);
+  }
+  launch_copy(Y->core(0), Mp, (size_t)4 * ocap[1], s);
+  return Y.release();
+}
+
+void to_dense_impl(qtt_ctx ctx, qtt_mps A, double* F) {
+  const int n = A->n;
+  cudaStream_t s = ctx->stream;
+  const size_t tot = (size_t)1 << (2 * n);
+  size_t mx = 4 * (size_t)A->cap[1];
+  for (int k = 1; k < n; k++) mx = std::max(mx, ((size_t)1 << (2 * (k + 1))) * A->cap[k + 1]);
+  DBuf<double> L0(std::max(mx, tot), s), L1(std::max(mx, tot), s);
+  launch_copy(L0.p, A->core(0), (size_t)4 * A->cap[1], s);
+  double* cur = L0.p;
+  double* nxt = L1.p;
+  for (int k = 1; k < n; k++) {
+    const int rows = clampi(1LL << (2 * k));
+    gemm(gemm_plain(cur, A->core(k), nxt, rows, 4 * A->cap[k + 1], A->cap[k], A->cap[k],
+                    4 * A->cap[k + 1], 4 * A->cap[k + 1]), s);
+    std::swap(cur, nxt);
+  }
+  launch_omega_to_dense(cur, F, n, s);
+}
+
+// --------------------------------------------------------------- errors
+qtt_status check_device_errors(qtt_ctx ctx) {
+  int h = 0;
+  QTT_CUDA_CHECK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    QTT_CUDA_CHECK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    if (h & QTT_DEVERR_NUMERIC) {
+      ctx->err = "non-finite value met on the device";
+      return QTT_ERR_NUMERIC;
+    }
+    if (h & QTT_DEVERR_TIMEOUT) {
+      ctx->err = "a bounded device-side wait gave up";
+      return QTT_ERR_TIMEOUT;
+    }
+    ctx->err = "device-side shape error";
+    return QTT_ERR_SHAPE;
+  }
+  return QTT_OK;
+}
+
+template <typename F>
+qtt_status guarded(qtt_ctx ctx, F&& f) {
+  if (!ctx) return QTT_ERR_ARG;
+  CtxGuard g(ctx);
+  try {
+    return f();
+  } catch (const QttError& e) {
+    ctx->err = e.msg;
+    return e.st;
+  } catch (const CudaError& e) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "CUDA error %s at line %d: %s", cudaGetErrorString(e.e), e.line,
+             e.what);
+    ctx->err = buf;
+    return QTT_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    ctx->err = "host allocation failed";
+    return QTT_ERR_ALLOC;
+  }
+}
+
+bool valid_params(const qtt_params* p) {
+  return p && p->n >= 1 && p->n <= 15 && p->L > 0 && p->eps >= 0 && p->chi_max >= 1 &&
+         p->mu >= 0 && p->cg_tol >= 0 && p->cg_maxit >= 1 && p->sweep_tol >= 0 &&
+         p->max_sweeps >= 1 && (p->precision == QTT_PREC_FP64 || p->precision == QTT_PREC_MIXED);
+}
+
+void check_mps(qtt_ctx ctx, qtt_mps m) {
+  if (!m) throw QttError(QTT_ERR_ARG, "null MPS");
+  if (m->n != ctx->p.n) throw QttError(QTT_ERR_SHAPE, "MPS has a different n than the context");
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* params) {
+  if (!out || !valid_params(params)) return QTT_ERR_ARG;
+  *out = nullptr;
+  auto ctx = new qtt_ctx_s;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->p = *params;
+  ctx->dx = params->L / (double)(1 << params->n);
+  qtt_status st = guarded(ctx, [&]() -> qtt_status {
+    QTT_CUDA_CHECK(cudaSetDevice(device));
+    cudaMemPool_t pool;
+    QTT_CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t thr = UINT64_MAX;
+    QTT_CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_err, sizeof(int)));
+    QTT_CUDA_CHECK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    const int n = params->n;
+    const double dx = ctx->dx;
+    HostMpo D1 = diff_mpo(n, 1, dx), D2 = diff_mpo(n, 2, dx);
+    ctx->D[0] = upload_mpo(ctx, D1);
+    ctx->D[1] = upload_mpo(ctx, D2);
+    // Laplacian D1 D1 + D2 D2 = (S1^{+2} + S1^{-2} + S2^{+2} + S2^{-2} - 4) / (4 dx^2)
+    const double c2 = 1.0 / (4.0 * dx * dx);
+    ctx->lap = upload_mpo(ctx, shift_sum_mpo(n, -4.0 * c2, {1, 1, 2, 2}, {2, -2, 2, -2},
+                                             {c2, c2, c2, c2}));
+    // projection blocks D_i^T D_j = -D_i D_j
+    HostMpo Ds[2] = {D1, D2};
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++) {
+        if (i == j) {
+          ctx->K[i][j] = upload_mpo(ctx, shift_sum_mpo(n, 2.0 * c2, {i + 1, i + 1}, {2, -2},
+                                                       {-c2, -c2}));
+        } else {
+          ctx->K[i][j] = upload_mpo(ctx, mpo_scaled(mpo_mul(Ds[i], Ds[j]), -1.0));
+        }
+      }
+    return QTT_OK;
+  });
+  if (st != QTT_OK) {
+    qtt_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return QTT_OK;
+}
+
+qtt_status qtt_destroy(qtt_ctx ctx) {
+  if (!ctx) return QTT_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (int i = 0; i < 2; i++) mpo_release(ctx->D[i]);
+  mpo_release(ctx->lap);
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) mpo_release(ctx->K[i][j]);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  delete ctx;
+  return QTT_OK;
+}
+
+qtt_status qtt_set_params(qtt_ctx ctx, const qtt_params* p) {
+  if (!ctx || !valid_params(p) || p->n != ctx->p.n || p->L != ctx->p.L) return QTT_ERR_ARG;
+  ctx->p = *p;
+  return QTT_OK;
+}
+
+qtt_status qtt_sync(qtt_ctx ctx) {
+  return guarded(ctx, [&]() -> qtt_status { return check_device_errors(ctx); });
+}
+
+const char* qtt_last_error(qtt_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+qtt_status qtt_from_dense(qtt_ctx ctx, const double* d_field, double eps, int chi_max,
+                          qtt_mps* out) {
+  if (!out || !d_field || eps < 0 || chi_max < 1) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    *out = from_dense_impl(ctx, d_field, eps, chi_max);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_to_dense(qtt_ctx ctx, qtt_mps mps, double* d_field_out) {
+  if (!d_field_out) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, mps);
+    to_dense_impl(ctx, mps, d_field_out);
+    return check_device_errors(ctx);
+  });
+}
+
+qtt_status qtt_mps_from_packed(qtt_ctx ctx, const double* cores, int cores_are_device,
+                               const int* bonds, qtt_mps* out) {
+  if (!out || !cores || !bonds) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    const int n = ctx->p.n;
+    std::vector<int> cap(bonds, bonds + n + 1);
+    if (cap[0] != 1 || cap[n] != 1) throw QttError(QTT_ERR_SHAPE, "end bonds must be 1");
+    for (int b = 1; b < n; b++)
+      if (cap[b] < 1 || cap[b] > (1 << 20)) throw QttError(QTT_ERR_SHAPE, "bad bond dimension");
+    MpsPtr m(new_mps(ctx, n, cap));
+    const cudaMemcpyKind kind = cores_are_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    QTT_CUDA_CHECK(cudaMemcpyAsync(m->data, cores, m->off[n] * sizeof(double), kind, ctx->stream));
+    QTT_CUDA_CHECK(cudaMemcpyAsync(m->dims, cap.data(), (n + 1) * sizeof(int),
+                                   cudaMemcpyHostToDevice, ctx->stream));
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    *out = m.release();
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_mps_to_packed(qtt_ctx ctx, qtt_mps mps, double* cores, int cores_are_device,
+                             size_t capacity, int* bonds) {
+  if (!cores || !bonds) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, mps);
+    const int n = mps->n;
+    std::vector<int> d(n + 1);
+    QTT_CUDA_CHECK(cudaMemcpyAsync(d.data(), mps->dims, (n + 1) * sizeof(int),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    size_t need = 0;
+    for (int k = 0; k < n; k++) need += (size_t)d[k] * 4 * d[k + 1];
+    if (need > capacity) throw QttError(QTT_ERR_ARG, "output capacity too small");
+    // pack: rows (a, s) of length d[k+1] from capacity storage
+    size_t o = 0;
+    const cudaMemcpyKind kind = cores_are_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int k = 0; k < n; k++) {
+      QTT_CUDA_CHECK(cudaMemcpy2DAsync(cores + o, d[k + 1] * sizeof(double), mps->core(k),
+                                       mps->cap[k + 1] * sizeof(double), d[k + 1] * sizeof(double),
+                                       (size_t)d[k] * 4, kind, ctx->stream));
+      o += (size_t)d[k] * 4 * d[k + 1];
+    }
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    for (int b = 0; b <= n; b++) bonds[b] = d[b];
+    return check_device_errors(ctx);
+  });
+}
+
+qtt_status qtt_mps_info(qtt_mps mps, int* n, int* bonds) {
+  if (!mps) return QTT_ERR_ARG;
+  qtt_ctx ctx = mps->ctx;
+  return guarded(ctx, [&]() -> qtt_status {
+    std::vector<int> d(mps->n + 1);
+    QTT_CUDA_CHECK(cudaMemcpyAsync(d.data(), mps->dims, (mps->n + 1) * sizeof(int),
+                                   cudaMemcpyDeviceToHost, mps->stream));
+    QTT_CUDA_CHECK(cudaStreamSynchronize(mps->stream));
+    if (n) *n = mps->n;
+    if (bonds)
+      for (int b = 0; b <= mps->n; b++) bonds[b] = d[b];
+    return check_device_errors(ctx);
+  });
+}
+
+void qtt_free_mps(qtt_mps mps) {
+  if (!mps) return;
+  cudaSetDevice(mps->ctx->device);
+  free_mps(mps);
+}
+
+qtt_status qtt_mpo_get(qtt_ctx ctx, int which, qtt_mpo* out) {
+  if (!ctx || !out) return QTT_ERR_ARG;
+  qtt_mpo m = nullptr;
+  if (which == 1) m = ctx->D[0];
+  else if (which == 2) m = ctx->D[1];
+  else if (which == 3) m = ctx->lap;
+  else if (which >= 4 && which <= 7) m = ctx->K[(which - 4) >> 1][(which - 4) & 1];
+  if (!m) return QTT_ERR_ARG;
+  m->refs++;
+  *out = m;
+  return QTT_OK;
+}
+
+void qtt_free_mpo(qtt_mpo mpo) { mpo_release(mpo); }
+
+qtt_status qtt_apply_mpo(qtt_ctx ctx, qtt_mpo mpo, qtt_mps in, double eps, int chi_max,
+                         qtt_mps* out) {
+  if (!mpo || !out || eps < 0 || chi_max < 1) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, in);
+    if (mpo->n != in->n) throw QttError(QTT_ERR_SHAPE, "MPO and MPS sizes differ");
+    *out = apply_impl(ctx, mpo, in, eps, chi_max);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_add(qtt_ctx ctx, int k, const double* coef, const qtt_mps* terms, double eps,
+                   int chi_max, qtt_mps* out) {
+  if (!out || !coef || !terms || k < 1 || k > 8 || eps < 0 || chi_max < 1) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    for (int t = 0; t < k; t++) check_mps(ctx, terms[t]);
+    *out = add_impl(ctx, k, coef, terms, eps, chi_max);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_hadamard(qtt_ctx ctx, qtt_mps a, qtt_mps b, double eps, int chi_max, qtt_mps* out) {
+  if (!out || eps < 0 || chi_max < 1) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, a);
+    check_mps(ctx, b);
+    *out = hadamard_impl(ctx, a, b, eps, chi_max);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_compress(qtt_ctx ctx, qtt_mps inout, double eps, int chi_max) {
+  if (eps < 0 || chi_max < 1) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, inout);
+    qtt_mps y = compress_impl(ctx, inout, eps, chi_max);
+    // swap contents so the caller's handle now holds the result
+    std::swap(inout->cap, y->cap);
+    std::swap(inout->off, y->off);
+    std::swap(inout->data, y->data);
+    std::swap(inout->dims, y->dims);
+    free_mps(y);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qtt_mps* v2,
+                       int* cg_iters, int* sweeps) {
+  if (!v1 || !v2 || !(h > 0)) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, w1);
+    check_mps(ctx, w2);
+    project_impl(ctx, w1, w2, h, v1, v2, cg_iters, sweeps);
+    qtt_status st = check_device_errors(ctx);
+    if (st != QTT_OK) return st;
+    if (ctx->last_not_converged) {
+      ctx->err = "projection reached its CG or sweep cap";
+      return QTT_ERR_NOT_CONVERGED;
+    }
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+  if (!u1 || !u2 || !(dt > 0) || nu < 0) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, *u1);
+    check_mps(ctx, *u2);
+    rk4_impl(ctx, u1, u2, dt, nu);
+    qtt_status st = check_device_errors(ctx);
+    if (st != QTT_OK) return st;
+    if (ctx->last_not_converged) {
+      ctx->err = "a projection reached its CG or sweep cap";
+      return QTT_ERR_NOT_CONVERGED;
+    }
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps, long long* launches) {
+  if (!ctx) return QTT_ERR_ARG;
+  if (cg_iters) *cg_iters = ctx->cg_iters;
+  if (sweeps) *sweeps = ctx->sweeps;
+  if (launches) *launches = ctx->launches.n;
+  return QTT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of the C ABI in include/qtt.h (argument marshalling only).
+
+Every computation happens in libqtt_b300.so on the GPU; this module only
+converts Python / torch arguments to pointers and sizes and turns status
+codes into exceptions.  Importing it without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_longlong, c_size_t, c_void_p
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqtt_b300.so")
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+STATUS = {0: "QTT_OK", 1: "QTT_ERR_ARG", 2: "QTT_ERR_SHAPE", 3: "QTT_ERR_ALLOC",
+          4: "QTT_ERR_CUDA", 5: "QTT_ERR_NOT_CONVERGED", 6: "QTT_ERR_TIMEOUT",
+          7: "QTT_ERR_NUMERIC"}
+NOT_CONVERGED = 5
+
+EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_error",
+           "qtt_from_dense", "qtt_to_dense", "qtt_mps_from_packed", "qtt_mps_to_packed",
+           "qtt_mps_info", "qtt_free_mps", "qtt_mpo_get", "qtt_free_mpo", "qtt_apply_mpo",
+           "qtt_add", "qtt_hadamard", "qtt_compress", "qtt_project", "qtt_rk4_step",
+           "qtt_stats")
+
+
+class QttError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n", c_int), ("L", c_double), ("eps", c_double), ("chi_max", c_int),
+                ("mu", c_double), ("cg_tol", c_double), ("cg_maxit", c_int),
+                ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libqtt_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                              "`python -m paper_2406_17823_b300.build`")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, ip = c_void_p, POINTER(c_int)
+        sig = {
+            "qtt_create": (c_int, [POINTER(vp), c_int, vp, POINTER(Params)]),
+            "qtt_destroy": (c_int, [vp]),
+            "qtt_set_params": (c_int, [vp, POINTER(Params)]),
+            "qtt_sync": (c_int, [vp]),
+            "qtt_last_error": (ctypes.c_char_p, [vp]),
+            "qtt_from_dense": (c_int, [vp, vp, c_double, c_int, POINTER(vp)]),
+            "qtt_to_dense": (c_int, [vp, vp, vp]),
+            "qtt_mps_from_packed": (c_int, [vp, vp, c_int, ip, POINTER(vp)]),
+            "qtt_mps_to_packed": (c_int, [vp, vp, vp, c_int, c_size_t, ip]),
+            "qtt_mps_info": (c_int, [vp, ip, ip]),
+            "qtt_free_mps": (None, [vp]),
+            "qtt_mpo_get": (c_int, [vp, c_int, POINTER(vp)]),
+            "qtt_free_mpo": (None, [vp]),
+            "qtt_apply_mpo": (c_int, [vp, vp, vp, c_double, c_int, POINTER(vp)]),
+            "qtt_add": (c_int, [vp, c_int, POINTER(c_double), POINTER(vp), c_double, c_int,
+                                POINTER(vp)]),
+            "qtt_hadamard": (c_int, [vp, vp, vp, c_double, c_int, POINTER(vp)]),
+            "qtt_compress": (c_int, [vp, vp, c_double, c_int]),
+            "qtt_project": (c_int, [vp, vp, vp, c_double, POINTER(vp), POINTER(vp), ip, ip]),
+            "qtt_rk4_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
+            "qtt_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong),
+                                  POINTER(c_longlong)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class MPS:
+    """Owning handle of a library MPS."""
+
+    def __init__(self, ctx: "Context", handle: int):
+        self.ctx = ctx
+        self.h = c_void_p(handle)
+
+    def free(self):
+        if self.h and self.h.value:
+            lib().qtt_free_mps(self.h)
+            self.h = c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def bonds(self):
+        n = self.ctx.params.n
+        b = (c_int * (n + 1))()
+        self.ctx._check(lib().qtt_mps_info(self.h, None, b))
+        return list(b)
+
+
+class Context:
+    """A library context bound to one CUDA device and the current torch stream."""
+
+    def __init__(self, n: int, L: float = 2 * np.pi, eps: float = 1e-8, chi_max: int = 64,
+                 mu: float = 2.5e5, cg_tol: float = 1e-5, cg_maxit: int = 100,
+                 sweep_tol: float = 1e-5, max_sweeps: int = 20, precision: int = PREC_FP64,
+                 device: int = 0, stream=None):
+        torch = _torch()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.params = Params(n, L, eps, chi_max, mu, cg_tol, cg_maxit, sweep_tol, max_sweeps,
+                             precision)
+        h = c_void_p()
+        st = lib().qtt_create(byref(h), device, c_void_p(stream.cuda_stream), byref(self.params))
+        if st != 0:
+            raise QttError(st, "qtt_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().qtt_destroy(self.h)
+            self.h = c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, allow_not_converged: bool = False):
+        if st == 0 or (allow_not_converged and st == NOT_CONVERGED):
+            return st
+        raise QttError(st, lib().qtt_last_error(self.h).decode())
+
+    @property
+    def N(self):
+        return 2 ** self.params.n
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        self._check(lib().qtt_set_params(self.h, byref(self.params)))
+
+    def sync(self):
+        self._check(lib().qtt_sync(self.h))
+
+    # -------------------------------------------------------------- I/O
+    def from_dense(self, field, eps=None, chi_max=None) -> MPS:
+        torch = _torch()
+        t = torch.as_tensor(field, dtype=torch.float64, device=f"cuda:{self.device}").contiguous()
+        out = c_void_p()
+        self._check(lib().qtt_from_dense(self.h, c_void_p(t.data_ptr()),
+                                         self.params.eps if eps is None else eps,
+                                         self.params.chi_max if chi_max is None else chi_max,
+                                         byref(out)))
+        self._keep = t
+        return MPS(self, out.value)
+
+    def to_dense(self, mps: MPS):
+        torch = _torch()
+        out = torch.empty((self.N, self.N), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(lib().qtt_to_dense(self.h, mps.h, c_void_p(out.data_ptr())))
+        return out
+
+    def from_cores(self, cores) -> MPS:
+        """Upload a list of numpy cores (D_{k-1}, 4, D_k) (host buffer path)."""
+        bonds = [1] + [int(c.shape[2]) for c in cores]
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(c, np.float64).reshape(-1)
+                                                    for c in cores]))
+        b = (c_int * len(bonds))(*bonds)
+        out = c_void_p()
+        self._check(lib().qtt_mps_from_packed(self.h, c_void_p(flat.ctypes.data), 0, b,
+                                              byref(out)))
+        return MPS(self, out.value)
+
+    def to_cores(self, mps: MPS):
+        n = self.params.n
+        bonds = mps.bonds
+        total = sum(bonds[k] * 4 * bonds[k + 1] for k in range(n))
+        buf = np.empty(total, np.float64)
+        b = (c_int * (n + 1))()
+        self._check(lib().qtt_mps_to_packed(self.h, mps.h, c_void_p(buf.ctypes.data), 0, total, b))
+        cores, o = [], 0
+        for k in range(n):
+            sz = b[k] * 4 * b[k + 1]
+            cores.append(buf[o:o + sz].reshape(b[k], 4, b[k + 1]).copy())
+            o += sz
+        return cores
+
+    # -------------------------------------------------------------- ops
+    def mpo(self, which: int):
+        out = c_void_p()
+        self._check(lib().qtt_mpo_get(self.h, which, byref(out)))
+        return out
+
+    def apply_mpo(self, which: int, mps: MPS, eps=None, chi_max=None) -> MPS:
+        m = self.mpo(which)
+        out = c_void_p()
+        try:
+            self._check(lib().qtt_apply_mpo(self.h, m, mps.h,
+                                            self.params.eps if eps is None else eps,
+                                            self.params.chi_max if chi_max is None else chi_max,
+                                            byref(out)))
+        finally:
+            lib().qtt_free_mpo(m)
+        return MPS(self, out.value)
+
+    def add(self, coefs, terms, eps=None, chi_max=None) -> MPS:
+        k = len(terms)
+        cf = (c_double * k)(*coefs)
+        hs = (c_void_p * k)(*[t.h.value for t in terms])
+        out = c_void_p()
+        self._check(lib().qtt_add(self.h, k, cf, hs, self.params.eps if eps is None else eps,
+                                  self.params.chi_max if chi_max is None else chi_max,
+                                  byref(out)))
+        return MPS(self, out.value)
+
+    def hadamard(self, a: MPS, b: MPS, eps=None, chi_max=None) -> MPS:
+        out = c_void_p()
+        self._check(lib().qtt_hadamard(self.h, a.h, b.h, self.params.eps if eps is None else eps,
+                                       self.params.chi_max if chi_max is None else chi_max,
+                                       byref(out)))
+        return MPS(self, out.value)
+
+    def compress(self, mps: MPS, eps=None, chi_max=None) -> MPS:
+        self._check(lib().qtt_compress(self.h, mps.h, self.params.eps if eps is None else eps,
+                                       self.params.chi_max if chi_max is None else chi_max))
+        return mps
+
+    def project(self, w1: MPS, w2: MPS, h: float):
+        v1, v2 = c_void_p(), c_void_p()
+        cg, sw = c_int(), c_int()
+        st = lib().qtt_project(self.h, w1.h, w2.h, h, byref(v1), byref(v2), byref(cg), byref(sw))
+        self._check(st, allow_not_converged=True)
+        return MPS(self, v1.value), MPS(self, v2.value), cg.value, sw.value, st == 0
+
+    def rk4_step(self, u1: MPS, u2: MPS, dt: float, nu: float):
+        """In place: u1, u2 receive the new state.  Returns True if every
+        projection converged within its caps."""
+        h1, h2 = c_void_p(u1.h.value), c_void_p(u2.h.value)
+        st = lib().qtt_rk4_step(self.h, byref(h1), byref(h2), dt, nu)
+        u1.h, u2.h = h1, h2
+        self._check(st, allow_not_converged=True)
+        return st == 0
+
+    def stats(self):
+        a, b, c = c_longlong(), c_longlong(), c_longlong()
+        self._check(lib().qtt_stats(self.h, byref(a), byref(b), byref(c)))
+        return {"cg_iters": a.value, "sweeps": b.value, "launches": c.value}
