@@ -123,21 +123,23 @@ def trunc_rank(s: np.ndarray, eps: float, chi_max: int) -> int:
 def from_dense(F: np.ndarray, eps: float, chi_max: int) -> list:
     """TT-SVD of a dense field into a QTT (Sec. II.B; truncation of Sec. III.E).
 
-    Left to right: at each bond the unfolding is split by an SVD, the rank
-    is chosen by :func:`trunc_rank`, U becomes the core and S V^T carries on.
+    Right to left: at each bond the unfolding (sites 1..k) x (site k+1 and
+    the carried rank) is split by an SVD, the rank is chosen by
+    :func:`trunc_rank`, V^T becomes core k+1 and U S carries on, so the
+    result has its centre at site 1 like every compression.
     """
     n = int(round(math.log2(F.shape[0])))
-    M = dense_to_tensor(np.asarray(F, dtype=np.float64)).reshape(1, -1)
-    cores = []
-    r = 1
-    for _ in range(n - 1):
-        M = M.reshape(r * D_PHYS, -1)
+    M = dense_to_tensor(np.asarray(F, dtype=np.float64)).reshape(-1)
+    cores = [None] * n
+    r_right = 1
+    for k in range(n - 1, 0, -1):
+        M = M.reshape(D_PHYS ** k, D_PHYS * r_right)
         U, S, Vt = np.linalg.svd(M, full_matrices=False)
-        rk = trunc_rank(S, eps, chi_max)
-        cores.append(U[:, :rk].reshape(r, D_PHYS, rk).copy())
-        M = S[:rk, None] * Vt[:rk]
-        r = rk
-    cores.append(M.reshape(r, D_PHYS, 1).copy())
+        r = trunc_rank(S, eps, chi_max)
+        cores[k] = Vt[:r].reshape(r, D_PHYS, r_right).copy()
+        M = U[:, :r] * S[:r]
+        r_right = r
+    cores[0] = M.reshape(1, D_PHYS, r_right).copy()
     return cores
 
 

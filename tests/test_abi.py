@@ -1,0 +1,72 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every symbol
+include/qtt.h declares, and the ctypes Params struct matches the header's
+layout (no compute call: there is no GPU here)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qtt.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qtt_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2406_17823_b300 import build
+    return build.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_2406_17823_b300 import qtt
+    assert sorted(qtt.EXPORTS) == names
+
+
+def test_params_layout_matches_header():
+    from paper_2406_17823_b300.qtt import Params
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "qtt.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(qtt_params),
+         offsetof(qtt_params, n), offsetof(qtt_params, L), offsetof(qtt_params, eps),
+         offsetof(qtt_params, chi_max), offsetof(qtt_params, mu), offsetof(qtt_params, cg_tol),
+         offsetof(qtt_params, cg_maxit), offsetof(qtt_params, sweep_tol),
+         offsetof(qtt_params, max_sweeps), offsetof(qtt_params, precision));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "p.c")
+        exe = os.path.join(d, "p")
+        open(c, "w").write(prog)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = list(map(int, subprocess.check_output([exe]).split()))
+    want = [ctypes.sizeof(Params)] + [getattr(Params, f).offset for f, _ in Params._fields_]
+    assert got == want
+
+
+def test_null_arguments_are_rejected_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.qtt_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.qtt_create.restype = ctypes.c_int
+    assert lib.qtt_create(None, 0, None, None) == 1  # QTT_ERR_ARG
+    lib.qtt_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.qtt_destroy(None) == 1
+    lib.qtt_last_error.restype = ctypes.c_char_p
+    lib.qtt_last_error.argtypes = [ctypes.c_void_p]
+    assert lib.qtt_last_error(None) == b"null context"
