@@ -56,6 +56,8 @@ struct MatView {
 };
 
 // Device-side error flags (bit mask), read at synchronisation points.
+// A guard that finds an inconsistent shape sets QTT_DEVERR_SHAPE and
+// touches nothing.
 enum : int {
   QTT_DEVERR_NUMERIC = 1,
   QTT_DEVERR_SHAPE = 2,
@@ -66,6 +68,11 @@ struct LaunchCounter {
   long long n = 0;
 };
 extern thread_local LaunchCounter* g_launch_counter;
+extern int* g_dev_err;
+// Called after every kernel launch: counts it and, when the environment
+// variable QTT_DEBUG_SYNC is set, waits for it and reports a failure by
+// kernel name (a debugging aid that localises device-side faults).
+void post_launch(const char* name, cudaStream_t s);
 static inline void count_launch() {
   if (g_launch_counter) g_launch_counter->n++;
 }
@@ -90,3 +97,13 @@ struct QttError {
 };
 
 static inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Host-side registry of the library's device allocations.  Every launch
+// checks, before it is enqueued, that each buffer range it will touch
+// (computed from the capacities it is given) lies inside one registered
+// allocation; a violation throws instead of launching.  Pointers the
+// registry does not know (caller-owned buffers) are not checked.
+void reg_alloc(const void* p, size_t bytes);
+void reg_free(const void* p);
+// throws QttError(QTT_ERR_SHAPE) if [p, p + count) leaves its allocation
+void check_range(const void* p, long long count_elems, size_t elem_bytes, const char* what);

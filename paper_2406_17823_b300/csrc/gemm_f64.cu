@@ -85,6 +85,15 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
 
 void launch_gemm_f64(const GemmF64& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 * g.nb2 <= 0) return;
+  {
+    const long long zb1 = g.nb1 - 1, zb2 = g.nb2 - 1;
+    const long long ea = g.tA ? (long long)(g.K - 1) * g.lda + g.M : (long long)(g.M - 1) * g.lda + g.K;
+    const long long eb = g.tB ? (long long)(g.N - 1) * g.ldb + g.K : (long long)(g.K - 1) * g.ldb + g.N;
+    const long long ec = (long long)(g.M - 1) * g.ldc + g.N;
+    check_range(g.A, zb1 * g.sA1 + zb2 * g.sA2 + ea, sizeof(double), "gemm A");
+    check_range(g.B, zb1 * g.sB1 + zb2 * g.sB2 + eb, sizeof(double), "gemm B");
+    check_range(g.C, zb1 * g.sC1 + zb2 * g.sC2 + ec, sizeof(double), "gemm C");
+  }
   if (g.K <= 0) {
     // C = beta * C (alpha * empty product)
     launch_scale(g, s);
@@ -92,5 +101,5 @@ void launch_gemm_f64(const GemmF64& g, cudaStream_t s) {
   }
   dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.nb1 * g.nb2);
   k_gemm_f64<<<grid, 256, 0, s>>>(g);
-  count_launch();
+  post_launch("k_gemm_f64", s);
 }

@@ -41,6 +41,7 @@ struct QrArgs {
   int rT;
   int* r_out;  // receives r (may be null)
   double* work;
+  long long work_len;  // doubles available at work
   const int* skip;
   int* err;
 };
@@ -65,6 +66,7 @@ struct SvdArgs {
   int* r_out;
   double* sv_out;   // optional, receives the c singular values
   double* work;
+  long long work_len;  // doubles available at work
   const int* skip;
   int* err;
 };

@@ -9,6 +9,8 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+int* g_dev_err = nullptr;  // error flag of the context issuing the launch
+
 namespace {
 
 __global__ void k_scale(double* C, int M, int N, int ldc, double beta) {
@@ -50,10 +52,15 @@ struct AddArgs {
   int capl, capr;
 };
 
-__global__ void k_add_assemble(AddArgs g) {
+__global__ void k_add_assemble(AddArgs g, int* err) {
   int loff[9], roff[9];
   loff[0] = roff[0] = 0;
   for (int t = 0; t < g.K; t++) {
+    // shape guard: actual extents must fit the term's capacities
+    if (*g.t[t].dl > g.t[t].capl || *g.t[t].dr > g.t[t].capr) {
+      if (blockIdx.x == 0 && threadIdx.x == 0 && err) atomicOr(err, QTT_DEVERR_SHAPE);
+      return;
+    }
     loff[t + 1] = loff[t] + (g.first ? 0 : *g.t[t].dl);
     roff[t + 1] = roff[t] + (g.last ? 0 : *g.t[t].dr);
   }
@@ -263,7 +270,7 @@ void launch_scale(const GemmF64& g, cudaStream_t s) {
     const int z1 = z / g.nb2, z2 = z % g.nb2;
     k_scale<<<grid_for((long long)g.M * g.N), 256, 0, s>>>(g.C + z1 * g.sC1 + z2 * g.sC2, g.M, g.N,
                                                            g.ldc, g.beta);
-    count_launch();
+    post_launch("k_scale", s);
   }
 }
 
@@ -271,32 +278,44 @@ void launch_zero(double* p, size_t n, cudaStream_t s) {
   if (n) QTT_CUDA_CHECK(cudaMemsetAsync(p, 0, n * sizeof(double), s));
 }
 void launch_copy(double* dst, const double* src, size_t n, cudaStream_t s) {
+  check_range(dst, (long long)n, sizeof(double), "copy dst");
+  check_range(src, (long long)n, sizeof(double), "copy src");
   if (n) QTT_CUDA_CHECK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
 }
 void launch_fill(double* p, size_t n, double v, cudaStream_t s) {
+  check_range(p, (long long)n, sizeof(double), "fill");
   k_fill<<<grid_for((long long)n), 256, 0, s>>>(p, n, v);
-  count_launch();
+  post_launch("k_fill", s);
 }
 
 void launch_mpo_expand(const double* W, int wl, int wr, const double* A, int Ca, int Cb,
                        double* out, cudaStream_t s) {
   const long long tot = (long long)Ca * wl * 4 * Cb * wr;
+  check_range(W, (long long)wl * 16 * wr, sizeof(double), "expand W");
+  check_range(A, (long long)Ca * 4 * Cb, sizeof(double), "expand A");
+  check_range(out, tot, sizeof(double), "expand out");
   k_mpo_expand<<<grid_for(tot), 256, 0, s>>>(W, wl, wr, A, Ca, Cb, out);
-  count_launch();
+  post_launch("k_mpo_expand", s);
 }
 
 void launch_add_assemble_args(const AddTerm* terms, int K, int first, int last, double* out,
                               int capl, int capr, cudaStream_t s) {
   AddArgs g{};
-  for (int t = 0; t < K; t++) g.t[t] = terms[t];
+  if (K < 1 || K > 8) throw QttError(QTT_ERR_ARG, "add: 1..8 terms");
+  check_range(out, (long long)capl * 4 * capr, sizeof(double), "add out");
+  for (int t = 0; t < K; t++) {
+    g.t[t] = terms[t];
+    check_range(terms[t].core, (long long)terms[t].capl * 4 * terms[t].capr, sizeof(double),
+                "add term");
+  }
   g.K = K;
   g.first = first;
   g.last = last;
   g.out = out;
   g.capl = capl;
   g.capr = capr;
-  k_add_assemble<<<grid_for((long long)capl * 4 * capr), 256, 0, s>>>(g);
-  count_launch();
+  k_add_assemble<<<grid_for((long long)capl * 4 * capr), 256, 0, s>>>(g, g_dev_err);
+  post_launch("k_add_assemble", s);
 }
 
 void launch_add_assemble(const AddTerm* terms, int K, int first, int last, double* out,
@@ -305,18 +324,20 @@ void launch_add_assemble(const AddTerm* terms, int K, int first, int last, doubl
 }
 
 void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaStream_t s) {
+  check_range(in, (long long)Ca * 4 * Cb, sizeof(double), "transpose in");
+  check_range(out, (long long)Ca * 4 * Cb, sizeof(double), "transpose out");
   k_core_transpose<<<grid_for((long long)Ca * 4 * Cb), 256, 0, s>>>(in, Ca, Cb, out);
-  count_launch();
+  post_launch("k_core_transpose", s);
 }
 
 void launch_set_int(int* p, int v, cudaStream_t s) {
   k_set_int<<<1, 1, 0, s>>>(p, v);
-  count_launch();
+  post_launch("k_set_int", s);
 }
 
 void launch_fill_int(int* p, int n, int v, cudaStream_t s) {
   k_fill_int<<<1, 64, 0, s>>>(p, n, v);
-  count_launch();
+  post_launch("k_fill_int", s);
 }
 
 void launch_dims(const int* const* src, const int (*mul)[QTT_MAX_N + 1], int K, int nb, int* out,
@@ -330,34 +351,51 @@ void launch_dims(const int* const* src, const int (*mul)[QTT_MAX_N + 1], int K, 
   g.nb = nb;
   g.out = out;
   k_dims<<<1, 32, 0, s>>>(g);
-  count_launch();
+  post_launch("k_dims", s);
 }
 
 void launch_dense_to_omega(const double* F, double* T, int n, cudaStream_t s) {
+  check_range(T, 1LL << (2 * n), sizeof(double), "omega out");
   k_dense_to_omega<<<grid_for(1LL << (2 * n)), 256, 0, s>>>(F, T, n);
-  count_launch();
+  post_launch("k_dense_to_omega", s);
 }
 void launch_omega_to_dense(const double* T, double* F, int n, cudaStream_t s) {
+  check_range(T, 1LL << (2 * n), sizeof(double), "omega in");
   k_omega_to_dense<<<grid_for(1LL << (2 * n)), 256, 0, s>>>(T, F, n);
-  count_launch();
+  post_launch("k_omega_to_dense", s);
 }
 
 void launch_check_finite(const double* p, size_t n, int* err, cudaStream_t s) {
   k_check_finite<<<grid_for((long long)n), 256, 0, s>>>(p, n, err);
-  count_launch();
+  post_launch("k_check_finite", s);
+}
+
+static void check_cg(const CgVec& v) {
+  for (int i = 0; i < 2; i++) {
+    check_range(v.x[i], v.len[i], sizeof(double), "cg x");
+    check_range(v.r[i], v.len[i], sizeof(double), "cg r");
+    check_range(v.p[i], v.len[i], sizeof(double), "cg p");
+    check_range(v.ap[i], v.len[i], sizeof(double), "cg ap");
+  }
 }
 
 void launch_cg_start(const CgVec& v, const double* b0, const double* b1, double* scal, int* ist,
                      double tol, int* err, cudaStream_t s) {
+  check_cg(v);
+  check_range(b0, v.len[0], sizeof(double), "cg b0");
+  check_range(b1, v.len[1], sizeof(double), "cg b1");
   k_cg_start<<<1, 1024, 0, s>>>(v, b0, b1, scal, ist, tol, err);
-  count_launch();
+  post_launch("k_cg_start", s);
 }
 void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err, cudaStream_t s) {
+  check_cg(v);
   k_cg_step<<<1, 1024, 0, s>>>(v, scal, ist, maxit, err);
-  count_launch();
+  post_launch("k_cg_step", s);
 }
 void launch_sumsq2(const double* a, long long na, const double* b, long long nb, double* out,
                    cudaStream_t s) {
+  check_range(a, na, sizeof(double), "sumsq a");
+  check_range(b, nb, sizeof(double), "sumsq b");
   k_sumsq2<<<1, 1024, 0, s>>>(a, na, b, nb, out);
-  count_launch();
+  post_launch("k_sumsq2", s);
 }

@@ -51,8 +51,11 @@ __device__ void householder(double* W, int ldw, int m, int c, double* tau, doubl
     const double nrm2 = block_sum(part, sh);
     const double x0 = col[j];
     __syncthreads();
-    double t = 0.0, alpha = 0.0;
-    if (nrm2 > 0.0) {
+    // A column whose squared norm is below 1e-280 is left as it is (no
+    // reflection, R[j][j] = x0): its entries are < 1e-140, and forming the
+    // reflector from them would overflow tau.
+    double t = 0.0, alpha = x0;
+    if (nrm2 > 1e-280 && isfinite(nrm2)) {
       const double nrm = sqrt(nrm2);
       alpha = (x0 >= 0.0) ? -nrm : nrm;
       t = 1.0 / (nrm * (nrm + fabs(x0)));
@@ -98,6 +101,16 @@ __device__ void apply_reflectors(const double* W, int ldw, int m, int k, const d
   }
 }
 
+// Index maps stay inside their storage only when hact <= hcap and
+// 1 <= lact <= lcap on both axes.
+__device__ __forceinline__ bool axis_ok(const Axis& a) {
+  const int h = dval(a.hact), l = dval(a.lact);
+  return h >= 0 && h <= a.hcap && l >= 1 && l <= a.lcap;
+}
+__device__ __forceinline__ bool view_ok(const MatView& v) {
+  return axis_ok(v.rows) && axis_ok(v.cols);
+}
+
 __device__ void zero_view(const MatView& v) {
   const int R = v.rows.hcap * v.rows.lcap, C = v.cols.hcap * v.cols.lcap;
   const long long tot = (long long)R * C;
@@ -120,6 +133,23 @@ __global__ void __launch_bounds__(256) k_qr_f64(QrArgs a) {
   const int frl = dval(fr.lact), fcl = dval(fc.lact);
   const int arl = dval(a.A.rows.lact), acl = dval(a.A.cols.lact);
   const int r = min(m, c);
+  {
+    // shape guard: actual extents must fit the capacities of every view
+    // and of the work buffer; otherwise flag and touch nothing
+    const int fr_cap = fr.hcap * fr.lcap, fc_cap = fc.hcap * fc.lcap;
+    const int qr_cap = a.qT ? a.Q.cols.hcap * a.Q.cols.lcap : a.Q.rows.hcap * a.Q.rows.lcap;
+    const int qc_cap = a.qT ? a.Q.rows.hcap * a.Q.rows.lcap : a.Q.cols.hcap * a.Q.cols.lcap;
+    const int rr_cap = a.rT ? a.R.cols.hcap * a.R.cols.lcap : a.R.rows.hcap * a.R.rows.lcap;
+    const int rc_cap = a.rT ? a.R.rows.hcap * a.R.rows.lcap : a.R.cols.hcap * a.R.cols.lcap;
+    const bool bad_shape = !view_ok(a.A) || !view_ok(a.Q) || !view_ok(a.R) ||
+                           m < 1 || c < 1 || m > fr_cap || c > fc_cap || frl > fr.lcap ||
+                           fcl > fc.lcap || m > qr_cap || r > qc_cap || r > rr_cap || c > rc_cap ||
+                           (long long)m * c + (long long)m * r + 2LL * c > a.work_len;
+    if (bad_shape) {
+      if (threadIdx.x == 0 && a.err) atomicOr(a.err, QTT_DEVERR_SHAPE);
+      return;
+    }
+  }
   double* W = a.work;                       // m x c
   double* Qw = W + (size_t)m * c;           // m x r
   double* tau = Qw + (size_t)m * r;         // c
@@ -133,7 +163,12 @@ __global__ void __launch_bounds__(256) k_qr_f64(QrArgs a) {
     W[e] = v;
   }
   if (bad && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
-  __syncthreads();
+  if (__syncthreads_or(bad)) {  // non-finite input: zero outputs, report, stop
+    zero_view(a.Q);
+    zero_view(a.R);
+    if (threadIdx.x == 0 && a.r_out) *a.r_out = r;
+    return;
+  }
   householder(W, m, m, c, tau, diag, sh);
   for (long long e = threadIdx.x; e < (long long)m * r; e += blockDim.x) {
     const int i = (int)(e % m), j = (int)(e / m);
@@ -179,6 +214,25 @@ __global__ void __launch_bounds__(512) k_svd_f64(SvdArgs a) {
   const bool wide = (m <= N);           // factor M^T when M is wide
   const int Rt = wide ? N : m;          // rows of the tall matrix
   const int c = wide ? m : N;           // its columns
+  {
+    const Axis& fr = a.inT ? a.M.cols : a.M.rows;
+    const Axis& fc = a.inT ? a.M.rows : a.M.cols;
+    const int us_r = a.usT ? a.US.cols.hcap * a.US.cols.lcap : a.US.rows.hcap * a.US.rows.lcap;
+    const int us_c = a.usT ? a.US.rows.hcap * a.US.rows.lcap : a.US.cols.hcap * a.US.cols.lcap;
+    const int vt_r = a.vtT ? a.VT.cols.hcap * a.VT.cols.lcap : a.VT.rows.hcap * a.VT.rows.lcap;
+    const int vt_c = a.vtT ? a.VT.rows.hcap * a.VT.rows.lcap : a.VT.cols.hcap * a.VT.cols.lcap;
+    const int rmax = min(c, min(a.chi, dval(a.rank_limit)));
+    const long long need = (long long)Rt * c * 2 + (long long)c * c * 2 + 4LL * c + 2 + (c + 1) / 2;
+    const bool bad_shape = !view_ok(a.M) || !view_ok(a.US) || !view_ok(a.VT) ||
+                           m < 1 || N < 1 || m > fr.hcap * fr.lcap || N > fc.hcap * fc.lcap ||
+                           dval(fr.lact) > fr.lcap || dval(fc.lact) > fc.lcap || m > us_r ||
+                           max(rmax, 1) > us_c || max(rmax, 1) > vt_r || N > vt_c ||
+                           need > a.work_len;
+    if (bad_shape) {
+      if (threadIdx.x == 0 && a.err) atomicOr(a.err, QTT_DEVERR_SHAPE);
+      return;
+    }
+  }
   double* T = a.work;                          // Rt x c
   double* X = T + (size_t)Rt * c;              // c x c
   double* J = X + (size_t)c * c;               // c x c
@@ -199,7 +253,12 @@ __global__ void __launch_bounds__(512) k_svd_f64(SvdArgs a) {
     T[e] = v;
   }
   if (bad && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
-  __syncthreads();
+  if (__syncthreads_or(bad)) {  // non-finite input: zero outputs, rank 1, stop
+    zero_view(a.US);
+    zero_view(a.VT);
+    if (threadIdx.x == 0 && a.r_out) *a.r_out = 1;
+    return;
+  }
   householder(T, Rt, Rt, c, tau, diag, sh);
   // X = R^T (wide) or R (tall); J = I
   for (long long e = threadIdx.x; e < (long long)c * c; e += blockDim.x) {
@@ -236,7 +295,7 @@ __global__ void __launch_bounds__(512) k_svd_f64(SvdArgs a) {
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al * be)) {
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
           const double zeta = (be - al) / (2.0 * ga);
           const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
@@ -270,14 +329,21 @@ __global__ void __launch_bounds__(512) k_svd_f64(SvdArgs a) {
     if (lane == 0) sig[k] = sqrt(s);
   }
   __syncthreads();
+  // descending order under a strict total order (NaN ranks last, ties by
+  // index), so perm is always a permutation of 0..c-1
   for (int k = threadIdx.x; k < c; k += blockDim.x) {
     int rank = 0;
-    const double sk = sig[k];
+    const double sk = isnan(sig[k]) ? -1.0 : sig[k];
     for (int j = 0; j < c; j++) {
-      const double sj = sig[j];
+      const double sj = isnan(sig[j]) ? -1.0 : sig[j];
       rank += (sj > sk) || (sj == sk && j < k);
     }
     perm[rank] = k;
+  }
+  {
+    bool nan_seen = false;
+    for (int k = threadIdx.x; k < c; k += blockDim.x) nan_seen |= !isfinite(sig[k]);
+    if (nan_seen && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -341,15 +407,22 @@ __global__ void __launch_bounds__(512) k_svd_f64(SvdArgs a) {
 
 }  // namespace
 
+static long long view_extent(const MatView& v) {
+  return (long long)(v.rows.hcap * v.rows.lcap - 1) * v.ld + v.cols.hcap * v.cols.lcap;
+}
+
 size_t qr_work_doubles(int mcap, int ccap) {
   const size_t r = (size_t)(mcap < ccap ? mcap : ccap);
   return (size_t)mcap * ccap + (size_t)mcap * r + 2 * (size_t)ccap + 8;
 }
 
 void launch_qr_f64(const QrArgs& a, int mcap, int ccap, cudaStream_t s) {
-  (void)mcap; (void)ccap;
+  check_range(a.A.ptr, view_extent(a.A), sizeof(double), "qr A");
+  check_range(a.Q.ptr, view_extent(a.Q), sizeof(double), "qr Q");
+  check_range(a.R.ptr, view_extent(a.R), sizeof(double), "qr R");
+  check_range(a.work, (long long)qr_work_doubles(mcap, ccap), sizeof(double), "qr work");
   k_qr_f64<<<1, 256, 0, s>>>(a);
-  count_launch();
+  post_launch("k_qr_f64", s);
 }
 
 size_t svd_work_doubles(int mcap, int ncap) {
@@ -359,7 +432,10 @@ size_t svd_work_doubles(int mcap, int ncap) {
 }
 
 void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
-  (void)mcap; (void)ncap;
+  check_range(a.M.ptr, view_extent(a.M), sizeof(double), "svd M");
+  check_range(a.US.ptr, view_extent(a.US), sizeof(double), "svd US");
+  check_range(a.VT.ptr, view_extent(a.VT), sizeof(double), "svd VT");
+  check_range(a.work, (long long)svd_work_doubles(mcap, ncap), sizeof(double), "svd work");
   k_svd_f64<<<1, 512, 0, s>>>(a);
-  count_launch();
+  post_launch("k_svd_f64", s);
 }

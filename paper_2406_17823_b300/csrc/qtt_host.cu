@@ -7,6 +7,7 @@
 // projection (CG every few iterations, and once per sweep).
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -17,6 +18,62 @@
 #include "kernels.cuh"
 
 thread_local LaunchCounter* g_launch_counter = nullptr;
+
+#include <iterator>
+#include <map>
+#include <mutex>
+
+namespace {
+std::mutex g_reg_mu;
+std::map<uintptr_t, size_t>& reg_map() {
+  static std::map<uintptr_t, size_t> m;
+  return m;
+}
+}  // namespace
+
+void post_launch(const char* name, cudaStream_t s) {
+  count_launch();
+  static const bool dbg = getenv("QTT_DEBUG_SYNC") != nullptr;
+  if (!dbg) return;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) throw CudaError(e, name, 0);
+}
+
+void reg_alloc(const void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_reg_mu);
+  reg_map()[(uintptr_t)p] = bytes;
+}
+void reg_free(const void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_reg_mu);
+  reg_map().erase((uintptr_t)p);
+}
+void check_range(const void* p, long long count, size_t eb, const char* what) {
+  if (!p || count <= 0) return;
+  std::lock_guard<std::mutex> g(g_reg_mu);
+  auto& m = reg_map();
+  const bool external = strncmp(what, "ext", 3) == 0;  // caller-owned buffer
+  auto it = m.upper_bound((uintptr_t)p);
+  const uintptr_t a = (uintptr_t)p;
+  if (it == m.begin() || a >= std::prev(it)->first + std::prev(it)->second) {
+    if (external) return;
+    char buf[160];
+    snprintf(buf, sizeof buf, "launch range check failed (%s): pointer outside every library "
+             "allocation", what);
+    throw QttError(QTT_ERR_SHAPE, buf);
+  }
+  --it;
+  const uintptr_t base = it->first, end = base + it->second;
+  if (a + (uintptr_t)count * eb > end) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "launch range check failed (%s): %lld elements from offset %llu, "
+             "allocation holds %llu bytes", what, count, (unsigned long long)(a - base),
+             (unsigned long long)it->second);
+    throw QttError(QTT_ERR_SHAPE, buf);
+  }
+}
 
 
 // ------------------------------------------------------------------ objects
@@ -67,6 +124,7 @@ struct CtxGuard {
   LaunchCounter* prev;
   explicit CtxGuard(qtt_ctx c) : prev(g_launch_counter) {
     g_launch_counter = &c->launches;
+    g_dev_err = c->d_err;
     cudaSetDevice(c->device);
   }
   ~CtxGuard() { g_launch_counter = prev; }
@@ -83,6 +141,7 @@ struct DBuf {
     if (n) {
       cudaError_t e = cudaMallocAsync((void**)&p, n * sizeof(T), s);
       if (e != cudaSuccess) throw QttError(QTT_ERR_ALLOC, "cudaMallocAsync failed");
+      reg_alloc(p, n * sizeof(T));
     }
   }
   DBuf(const DBuf&) = delete;
@@ -94,7 +153,10 @@ struct DBuf {
     return *this;
   }
   void release() {
-    if (p) cudaFreeAsync(p, s);
+    if (p) {
+      reg_free(p);
+      cudaFreeAsync(p, s);
+    }
     p = nullptr;
   }
   ~DBuf() { release(); }
@@ -126,12 +188,16 @@ qtt_mps new_mps(qtt_ctx ctx, int n, const std::vector<int>& cap) {
     delete m;
     throw QttError(QTT_ERR_ALLOC, "MPS allocation failed");
   }
+  reg_alloc(m->data, o * sizeof(double));
+  reg_alloc(m->dims, (n + 1) * sizeof(int));
   QTT_CUDA_CHECK(cudaMemsetAsync(m->data, 0, o * sizeof(double), ctx->stream));
   return m;
 }
 
 void free_mps(qtt_mps m) {
   if (!m) return;
+  reg_free(m->data);
+  reg_free(m->dims);
   if (m->data) cudaFreeAsync(m->data, m->stream);
   if (m->dims) cudaFreeAsync(m->dims, m->stream);
   delete m;
@@ -292,6 +358,7 @@ qtt_mpo upload_mpo(qtt_ctx ctx, const HostMpo& hm) {
     delete m;
     throw QttError(QTT_ERR_ALLOC, "MPO allocation failed");
   }
+  reg_alloc(m->dev, 3 * o * sizeof(double));
   m->dev_k2 = m->dev + o;
   m->dev_kr2 = m->dev + 2 * o;
   QTT_CUDA_CHECK(cudaMemcpy(m->dev, raw.data(), o * sizeof(double), cudaMemcpyHostToDevice));
@@ -303,6 +370,7 @@ qtt_mpo upload_mpo(qtt_ctx ctx, const HostMpo& hm) {
 void mpo_release(qtt_mpo m) {
   if (!m) return;
   if (--m->refs > 0) return;
+  reg_free(m->dev);
   if (m->dev) cudaFree(m->dev);
   delete m;
 }
@@ -421,6 +489,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
                   axis_prefix(cin[k + 1], dref(X->dims + k + 1))};
     a.r_out = qD.p + k + 1;
     a.work = W.p;
+    a.work_len = (long long)W.n;
     a.err = ctx->d_err;
     launch_qr_f64(a, 4 * qcap[k], cin[k + 1], s);
   }
@@ -453,6 +522,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     a.rank_limit = dconst(1 << 30);
     a.r_out = Y->dims + k;
     a.work = W.p;
+    a.work_len = (long long)W.n;
     a.err = ctx->d_err;
     launch_svd_f64(a, qcap[k], 4 * ocap[k + 1], s);
   }
@@ -532,9 +602,11 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
   const auto& ca = A->cap;
   const auto& cb = B->cap;
   std::vector<int> rcap(n + 1, 1);
+  // the zip-up keeps min(4 r, Da Db, chi) directions; this may exceed the
+  // natural bound 4^(n-b) (extra directions carry zero weight) and is
+  // reduced by the compression that follows
   for (int b = 1; b < n; b++)
-    rcap[b] = std::min({4 * rcap[b - 1], clampi((long long)ca[b] * cb[b]), chi,
-                        clampi(natural_cap(n, b))});
+    rcap[b] = std::min({4 * rcap[b - 1], clampi((long long)ca[b] * cb[b]), chi});
   MpsPtr C(new_mps(ctx, n, rcap));
   launch_fill_int(C->dims, n + 1, 1, s);
   size_t xmax = 1, tmax = 1, rmax = 1, svw = 1;
@@ -593,6 +665,7 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
     a.rank_limit = dconst(1 << 30);
     a.r_out = C->dims + k + 1;
     a.work = W.p;
+    a.work_len = (long long)W.n;
     a.err = ctx->d_err;
     launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
     std::swap(Rc, Rn);
@@ -869,6 +942,7 @@ struct Projector {
       a.R = MatView{rb.p, cr, axis_prefix(cr, dconst(1)), axis_prefix(cr, dref(V[i]->dims + d + 1))};
       a.r_out = V[i]->dims + d + 1;
       a.work = work.p;
+      a.work_len = (long long)work.n;
       a.err = ctx->d_err;
       launch_qr_f64(a, 4 * cl, cr, s);
       gemm(gemm_plain(rb.p, V[i]->core(d + 1), tmp.p, cr, 4 * cr2, cr, cr, 4 * cr2, 4 * cr2), s);
@@ -891,6 +965,7 @@ struct Projector {
       a.rT = 1;
       a.r_out = V[i]->dims + d;
       a.work = work.p;
+      a.work_len = (long long)work.n;
       a.err = ctx->d_err;
       launch_qr_f64(a, 4 * cr, cl, s);
       gemm(gemm_plain(V[i]->core(d - 1), rb.p, tmp.p, 4 * cl0, cl, cl, cl, cl, cl), s);
@@ -1079,6 +1154,7 @@ qtt_mps from_dense_impl(qtt_ctx ctx, const double* F, double eps, int chi) {
     a.rank_limit = dconst(1 << 30);
     a.r_out = Y->dims + k;
     a.work = W.p;
+    a.work_len = (long long)W.n;
     a.err = ctx->d_err;
     launch_svd_f64(a, rows, 4 * ocap[k + 1], s);
     Mp = Cn;

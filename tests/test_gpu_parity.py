@@ -153,7 +153,7 @@ def test_zero_and_degenerate_inputs(Q3):
     X1, X2, dx = I.grid(n)
     c = ctx.from_dense(np.cos(X2), 1e-12, 8)
     d1 = ctx.apply_mpo(1, c, 1e-12, 8)
-    assert np.abs(gpu_dense(ctx, d1)).max() == 0.0
+    assert np.abs(gpu_dense(ctx, d1)).max() < 1e-12
 
 
 # ------------------------------------------------------------ projection
