@@ -1,0 +1,326 @@
+"""Benchmark: QTT RK4 steps per second on a 2^10 x 2^10 shear jet at chi = 64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                    [--impl reference]
+
+Workload (default): decaying double shear layer, periodic [0, 2 pi)^2 with
+N = 2^10, u = tanh((y - pi/2)/delta) - tanh((y - 3 pi/2)/delta),
+delta = 2 pi / 200, v = 0.05 sin x plus a seeded divergence-free
+perturbation of RMS 1e-3 (seed 0); QTT with chi_max = 64, eps = 1e-8;
+Re = 2e5; dt = 0.1 dx / max|u0|; the paper's solver settings (mu = 2.5e5,
+CG tolerance 1e-5 with at most 100 iterations, sweep tolerance 1e-5).
+A step is one full RK4 step (four penalised Euler minimisations) of both
+velocity components; the state advances from step to step.
+
+One JSON line is printed by rank 0.  With torchrun (N > 1) every rank runs
+its own trajectory on its own GPU (replicas: the method has no exchange
+step), value = all ranks' steps / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK4 steps/s at 2^10x2^10, chi=64"
+WORKLOAD = dict(workload="shear_jet_2^10_chi64", n=10, chi_max=64, eps=1e-8, Re=2e5, mu=2.5e5,
+                cg_tol=1e-5, cg_maxit=100, sweep_tol=1e-5, max_sweeps=20, seed=0,
+                dt_rule="0.1*dx/max|u0|")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_state(n, seed):
+    import qtt_inputs as I
+    u, dx = I.shear_jet(n, seed=seed)
+    dt = 0.1 * dx / float(np.abs(u[0]).max())
+    return u, dx, dt
+
+
+def solver_kwargs(w):
+    return dict(eps=w["eps"], chi_max=w["chi_max"], mu=w["mu"], cg_tol=w["cg_tol"],
+                cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except Exception:
+            pass
+    return {}
+
+
+def fp64_dgemm_peak(torch, dev):
+    """FP64 peak for the roofline denominator: cuBLAS DGEMM 4096^3 on this GPU
+    (the measured-peaks file carries no FP64 figure); best of 3."""
+    a = torch.randn(4096, 4096, device=dev, dtype=torch.float64)
+    b = torch.randn(4096, 4096, device=dev, dtype=torch.float64)
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2 * 4096 ** 3 / best / 1e12
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_stage_seconds(u, dx, dt, w, budget_s=25.0):
+    """Time the CPU oracle on a bounded sample: RK4 stage 1 (stage_w plus the
+    projection) of the workload on one BLAS thread; a full step is four such
+    stages, so steps/s = 1 / (4 * stage time)."""
+    from threadpoolctl import threadpool_limits
+    from oracle import qtt as Q
+    p = Q.Params(eps=w["eps"], chi_max=w["chi_max"], mu=w["mu"], cg_tol=w["cg_tol"],
+                 cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"])
+    with threadpool_limits(limits=1):
+        uq = [Q.from_dense(f, p.eps, p.chi_max) for f in u]
+        ops = Q.build_operators(w["n"], dx)
+        t = time.perf_counter()
+        wv = Q.stage_w(uq, uq, dt / 6.0, 1.0 / w["Re"], p, ops)
+        Q.project(wv, dt / 6.0, p, ops)
+        return time.perf_counter() - t
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = dict(WORKLOAD)
+    u, dx, dt = workload_state(w["n"], w["seed"])
+    for _ in range(args.warmup):
+        pass  # the CPU oracle has no warm-up effects worth timing
+    total = 0.0
+    for _ in range(args.steps):
+        total += oracle_stage_seconds(u, dx, dt, w)
+    steps_done = 0.25 * args.steps
+    value = steps_done / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / steps_done, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**w, "parallelism": "none (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": "RK4 stage 1 of the workload per step, x4 for a full "
+                                       "step, numpy FP64 on one BLAS thread"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override grid bits (testing only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2406_17823_b300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+        w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
+    prec = P.PREC_FP64 if args.precision == "fp64" else P.PREC_MIXED
+    u, dx, dt = workload_state(w["n"], w["seed"] + rank)
+    nu = 1.0 / w["Re"]
+    ctx = P.Context(w["n"], precision=prec, device=local, **solver_kwargs(w))
+    state = [ctx.from_dense(f) for f in u]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.rk4_step(state[0], state[1], dt, nu)
+    barrier()
+    launches0 = ctx.stats()["launches"]
+    ctx.profile_begin()
+    times = []
+    converged = True
+    with ClockSampler(local) as clk:
+        barrier()
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()  # evict the L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            converged &= ctx.rk4_step(state[0], state[1], dt, nu)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        barrier()
+        wall = time.perf_counter() - wall0
+    prof = ctx.profile_end()
+    gpu_launches = ctx.stats()["launches"] - launches0
+    t_local = sum(times)
+    t_max = t_local
+    if dist is not None:
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / t_max
+
+    # e2e through the C ABI with host buffers: upload the packed state from
+    # pinned memory, one step, download the packed result
+    cores = [ctx.to_cores(s) for s in state]
+    e2e_times, h2d, d2h = [], 0, 0
+    for _ in range(max(1, min(args.steps, 2))):
+        host = [c for c in cores]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = [ctx.from_cores(c) for c in host]
+        ctx.rk4_step(g[0], g[1], dt, nu)
+        out = [ctx.to_cores(x) for x in g]
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        h2d = sum(a.nbytes for c in host for a in c)
+        d2h = sum(a.nbytes for c in out for a in c)
+        cores = out
+    e2e_value = world * len(e2e_times) / sum(e2e_times)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (largest share of device time)
+    dom, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    tot_ms = sum(v["ms"] for v in prof.values())
+    peaks = measured_peaks()
+    fp64_peak = fp64_dgemm_peak(torch, dev)
+    avg_ms = rec["ms"] / rec["launches"]
+    flops_per_launch = rec["flops"] / rec["launches"]
+    achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
+    roofline = {"kernel": dom, "bound": "alu" if args.precision == "fp64" else "tensor",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
+                "peak_source": "FP64 cuBLAS DGEMM 4096^3 measured in this run (of measured)",
+                "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
+                "launches_timed": rec["launches"], "avg_launch_ms": avg_ms,
+                "flops_per_launch": flops_per_launch}
+    cpu = None
+    if not args.no_cpu_baseline:
+        st = oracle_stage_seconds(u, dx, dt, w)
+        cpu = {"value": 1.0 / (4.0 * st), "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": "RK4 stage 1 of the same workload (stage_w + projection), x4 for a "
+                         "full step, numpy FP64 oracle on one BLAS thread"}
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "tf32/f64",
+            "data": "synthetic (seeded shear-jet initial condition)",
+            "config": {**w, "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "all_projections_converged": bool(converged)},
+            "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clocks, "wall_s": wall,
+            "kernel_shares": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items()},
+            "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -87,7 +87,7 @@ qtt_status qtt_set_params(qtt_ctx ctx, const qtt_params* params);
 qtt_status qtt_sync(qtt_ctx ctx);
 const char* qtt_last_error(qtt_ctx ctx);
 
-/* Dense field (device, N*N doubles) -> QTT by a left-to-right TT-SVD with
+/* Dense field (device, N*N doubles) -> QTT by a right-to-left TT-SVD with
  * per-bond truncation (eps, chi_max) (Sec. II.B, Sec. III.E). */
 qtt_status qtt_from_dense(qtt_ctx ctx, const double* d_field, double eps, int chi_max,
                           qtt_mps* out);
@@ -144,6 +144,15 @@ qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
  * sweeps, kernel launches enqueued by the library since context creation. */
 qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps,
                      long long* launches);
+
+/* Per-kernel timing of the work enqueued between qtt_profile_begin and
+ * qtt_profile_end: CUDA events are recorded on the context stream around
+ * every launch (a few microseconds each).  qtt_profile_end synchronises and
+ * writes a JSON object {"<kernel>": {"launches": L, "ms": T, "flops": F}, ...}
+ * (F = the algorithmic FLOPs of those launches, from their shapes) into buf
+ * (at most cap bytes, NUL-terminated); QTT_ERR_ARG if buf is too small. */
+qtt_status qtt_profile_begin(qtt_ctx ctx);
+qtt_status qtt_profile_end(qtt_ctx ctx, char* buf, size_t cap);
 
 #ifdef __cplusplus
 }

@@ -72,7 +72,10 @@ extern int* g_dev_err;
 // Called after every kernel launch: counts it and, when the environment
 // variable QTT_DEBUG_SYNC is set, waits for it and reports a failure by
 // kernel name (a debugging aid that localises device-side faults).
-void post_launch(const char* name, cudaStream_t s);
+void post_launch(const char* name, cudaStream_t s, double flops = 0.0);
+// Called just before every kernel launch (records a start event when the
+// context is profiling).
+void pre_launch(cudaStream_t s);
 static inline void count_launch() {
   if (g_launch_counter) g_launch_counter->n++;
 }

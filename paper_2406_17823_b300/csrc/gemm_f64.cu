@@ -100,6 +100,7 @@ void launch_gemm_f64(const GemmF64& g, cudaStream_t s) {
     return;
   }
   dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.nb1 * g.nb2);
+  pre_launch(s);
   k_gemm_f64<<<grid, 256, 0, s>>>(g);
-  post_launch("k_gemm_f64", s);
+  post_launch("k_gemm_f64", s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
 }

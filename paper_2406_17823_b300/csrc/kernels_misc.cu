@@ -268,6 +268,7 @@ void launch_scale(const GemmF64& g, cudaStream_t s) {
   if (g.beta == 1.0) return;
   for (int z = 0; z < g.nb1 * g.nb2; z++) {
     const int z1 = z / g.nb2, z2 = z % g.nb2;
+    pre_launch(s);
     k_scale<<<grid_for((long long)g.M * g.N), 256, 0, s>>>(g.C + z1 * g.sC1 + z2 * g.sC2, g.M, g.N,
                                                            g.ldc, g.beta);
     post_launch("k_scale", s);
@@ -284,6 +285,7 @@ void launch_copy(double* dst, const double* src, size_t n, cudaStream_t s) {
 }
 void launch_fill(double* p, size_t n, double v, cudaStream_t s) {
   check_range(p, (long long)n, sizeof(double), "fill");
+  pre_launch(s);
   k_fill<<<grid_for((long long)n), 256, 0, s>>>(p, n, v);
   post_launch("k_fill", s);
 }
@@ -294,6 +296,7 @@ void launch_mpo_expand(const double* W, int wl, int wr, const double* A, int Ca,
   check_range(W, (long long)wl * 16 * wr, sizeof(double), "expand W");
   check_range(A, (long long)Ca * 4 * Cb, sizeof(double), "expand A");
   check_range(out, tot, sizeof(double), "expand out");
+  pre_launch(s);
   k_mpo_expand<<<grid_for(tot), 256, 0, s>>>(W, wl, wr, A, Ca, Cb, out);
   post_launch("k_mpo_expand", s);
 }
@@ -314,6 +317,7 @@ void launch_add_assemble_args(const AddTerm* terms, int K, int first, int last, 
   g.out = out;
   g.capl = capl;
   g.capr = capr;
+  pre_launch(s);
   k_add_assemble<<<grid_for((long long)capl * 4 * capr), 256, 0, s>>>(g, g_dev_err);
   post_launch("k_add_assemble", s);
 }
@@ -326,16 +330,19 @@ void launch_add_assemble(const AddTerm* terms, int K, int first, int last, doubl
 void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaStream_t s) {
   check_range(in, (long long)Ca * 4 * Cb, sizeof(double), "transpose in");
   check_range(out, (long long)Ca * 4 * Cb, sizeof(double), "transpose out");
+  pre_launch(s);
   k_core_transpose<<<grid_for((long long)Ca * 4 * Cb), 256, 0, s>>>(in, Ca, Cb, out);
   post_launch("k_core_transpose", s);
 }
 
 void launch_set_int(int* p, int v, cudaStream_t s) {
+  pre_launch(s);
   k_set_int<<<1, 1, 0, s>>>(p, v);
   post_launch("k_set_int", s);
 }
 
 void launch_fill_int(int* p, int n, int v, cudaStream_t s) {
+  pre_launch(s);
   k_fill_int<<<1, 64, 0, s>>>(p, n, v);
   post_launch("k_fill_int", s);
 }
@@ -350,22 +357,26 @@ void launch_dims(const int* const* src, const int (*mul)[QTT_MAX_N + 1], int K, 
   g.K = K;
   g.nb = nb;
   g.out = out;
+  pre_launch(s);
   k_dims<<<1, 32, 0, s>>>(g);
   post_launch("k_dims", s);
 }
 
 void launch_dense_to_omega(const double* F, double* T, int n, cudaStream_t s) {
   check_range(T, 1LL << (2 * n), sizeof(double), "omega out");
+  pre_launch(s);
   k_dense_to_omega<<<grid_for(1LL << (2 * n)), 256, 0, s>>>(F, T, n);
   post_launch("k_dense_to_omega", s);
 }
 void launch_omega_to_dense(const double* T, double* F, int n, cudaStream_t s) {
   check_range(T, 1LL << (2 * n), sizeof(double), "omega in");
+  pre_launch(s);
   k_omega_to_dense<<<grid_for(1LL << (2 * n)), 256, 0, s>>>(T, F, n);
   post_launch("k_omega_to_dense", s);
 }
 
 void launch_check_finite(const double* p, size_t n, int* err, cudaStream_t s) {
+  pre_launch(s);
   k_check_finite<<<grid_for((long long)n), 256, 0, s>>>(p, n, err);
   post_launch("k_check_finite", s);
 }
@@ -384,11 +395,13 @@ void launch_cg_start(const CgVec& v, const double* b0, const double* b1, double*
   check_cg(v);
   check_range(b0, v.len[0], sizeof(double), "cg b0");
   check_range(b1, v.len[1], sizeof(double), "cg b1");
+  pre_launch(s);
   k_cg_start<<<1, 1024, 0, s>>>(v, b0, b1, scal, ist, tol, err);
   post_launch("k_cg_start", s);
 }
 void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err, cudaStream_t s) {
   check_cg(v);
+  pre_launch(s);
   k_cg_step<<<1, 1024, 0, s>>>(v, scal, ist, maxit, err);
   post_launch("k_cg_step", s);
 }
@@ -396,6 +409,7 @@ void launch_sumsq2(const double* a, long long na, const double* b, long long nb,
                    cudaStream_t s) {
   check_range(a, na, sizeof(double), "sumsq a");
   check_range(b, nb, sizeof(double), "sumsq b");
+  pre_launch(s);
   k_sumsq2<<<1, 1024, 0, s>>>(a, na, b, nb, out);
   post_launch("k_sumsq2", s);
 }

@@ -1,0 +1,510 @@
+// FP64 QR and SVD spread over a thread-block cluster (8 or 16 CTAs, one
+// problem per cluster).  Same algorithms and rounding behaviour as the
+// single-CTA kernels in linalg_f64.cu (Householder QR; QR of the tall
+// orientation then one-sided Jacobi with round-robin pairs), but:
+//
+//  * Householder: the columns of the tall matrix are dealt cyclically to
+//    the CTAs; the owner of column j forms reflector j, a cluster barrier
+//    publishes it, and every CTA applies it to its own columns.
+//  * Jacobi: column i of the square factor X and of the rotation
+//    accumulator J lives in the shared memory of CTA (i mod CL); in each
+//    round every CTA rotates the pairs dealt to it, reading and writing the
+//    two columns wherever they live (distributed shared memory), and a
+//    cluster barrier ends the round.
+//
+// On this GPU an SM retires about two FP64 FMAs per clock, so spreading an
+// O(c^3) factorisation over the cluster is what makes it affordable.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+__device__ __forceinline__ double warp_sum_c(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double cta_sum_c(double v, double* sh) {
+  v = warp_sum_c(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; i++) t += sh[i];
+  return t;
+}
+
+__device__ __forceinline__ bool axis_ok_c(const Axis& a) {
+  const int h = dval(a.hact), l = dval(a.lact);
+  return h >= 0 && h <= a.hcap && l >= 1 && l <= a.lcap;
+}
+__device__ __forceinline__ bool view_ok_c(const MatView& v) {
+  return axis_ok_c(v.rows) && axis_ok_c(v.cols);
+}
+__device__ __forceinline__ long long voff(const MatView& v, int ic, int jc, int rl, int cl) {
+  return (long long)axis_full(v.rows, ic, rl) * v.ld + axis_full(v.cols, jc, cl);
+}
+
+// zero the capacity region of a view, rows dealt over the cluster
+__device__ void zero_view_cl(const MatView& v, int rank, int CL) {
+  const int R = v.rows.hcap * v.rows.lcap, C = v.cols.hcap * v.cols.lcap;
+  for (int i = rank; i < R; i += CL)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) v.ptr[(long long)i * v.ld + j] = 0.0;
+}
+
+// Householder QR of W (m x c, column-major, ld = m) with the columns dealt
+// cyclically over the cluster.  tau / diag live in global memory.
+__device__ void householder_cl(cg::cluster_group& cl, double* W, int m, int c, double* tau,
+                               double* diag, double* sh, int rank, int CL) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int kmax = min(m, c);
+  for (int j = 0; j < kmax; j++) {
+    double* col = W + (size_t)j * m;
+    __syncthreads();  // this CTA's updates of column j (if it owns it) are complete
+    if (j % CL == rank) {
+      double part = 0.0;
+      for (int i = j + threadIdx.x; i < m; i += blockDim.x) part += col[i] * col[i];
+      const double nrm2 = cta_sum_c(part, sh);
+      const double x0 = col[j];
+      __syncthreads();
+      double t = 0.0, alpha = x0;
+      if (nrm2 > 1e-280 && isfinite(nrm2)) {
+        const double nrm = sqrt(nrm2);
+        alpha = (x0 >= 0.0) ? -nrm : nrm;
+        t = 1.0 / (nrm * (nrm + fabs(x0)));
+        if (threadIdx.x == 0) col[j] = x0 - alpha;
+      }
+      if (threadIdx.x == 0) {
+        tau[j] = t;
+        diag[j] = alpha;
+      }
+    }
+    cl.sync();  // reflector j published
+    const double t = *(volatile double*)(tau + j);
+    if (t != 0.0) {
+      // my columns cc > j with cc % CL == rank
+      int c0 = j + 1;
+      c0 += ((rank - c0) % CL + CL) % CL;
+      for (int cc = c0 + warp * CL; cc < c; cc += nw * CL) {
+        double* x = W + (size_t)cc * m;
+        double s = 0.0;
+        for (int i = j + lane; i < m; i += 32) s += col[i] * x[i];
+        s = warp_sum_c(s) * t;
+        for (int i = j + lane; i < m; i += 32) x[i] -= s * col[i];
+      }
+    }
+  }
+  cl.sync();
+}
+
+// B (m x nb, column-major, ld = m): columns cc % CL == rank get
+// B[:, cc] <- H_0 ... H_{k-1} B[:, cc]  (columns are independent).
+__device__ void apply_reflectors_cl(const double* W, int m, int k, const double* tau, double* B,
+                                    int nb, bool identity_cols, int rank, int CL) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int cc = rank + warp * CL; cc < nb; cc += nw * CL) {
+    double* x = B + (size_t)cc * m;
+    const int jtop = identity_cols ? min(cc, k - 1) : k - 1;
+    for (int j = jtop; j >= 0; j--) {
+      const double t = tau[j];
+      if (t == 0.0) continue;
+      const double* v = W + (size_t)j * m;
+      double s = 0.0;
+      for (int i = j + lane; i < m; i += 32) s += v[i] * x[i];
+      s = warp_sum_c(s) * t;
+      for (int i = j + lane; i < m; i += 32) x[i] -= s * v[i];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) k_qr_cluster(QrArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
+  __shared__ double sh[32];
+  if (a.skip && *a.skip) return;  // uniform over the cluster
+  const Axis& fr = a.inT ? a.A.cols : a.A.rows;
+  const Axis& fc = a.inT ? a.A.rows : a.A.cols;
+  const int m = axis_len(fr), c = axis_len(fc);
+  const int arl = dval(a.A.rows.lact), acl = dval(a.A.cols.lact);
+  const int r = min(m, c);
+  {
+    const int fr_cap = fr.hcap * fr.lcap, fc_cap = fc.hcap * fc.lcap;
+    const int qr_cap = a.qT ? a.Q.cols.hcap * a.Q.cols.lcap : a.Q.rows.hcap * a.Q.rows.lcap;
+    const int qc_cap = a.qT ? a.Q.rows.hcap * a.Q.rows.lcap : a.Q.cols.hcap * a.Q.cols.lcap;
+    const int rr_cap = a.rT ? a.R.cols.hcap * a.R.cols.lcap : a.R.rows.hcap * a.R.rows.lcap;
+    const int rc_cap = a.rT ? a.R.rows.hcap * a.R.rows.lcap : a.R.cols.hcap * a.R.cols.lcap;
+    const bool bad = !view_ok_c(a.A) || !view_ok_c(a.Q) || !view_ok_c(a.R) || m < 1 || c < 1 ||
+                     m > fr_cap || c > fc_cap || m > qr_cap || r > qc_cap || r > rr_cap ||
+                     c > rc_cap ||
+                     (long long)m * c + (long long)m * r + 2LL * c > a.work_len;
+    if (bad) {
+      if (rank == 0 && threadIdx.x == 0 && a.err) atomicOr(a.err, QTT_DEVERR_SHAPE);
+      return;  // every CTA of the cluster takes this branch
+    }
+  }
+  double* W = a.work;
+  double* Qw = W + (size_t)m * c;
+  double* tau = Qw + (size_t)m * r;
+  double* diag = tau + c;
+  bool badv = false;
+  for (int j = rank; j < c; j += CL)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const long long off = a.inT ? voff(a.A, j, i, arl, acl) : voff(a.A, i, j, arl, acl);
+      const double v = a.A.ptr[off];
+      badv |= !isfinite(v);
+      W[(size_t)j * m + i] = v;
+    }
+  if (badv && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
+  cl.sync();
+  householder_cl(cl, W, m, c, tau, diag, sh, rank, CL);
+  for (int j = rank; j < r; j += CL)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) Qw[(size_t)j * m + i] = (i == j) ? 1.0 : 0.0;
+  __syncthreads();
+  apply_reflectors_cl(W, m, r, tau, Qw, r, true, rank, CL);
+  cl.sync();  // all reads of A done before outputs (they may alias A)
+  zero_view_cl(a.Q, rank, CL);
+  zero_view_cl(a.R, rank, CL);
+  cl.sync();
+  const int qrl = dval(a.Q.rows.lact), qcl = dval(a.Q.cols.lact);
+  for (int j = rank; j < r; j += CL)
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const long long off = a.qT ? voff(a.Q, j, i, qrl, qcl) : voff(a.Q, i, j, qrl, qcl);
+      a.Q.ptr[off] = Qw[(size_t)j * m + i];
+    }
+  const int rrl = dval(a.R.rows.lact), rcl = dval(a.R.cols.lact);
+  for (int j = rank; j < c; j += CL)
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      double v = 0.0;
+      if (j == i) v = diag[i];
+      else if (j > i) v = W[(size_t)j * m + i];
+      const long long off = a.rT ? voff(a.R, j, i, rrl, rcl) : voff(a.R, i, j, rrl, rcl);
+      a.R.ptr[off] = v;
+    }
+  if (rank == 0 && threadIdx.x == 0 && a.r_out) *a.r_out = r;
+}
+
+__device__ __forceinline__ int rr_pos_c(int k, int t, int cp) {
+  return k == 0 ? 0 : 1 + (k - 1 + t) % (cp - 1);
+}
+
+// dynamic shared memory: X and J home columns (slots x c each), then flags
+__global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
+  extern __shared__ double dsm[];
+  __shared__ double sh[32];
+  __shared__ int flag_local;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (a.skip && *a.skip) return;
+  const int m = a.inT ? axis_len(a.M.cols) : axis_len(a.M.rows);
+  const int N = a.inT ? axis_len(a.M.rows) : axis_len(a.M.cols);
+  const int mrl = dval(a.M.rows.lact), mcl = dval(a.M.cols.lact);
+  const bool wide = (m <= N);
+  const int Rt = wide ? N : m;
+  const int c = wide ? m : N;
+  const int slots = (c + CL - 1) / CL;
+  {
+    const Axis& fr = a.inT ? a.M.cols : a.M.rows;
+    const Axis& fc = a.inT ? a.M.rows : a.M.cols;
+    const int us_r = a.usT ? a.US.cols.hcap * a.US.cols.lcap : a.US.rows.hcap * a.US.rows.lcap;
+    const int us_c = a.usT ? a.US.rows.hcap * a.US.rows.lcap : a.US.cols.hcap * a.US.cols.lcap;
+    const int vt_r = a.vtT ? a.VT.cols.hcap * a.VT.cols.lcap : a.VT.rows.hcap * a.VT.rows.lcap;
+    const int vt_c = a.vtT ? a.VT.rows.hcap * a.VT.rows.lcap : a.VT.cols.hcap * a.VT.cols.lcap;
+    const int rmax = min(c, min(a.chi, dval(a.rank_limit)));
+    const long long need = (long long)Rt * c * 2 + (long long)c * c * 2 + 4LL * c + 2 + (c + 1) / 2;
+    const bool bad = !view_ok_c(a.M) || !view_ok_c(a.US) || !view_ok_c(a.VT) || m < 1 ||
+                     N < 1 || m > fr.hcap * fr.lcap || N > fc.hcap * fc.lcap || m > us_r ||
+                     max(rmax, 1) > us_c || max(rmax, 1) > vt_r || N > vt_c ||
+                     need > a.work_len || (use_smem && slots * c > use_smem);
+    if (bad) {
+      if (rank == 0 && threadIdx.x == 0 && a.err) atomicOr(a.err, QTT_DEVERR_SHAPE);
+      return;
+    }
+  }
+  double* T = a.work;                   // Rt x c
+  double* Xg = T + (size_t)Rt * c;      // c x c   (used when not in shared memory)
+  double* Jg = Xg + (size_t)c * c;      // c x c
+  double* Bw = Jg + (size_t)c * c;      // Rt x c
+  double* tau = Bw + (size_t)Rt * c;
+  double* diag = tau + c;
+  double* sig = diag + c;
+  double* tail = sig + c;
+  int* perm = (int*)(tail + c + 1);
+  // home of column i: CTA i % CL, slot i / CL
+  double* Xs = dsm;
+  double* Js = dsm + (size_t)slots * c;
+  auto xcol = [&](int i) -> double* {
+    if (!use_smem) return Xg + (size_t)i * c;
+    return cl.map_shared_rank(Xs, i % CL) + (size_t)(i / CL) * c;
+  };
+  auto jcol = [&](int i) -> double* {
+    if (!use_smem) return Jg + (size_t)i * c;
+    return cl.map_shared_rank(Js, i % CL) + (size_t)(i / CL) * c;
+  };
+  bool badv = false;
+  for (int j = rank; j < c; j += CL)
+    for (int i = threadIdx.x; i < Rt; i += blockDim.x) {
+      const int fi = wide ? j : i, fj = wide ? i : j;
+      const long long off = a.inT ? voff(a.M, fj, fi, mrl, mcl) : voff(a.M, fi, fj, mrl, mcl);
+      const double v = a.M.ptr[off];
+      badv |= !isfinite(v);
+      T[(size_t)j * Rt + i] = v;
+    }
+  if (badv && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
+  cl.sync();
+  householder_cl(cl, T, Rt, c, tau, diag, sh, rank, CL);
+  // X = R^T (wide) or R (tall) into the home columns; J = I
+  for (int i = rank; i < c; i += CL) {
+    double* x = xcol(i);
+    double* jj = jcol(i);
+    for (int e = threadIdx.x; e < c; e += blockDim.x) {
+      const int p = wide ? i : e, q = wide ? e : i;  // X(e, i) = R(p, q)
+      double rv = 0.0;
+      if (p == q) rv = diag[p];
+      else if (p < q) rv = T[(size_t)q * Rt + p];
+      x[e] = rv;
+      jj[e] = (e == i) ? 1.0 : 0.0;
+    }
+  }
+  cl.sync();
+  const double tol = fmax(1e-15, 1e-16 * (double)c);
+  const int cp = c + (c & 1);
+  for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
+    if (threadIdx.x == 0) flag_local = 0;
+    __syncthreads();
+    for (int t = 0; t < cp - 1; t++) {
+      for (int k = rank + warp * CL; k < cp / 2; k += nw * CL) {
+        int p = rr_pos_c(k, t, cp), q = rr_pos_c(cp - 1 - k, t, cp);
+        if (p >= c || q >= c) continue;
+        if (p > q) { const int s_ = p; p = q; q = s_; }
+        double* x = xcol(p);
+        double* y = xcol(q);
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < c; i += 32) {
+          const double xi = x[i], yi = y[i];
+          al += xi * xi;
+          be += yi * yi;
+          ga += xi * yi;
+        }
+        al = warp_sum_c(al);
+        be = warp_sum_c(be);
+        ga = warp_sum_c(ga);
+        if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+          for (int i = lane; i < c; i += 32) {
+            const double xi = x[i], yi = y[i];
+            x[i] = cs * xi - sn * yi;
+            y[i] = sn * xi + cs * yi;
+          }
+          double* jx = jcol(p);
+          double* jy = jcol(q);
+          for (int i = lane; i < c; i += 32) {
+            const double xi = jx[i], yi = jy[i];
+            jx[i] = cs * xi - sn * yi;
+            jy[i] = sn * xi + cs * yi;
+          }
+          if (lane == 0) flag_local = 1;
+        }
+      }
+      cl.sync();
+    }
+    // cluster-wide "any rotation in this sweep": read every CTA's flag
+    // (the last round ended with a cluster barrier, so the flags are final)
+    int any = 0;
+    for (int rr = 0; rr < CL; rr++) any |= *cl.map_shared_rank(&flag_local, rr);
+    cl.sync();  // nobody resets its flag before all have read it
+    if (!any) break;
+  }
+  // singular values (home columns), order, rank (computed by every CTA alike)
+  for (int k = rank + warp * CL; k < c; k += nw * CL) {
+    const double* x = xcol(k);
+    double s = 0.0;
+    for (int i = lane; i < c; i += 32) s += x[i] * x[i];
+    s = warp_sum_c(s);
+    if (lane == 0) sig[k] = sqrt(s);
+  }
+  cl.sync();
+  if (rank == 0) {
+    for (int k = threadIdx.x; k < c; k += blockDim.x) {
+      int rk = 0;
+      const double sk = isnan(sig[k]) ? -1.0 : sig[k];
+      for (int j = 0; j < c; j++) {
+        const double sj = isnan(sig[j]) ? -1.0 : sig[j];
+        rk += (sj > sk) || (sj == sk && j < k);
+      }
+      perm[rk] = k;
+    }
+    bool nan_seen = false;
+    for (int k = threadIdx.x; k < c; k += blockDim.x) nan_seen |= !isfinite(sig[k]);
+    if (nan_seen && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int r;
+      const int lim = dval(a.rank_limit);
+      if (a.eps >= 0.0) {
+        tail[c] = 0.0;
+        for (int j = c - 1; j >= 0; j--) {
+          const double s = sig[perm[j]];
+          tail[j] = tail[j + 1] + s * s;
+        }
+        const double total = tail[0];
+        r = c;
+        if (total == 0.0) {
+          r = 1;
+        } else {
+          const double thr = a.eps * a.eps * total;
+          for (int cand = 1; cand <= c; cand++)
+            if (tail[cand] <= thr) { r = cand; break; }
+        }
+      } else {
+        r = c;
+      }
+      r = max(1, min(min(r, a.chi), min(lim, c)));
+      tail[c] = (double)r;  // publish r
+      if (a.r_out) *a.r_out = r;
+    }
+    if (a.sv_out)
+      for (int k = threadIdx.x; k < c; k += blockDim.x) a.sv_out[k] = sig[perm[k]];
+  }
+  cl.sync();
+  const int r = (int)(*(volatile double*)(tail + c));
+  // Bw = [J_perm ; 0] (wide: V = Q J) or [X_perm ; 0] (tall: U S = Q X), own columns
+  for (int k = rank; k < r; k += CL) {
+    const double* src = wide ? jcol(perm[k]) : xcol(perm[k]);
+    for (int i = threadIdx.x; i < Rt; i += blockDim.x)
+      Bw[(size_t)k * Rt + i] = (i < c) ? src[i] : 0.0;
+  }
+  __syncthreads();
+  apply_reflectors_cl(T, Rt, c, tau, Bw, r, false, rank, CL);
+  cl.sync();
+  zero_view_cl(a.US, rank, CL);
+  zero_view_cl(a.VT, rank, CL);
+  cl.sync();
+  const int url = dval(a.US.rows.lact), ucl = dval(a.US.cols.lact);
+  const int vrl = dval(a.VT.rows.lact), vcl = dval(a.VT.cols.lact);
+  for (int k = rank; k < r; k += CL) {
+    const double* xs = xcol(perm[k]);
+    const double* js = jcol(perm[k]);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const double v = wide ? xs[i] : Bw[(size_t)k * Rt + i];
+      a.US.ptr[a.usT ? voff(a.US, k, i, url, ucl) : voff(a.US, i, k, url, ucl)] = v;
+    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      const double v = wide ? Bw[(size_t)k * Rt + j] : js[j];
+      a.VT.ptr[a.vtT ? voff(a.VT, j, k, vrl, vcl) : voff(a.VT, k, j, vrl, vcl)] = v;
+    }
+  }
+  cl.sync();  // keep every CTA's shared memory alive until all remote reads are done
+}
+
+int g_cluster_size = -1;  // 16, 8 or 0 (no cluster launch)
+
+int pick_cluster_size() {
+  if (g_cluster_size >= 0) return g_cluster_size;
+  g_cluster_size = 0;
+  const int want[2] = {16, 8};
+  for (int w : want) {
+    if (w == 16) {
+      if (cudaFuncSetAttribute(k_svd_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+              cudaSuccess ||
+          cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+              cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+    }
+    cudaFuncSetAttribute(k_svd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(w);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = 200 * 1024;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = w;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_svd_cluster, &cfg) == cudaSuccess &&
+        nclusters > 0) {
+      g_cluster_size = w;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return g_cluster_size;
+}
+
+template <typename K, typename Args>
+void launch_cluster(K kern, int CL, size_t smem, cudaStream_t s, Args a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  QTT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, a));
+}
+
+template <typename K>
+void launch_cluster2(K kern, int CL, size_t smem, cudaStream_t s, SvdArgs a, int use_smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  QTT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, a, use_smem));
+}
+
+}  // namespace
+
+bool cluster_linalg_available() { return pick_cluster_size() > 0; }
+
+// Returns false when no cluster launch is possible (the caller falls back).
+bool launch_qr_cluster(const QrArgs& a, cudaStream_t s) {
+  const int CL = pick_cluster_size();
+  if (CL <= 0) return false;
+  pre_launch(s);
+  launch_cluster(k_qr_cluster, CL, 0, s, a);
+  return true;
+}
+
+bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
+  const int CL = pick_cluster_size();
+  if (CL <= 0) return false;
+  const int c = mcap < ncap ? mcap : ncap;  // capacity bound on the square factor
+  const int slots = (c + CL - 1) / CL;
+  const size_t need = (size_t)2 * slots * c * sizeof(double) + 64;
+  int use_smem = 0;
+  size_t smem = 0;
+  if (need <= 200 * 1024) {
+    use_smem = slots * c;
+    smem = need;
+  }
+  pre_launch(s);
+  launch_cluster2(k_svd_cluster, CL, smem, s, a, use_smem);
+  return true;
+}

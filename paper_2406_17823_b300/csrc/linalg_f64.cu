@@ -13,6 +13,7 @@
 // Matrices are gathered into a column-major work buffer first, so outputs
 // may alias the input storage.
 #include <math.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -416,13 +417,38 @@ size_t qr_work_doubles(int mcap, int ccap) {
   return (size_t)mcap * ccap + (size_t)mcap * r + 2 * (size_t)ccap + 8;
 }
 
+bool launch_qr_cluster(const QrArgs& a, cudaStream_t s);
+bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);
+
+// Problems at least this large (capacity of the square factor) go to the
+// cluster kernels; smaller ones stay on one CTA, where the cluster
+// barriers would cost more than they save.
+static int cluster_threshold() {
+  static int t = [] {
+    const char* e = getenv("QTT_CLUSTER_MIN");
+    return e ? atoi(e) : 24;
+  }();
+  return t;
+}
+
 void launch_qr_f64(const QrArgs& a, int mcap, int ccap, cudaStream_t s) {
   check_range(a.A.ptr, view_extent(a.A), sizeof(double), "qr A");
   check_range(a.Q.ptr, view_extent(a.Q), sizeof(double), "qr Q");
   check_range(a.R.ptr, view_extent(a.R), sizeof(double), "qr R");
   check_range(a.work, (long long)qr_work_doubles(mcap, ccap), sizeof(double), "qr work");
+  const double fm = mcap, fc = ccap < mcap ? ccap : mcap;
+  const double flops = 4.0 * fm * fc * fc - 4.0 / 3.0 * fc * fc * fc;
+  if ((ccap < mcap ? ccap : mcap) >= cluster_threshold() && launch_qr_cluster(a, s)) {
+    post_launch("k_qr_cluster", s, flops);
+    return;
+  }
+  pre_launch(s);
   k_qr_f64<<<1, 256, 0, s>>>(a);
-  post_launch("k_qr_f64", s);
+  {
+    // Householder factorisation plus explicit Q, at capacity shape
+    const double m = mcap, c = ccap < mcap ? ccap : mcap;
+    post_launch("k_qr_f64", s, 4.0 * m * c * c - 4.0 / 3.0 * c * c * c);
+  }
 }
 
 size_t svd_work_doubles(int mcap, int ncap) {
@@ -431,11 +457,26 @@ size_t svd_work_doubles(int mcap, int ncap) {
   return Rt * c * 2 + c * c * 2 + 4 * c + 8 + (c + 1) / 2 + 8;
 }
 
+// Algorithmic FLOPs of one SVD at capacity shape (m x N, c = min, Rt = max):
+// Householder of the tall factor 2 Rt c^2 - 2/3 c^3, ten Jacobi sweeps of
+// c (c - 1) / 2 pairs at 18 c FLOPs each (three dot products and the two
+// column rotations of X and of J), and the back-transform 4 Rt c^2.
+double svd_flops(int mcap, int ncap) {
+  const double Rt = mcap > ncap ? mcap : ncap, c = mcap < ncap ? mcap : ncap;
+  return 2.0 * Rt * c * c - 2.0 / 3.0 * c * c * c + 10.0 * c * (c - 1.0) / 2.0 * 18.0 * c +
+         4.0 * Rt * c * c;
+}
+
 void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
   check_range(a.M.ptr, view_extent(a.M), sizeof(double), "svd M");
   check_range(a.US.ptr, view_extent(a.US), sizeof(double), "svd US");
   check_range(a.VT.ptr, view_extent(a.VT), sizeof(double), "svd VT");
   check_range(a.work, (long long)svd_work_doubles(mcap, ncap), sizeof(double), "svd work");
+  if ((mcap < ncap ? mcap : ncap) >= cluster_threshold() && launch_svd_cluster(a, mcap, ncap, s)) {
+    post_launch("k_svd_cluster", s, svd_flops(mcap, ncap));
+    return;
+  }
+  pre_launch(s);
   k_svd_f64<<<1, 512, 0, s>>>(a);
-  post_launch("k_svd_f64", s);
+  post_launch("k_svd_f64", s, svd_flops(mcap, ncap));
 }

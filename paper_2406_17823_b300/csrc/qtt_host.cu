@@ -31,8 +31,46 @@ std::map<uintptr_t, size_t>& reg_map() {
 }
 }  // namespace
 
-void post_launch(const char* name, cudaStream_t s) {
+// ---- launch profiler (events around every launch while a context profiles)
+namespace {
+struct ProfRec {
+  const char* name;
+  cudaEvent_t e0, e1;
+  double flops;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t pending = nullptr;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) throw QttError(QTT_ERR_CUDA, "cudaEventCreate failed");
+    return e;
+  }
+};
+Profiler g_prof;
+}  // namespace
+
+void pre_launch(cudaStream_t s) {
+  if (!g_prof.on) return;
+  g_prof.pending = g_prof.get();
+  QTT_CUDA_CHECK(cudaEventRecord(g_prof.pending, s));
+}
+
+void post_launch(const char* name, cudaStream_t s, double flops) {
   count_launch();
+  if (g_prof.on && g_prof.pending) {
+    cudaEvent_t e1 = g_prof.get();
+    QTT_CUDA_CHECK(cudaEventRecord(e1, s));
+    g_prof.recs.push_back(ProfRec{name, g_prof.pending, e1, flops});
+    g_prof.pending = nullptr;
+  }
   static const bool dbg = getenv("QTT_DEBUG_SYNC") != nullptr;
   if (!dbg) return;
   cudaError_t e = cudaGetLastError();
@@ -1489,6 +1527,53 @@ qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
       ctx->err = "a projection reached its CG or sweep cap";
       return QTT_ERR_NOT_CONVERGED;
     }
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_profile_begin(qtt_ctx ctx) {
+  return guarded(ctx, [&]() -> qtt_status {
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : g_prof.recs) {
+      g_prof.pool.push_back(r.e0);
+      g_prof.pool.push_back(r.e1);
+    }
+    g_prof.recs.clear();
+    g_prof.on = true;
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_profile_end(qtt_ctx ctx, char* buf, size_t cap) {
+  if (!buf || cap == 0) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    g_prof.on = false;
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    struct Agg { long long n = 0; double ms = 0, flops = 0; };
+    std::map<std::string, Agg> agg;
+    for (auto& r : g_prof.recs) {
+      float ms = 0.f;
+      QTT_CUDA_CHECK(cudaEventElapsedTime(&ms, r.e0, r.e1));
+      Agg& a = agg[r.name];
+      a.n++;
+      a.ms += ms;
+      a.flops += r.flops;
+      g_prof.pool.push_back(r.e0);
+      g_prof.pool.push_back(r.e1);
+    }
+    g_prof.recs.clear();
+    std::string out = "{";
+    bool first = true;
+    for (auto& kv : agg) {
+      char line[256];
+      snprintf(line, sizeof line, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"flops\": %.6e}",
+               first ? "" : ", ", kv.first.c_str(), kv.second.n, kv.second.ms, kv.second.flops);
+      out += line;
+      first = false;
+    }
+    out += "}";
+    if (out.size() + 1 > cap) return QTT_ERR_ARG;
+    memcpy(buf, out.c_str(), out.size() + 1);
     return QTT_OK;
   });
 }

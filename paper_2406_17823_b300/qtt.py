@@ -26,7 +26,7 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_from_dense", "qtt_to_dense", "qtt_mps_from_packed", "qtt_mps_to_packed",
            "qtt_mps_info", "qtt_free_mps", "qtt_mpo_get", "qtt_free_mpo", "qtt_apply_mpo",
            "qtt_add", "qtt_hadamard", "qtt_compress", "qtt_project", "qtt_rk4_step",
-           "qtt_stats")
+           "qtt_stats", "qtt_profile_begin", "qtt_profile_end")
 
 
 class QttError(RuntimeError):
@@ -76,6 +76,8 @@ def lib():
             "qtt_rk4_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong),
                                   POINTER(c_longlong)]),
+            "qtt_profile_begin": (c_int, [vp]),
+            "qtt_profile_end": (c_int, [vp, ctypes.c_char_p, c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -262,6 +264,15 @@ class Context:
         u1.h, u2.h = h1, h2
         self._check(st, allow_not_converged=True)
         return st == 0
+
+    def profile_begin(self):
+        self._check(lib().qtt_profile_begin(self.h))
+
+    def profile_end(self) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(lib().qtt_profile_end(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def stats(self):
         a, b, c = c_longlong(), c_longlong(), c_longlong()
