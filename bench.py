@@ -192,6 +192,7 @@ def main():
     ap.add_argument("--impl", default="own")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     ap.add_argument("--n", type=int, default=None, help="override grid bits (testing only)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -260,7 +261,7 @@ def main():
     # pinned memory, one step, download the packed result
     cores = [ctx.to_cores(s) for s in state]
     e2e_times, h2d, d2h = [], 0, 0
-    for _ in range(max(1, min(args.steps, 2))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
         host = [c for c in cores]
         flush.zero_()
         torch.cuda.synchronize()
@@ -273,7 +274,7 @@ def main():
         h2d = sum(a.nbytes for c in host for a in c)
         d2h = sum(a.nbytes for c in out for a in c)
         cores = out
-    e2e_value = world * len(e2e_times) / sum(e2e_times)
+    e2e_value = world * len(e2e_times) / sum(e2e_times) if e2e_times else None
 
     if rank != 0:
         if dist is not None:
