@@ -138,21 +138,31 @@ def fp64_dgemm_peak(torch, dev):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_stage_seconds(u, dx, dt, w, budget_s=25.0):
+def oracle_stage_seconds(w):
     """Time the CPU oracle on a bounded sample: RK4 stage 1 (stage_w plus the
-    projection) of the workload on one BLAS thread; a full step is four such
-    stages, so steps/s = 1 / (4 * stage time)."""
-    from threadpoolctl import threadpool_limits
+    projection) of the workload, in a fresh interpreter whose BLAS is held to
+    one thread; a full step is four such stages, so steps/s = 1 / (4 t)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-stage",
+                        json.dumps(w)], env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed:\n" + r.stderr[-2000:])
+    return float(r.stdout.strip().splitlines()[-1])
+
+
+def _oracle_stage_child(wjson):
+    w = json.loads(wjson)
     from oracle import qtt as Q
+    u, dx, dt = workload_state(w["n"], w["seed"])
     p = Q.Params(eps=w["eps"], chi_max=w["chi_max"], mu=w["mu"], cg_tol=w["cg_tol"],
                  cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"])
-    with threadpool_limits(limits=1):
-        uq = [Q.from_dense(f, p.eps, p.chi_max) for f in u]
-        ops = Q.build_operators(w["n"], dx)
-        t = time.perf_counter()
-        wv = Q.stage_w(uq, uq, dt / 6.0, 1.0 / w["Re"], p, ops)
-        Q.project(wv, dt / 6.0, p, ops)
-        return time.perf_counter() - t
+    uq = [Q.from_dense(f, p.eps, p.chi_max) for f in u]
+    ops = Q.build_operators(w["n"], dx)
+    t = time.perf_counter()
+    wv = Q.stage_w(uq, uq, dt / 6.0, 1.0 / w["Re"], p, ops)
+    Q.project(wv, dt / 6.0, p, ops)
+    print(time.perf_counter() - t)
 
 
 # ------------------------------------------------------------------ reference arm
@@ -161,12 +171,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = dict(WORKLOAD)
-    u, dx, dt = workload_state(w["n"], w["seed"])
-    for _ in range(args.warmup):
-        pass  # the CPU oracle has no warm-up effects worth timing
     total = 0.0
-    for _ in range(args.steps):
-        total += oracle_stage_seconds(u, dx, dt, w)
+    for _ in range(args.steps):  # no warm-up: the CPU oracle has no warm-up effects
+        total += oracle_stage_seconds(w)
     steps_done = 0.25 * args.steps
     value = steps_done / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
@@ -298,7 +305,7 @@ def main():
                 "flops_per_launch": flops_per_launch}
     cpu = None
     if not args.no_cpu_baseline:
-        st = oracle_stage_seconds(u, dx, dt, w)
+        st = oracle_stage_seconds(w)
         cpu = {"value": 1.0 / (4.0 * st), "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": "RK4 stage 1 of the same workload (stage_w + projection), x4 for a "
                          "full step, numpy FP64 oracle on one BLAS thread"}
@@ -324,4 +331,7 @@ def main():
 
 
 if __name__ == "__main__":
+    if len(sys.argv) == 3 and sys.argv[1] == "--oracle-stage":
+        _oracle_stage_child(sys.argv[2])
+        sys.exit(0)
     sys.exit(main())
