@@ -154,6 +154,26 @@ qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps,
 qtt_status qtt_profile_begin(qtt_ctx ctx);
 qtt_status qtt_profile_end(qtt_ctx ctx, char* buf, size_t cap);
 
+/* Dense readout that allocates nothing (the paper has no counterpart): for
+ * callers that cannot allocate device memory when they need the field, such
+ * as code running during CUDA graph capture, real-time loops that must not
+ * enter an allocator, or hosts whose device memory is owned by another
+ * framework's pool.  Same result as qtt_to_dense, but the MPS comes as
+ * packed cores in a caller-owned device buffer (d_cores, bonds[0..n] on the
+ * host) and the field is written to the caller's d_field_out (N*N doubles,
+ * N = 2^n), enqueued on cuda_stream (a cudaStream_t, NULL = legacy default).
+ * Intermediates live in a static 4 MiB device array: n <= 9 and every
+ * partial contraction 4^k * bonds[k] (k < n) at most 2^18 doubles, else
+ * QTT_ERR_SHAPE; QTT_ERR_ARG for null pointers or n outside 1..9.  The
+ * first call on a device looks up the array's address with that device
+ * current, so make it before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU race and must be ordered by
+ * the caller.  Uses no cudaMalloc / cudaFree.  Asynchronous: launch errors
+ * are returned (QTT_ERR_CUDA), execution errors surface at the caller's
+ * next synchronisation. */
+qtt_status qtt_to_dense_noalloc(const double* d_cores, const int* bonds, int n,
+                                double* d_field_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_from_dense", "qtt_to_dense", "qtt_mps_from_packed", "qtt_mps_to_packed",
            "qtt_mps_info", "qtt_free_mps", "qtt_mpo_get", "qtt_free_mpo", "qtt_apply_mpo",
            "qtt_add", "qtt_hadamard", "qtt_compress", "qtt_project", "qtt_rk4_step",
-           "qtt_stats", "qtt_profile_begin", "qtt_profile_end")
+           "qtt_stats", "qtt_profile_begin", "qtt_profile_end", "qtt_to_dense_noalloc")
 
 
 class QttError(RuntimeError):
@@ -78,6 +78,7 @@ def lib():
                                   POINTER(c_longlong)]),
             "qtt_profile_begin": (c_int, [vp]),
             "qtt_profile_end": (c_int, [vp, ctypes.c_char_p, c_size_t]),
+            "qtt_to_dense_noalloc": (c_int, [vp, ip, c_int, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
