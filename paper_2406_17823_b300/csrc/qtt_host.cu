@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <memory>
 #include <vector>
 
@@ -154,6 +155,13 @@ struct qtt_ctx_s {
   LaunchCounter launches;
   long long cg_iters = 0, sweeps = 0;
   int last_not_converged = 0;
+  // worker streams for independent operations of a stage (non-blocking, so
+  // the legacy default stream does not serialise them), joined by events
+  static constexpr int kWorkers = 9;
+  cudaStream_t workers[kWorkers] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kWorkers] = {};
+  cudaStream_t cur = nullptr;  // stream the current operation enqueues on
 };
 
 namespace {
@@ -200,6 +208,10 @@ struct DBuf {
   ~DBuf() { release(); }
 };
 
+// The stream operations enqueue on: a worker stream while a stage runs its
+// independent operations concurrently, else the context stream.
+cudaStream_t stream_of(qtt_ctx ctx) { return ctx->cur ? ctx->cur : ctx->stream; }
+
 long long natural_cap(int n, int b) {
   long long a = 1, c = 1;
   for (int i = 0; i < b && a < (1LL << 40); i++) a *= 4;
@@ -220,15 +232,15 @@ qtt_mps new_mps(qtt_ctx ctx, int n, const std::vector<int>& cap) {
     o += (size_t)cap[k] * 4 * cap[k + 1];
   }
   m->off[n] = o;
-  m->stream = ctx->stream;
-  if (cudaMallocAsync((void**)&m->data, o * sizeof(double), ctx->stream) != cudaSuccess ||
-      cudaMallocAsync((void**)&m->dims, (n + 1) * sizeof(int), ctx->stream) != cudaSuccess) {
+  m->stream = stream_of(ctx);
+  if (cudaMallocAsync((void**)&m->data, o * sizeof(double), m->stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&m->dims, (n + 1) * sizeof(int), m->stream) != cudaSuccess) {
     delete m;
     throw QttError(QTT_ERR_ALLOC, "MPS allocation failed");
   }
   reg_alloc(m->data, o * sizeof(double));
   reg_alloc(m->dims, (n + 1) * sizeof(int));
-  QTT_CUDA_CHECK(cudaMemsetAsync(m->data, 0, o * sizeof(double), ctx->stream));
+  QTT_CUDA_CHECK(cudaMemsetAsync(m->data, 0, o * sizeof(double), m->stream));
   return m;
 }
 
@@ -477,7 +489,7 @@ HostMpo mpo_scaled(HostMpo m, double s) {
 // compress X -> new MPS with caps ocap; X unchanged.
 qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   const int n = X->n;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = stream_of(ctx);
   const auto& cin = X->cap;
   std::vector<int> qcap(n + 1, 1), ocap(n + 1, 1);
   for (int b = 1; b < n; b++) qcap[b] = std::min(4 * qcap[b - 1], cin[b]);
@@ -576,7 +588,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
 // ------------------------------------------------------------ apply / add
 qtt_mps expand_mpo(qtt_ctx ctx, qtt_mpo W, qtt_mps A) {
   const int n = A->n;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = stream_of(ctx);
   std::vector<int> cap(n + 1);
   for (int b = 0; b <= n; b++) cap[b] = A->cap[b] * W->w[b];
   MpsPtr X(new_mps(ctx, n, cap));
@@ -592,7 +604,7 @@ qtt_mps expand_mpo(qtt_ctx ctx, qtt_mpo W, qtt_mps A) {
 
 qtt_mps add_exact(qtt_ctx ctx, int K, const double* coef, const qtt_mps* terms) {
   const int n = terms[0]->n;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = stream_of(ctx);
   std::vector<int> cap(n + 1, 0);
   for (int b = 0; b <= n; b++)
     for (int t = 0; t < K; t++) cap[b] += terms[t]->cap[b];
@@ -636,7 +648,7 @@ qtt_mps add2(qtt_ctx ctx, double c1, qtt_mps a, double c2, qtt_mps b) {
 // ------------------------------------------------------------ Hadamard
 qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
   const int n = A->n;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = stream_of(ctx);
   const auto& ca = A->cap;
   const auto& cb = B->cap;
   std::vector<int> rcap(n + 1, 1);
@@ -1023,9 +1035,9 @@ struct Projector {
 
 qtt_mps copy_mps(qtt_ctx ctx, qtt_mps A) {
   MpsPtr X(new_mps(ctx, A->n, A->cap));
-  launch_copy(X->data, A->data, A->off[A->n], ctx->stream);
+  launch_copy(X->data, A->data, A->off[A->n], stream_of(ctx));
   QTT_CUDA_CHECK(cudaMemcpyAsync(X->dims, A->dims, (A->n + 1) * sizeof(int),
-                                 cudaMemcpyDeviceToDevice, ctx->stream));
+                                 cudaMemcpyDeviceToDevice, stream_of(ctx)));
   return X.release();
 }
 
@@ -1083,30 +1095,97 @@ void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qt
 }
 
 // ===================================================================== RK4
+// Concurrency of independent operations: fork() makes every worker stream
+// wait for the context stream, run(k, f) enqueues operation f on worker k,
+// join() makes the context stream wait for every worker and hands the
+// outputs (allocated on workers) to the context stream for release.
+struct Workers {
+  qtt_ctx ctx;
+  bool serial;
+  explicit Workers(qtt_ctx c) : ctx(c) {
+    static const bool ser = getenv("QTT_SERIAL") != nullptr;
+    serial = ser || !c->workers[0];
+  }
+  void fork() {
+    if (serial) return;
+    QTT_CUDA_CHECK(cudaEventRecord(ctx->fork_ev, ctx->stream));
+    for (int k = 0; k < qtt_ctx_s::kWorkers; k++)
+      QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[k], ctx->fork_ev, 0));
+  }
+  template <typename F>
+  qtt_mps run(int k, F&& f) {
+    if (serial) return f();
+    ctx->cur = ctx->workers[k % qtt_ctx_s::kWorkers];
+    qtt_mps out = nullptr;
+    try {
+      out = f();
+    } catch (...) {
+      ctx->cur = nullptr;
+      throw;
+    }
+    ctx->cur = nullptr;
+    return out;
+  }
+  void join(std::initializer_list<qtt_mps> outs) {
+    if (serial) return;
+    for (int k = 0; k < qtt_ctx_s::kWorkers; k++) {
+      QTT_CUDA_CHECK(cudaEventRecord(ctx->join_ev[k], ctx->workers[k]));
+      QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[k], 0));
+    }
+    for (qtt_mps m : outs)
+      if (m) m->stream = ctx->stream;
+  }
+};
+
 void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2]) {
   const double eps = ctx->p.eps;
   const int chi = ctx->p.chi_max;
+  Workers wk(ctx);
   MpsPtr Db[2][2], P[2][2], Q[2][2], DQ[2][2], Lb[2];
+  // wave 1: D_j b_i, b_j (.) b_i, Lap b_i are independent
+  wk.fork();
+  int k = 0;
   for (int i = 0; i < 2; i++)
-    for (int j = 0; j < 2; j++) Db[j][i] = MpsPtr(apply_impl(ctx, ctx->D[j], b[i], eps, chi));
+    for (int j = 0; j < 2; j++)
+      Db[j][i] = MpsPtr(wk.run(k++, [&] { return apply_impl(ctx, ctx->D[j], b[i], eps, chi); }));
+  Q[0][0] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[0], b[0], eps, chi); }));
+  Q[0][1] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[0], b[1], eps, chi); }));
+  Q[1][1] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[1], b[1], eps, chi); }));
   for (int i = 0; i < 2; i++)
-    for (int j = 0; j < 2; j++) P[j][i] = MpsPtr(hadamard_impl(ctx, b[j], Db[j][i].get(), eps, chi));
-  for (int i = 0; i < 2; i++)
-    for (int j = 0; j < 2; j++) Db[j][i] = MpsPtr();
-  Q[0][0] = MpsPtr(hadamard_impl(ctx, b[0], b[0], eps, chi));
-  Q[0][1] = MpsPtr(hadamard_impl(ctx, b[0], b[1], eps, chi));
-  Q[1][1] = MpsPtr(hadamard_impl(ctx, b[1], b[1], eps, chi));
+    Lb[i] = MpsPtr(wk.run(k++, [&] { return apply_impl(ctx, ctx->lap, b[i], eps, chi); }));
+  wk.join({Db[0][0].get(), Db[0][1].get(), Db[1][0].get(), Db[1][1].get(), Q[0][0].get(),
+           Q[0][1].get(), Q[1][1].get(), Lb[0].get(), Lb[1].get()});
   auto q = [&](int j, int i) { return (j == 1 && i == 0) ? Q[0][1].get() : Q[j][i].get(); };
+  // wave 2: b_j (.) D_j b_i and D_j (b_j (.) b_i)
+  wk.fork();
+  k = 0;
   for (int i = 0; i < 2; i++)
-    for (int j = 0; j < 2; j++) DQ[j][i] = MpsPtr(apply_impl(ctx, ctx->D[j], q(j, i), eps, chi));
-  for (int i = 0; i < 2; i++) Lb[i] = MpsPtr(apply_impl(ctx, ctx->lap, b[i], eps, chi));
+    for (int j = 0; j < 2; j++) {
+      P[j][i] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[j], Db[j][i].get(), eps, chi); }));
+      DQ[j][i] = MpsPtr(wk.run(k++, [&] { return apply_impl(ctx, ctx->D[j], q(j, i), eps, chi); }));
+    }
+  wk.join({P[0][0].get(), P[0][1].get(), P[1][0].get(), P[1][1].get(), DQ[0][0].get(),
+           DQ[0][1].get(), DQ[1][0].get(), DQ[1][1].get()});
+  // wave 3: the sums, per component
+  MpsPtr ca[2], cb[2], conv[2], B[2];
+  wk.fork();
   for (int i = 0; i < 2; i++) {
-    MpsPtr ca(add2(ctx, 1.0, P[0][i].get(), 1.0, P[1][i].get()));
-    MpsPtr cb(add2(ctx, 1.0, DQ[0][i].get(), 1.0, DQ[1][i].get()));
-    MpsPtr conv(add2(ctx, 0.5, ca.get(), 0.5, cb.get()));
-    MpsPtr B(add2(ctx, 1.0, conv.get(), -nu, Lb[i].get()));
-    w[i] = MpsPtr(add2(ctx, 0.25, u[i], -h, B.get()));
+    ca[i] = MpsPtr(wk.run(2 * i, [&] { return add2(ctx, 1.0, P[0][i].get(), 1.0, P[1][i].get()); }));
+    cb[i] = MpsPtr(wk.run(2 * i + 1, [&] { return add2(ctx, 1.0, DQ[0][i].get(), 1.0, DQ[1][i].get()); }));
   }
+  wk.join({ca[0].get(), ca[1].get(), cb[0].get(), cb[1].get()});
+  wk.fork();
+  for (int i = 0; i < 2; i++)
+    conv[i] = MpsPtr(wk.run(i, [&] { return add2(ctx, 0.5, ca[i].get(), 0.5, cb[i].get()); }));
+  wk.join({conv[0].get(), conv[1].get()});
+  wk.fork();
+  for (int i = 0; i < 2; i++)
+    B[i] = MpsPtr(wk.run(i, [&] { return add2(ctx, 1.0, conv[i].get(), -nu, Lb[i].get()); }));
+  wk.join({B[0].get(), B[1].get()});
+  wk.fork();
+  for (int i = 0; i < 2; i++)
+    w[i] = MpsPtr(wk.run(i, [&] { return add2(ctx, 0.25, u[i], -h, B[i].get()); }));
+  wk.join({w[0].get(), w[1].get()});
 }
 
 void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
@@ -1120,10 +1199,13 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
     MpsPtr bown[2];
     qtt_mps b[2] = {u[0], u[1]};
     if (st > 0) {
+      Workers wk(ctx);
+      wk.fork();
       for (int i = 0; i < 2; i++) {
-        bown[i] = MpsPtr(add2(ctx, BC[st][0], U[st - 1][i].get(), BC[st][1], u[i]));
+        bown[i] = MpsPtr(wk.run(i, [&] { return add2(ctx, BC[st][0], U[st - 1][i].get(), BC[st][1], u[i]); }));
         b[i] = bown[i].get();
       }
+      wk.join({b[0], b[1]});
     }
     const double h = HS[st] * dt;
     MpsPtr w[2];
@@ -1138,10 +1220,16 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
     U[st][1] = MpsPtr(v2);
   }
   MpsPtr out[2];
-  for (int i = 0; i < 2; i++) {
-    MpsPtr acc(add2(ctx, 1.0, U[0][i].get(), 1.0, U[1][i].get()));
-    acc = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[2][i].get()));
-    out[i] = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[3][i].get()));
+  {
+    Workers wk(ctx);
+    wk.fork();
+    for (int i = 0; i < 2; i++)
+      out[i] = MpsPtr(wk.run(i, [&] {
+        MpsPtr acc(add2(ctx, 1.0, U[0][i].get(), 1.0, U[1][i].get()));
+        acc = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[2][i].get()));
+        return add2(ctx, 1.0, acc.get(), 1.0, U[3][i].get());
+      }));
+    wk.join({out[0].get(), out[1].get()});
   }
   free_mps(*u1);
   free_mps(*u2);
@@ -1155,7 +1243,7 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
 // ---------------------------------------------------------------- dense I/O
 qtt_mps from_dense_impl(qtt_ctx ctx, const double* F, double eps, int chi) {
   const int n = ctx->p.n;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = stream_of(ctx);
   std::vector<int> ocap(n + 1, 1);
   for (int b = 1; b < n; b++) ocap[b] = std::min(chi, clampi(natural_cap(n, b)));
   MpsPtr Y(new_mps(ctx, n, ocap));
@@ -1204,7 +1292,7 @@ qtt_mps from_dense_impl(qtt_ctx ctx, const double* F, double eps, int chi) {
 
 void to_dense_impl(qtt_ctx ctx, qtt_mps A, double* F) {
   const int n = A->n;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = stream_of(ctx);
   const size_t tot = (size_t)1 << (2 * n);
   size_t mx = 4 * (size_t)A->cap[1];
   for (int k = 1; k < n; k++) mx = std::max(mx, ((size_t)1 << (2 * (k + 1))) * A->cap[k + 1]);
@@ -1294,6 +1382,11 @@ qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* 
     uint64_t thr = UINT64_MAX;
     QTT_CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
     QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_err, sizeof(int)));
+    for (int k = 0; k < qtt_ctx_s::kWorkers; k++) {
+      QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->workers[k], cudaStreamNonBlocking));
+      QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming));
+    }
+    QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
     QTT_CUDA_CHECK(cudaMemset(ctx->d_err, 0, sizeof(int)));
     const int n = params->n;
     const double dx = ctx->dx;
@@ -1334,6 +1427,11 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) mpo_release(ctx->K[i][j]);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  for (int k = 0; k < qtt_ctx_s::kWorkers; k++) {
+    if (ctx->workers[k]) cudaStreamDestroy(ctx->workers[k]);
+    if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   delete ctx;
   return QTT_OK;
 }
