@@ -72,6 +72,7 @@ struct SvdArgs {
 };
 size_t svd_work_doubles(int mcap, int ncap);
 void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);
+bool launch_svd_subspace_f32(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);
 
 // ---------------------------------------------------------------- misc
 void launch_zero(double* p, size_t n, cudaStream_t s);

@@ -24,22 +24,36 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-__device__ __forceinline__ double warp_sum_c(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum_c(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__device__ double cta_sum_c(double v, double* sh) {
+template <typename T>
+__device__ T cta_sum_c(T v, double* sh) {
   v = warp_sum_c(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
-  if (l == 0) sh[w] = v;
+  if (l == 0) sh[w] = (double)v;
   __syncthreads();
   double t = 0.0;
   for (int i = 0; i < nw; i++) t += sh[i];
-  return t;
+  return (T)t;
 }
+
+// numerical constants per working precision: columns below `tiny` in
+// squared norm are not reflected; Jacobi stops rotating below `cos_tol`
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static __device__ double tiny() { return 1e-280; }
+  static __device__ double cos_tol(int c) { return fmax(1e-15, 1e-16 * (double)c); }
+};
+template <> struct Prec<float> {
+  static __device__ float tiny() { return 1e-30f; }
+  static __device__ float cos_tol(int) { return 1e-5f; }
+};
 
 __device__ __forceinline__ bool axis_ok_c(const Axis& a) {
   const int h = dval(a.hact), l = dval(a.lact);
@@ -61,24 +75,25 @@ __device__ void zero_view_cl(const MatView& v, int rank, int CL) {
 
 // Householder QR of W (m x c, column-major, ld = m) with the columns dealt
 // cyclically over the cluster.  tau / diag live in global memory.
-__device__ void householder_cl(cg::cluster_group& cl, double* W, int m, int c, double* tau,
-                               double* diag, double* sh, int rank, int CL) {
+template <typename T>
+__device__ void householder_cl(cg::cluster_group& cl, T* W, int m, int c, T* tau, T* diag,
+                               double* sh, int rank, int CL) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int kmax = min(m, c);
   for (int j = 0; j < kmax; j++) {
-    double* col = W + (size_t)j * m;
+    T* col = W + (size_t)j * m;
     __syncthreads();  // this CTA's updates of column j (if it owns it) are complete
     if (j % CL == rank) {
-      double part = 0.0;
+      T part = 0;
       for (int i = j + threadIdx.x; i < m; i += blockDim.x) part += col[i] * col[i];
-      const double nrm2 = cta_sum_c(part, sh);
-      const double x0 = col[j];
+      const T nrm2 = cta_sum_c(part, sh);
+      const T x0 = col[j];
       __syncthreads();
-      double t = 0.0, alpha = x0;
-      if (nrm2 > 1e-280 && isfinite(nrm2)) {
-        const double nrm = sqrt(nrm2);
-        alpha = (x0 >= 0.0) ? -nrm : nrm;
-        t = 1.0 / (nrm * (nrm + fabs(x0)));
+      T t = 0, alpha = x0;
+      if (nrm2 > Prec<T>::tiny() && isfinite((double)nrm2)) {
+        const T nrm = sqrt(nrm2);
+        alpha = (x0 >= 0) ? -nrm : nrm;
+        t = (T)1 / (nrm * (nrm + fabs(x0)));
         if (threadIdx.x == 0) col[j] = x0 - alpha;
       }
       if (threadIdx.x == 0) {
@@ -87,14 +102,14 @@ __device__ void householder_cl(cg::cluster_group& cl, double* W, int m, int c, d
       }
     }
     cl.sync();  // reflector j published
-    const double t = *(volatile double*)(tau + j);
-    if (t != 0.0) {
+    const T t = *(volatile T*)(tau + j);
+    if (t != (T)0) {
       // my columns cc > j with cc % CL == rank
       int c0 = j + 1;
       c0 += ((rank - c0) % CL + CL) % CL;
       for (int cc = c0 + warp * CL; cc < c; cc += nw * CL) {
-        double* x = W + (size_t)cc * m;
-        double s = 0.0;
+        T* x = W + (size_t)cc * m;
+        T s = 0;
         for (int i = j + lane; i < m; i += 32) s += col[i] * x[i];
         s = warp_sum_c(s) * t;
         for (int i = j + lane; i < m; i += 32) x[i] -= s * col[i];
@@ -106,17 +121,18 @@ __device__ void householder_cl(cg::cluster_group& cl, double* W, int m, int c, d
 
 // B (m x nb, column-major, ld = m): columns cc % CL == rank get
 // B[:, cc] <- H_0 ... H_{k-1} B[:, cc]  (columns are independent).
-__device__ void apply_reflectors_cl(const double* W, int m, int k, const double* tau, double* B,
-                                    int nb, bool identity_cols, int rank, int CL) {
+template <typename T>
+__device__ void apply_reflectors_cl(const T* W, int m, int k, const T* tau, T* B, int nb,
+                                    bool identity_cols, int rank, int CL) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int cc = rank + warp * CL; cc < nb; cc += nw * CL) {
-    double* x = B + (size_t)cc * m;
+    T* x = B + (size_t)cc * m;
     const int jtop = identity_cols ? min(cc, k - 1) : k - 1;
     for (int j = jtop; j >= 0; j--) {
-      const double t = tau[j];
-      if (t == 0.0) continue;
-      const double* v = W + (size_t)j * m;
-      double s = 0.0;
+      const T t = tau[j];
+      if (t == (T)0) continue;
+      const T* v = W + (size_t)j * m;
+      T s = 0;
       for (int i = j + lane; i < m; i += 32) s += v[i] * x[i];
       s = warp_sum_c(s) * t;
       for (int i = j + lane; i < m; i += 32) x[i] -= s * v[i];
@@ -163,11 +179,11 @@ __global__ void __launch_bounds__(512) k_qr_cluster(QrArgs a) {
     }
   if (badv && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
   cl.sync();
-  householder_cl(cl, W, m, c, tau, diag, sh, rank, CL);
+  householder_cl<double>(cl, W, m, c, tau, diag, sh, rank, CL);
   for (int j = rank; j < r; j += CL)
     for (int i = threadIdx.x; i < m; i += blockDim.x) Qw[(size_t)j * m + i] = (i == j) ? 1.0 : 0.0;
   __syncthreads();
-  apply_reflectors_cl(W, m, r, tau, Qw, r, true, rank, CL);
+  apply_reflectors_cl<double>(W, m, r, tau, Qw, r, true, rank, CL);
   cl.sync();  // all reads of A done before outputs (they may alias A)
   zero_view_cl(a.Q, rank, CL);
   zero_view_cl(a.R, rank, CL);
@@ -194,11 +210,15 @@ __device__ __forceinline__ int rr_pos_c(int k, int t, int cp) {
   return k == 0 ? 0 : 1 + (k - 1 + t) % (cp - 1);
 }
 
-// dynamic shared memory: X and J home columns (slots x c each), then flags
-__global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
+// dynamic shared memory: X and J home columns (slots x c each).  T is the
+// working precision: double for the FP64 path; float for the mixed path,
+// whose callers re-orthonormalise the returned factor in FP64.
+template <typename T>
+__global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
-  extern __shared__ double dsm[];
+  extern __shared__ double dsm_raw[];
+  T* dsm = (T*)dsm_raw;
   __shared__ double sh[32];
   __shared__ int flag_local;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -228,23 +248,24 @@ __global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
       return;
     }
   }
-  double* T = a.work;                   // Rt x c
-  double* Xg = T + (size_t)Rt * c;      // c x c   (used when not in shared memory)
-  double* Jg = Xg + (size_t)c * c;      // c x c
-  double* Bw = Jg + (size_t)c * c;      // Rt x c
-  double* tau = Bw + (size_t)Rt * c;
-  double* diag = tau + c;
-  double* sig = diag + c;
+  // work layout (in units of T, then doubles for the FP64 bookkeeping)
+  T* Tm = (T*)a.work;                   // Rt x c
+  T* Xg = Tm + (size_t)Rt * c;          // c x c   (used when not in shared memory)
+  T* Jg = Xg + (size_t)c * c;           // c x c
+  T* Bw = Jg + (size_t)c * c;           // Rt x c
+  T* tau = Bw + (size_t)Rt * c;
+  T* diag = tau + c;
+  double* sig = a.work + ((size_t)(2 * Rt * c + 2 * c * c + 2 * c) * sizeof(T) + 7) / 8;
   double* tail = sig + c;
   int* perm = (int*)(tail + c + 1);
   // home of column i: CTA i % CL, slot i / CL
-  double* Xs = dsm;
-  double* Js = dsm + (size_t)slots * c;
-  auto xcol = [&](int i) -> double* {
+  T* Xs = dsm;
+  T* Js = dsm + (size_t)slots * c;
+  auto xcol = [&](int i) -> T* {
     if (!use_smem) return Xg + (size_t)i * c;
     return cl.map_shared_rank(Xs, i % CL) + (size_t)(i / CL) * c;
   };
-  auto jcol = [&](int i) -> double* {
+  auto jcol = [&](int i) -> T* {
     if (!use_smem) return Jg + (size_t)i * c;
     return cl.map_shared_rank(Js, i % CL) + (size_t)(i / CL) * c;
   };
@@ -255,26 +276,26 @@ __global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
       const long long off = a.inT ? voff(a.M, fj, fi, mrl, mcl) : voff(a.M, fi, fj, mrl, mcl);
       const double v = a.M.ptr[off];
       badv |= !isfinite(v);
-      T[(size_t)j * Rt + i] = v;
+      Tm[(size_t)j * Rt + i] = (T)v;
     }
   if (badv && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
   cl.sync();
-  householder_cl(cl, T, Rt, c, tau, diag, sh, rank, CL);
+  householder_cl<T>(cl, Tm, Rt, c, tau, diag, sh, rank, CL);
   // X = R^T (wide) or R (tall) into the home columns; J = I
   for (int i = rank; i < c; i += CL) {
-    double* x = xcol(i);
-    double* jj = jcol(i);
+    T* x = xcol(i);
+    T* jj = jcol(i);
     for (int e = threadIdx.x; e < c; e += blockDim.x) {
       const int p = wide ? i : e, q = wide ? e : i;  // X(e, i) = R(p, q)
-      double rv = 0.0;
+      T rv = 0;
       if (p == q) rv = diag[p];
-      else if (p < q) rv = T[(size_t)q * Rt + p];
+      else if (p < q) rv = Tm[(size_t)q * Rt + p];
       x[e] = rv;
-      jj[e] = (e == i) ? 1.0 : 0.0;
+      jj[e] = (e == i) ? (T)1 : (T)0;
     }
   }
   cl.sync();
-  const double tol = fmax(1e-15, 1e-16 * (double)c);
+  const T tol = Prec<T>::cos_tol(c);
   const int cp = c + (c & 1);
   for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
     if (threadIdx.x == 0) flag_local = 0;
@@ -284,11 +305,11 @@ __global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
         int p = rr_pos_c(k, t, cp), q = rr_pos_c(cp - 1 - k, t, cp);
         if (p >= c || q >= c) continue;
         if (p > q) { const int s_ = p; p = q; q = s_; }
-        double* x = xcol(p);
-        double* y = xcol(q);
-        double al = 0.0, be = 0.0, ga = 0.0;
+        T* x = xcol(p);
+        T* y = xcol(q);
+        T al = 0, be = 0, ga = 0;
         for (int i = lane; i < c; i += 32) {
-          const double xi = x[i], yi = y[i];
+          const T xi = x[i], yi = y[i];
           al += xi * xi;
           be += yi * yi;
           ga += xi * yi;
@@ -296,19 +317,21 @@ __global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
         al = warp_sum_c(al);
         be = warp_sum_c(be);
         ga = warp_sum_c(ga);
-        if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          const double zeta = (be - al) / (2.0 * ga);
+        if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          // rotation angle from FP64 scalars (a handful of operations per pair)
+          const double zeta = ((double)be - (double)al) / (2.0 * (double)ga);
           const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+          const double csd = 1.0 / sqrt(1.0 + tt * tt);
+          const T cs = (T)csd, sn = (T)(csd * tt);
           for (int i = lane; i < c; i += 32) {
-            const double xi = x[i], yi = y[i];
+            const T xi = x[i], yi = y[i];
             x[i] = cs * xi - sn * yi;
             y[i] = sn * xi + cs * yi;
           }
-          double* jx = jcol(p);
-          double* jy = jcol(q);
+          T* jx = jcol(p);
+          T* jy = jcol(q);
           for (int i = lane; i < c; i += 32) {
-            const double xi = jx[i], yi = jy[i];
+            const T xi = jx[i], yi = jy[i];
             jx[i] = cs * xi - sn * yi;
             jy[i] = sn * xi + cs * yi;
           }
@@ -326,9 +349,9 @@ __global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
   }
   // singular values (home columns), order, rank (computed by every CTA alike)
   for (int k = rank + warp * CL; k < c; k += nw * CL) {
-    const double* x = xcol(k);
-    double s = 0.0;
-    for (int i = lane; i < c; i += 32) s += x[i] * x[i];
+    const T* x = xcol(k);
+    double s = 0.0;  // FP64 sum of squares: the truncation weights
+    for (int i = lane; i < c; i += 32) s += (double)x[i] * (double)x[i];
     s = warp_sum_c(s);
     if (lane == 0) sig[k] = sqrt(s);
   }
@@ -379,12 +402,12 @@ __global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
   const int r = (int)(*(volatile double*)(tail + c));
   // Bw = [J_perm ; 0] (wide: V = Q J) or [X_perm ; 0] (tall: U S = Q X), own columns
   for (int k = rank; k < r; k += CL) {
-    const double* src = wide ? jcol(perm[k]) : xcol(perm[k]);
+    const T* src = wide ? jcol(perm[k]) : xcol(perm[k]);
     for (int i = threadIdx.x; i < Rt; i += blockDim.x)
-      Bw[(size_t)k * Rt + i] = (i < c) ? src[i] : 0.0;
+      Bw[(size_t)k * Rt + i] = (i < c) ? src[i] : (T)0;
   }
   __syncthreads();
-  apply_reflectors_cl(T, Rt, c, tau, Bw, r, false, rank, CL);
+  apply_reflectors_cl<T>(Tm, Rt, c, tau, Bw, r, false, rank, CL);
   cl.sync();
   zero_view_cl(a.US, rank, CL);
   zero_view_cl(a.VT, rank, CL);
@@ -392,14 +415,14 @@ __global__ void __launch_bounds__(512) k_svd_cluster(SvdArgs a, int use_smem) {
   const int url = dval(a.US.rows.lact), ucl = dval(a.US.cols.lact);
   const int vrl = dval(a.VT.rows.lact), vcl = dval(a.VT.cols.lact);
   for (int k = rank; k < r; k += CL) {
-    const double* xs = xcol(perm[k]);
-    const double* js = jcol(perm[k]);
+    const T* xs = xcol(perm[k]);
+    const T* js = jcol(perm[k]);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const double v = wide ? xs[i] : Bw[(size_t)k * Rt + i];
+      const double v = wide ? (double)xs[i] : (double)Bw[(size_t)k * Rt + i];
       a.US.ptr[a.usT ? voff(a.US, k, i, url, ucl) : voff(a.US, i, k, url, ucl)] = v;
     }
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      const double v = wide ? Bw[(size_t)k * Rt + j] : js[j];
+      const double v = wide ? (double)Bw[(size_t)k * Rt + j] : (double)js[j];
       a.VT.ptr[a.vtT ? voff(a.VT, j, k, vrl, vcl) : voff(a.VT, k, j, vrl, vcl)] = v;
     }
   }
@@ -414,7 +437,9 @@ int pick_cluster_size() {
   const int want[2] = {16, 8};
   for (int w : want) {
     if (w == 16) {
-      if (cudaFuncSetAttribute(k_svd_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+      if (cudaFuncSetAttribute(k_svd_cluster_t<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+              cudaSuccess ||
+          cudaFuncSetAttribute(k_svd_cluster_t<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
               cudaSuccess ||
           cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
               cudaSuccess) {
@@ -422,7 +447,8 @@ int pick_cluster_size() {
         continue;
       }
     }
-    cudaFuncSetAttribute(k_svd_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_svd_cluster_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_svd_cluster_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(w);
     cfg.blockDim = dim3(512);
@@ -435,7 +461,7 @@ int pick_cluster_size() {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_svd_cluster, &cfg) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_svd_cluster_t<double>, &cfg) == cudaSuccess &&
         nclusters > 0) {
       g_cluster_size = w;
       break;
@@ -492,12 +518,12 @@ bool launch_qr_cluster(const QrArgs& a, cudaStream_t s) {
   return true;
 }
 
-bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
+bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s, bool fp32) {
   const int CL = pick_cluster_size();
   if (CL <= 0) return false;
   const int c = mcap < ncap ? mcap : ncap;  // capacity bound on the square factor
   const int slots = (c + CL - 1) / CL;
-  const size_t need = (size_t)2 * slots * c * sizeof(double) + 64;
+  const size_t need = (size_t)2 * slots * c * (fp32 ? sizeof(float) : sizeof(double)) + 64;
   int use_smem = 0;
   size_t smem = 0;
   if (need <= 200 * 1024) {
@@ -505,6 +531,7 @@ bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
     smem = need;
   }
   pre_launch(s);
-  launch_cluster2(k_svd_cluster, CL, smem, s, a, use_smem);
+  if (fp32) launch_cluster2(k_svd_cluster_t<float>, CL, smem, s, a, use_smem);
+  else launch_cluster2(k_svd_cluster_t<double>, CL, smem, s, a, use_smem);
   return true;
 }

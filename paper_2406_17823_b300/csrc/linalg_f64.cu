@@ -418,7 +418,7 @@ size_t qr_work_doubles(int mcap, int ccap) {
 }
 
 bool launch_qr_cluster(const QrArgs& a, cudaStream_t s);
-bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);
+bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s, bool fp32);
 
 // Problems at least this large (capacity of the square factor) go to the
 // cluster kernels; smaller ones stay on one CTA, where the cluster
@@ -451,6 +451,22 @@ void launch_qr_f64(const QrArgs& a, int mcap, int ccap, cudaStream_t s) {
   }
 }
 
+double svd_flops(int mcap, int ncap);
+
+// FP32 working precision for the subspace search of the mixed path; the
+// caller re-orthonormalises the returned factor in FP64.  Returns false when
+// no cluster launch is possible or the problem is small (FP64 is used then).
+bool launch_svd_subspace_f32(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
+  check_range(a.M.ptr, view_extent(a.M), sizeof(double), "svd M");
+  check_range(a.US.ptr, view_extent(a.US), sizeof(double), "svd US");
+  check_range(a.VT.ptr, view_extent(a.VT), sizeof(double), "svd VT");
+  check_range(a.work, (long long)svd_work_doubles(mcap, ncap), sizeof(double), "svd work");
+  if ((mcap < ncap ? mcap : ncap) < cluster_threshold()) return false;
+  if (!launch_svd_cluster(a, mcap, ncap, s, true)) return false;
+  post_launch("k_svd_cluster_f32", s, svd_flops(mcap, ncap));
+  return true;
+}
+
 size_t svd_work_doubles(int mcap, int ncap) {
   const size_t Rt = (size_t)(mcap > ncap ? mcap : ncap);
   const size_t c = (size_t)(mcap < ncap ? mcap : ncap);
@@ -472,7 +488,7 @@ void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
   check_range(a.US.ptr, view_extent(a.US), sizeof(double), "svd US");
   check_range(a.VT.ptr, view_extent(a.VT), sizeof(double), "svd VT");
   check_range(a.work, (long long)svd_work_doubles(mcap, ncap), sizeof(double), "svd work");
-  if ((mcap < ncap ? mcap : ncap) >= cluster_threshold() && launch_svd_cluster(a, mcap, ncap, s)) {
+  if ((mcap < ncap ? mcap : ncap) >= cluster_threshold() && launch_svd_cluster(a, mcap, ncap, s, false)) {
     post_launch("k_svd_cluster", s, svd_flops(mcap, ncap));
     return;
   }

@@ -519,6 +519,10 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       W(std::max(qrw, svw), s);
   DBuf<int> qD(n + 1, s);
   launch_fill_int(qD.p, n + 1, 1, s);
+  const bool mixed = ctx->p.precision == QTT_PREC_MIXED;
+  int omax = 1;
+  for (int b = 0; b <= n; b++) omax = std::max(omax, ocap[b]);
+  DBuf<double> Rs(mixed ? (size_t)omax * omax : 0, s);
   // left-to-right QR
   for (int k = 0; k < n - 1; k++) {
     const double* Tp;
@@ -574,7 +578,28 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     a.work = W.p;
     a.work_len = (long long)W.n;
     a.err = ctx->d_err;
-    launch_svd_f64(a, qcap[k], 4 * ocap[k + 1], s);
+    if (mixed && launch_svd_subspace_f32(a, qcap[k], 4 * ocap[k + 1], s)) {
+      // FP64 gauge: re-orthonormalise the new core V^T (its rows) by a
+      // Householder QR in FP64, then U S = M V exactly in FP64
+      QrArgs q{};
+      q.A = MatView{Y->core(k), 4 * ocap[k + 1], axis_prefix(ocap[k], dref(Y->dims + k)),
+                    axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
+      q.inT = 1;
+      q.Q = q.A;
+      q.Q.rows = axis_prefix(ocap[k], dconst(1));
+      q.qT = 1;
+      q.R = MatView{Rs.p, ocap[k], axis_prefix(ocap[k], dconst(1)), axis_prefix(ocap[k], dconst(1))};
+      q.work = W.p;
+      q.work_len = (long long)W.n;
+      q.err = ctx->d_err;
+      launch_qr_f64(q, 4 * ocap[k + 1], ocap[k], s);
+      GemmF64 g = gemm_plain(Mp, Y->core(k), USb.p, qcap[k], ocap[k], 4 * ocap[k + 1],
+                             4 * ocap[k + 1], 4 * ocap[k + 1], ocap[k]);
+      g.tB = 1;
+      gemm(g, s);
+    } else {
+      launch_svd_f64(a, qcap[k], 4 * ocap[k + 1], s);
+    }
   }
   // first core: Y_0 = Qcore_0 (4 x qcap[1]) * US (qcap[1] x ocap[1])
   {
@@ -667,7 +692,13 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
     if (k < n - 1)
       svw = std::max(svw, svd_work_doubles(4 * rcap[k], ca[k + 1] * cb[k + 1]));
   }
-  DBuf<double> R0(rmax, s), R1(rmax, s), Xb(xmax, s), Tb(tmax, s), W(svw, s);
+  const bool mixed = ctx->p.precision == QTT_PREC_MIXED;
+  int rcmax = 1;
+  for (int b = 0; b <= n; b++) rcmax = std::max(rcmax, rcap[b]);
+  size_t qrw = 1;
+  for (int k = 0; k < n - 1; k++) qrw = std::max(qrw, qr_work_doubles(4 * rcap[k], rcap[k + 1]));
+  DBuf<double> R0(rmax, s), R1(rmax, s), Xb(xmax, s), Tb(tmax, s), W(std::max(svw, qrw), s);
+  DBuf<double> Rs(mixed ? (size_t)rcmax * rcmax : 0, s);
   launch_fill(R0.p, 1, 1.0, s);
   double* Rc = R0.p;
   double* Rn = R1.p;
@@ -717,7 +748,26 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
     a.work = W.p;
     a.work_len = (long long)W.n;
     a.err = ctx->d_err;
-    launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+    if (mixed && launch_svd_subspace_f32(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s)) {
+      // FP64 gauge on the core U ((r, s) x r'), then the carry U^T T in FP64
+      QrArgs q{};
+      q.A = a.VT;
+      q.Q = a.VT;
+      q.Q.cols = axis_prefix(rcap[k + 1], dconst(1));
+      q.A.cols = axis_prefix(rcap[k + 1], dref(C->dims + k + 1));
+      q.R = MatView{Rs.p, rcap[k + 1], axis_prefix(rcap[k + 1], dconst(1)),
+                    axis_prefix(rcap[k + 1], dconst(1))};
+      q.work = W.p;
+      q.work_len = (long long)W.n;
+      q.err = ctx->d_err;
+      launch_qr_f64(q, 4 * rcap[k], rcap[k + 1], s);
+      GemmF64 g = gemm_plain(C->core(k), Tb.p, Rn, rcap[k + 1], ca[k + 1] * cb[k + 1], 4 * rcap[k],
+                             rcap[k + 1], ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
+      g.tA = 1;
+      gemm(g, s);
+    } else {
+      launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+    }
     std::swap(Rc, Rn);
   }
   return compress_impl(ctx, C.get(), eps, chi);
