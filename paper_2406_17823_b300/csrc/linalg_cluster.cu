@@ -16,6 +16,7 @@
 // O(c^3) factorisation over the cluster is what makes it affordable.
 #include <cooperative_groups.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -210,11 +211,125 @@ __device__ __forceinline__ int rr_pos_c(int k, int t, int cp) {
   return k == 0 ? 0 : 1 + (k - 1 + t) % (cp - 1);
 }
 
+
+// Block one-sided Jacobi across the cluster.  The c columns of X (and of the
+// rotation accumulator J) are cut into 2 CL blocks of b columns (zero
+// columns pad the last ones).  Tournament position p (0 .. 2CL-1) lives in
+// CTA p (p < CL, slot 0) or CTA 2CL-1-p (slot 1), so CTA k pairs positions k
+// and 2CL-1-k.  In each outer round a CTA rotates every pair of its 2b
+// columns in its own shared memory (an inner round-robin sweep), then all
+// blocks advance one position (position 0 stays) by copying into the
+// destination CTA's other buffer; one cluster barrier per outer round.
+// 2CL-1 outer rounds meet every pair of blocks once (one sweep).  X and J are
+// read from and written back to global memory column-major (c x c).
+template <typename T>
+__device__ void jacobi_blocks(cg::cluster_group& cl, T* Xg, T* Jg, int c, int b, T* sm, T tol,
+                              int rank, int CL) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ int blk[2][2];
+  __shared__ int flag_b;
+  const size_t blk_elems = (size_t)b * c;                   // one block, X or J
+  auto buf = [&](int which, int slot, int xj) -> T* {       // local pointer
+    return sm + (((size_t)which * 2 + slot) * 2 + xj) * blk_elems;
+  };
+  const int P2 = 2 * CL;
+  int cur = 0;
+  for (int slot = 0; slot < 2; slot++) {
+    const int beta = slot == 0 ? rank : P2 - 1 - rank;
+    if (threadIdx.x == 0) blk[0][slot] = beta;
+    for (int col = 0; col < b; col++) {
+      const int gi = beta * b + col;
+      T* x = buf(0, slot, 0) + (size_t)col * c;
+      T* jj = buf(0, slot, 1) + (size_t)col * c;
+      for (int e = threadIdx.x; e < c; e += blockDim.x) {
+        x[e] = gi < c ? Xg[(size_t)gi * c + e] : (T)0;
+        jj[e] = gi < c ? Jg[(size_t)gi * c + e] : (T)0;
+      }
+    }
+  }
+  cl.sync();
+  const int cq = 2 * b;  // local columns, even
+  for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
+    if (threadIdx.x == 0) flag_b = 0;
+    __syncthreads();
+    for (int t = 0; t < P2 - 1; t++) {
+      for (int it = 0; it < cq - 1; it++) {
+        for (int k = warp; k < b; k += nw) {
+          int p = rr_pos_c(k, it, cq), q = rr_pos_c(cq - 1 - k, it, cq);
+          if (p > q) { const int s_ = p; p = q; q = s_; }
+          T* x = buf(cur, p / b, 0) + (size_t)(p % b) * c;
+          T* y = buf(cur, q / b, 0) + (size_t)(q % b) * c;
+          T al = 0, be = 0, ga = 0;
+          for (int i = lane; i < c; i += 32) {
+            const T xi = x[i], yi = y[i];
+            al += xi * xi;
+            be += yi * yi;
+            ga += xi * yi;
+          }
+          al = warp_sum_c(al);
+          be = warp_sum_c(be);
+          ga = warp_sum_c(ga);
+          if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+            const double zeta = ((double)be - (double)al) / (2.0 * (double)ga);
+            const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double csd = 1.0 / sqrt(1.0 + tt * tt);
+            const T cs = (T)csd, sn = (T)(csd * tt);
+            for (int i = lane; i < c; i += 32) {
+              const T xi = x[i], yi = y[i];
+              x[i] = cs * xi - sn * yi;
+              y[i] = sn * xi + cs * yi;
+            }
+            T* jx = buf(cur, p / b, 1) + (size_t)(p % b) * c;
+            T* jy = buf(cur, q / b, 1) + (size_t)(q % b) * c;
+            for (int i = lane; i < c; i += 32) {
+              const T xi = jx[i], yi = jy[i];
+              jx[i] = cs * xi - sn * yi;
+              jy[i] = sn * xi + cs * yi;
+            }
+            if (lane == 0) flag_b = 1;
+          }
+        }
+        __syncthreads();
+      }
+      // advance every block one tournament position (position 0 stays)
+      for (int slot = 0; slot < 2; slot++) {
+        const int pos = slot == 0 ? rank : P2 - 1 - rank;
+        const int np = pos == 0 ? 0 : (pos % (P2 - 1)) + 1;
+        const int dcta = np < CL ? np : P2 - 1 - np, dslot = np < CL ? 0 : 1;
+        T* dst = cl.map_shared_rank(buf(cur ^ 1, dslot, 0), dcta);
+        const T* src = buf(cur, slot, 0);
+        for (size_t e = threadIdx.x; e < 2 * blk_elems; e += blockDim.x) dst[e] = src[e];
+        if (threadIdx.x == 0) *cl.map_shared_rank(&blk[cur ^ 1][dslot], dcta) = blk[cur][slot];
+      }
+      cl.sync();
+      cur ^= 1;
+    }
+    int any = 0;
+    for (int rr = 0; rr < CL; rr++) any |= *cl.map_shared_rank(&flag_b, rr);
+    cl.sync();
+    if (!any) break;
+  }
+  for (int slot = 0; slot < 2; slot++) {
+    const int beta = blk[cur][slot];
+    for (int col = 0; col < b; col++) {
+      const int gi = beta * b + col;
+      if (gi >= c) continue;
+      const T* x = buf(cur, slot, 0) + (size_t)col * c;
+      const T* jj = buf(cur, slot, 1) + (size_t)col * c;
+      for (int e = threadIdx.x; e < c; e += blockDim.x) {
+        Xg[(size_t)gi * c + e] = x[e];
+        Jg[(size_t)gi * c + e] = jj[e];
+      }
+    }
+  }
+  cl.sync();
+}
+
 // dynamic shared memory: X and J home columns (slots x c each).  T is the
 // working precision: double for the FP64 path; float for the mixed path,
 // whose callers re-orthonormalise the returned factor in FP64.
 template <typename T>
-__global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) {
+__global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem, int bcols) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
   extern __shared__ double dsm_raw[];
@@ -242,7 +357,8 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
     const bool bad = !view_ok_c(a.M) || !view_ok_c(a.US) || !view_ok_c(a.VT) || m < 1 ||
                      N < 1 || m > fr.hcap * fr.lcap || N > fc.hcap * fc.lcap || m > us_r ||
                      max(rmax, 1) > us_c || max(rmax, 1) > vt_r || N > vt_c ||
-                     need > a.work_len || (use_smem && slots * c > use_smem);
+                     need > a.work_len || (use_smem && slots * c > use_smem) ||
+                     (bcols && 2 * CL * bcols < c);
     if (bad) {
       if (rank == 0 && threadIdx.x == 0 && a.err) atomicOr(a.err, QTT_DEVERR_SHAPE);
       return;
@@ -297,6 +413,9 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
   cl.sync();
   const T tol = Prec<T>::cos_tol(c);
   const int cp = c + (c & 1);
+  if (bcols) {
+    jacobi_blocks<T>(cl, Xg, Jg, c, bcols, dsm, tol, rank, CL);
+  } else
   for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
     if (threadIdx.x == 0) flag_local = 0;
     __syncthreads();
@@ -489,7 +608,8 @@ void launch_cluster(K kern, int CL, size_t smem, cudaStream_t s, Args a) {
 }
 
 template <typename K>
-void launch_cluster2(K kern, int CL, size_t smem, cudaStream_t s, SvdArgs a, int use_smem) {
+void launch_cluster2(K kern, int CL, size_t smem, cudaStream_t s, SvdArgs a, int use_smem,
+                     int bcols) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(512);
@@ -502,7 +622,7 @@ void launch_cluster2(K kern, int CL, size_t smem, cudaStream_t s, SvdArgs a, int
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  QTT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, a, use_smem));
+  QTT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, a, use_smem, bcols));
 }
 
 }  // namespace
@@ -522,16 +642,27 @@ bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s, bo
   const int CL = pick_cluster_size();
   if (CL <= 0) return false;
   const int c = mcap < ncap ? mcap : ncap;  // capacity bound on the square factor
-  const int slots = (c + CL - 1) / CL;
-  const size_t need = (size_t)2 * slots * c * (fp32 ? sizeof(float) : sizeof(double)) + 64;
-  int use_smem = 0;
+  const size_t es = fp32 ? sizeof(float) : sizeof(double);
+  const size_t limit = 200 * 1024;
+  static const bool scalar_only = getenv("QTT_SCALAR_JACOBI") != nullptr;
+  // preferred: block Jacobi, double-buffered blocks in each CTA's memory
+  const int b = (c + 2 * CL - 1) / (2 * CL);
+  const size_t need_block = (size_t)8 * b * c * es + 64;
+  int use_smem = 0, bcols = 0;
   size_t smem = 0;
-  if (need <= 200 * 1024) {
-    use_smem = slots * c;
-    smem = need;
+  if (!scalar_only && need_block <= limit) {
+    bcols = b;
+    smem = need_block;
+  } else {
+    const int slots = (c + CL - 1) / CL;
+    const size_t need = (size_t)2 * slots * c * es + 64;
+    if (need <= limit) {
+      use_smem = slots * c;
+      smem = need;
+    }
   }
   pre_launch(s);
-  if (fp32) launch_cluster2(k_svd_cluster_t<float>, CL, smem, s, a, use_smem);
-  else launch_cluster2(k_svd_cluster_t<double>, CL, smem, s, a, use_smem);
+  if (fp32) launch_cluster2(k_svd_cluster_t<float>, CL, smem, s, a, use_smem, bcols);
+  else launch_cluster2(k_svd_cluster_t<double>, CL, smem, s, a, use_smem, bcols);
   return true;
 }
