@@ -21,7 +21,9 @@ TOL = 1e-6
 
 
 def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    r = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    print(f"relative L2 error {r:.3e}")
+    return r
 
 
 @pytest.fixture(scope="module")
