@@ -697,8 +697,24 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
   for (int b = 0; b <= n; b++) rcmax = std::max(rcmax, rcap[b]);
   size_t qrw = 1;
   for (int k = 0; k < n - 1; k++) qrw = std::max(qrw, qr_work_doubles(4 * rcap[k], rcap[k + 1]));
+  // mixed path buffers: oversampled factor, projected matrix, small factor
+  constexpr int kOver = 16;
+  size_t utm = 1, btm = 1, ubm = 1, rsm = 1;
+  if (mixed) {
+    for (int k = 0; k < n - 1; k++) {
+      const size_t rpo = std::min({4 * rcap[k], ca[k + 1] * cb[k + 1], chi + kOver});
+      utm = std::max(utm, (size_t)4 * rcap[k] * rpo);
+      btm = std::max(btm, rpo * ca[k + 1] * cb[k + 1]);
+      ubm = std::max(ubm, rpo * rcap[k + 1]);
+      rsm = std::max(rsm, rpo * rpo);
+      qrw = std::max(qrw, qr_work_doubles(4 * rcap[k], (int)rpo));
+    }
+  }
   DBuf<double> R0(rmax, s), R1(rmax, s), Xb(xmax, s), Tb(tmax, s), W(std::max(svw, qrw), s);
-  DBuf<double> Rs(mixed ? (size_t)rcmax * rcmax : 0, s);
+  DBuf<double> Rs(mixed ? rsm : 0, s), Ut(mixed ? utm : 0, s), Bt(mixed ? btm : 0, s),
+      Ub(mixed ? ubm : 0, s);
+  DBuf<int> rp(1, s);
+  (void)rcmax;
   launch_fill(R0.p, 1, 1.0, s);
   double* Rc = R0.p;
   double* Rn = R1.p;
@@ -748,26 +764,46 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
     a.work = W.p;
     a.work_len = (long long)W.n;
     a.err = ctx->d_err;
-    if (mixed && launch_svd_subspace_f32(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s)) {
-      // FP64 gauge on the core U ((r, s) x r'), then the carry U^T T in FP64
-      QrArgs q{};
-      q.A = a.VT;
-      q.Q = a.VT;
-      q.Q.cols = axis_prefix(rcap[k + 1], dconst(1));
-      q.A.cols = axis_prefix(rcap[k + 1], dref(C->dims + k + 1));
-      q.R = MatView{Rs.p, rcap[k + 1], axis_prefix(rcap[k + 1], dconst(1)),
-                    axis_prefix(rcap[k + 1], dconst(1))};
-      q.work = W.p;
-      q.work_len = (long long)W.n;
-      q.err = ctx->d_err;
-      launch_qr_f64(q, 4 * rcap[k], rcap[k + 1], s);
-      GemmF64 g = gemm_plain(C->core(k), Tb.p, Rn, rcap[k + 1], ca[k + 1] * cb[k + 1], 4 * rcap[k],
-                             rcap[k + 1], ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
-      g.tA = 1;
-      gemm(g, s);
-    } else {
-      launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+    bool done = false;
+    if (mixed) {
+      // Rayleigh-Ritz: FP32 finds an oversampled subspace (chi + kOver
+      // directions), FP64 orthonormalises it (Householder), projects
+      // B = Q^T T exactly and makes the cap-chi cut by an FP64 SVD of B.
+      const int rpo = std::min({4 * rcap[k], ca[k + 1] * cb[k + 1], chi + kOver});
+      SvdArgs a32 = a;
+      a32.chi = chi + kOver;
+      a32.US = MatView{Bt.p, ca[k + 1] * cb[k + 1], axis_prefix(rpo, dconst(1)), a.US.cols};
+      a32.VT = MatView{Ut.p, rpo, a.VT.rows, axis_prefix(rpo, dconst(1))};
+      a32.r_out = rp.p;
+      if (launch_svd_subspace_f32(a32, ca[k + 1] * cb[k + 1], 4 * rcap[k], s)) {
+        QrArgs q{};
+        q.A = MatView{Ut.p, rpo, a.VT.rows, axis_prefix(rpo, dref(rp.p))};
+        q.Q = MatView{Ut.p, rpo, a.VT.rows, axis_prefix(rpo, dconst(1))};
+        q.R = MatView{Rs.p, rpo, axis_prefix(rpo, dconst(1)), axis_prefix(rpo, dconst(1))};
+        q.work = W.p;
+        q.work_len = (long long)W.n;
+        q.err = ctx->d_err;
+        launch_qr_f64(q, 4 * rcap[k], rpo, s);
+        // B = Q^T T  (rpo x (a', b'))
+        GemmF64 g = gemm_plain(Ut.p, Tb.p, Bt.p, rpo, ca[k + 1] * cb[k + 1], 4 * rcap[k], rpo,
+                               ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
+        g.tA = 1;
+        gemm(g, s);
+        // FP64 SVD of B^T: carry S V_B^T (written transposed), U_B into Ub
+        SvdArgs b64 = a;
+        b64.M = MatView{Bt.p, ca[k + 1] * cb[k + 1], axis_prefix(rpo, dref(rp.p)), a.M.cols};
+        b64.inT = 1;
+        b64.VT = MatView{Ub.p, rcap[k + 1], axis_prefix(rpo, dconst(1)),
+                         axis_prefix(rcap[k + 1], dconst(1))};
+        b64.vtT = 1;
+        launch_svd_f64(b64, ca[k + 1] * cb[k + 1], rpo, s);
+        // core = Q U_B  ((r, s) x r')
+        gemm(gemm_plain(Ut.p, Ub.p, C->core(k), 4 * rcap[k], rcap[k + 1], rpo, rpo, rcap[k + 1],
+                        rcap[k + 1]), s);
+        done = true;
+      }
     }
+    if (!done) launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
     std::swap(Rc, Rn);
   }
   return compress_impl(ctx, C.get(), eps, chi);
