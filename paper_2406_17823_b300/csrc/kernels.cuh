@@ -65,6 +65,9 @@ struct SvdArgs {
   DimRef rank_limit;
   int* r_out;
   double* sv_out;   // optional, receives the c singular values
+  // optional: the squared Frobenius norm of a larger matrix of which M is
+  // a projection; the weight M lacks counts as discarded in the eps rule
+  const double* total_weight;
   double* work;
   long long work_len;  // doubles available at work
   const int* skip;

@@ -498,6 +498,10 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem, 
           const double s = sig[perm[j]];
           tail[j] = tail[j + 1] + s * s;
         }
+        if (a.total_weight) {  // weight outside M's subspace, counted as discarded
+          const double extra = fmax(0.0, *a.total_weight - tail[0]);
+          for (int j = 0; j <= c; j++) tail[j] += extra;
+        }
         const double total = tail[0];
         r = c;
         if (total == 0.0) {

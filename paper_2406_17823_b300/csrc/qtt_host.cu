@@ -520,9 +520,19 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   DBuf<int> qD(n + 1, s);
   launch_fill_int(qD.p, n + 1, 1, s);
   const bool mixed = ctx->p.precision == QTT_PREC_MIXED;
-  int omax = 1;
-  for (int b = 0; b <= n; b++) omax = std::max(omax, ocap[b]);
-  DBuf<double> Rs(mixed ? (size_t)omax * omax : 0, s);
+  constexpr int kOver = 16;
+  size_t vtm = 1, bmm = 1, vbm = 1, rsm = 1;
+  if (mixed)
+    for (int k = 1; k < n; k++) {
+      const size_t rpo = std::min({qcap[k], 4 * ocap[k + 1], chi + kOver});
+      vtm = std::max(vtm, rpo * 4 * ocap[k + 1]);
+      bmm = std::max(bmm, (size_t)qcap[k] * rpo);
+      vbm = std::max(vbm, (size_t)ocap[k] * rpo);
+      rsm = std::max(rsm, rpo * rpo);
+    }
+  DBuf<double> Rs(mixed ? rsm : 0, s), Vt(mixed ? vtm : 0, s), Bm(mixed ? bmm : 0, s),
+      Vb(mixed ? vbm : 0, s), wM(1, s);
+  DBuf<int> rp(1, s);
   // left-to-right QR
   for (int k = 0; k < n - 1; k++) {
     const double* Tp;
@@ -578,26 +588,48 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     a.work = W.p;
     a.work_len = (long long)W.n;
     a.err = ctx->d_err;
-    if (mixed && launch_svd_subspace_f32(a, qcap[k], 4 * ocap[k + 1], s)) {
-      // FP64 gauge: re-orthonormalise the new core V^T (its rows) by a
-      // Householder QR in FP64, then U S = M V exactly in FP64
-      QrArgs q{};
-      q.A = MatView{Y->core(k), 4 * ocap[k + 1], axis_prefix(ocap[k], dref(Y->dims + k)),
-                    axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
-      q.inT = 1;
-      q.Q = q.A;
-      q.Q.rows = axis_prefix(ocap[k], dconst(1));
-      q.qT = 1;
-      q.R = MatView{Rs.p, ocap[k], axis_prefix(ocap[k], dconst(1)), axis_prefix(ocap[k], dconst(1))};
-      q.work = W.p;
-      q.work_len = (long long)W.n;
-      q.err = ctx->d_err;
-      launch_qr_f64(q, 4 * ocap[k + 1], ocap[k], s);
-      GemmF64 g = gemm_plain(Mp, Y->core(k), USb.p, qcap[k], ocap[k], 4 * ocap[k + 1],
-                             4 * ocap[k + 1], 4 * ocap[k + 1], ocap[k]);
-      g.tB = 1;
-      gemm(g, s);
-    } else {
+    bool done = false;
+    if (mixed) {
+      // Rayleigh-Ritz: FP32 finds an oversampled subspace of right vectors,
+      // FP64 orthonormalises it, projects B = M V exactly and makes the
+      // (eps, chi) cut by an FP64 SVD of B, counting the weight of M outside
+      // the subspace (|M|^2 - |B|^2, FP64) as discarded.
+      const int rpo = std::min({qcap[k], 4 * ocap[k + 1], chi + kOver});
+      SvdArgs a32 = a;
+      a32.eps = -1.0;
+      a32.chi = chi + kOver;
+      a32.US = MatView{Bm.p, rpo, a.US.rows, axis_prefix(rpo, dconst(1))};
+      a32.VT = MatView{Vt.p, 4 * ocap[k + 1], axis_prefix(rpo, dconst(1)), a.VT.cols};
+      a32.r_out = rp.p;
+      if (launch_svd_subspace_f32(a32, qcap[k], 4 * ocap[k + 1], s)) {
+        QrArgs q{};
+        q.A = MatView{Vt.p, 4 * ocap[k + 1], axis_prefix(rpo, dref(rp.p)), a.VT.cols};
+        q.inT = 1;
+        q.Q = MatView{Vt.p, 4 * ocap[k + 1], axis_prefix(rpo, dconst(1)), a.VT.cols};
+        q.qT = 1;
+        q.R = MatView{Rs.p, rpo, axis_prefix(rpo, dconst(1)), axis_prefix(rpo, dconst(1))};
+        q.work = W.p;
+        q.work_len = (long long)W.n;
+        q.err = ctx->d_err;
+        launch_qr_f64(q, 4 * ocap[k + 1], rpo, s);
+        // B = M V  (qcap x rpo), and |M|_F^2
+        GemmF64 g = gemm_plain(Mp, Vt.p, Bm.p, qcap[k], rpo, 4 * ocap[k + 1], 4 * ocap[k + 1],
+                               4 * ocap[k + 1], rpo);
+        g.tB = 1;
+        gemm(g, s);
+        launch_sumsq2(Mp, (long long)qcap[k] * 4 * ocap[k + 1], Mp, 0, wM.p, s);
+        SvdArgs b64 = a;
+        b64.M = MatView{Bm.p, rpo, a.M.rows, axis_prefix(rpo, dref(rp.p))};
+        b64.VT = MatView{Vb.p, rpo, axis_prefix(ocap[k], dconst(1)), axis_prefix(rpo, dconst(1))};
+        b64.total_weight = wM.p;
+        launch_svd_f64(b64, qcap[k], rpo, s);
+        // core = V_B^T V^T  (r x N)
+        gemm(gemm_plain(Vb.p, Vt.p, Y->core(k), ocap[k], 4 * ocap[k + 1], rpo, rpo,
+                        4 * ocap[k + 1], 4 * ocap[k + 1]), s);
+        done = true;
+      }
+    }
+    if (!done) {
       launch_svd_f64(a, qcap[k], 4 * ocap[k + 1], s);
     }
   }
