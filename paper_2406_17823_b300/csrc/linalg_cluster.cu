@@ -212,113 +212,166 @@ __device__ __forceinline__ int rr_pos_c(int k, int t, int cp) {
 }
 
 
-// Block one-sided Jacobi across the cluster.  The c columns of X (and of the
-// rotation accumulator J) are cut into 2 CL blocks of b columns (zero
-// columns pad the last ones).  Tournament position p (0 .. 2CL-1) lives in
-// CTA p (p < CL, slot 0) or CTA 2CL-1-p (slot 1), so CTA k pairs positions k
-// and 2CL-1-k.  In each outer round a CTA rotates every pair of its 2b
-// columns in its own shared memory (an inner round-robin sweep), then all
-// blocks advance one position (position 0 stays) by copying into the
-// destination CTA's other buffer; one cluster barrier per outer round.
-// 2CL-1 outer rounds meet every pair of blocks once (one sweep).  X and J are
-// read from and written back to global memory column-major (c x c).
-template <typename T>
-__device__ void jacobi_blocks(cg::cluster_group& cl, T* Xg, T* Jg, int c, int b, T* sm, T tol,
-                              int rank, int CL) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __shared__ int blk[2][2];
-  __shared__ int flag_b;
-  const size_t blk_elems = (size_t)b * c;                   // one block, X or J
-  auto buf = [&](int which, int slot, int xj) -> T* {       // local pointer
-    return sm + (((size_t)which * 2 + slot) * 2 + xj) * blk_elems;
+// Systolic one-sided Jacobi (circle ordering of the round-robin
+// tournament).  Pair slot s (0 .. P-1, P = cp/2) is held in REGISTERS by warp
+// (s mod spc) of CTA (s / spc): lane l keeps rows l, l+32, ... of the slot's
+// two columns of X and of J, so a round needs no shared-memory reads for its
+// dot products or rotations.  After rotating, the columns move one place
+// along the circle (slot 0 keeps its first column): slot s hands its first
+// column (slot 0: its second) to slot s+1 and its second column to slot s-1,
+// through mailboxes in the receiver's shared memory (double-buffered by
+// round parity, so one cluster barrier per round suffices: a mailbox of
+// parity t is rewritten only after every reader of round t-2 has passed
+// the barrier of round t-1).  Column ids travel with the columns and fix
+// the orientation of each pair (lower id first), as in the scalar kernel.
+// The circle has period cp-1, so after each sweep every column is back in
+// its starting slot.  Rows at and beyond c are zero in every register.
+template <typename T, int EPL, typename XC, typename JC>
+__device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, T tol, T* box,
+                                int spc, int rank, int* flag_local) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cp = c + (c & 1), P = cp / 2;
+  const int s = rank * spc + warp;
+  const bool active = warp < spc && s < P;
+  __shared__ int mb_id[2][16][2];
+  constexpr int L = 32 * EPL;                  // mailbox column length
+  // box[buf][lslot][which][xj][L]; which 0 = new first column, 1 = new second
+  auto mbox = [&](T* base, int buf, int ls, int which, int xj) -> T* {
+    return base + ((((size_t)buf * spc + ls) * 2 + which) * 2 + xj) * L;
   };
-  const int P2 = 2 * CL;
-  int cur = 0;
-  for (int slot = 0; slot < 2; slot++) {
-    const int beta = slot == 0 ? rank : P2 - 1 - rank;
-    if (threadIdx.x == 0) blk[0][slot] = beta;
-    for (int col = 0; col < b; col++) {
-      const int gi = beta * b + col;
-      T* x = buf(0, slot, 0) + (size_t)col * c;
-      T* jj = buf(0, slot, 1) + (size_t)col * c;
-      for (int e = threadIdx.x; e < c; e += blockDim.x) {
-        x[e] = gi < c ? Xg[(size_t)gi * c + e] : (T)0;
-        jj[e] = gi < c ? Jg[(size_t)gi * c + e] : (T)0;
-      }
+  T xa[EPL], xb[EPL], ja[EPL], jb[EPL];
+  int ida = 2 * s, idb = 2 * s + 1;
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < EPL; e++) {
+      const int i = lane + 32 * e;
+      const bool ok = i < c;
+      xa[e] = (ok && ida < c) ? xcol(ida)[i] : (T)0;
+      ja[e] = (ok && ida < c) ? jcol(ida)[i] : (T)0;
+      xb[e] = (ok && idb < c) ? xcol(idb)[i] : (T)0;
+      jb[e] = (ok && idb < c) ? jcol(idb)[i] : (T)0;
     }
   }
-  cl.sync();
-  const int cq = 2 * b;  // local columns, even
+  // destinations are fixed per slot: next slot (as its first column) and
+  // previous slot (as its second column)
+  const int sn_ = s + 1, sp_ = s - 1;
+  T* to_next = (active && sn_ < P) ? cl.map_shared_rank(box, sn_ / spc) : nullptr;
+  T* to_prev = (active && s >= 1) ? cl.map_shared_rank(box, sp_ / spc) : nullptr;
+  int* id_next = (active && sn_ < P) ? cl.map_shared_rank(&mb_id[0][0][0], sn_ / spc) : nullptr;
+  int* id_prev = (active && s >= 1) ? cl.map_shared_rank(&mb_id[0][0][0], sp_ / spc) : nullptr;
+  cl.sync();  // every CTA has read its homes before anything is rotated
   for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
-    if (threadIdx.x == 0) flag_b = 0;
+    if (threadIdx.x == 0) *flag_local = 0;
     __syncthreads();
-    for (int t = 0; t < P2 - 1; t++) {
-      for (int it = 0; it < cq - 1; it++) {
-        for (int k = warp; k < b; k += nw) {
-          int p = rr_pos_c(k, it, cq), q = rr_pos_c(cq - 1 - k, it, cq);
-          if (p > q) { const int s_ = p; p = q; q = s_; }
-          T* x = buf(cur, p / b, 0) + (size_t)(p % b) * c;
-          T* y = buf(cur, q / b, 0) + (size_t)(q % b) * c;
-          T al = 0, be = 0, ga = 0;
-          for (int i = lane; i < c; i += 32) {
-            const T xi = x[i], yi = y[i];
-            al += xi * xi;
-            be += yi * yi;
-            ga += xi * yi;
+    for (int t = 0; t < cp - 1; t++) {
+      const int buf = t & 1;
+      if (active) {
+        T saa = 0, sbb = 0, sab = 0;
+#pragma unroll
+        for (int e = 0; e < EPL; e++) {
+          saa += xa[e] * xa[e];
+          sbb += xb[e] * xb[e];
+          sab += xa[e] * xb[e];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          saa += __shfl_xor_sync(0xffffffffu, saa, o);
+          sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
+          sab += __shfl_xor_sync(0xffffffffu, sab, o);
+        }
+        const bool swp = ida > idb;  // orientation: lower column id is "x"
+        const T al = swp ? sbb : saa, be = swp ? saa : sbb, ga = sab;
+        if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          const T zeta = (be - al) / ((T)2 * ga);
+          const T tt = copysign((T)1, zeta) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+          const T cs = (T)1 / sqrt((T)1 + tt * tt);
+          const T sn = swp ? -(cs * tt) : cs * tt;
+#pragma unroll
+          for (int e = 0; e < EPL; e++) {
+            const T x0 = xa[e], y0 = xb[e];
+            xa[e] = cs * x0 - sn * y0;
+            xb[e] = sn * x0 + cs * y0;
+            const T j0 = ja[e], k0 = jb[e];
+            ja[e] = cs * j0 - sn * k0;
+            jb[e] = sn * j0 + cs * k0;
           }
-          al = warp_sum_c(al);
-          be = warp_sum_c(be);
-          ga = warp_sum_c(ga);
-          if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-            const double zeta = ((double)be - (double)al) / (2.0 * (double)ga);
-            const double tt = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double csd = 1.0 / sqrt(1.0 + tt * tt);
-            const T cs = (T)csd, sn = (T)(csd * tt);
-            for (int i = lane; i < c; i += 32) {
-              const T xi = x[i], yi = y[i];
-              x[i] = cs * xi - sn * yi;
-              y[i] = sn * xi + cs * yi;
+          if (lane == 0) *flag_local = 1;
+        }
+        if (P > 1) {
+          if (to_next) {  // slot 0 sends its second column forward, the others their first
+            T* dx = mbox(to_next, buf, sn_ % spc, 0, 0);
+            T* dj = mbox(to_next, buf, sn_ % spc, 0, 1);
+#pragma unroll
+            for (int e = 0; e < EPL; e++) {
+              dx[lane + 32 * e] = s == 0 ? xb[e] : xa[e];
+              dj[lane + 32 * e] = s == 0 ? jb[e] : ja[e];
             }
-            T* jx = buf(cur, p / b, 1) + (size_t)(p % b) * c;
-            T* jy = buf(cur, q / b, 1) + (size_t)(q % b) * c;
-            for (int i = lane; i < c; i += 32) {
-              const T xi = jx[i], yi = jy[i];
-              jx[i] = cs * xi - sn * yi;
-              jy[i] = sn * xi + cs * yi;
+            if (lane == 0) id_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? idb : ida;
+          }
+          if (to_prev) {  // second column backward
+            T* dx = mbox(to_prev, buf, sp_ % spc, 1, 0);
+            T* dj = mbox(to_prev, buf, sp_ % spc, 1, 1);
+#pragma unroll
+            for (int e = 0; e < EPL; e++) {
+              dx[lane + 32 * e] = xb[e];
+              dj[lane + 32 * e] = jb[e];
             }
-            if (lane == 0) flag_b = 1;
+            if (lane == 0) id_prev[(buf * 16 + sp_ % spc) * 2 + 1] = idb;
           }
         }
-        __syncthreads();
-      }
-      // advance every block one tournament position (position 0 stays)
-      for (int slot = 0; slot < 2; slot++) {
-        const int pos = slot == 0 ? rank : P2 - 1 - rank;
-        const int np = pos == 0 ? 0 : (pos % (P2 - 1)) + 1;
-        const int dcta = np < CL ? np : P2 - 1 - np, dslot = np < CL ? 0 : 1;
-        T* dst = cl.map_shared_rank(buf(cur ^ 1, dslot, 0), dcta);
-        const T* src = buf(cur, slot, 0);
-        for (size_t e = threadIdx.x; e < 2 * blk_elems; e += blockDim.x) dst[e] = src[e];
-        if (threadIdx.x == 0) *cl.map_shared_rank(&blk[cur ^ 1][dslot], dcta) = blk[cur][slot];
       }
       cl.sync();
-      cur ^= 1;
+      if (active && P > 1) {
+        const int ls = warp;
+        if (s == P - 1) {  // last slot: its first column becomes its second
+#pragma unroll
+          for (int e = 0; e < EPL; e++) {
+            xb[e] = xa[e];
+            jb[e] = ja[e];
+          }
+          idb = ida;
+        }
+        if (s >= 1) {  // new first column from slot s-1
+          const T* sx = mbox(box, buf, ls, 0, 0);
+          const T* sj = mbox(box, buf, ls, 0, 1);
+#pragma unroll
+          for (int e = 0; e < EPL; e++) {
+            xa[e] = sx[lane + 32 * e];
+            ja[e] = sj[lane + 32 * e];
+          }
+          ida = mb_id[buf][ls][0];
+        }
+        if (s < P - 1) {  // new second column from slot s+1
+          const T* sx = mbox(box, buf, ls, 1, 0);
+          const T* sj = mbox(box, buf, ls, 1, 1);
+#pragma unroll
+          for (int e = 0; e < EPL; e++) {
+            xb[e] = sx[lane + 32 * e];
+            jb[e] = sj[lane + 32 * e];
+          }
+          idb = mb_id[buf][ls][1];
+        }
+      }
     }
+    // the last round ended with a cluster barrier, so every flag is final
     int any = 0;
-    for (int rr = 0; rr < CL; rr++) any |= *cl.map_shared_rank(&flag_b, rr);
-    cl.sync();
+    for (int rr = 0; rr < (int)cl.num_blocks(); rr++) any |= *cl.map_shared_rank(flag_local, rr);
+    cl.sync();  // nobody resets its flag before all have read it
     if (!any) break;
   }
-  for (int slot = 0; slot < 2; slot++) {
-    const int beta = blk[cur][slot];
-    for (int col = 0; col < b; col++) {
-      const int gi = beta * b + col;
-      if (gi >= c) continue;
-      const T* x = buf(cur, slot, 0) + (size_t)col * c;
-      const T* jj = buf(cur, slot, 1) + (size_t)col * c;
-      for (int e = threadIdx.x; e < c; e += blockDim.x) {
-        Xg[(size_t)gi * c + e] = x[e];
-        Jg[(size_t)gi * c + e] = jj[e];
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < EPL; e++) {
+      const int i = lane + 32 * e;
+      if (i < c) {
+        if (ida < c) {
+          xcol(ida)[i] = xa[e];
+          jcol(ida)[i] = ja[e];
+        }
+        if (idb < c) {
+          xcol(idb)[i] = xb[e];
+          jcol(idb)[i] = jb[e];
+        }
       }
     }
   }
@@ -328,8 +381,8 @@ __device__ void jacobi_blocks(cg::cluster_group& cl, T* Xg, T* Jg, int c, int b,
 // dynamic shared memory: X and J home columns (slots x c each).  T is the
 // working precision: double for the FP64 path; float for the mixed path,
 // whose callers re-orthonormalise the returned factor in FP64.
-template <typename T>
-__global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem, int bcols) {
+template <typename T, int EPL>
+__global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
   extern __shared__ double dsm_raw[];
@@ -357,8 +410,7 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem, 
     const bool bad = !view_ok_c(a.M) || !view_ok_c(a.US) || !view_ok_c(a.VT) || m < 1 ||
                      N < 1 || m > fr.hcap * fr.lcap || N > fc.hcap * fc.lcap || m > us_r ||
                      max(rmax, 1) > us_c || max(rmax, 1) > vt_r || N > vt_c ||
-                     need > a.work_len || (use_smem && slots * c > use_smem) ||
-                     (bcols && 2 * CL * bcols < c);
+                     need > a.work_len || (use_smem && slots * c > use_smem);
     if (bad) {
       if (rank == 0 && threadIdx.x == 0 && a.err) atomicOr(a.err, QTT_DEVERR_SHAPE);
       return;
@@ -413,9 +465,17 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem, 
   cl.sync();
   const T tol = Prec<T>::cos_tol(c);
   const int cp = c + (c & 1);
-  if (bcols) {
-    jacobi_blocks<T>(cl, Xg, Jg, c, bcols, dsm, tol, rank, CL);
-  } else
+  const int spc = ((cp / 2) + CL - 1) / CL;
+  bool done = false;
+  if constexpr (EPL > 0) {
+    if (c <= 32 * EPL && spc <= nw && spc <= 16 && !use_smem) {
+      // the homes are in global memory and the whole dynamic shared memory
+      // holds the mailboxes (sized by the launcher for the capacity shape)
+      jacobi_systolic<T, EPL>(cl, xcol, jcol, c, tol, dsm, spc, rank, &flag_local);
+      done = true;
+    }
+  }
+  if (!done)
   for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
     if (threadIdx.x == 0) flag_local = 0;
     __syncthreads();
@@ -554,24 +614,40 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem, 
 
 int g_cluster_size = -1;  // 16, 8 or 0 (no cluster launch)
 
+// every cluster SVD instantiation: <precision, elements per lane> (0 = the
+// scalar tournament with homes in distributed shared memory)
+template <typename F>
+void for_each_svd_kernel(F f) {
+  f((const void*)k_svd_cluster_t<double, 0>);
+  f((const void*)k_svd_cluster_t<double, 2>);
+  f((const void*)k_svd_cluster_t<double, 4>);
+  f((const void*)k_svd_cluster_t<double, 8>);
+  f((const void*)k_svd_cluster_t<float, 0>);
+  f((const void*)k_svd_cluster_t<float, 2>);
+  f((const void*)k_svd_cluster_t<float, 4>);
+  f((const void*)k_svd_cluster_t<float, 8>);
+}
+
 int pick_cluster_size() {
   if (g_cluster_size >= 0) return g_cluster_size;
   g_cluster_size = 0;
   const int want[2] = {16, 8};
   for (int w : want) {
     if (w == 16) {
-      if (cudaFuncSetAttribute(k_svd_cluster_t<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-              cudaSuccess ||
-          cudaFuncSetAttribute(k_svd_cluster_t<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-              cudaSuccess ||
-          cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-              cudaSuccess) {
+      bool ok = cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                     1) == cudaSuccess;
+      for_each_svd_kernel([&](const void* k) {
+        ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                       cudaSuccess;
+      });
+      if (!ok) {
         cudaGetLastError();
         continue;
       }
     }
-    cudaFuncSetAttribute(k_svd_cluster_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_svd_cluster_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    for_each_svd_kernel([&](const void* k) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(w);
     cfg.blockDim = dim3(512);
@@ -584,7 +660,8 @@ int pick_cluster_size() {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, k_svd_cluster_t<double>, &cfg) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_svd_cluster_t<double, 8>,
+                                       &cfg) == cudaSuccess &&
         nclusters > 0) {
       g_cluster_size = w;
       break;
@@ -611,9 +688,8 @@ void launch_cluster(K kern, int CL, size_t smem, cudaStream_t s, Args a) {
   QTT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, a));
 }
 
-template <typename K>
-void launch_cluster2(K kern, int CL, size_t smem, cudaStream_t s, SvdArgs a, int use_smem,
-                     int bcols) {
+void launch_svd_kernel(const void* kern, int CL, size_t smem, cudaStream_t s, SvdArgs a,
+                       int use_smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(512);
@@ -626,7 +702,8 @@ void launch_cluster2(K kern, int CL, size_t smem, cudaStream_t s, SvdArgs a, int
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  QTT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, a, use_smem, bcols));
+  void* args[2] = {(void*)&a, (void*)&use_smem};
+  QTT_CUDA_CHECK(cudaLaunchKernelExC(&cfg, kern, args));
 }
 
 }  // namespace
@@ -648,27 +725,34 @@ bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s, bo
   const int c = mcap < ncap ? mcap : ncap;  // capacity bound on the square factor
   const size_t es = fp32 ? sizeof(float) : sizeof(double);
   const size_t limit = 200 * 1024;
-  // block Jacobi measured slower than the scalar tournament on this GPU
-  // (intra-block pairs are repeated every outer round); kept behind a switch
-  static const bool use_block = getenv("QTT_BLOCK_JACOBI") != nullptr;
-  // preferred: block Jacobi, double-buffered blocks in each CTA's memory
-  const int b = (c + 2 * CL - 1) / (2 * CL);
-  const size_t need_block = (size_t)8 * b * c * es + 64;
-  int use_smem = 0, bcols = 0;
+  static const bool scalar_only = getenv("QTT_SCALAR_JACOBI") != nullptr;
+  // preferred: the systolic kernel, columns in registers, mailboxes in
+  // shared memory (2 parities x slots per CTA x 2 columns x (X, J))
+  const int epl = c <= 64 ? 2 : c <= 128 ? 4 : c <= 256 ? 8 : 0;
+  const int spc = ((c + 1) / 2 + CL - 1) / CL;
+  const size_t need_sys = (size_t)8 * spc * 32 * epl * es;
+  if (!scalar_only && epl > 0 && spc <= 16 && need_sys <= limit) {
+    pre_launch(s);
+    const void* k = nullptr;
+    if (fp32) k = epl == 2 ? (const void*)k_svd_cluster_t<float, 2>
+                 : epl == 4 ? (const void*)k_svd_cluster_t<float, 4>
+                            : (const void*)k_svd_cluster_t<float, 8>;
+    else k = epl == 2 ? (const void*)k_svd_cluster_t<double, 2>
+           : epl == 4 ? (const void*)k_svd_cluster_t<double, 4>
+                      : (const void*)k_svd_cluster_t<double, 8>;
+    launch_svd_kernel(k, CL, need_sys, s, a, 0);
+    return true;
+  }
+  int use_smem = 0;
   size_t smem = 0;
-  if (use_block && need_block <= limit) {
-    bcols = b;
-    smem = need_block;
-  } else {
-    const int slots = (c + CL - 1) / CL;
-    const size_t need = (size_t)2 * slots * c * es + 64;
-    if (need <= limit) {
-      use_smem = slots * c;
-      smem = need;
-    }
+  const int slots = (c + CL - 1) / CL;
+  const size_t need = (size_t)2 * slots * c * es + 64;
+  if (need <= limit) {
+    use_smem = slots * c;
+    smem = need;
   }
   pre_launch(s);
-  if (fp32) launch_cluster2(k_svd_cluster_t<float>, CL, smem, s, a, use_smem, bcols);
-  else launch_cluster2(k_svd_cluster_t<double>, CL, smem, s, a, use_smem, bcols);
+  launch_svd_kernel(fp32 ? (const void*)k_svd_cluster_t<float, 0> : (const void*)k_svd_cluster_t<double, 0>,
+                    CL, smem, s, a, use_smem);
   return true;
 }
