@@ -226,21 +226,54 @@ __device__ __forceinline__ int rr_pos_c(int k, int t, int cp) {
 // the orientation of each pair (lower id first), as in the scalar kernel.
 // The circle has period cp-1, so after each sweep every column is back in
 // its starting slot.  Rows at and beyond c are zero in every register.
+//
+// FP64 (about two FMAs per clock per SM on this GPU) takes two shortcuts
+// that keep the arithmetic but cut the instruction count: the squared
+// column norms travel with the columns and are updated by the exact Jacobi
+// identities |x'|^2 = |x|^2 - t g, |y'|^2 = |y|^2 + t g (recomputed at the
+// start of every sweep and whenever an update cancels more than 99%), so a
+// round computes one dot product instead of three; and the rotation
+// scalars of all pairs of a CTA are computed by one warp, one pair per
+// lane, instead of redundantly by all 32 lanes of every pair's warp.
+template <typename T>
+__device__ __forceinline__ bool jacobi_angle(T al, T be, T ga, T tol, T& cs, T& sn, T& tt) {
+  if (!(ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
+  const T zeta = (be - al) / ((T)2 * ga);
+  tt = copysign((T)1, zeta) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+  cs = (T)1 / sqrt((T)1 + tt * tt);
+  sn = cs * tt;
+  return true;
+}
+
+template <typename T, int EPL>
+__device__ __forceinline__ T warp_dot(const T (&u)[EPL], const T (&v)[EPL]) {
+  T s = 0;
+#pragma unroll
+  for (int e = 0; e < EPL; e++) s += u[e] * v[e];
+  return warp_sum_c(s);
+}
+
 template <typename T, int EPL, typename XC, typename JC>
 __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, T tol, T* box,
                                 int spc, int rank, int* flag_local) {
+  constexpr bool kTrack = sizeof(T) == 8;  // FP64: tracked norms, shared scalars
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cp = c + (c & 1), P = cp / 2;
   const int s = rank * spc + warp;
   const bool active = warp < spc && s < P;
+  const int nact = max(0, min(spc, P - rank * spc));  // active slots of this CTA
   __shared__ int mb_id[2][16][2];
-  constexpr int L = 32 * EPL;                  // mailbox column length
+  __shared__ T mb_nrm[2][16][2];
+  __shared__ T sc_in[16][3];   // (alpha, beta, gamma) per slot, FP64 only
+  __shared__ T sc_out[16][3];  // (cs, sn, t) per slot; t = 0 means no rotation
+  constexpr int L = 32 * EPL;  // mailbox column length
   // box[buf][lslot][which][xj][L]; which 0 = new first column, 1 = new second
   auto mbox = [&](T* base, int buf, int ls, int which, int xj) -> T* {
     return base + ((((size_t)buf * spc + ls) * 2 + which) * 2 + xj) * L;
   };
   T xa[EPL], xb[EPL], ja[EPL], jb[EPL];
   int ida = 2 * s, idb = 2 * s + 1;
+  T na = -1, nb = -1;  // tracked squared norms (negative: recompute)
   if (active) {
 #pragma unroll
     for (int e = 0; e < EPL; e++) {
@@ -259,33 +292,72 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
   T* to_prev = (active && s >= 1) ? cl.map_shared_rank(box, sp_ / spc) : nullptr;
   int* id_next = (active && sn_ < P) ? cl.map_shared_rank(&mb_id[0][0][0], sn_ / spc) : nullptr;
   int* id_prev = (active && s >= 1) ? cl.map_shared_rank(&mb_id[0][0][0], sp_ / spc) : nullptr;
+  T* nr_next = (active && sn_ < P) ? cl.map_shared_rank(&mb_nrm[0][0][0], sn_ / spc) : nullptr;
+  T* nr_prev = (active && s >= 1) ? cl.map_shared_rank(&mb_nrm[0][0][0], sp_ / spc) : nullptr;
   cl.sync();  // every CTA has read its homes before anything is rotated
   for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
     if (threadIdx.x == 0) *flag_local = 0;
+    na = nb = (T)-1;  // exact norms at the start of every sweep
     __syncthreads();
     for (int t = 0; t < cp - 1; t++) {
       const int buf = t & 1;
+      T al = 0, be = 0, ga = 0, cs = 1, sn = 0, tt = 0;
+      bool swp = false, rot = false;
       if (active) {
-        T saa = 0, sbb = 0, sab = 0;
+        swp = ida > idb;  // orientation: lower column id is "x"
+        if constexpr (kTrack) {
+          if (na < (T)0) na = warp_dot<T, EPL>(xa, xa);
+          if (nb < (T)0) nb = warp_dot<T, EPL>(xb, xb);
+          ga = warp_dot<T, EPL>(xa, xb);
+        } else {
+          T saa = 0, sbb = 0, sab = 0;
 #pragma unroll
-        for (int e = 0; e < EPL; e++) {
-          saa += xa[e] * xa[e];
-          sbb += xb[e] * xb[e];
-          sab += xa[e] * xb[e];
-        }
+          for (int e = 0; e < EPL; e++) {
+            saa += xa[e] * xa[e];
+            sbb += xb[e] * xb[e];
+            sab += xa[e] * xb[e];
+          }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          saa += __shfl_xor_sync(0xffffffffu, saa, o);
-          sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
-          sab += __shfl_xor_sync(0xffffffffu, sab, o);
+          for (int o = 16; o > 0; o >>= 1) {
+            saa += __shfl_xor_sync(0xffffffffu, saa, o);
+            sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
+            sab += __shfl_xor_sync(0xffffffffu, sab, o);
+          }
+          na = saa;
+          nb = sbb;
+          ga = sab;
         }
-        const bool swp = ida > idb;  // orientation: lower column id is "x"
-        const T al = swp ? sbb : saa, be = swp ? saa : sbb, ga = sab;
-        if (ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          const T zeta = (be - al) / ((T)2 * ga);
-          const T tt = copysign((T)1, zeta) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-          const T cs = (T)1 / sqrt((T)1 + tt * tt);
-          const T sn = swp ? -(cs * tt) : cs * tt;
+        al = swp ? nb : na;
+        be = swp ? na : nb;
+      }
+      if constexpr (kTrack) {
+        if (active && lane == 0) {
+          sc_in[warp][0] = al;
+          sc_in[warp][1] = be;
+          sc_in[warp][2] = ga;
+        }
+        __syncthreads();
+        if (warp == 0 && lane < nact) {
+          T c_ = 1, s_ = 0, t_ = 0;
+          if (!jacobi_angle<T>(sc_in[lane][0], sc_in[lane][1], sc_in[lane][2], tol, c_, s_, t_))
+            t_ = 0;
+          sc_out[lane][0] = c_;
+          sc_out[lane][1] = s_;
+          sc_out[lane][2] = t_;
+        }
+        __syncthreads();
+        if (active) {
+          cs = sc_out[warp][0];
+          sn = sc_out[warp][1];
+          tt = sc_out[warp][2];
+          rot = tt != (T)0;
+        }
+      } else {
+        if (active) rot = jacobi_angle<T>(al, be, ga, tol, cs, sn, tt);
+      }
+      if (active) {
+        if (rot) {
+          if (swp) sn = -sn;
 #pragma unroll
           for (int e = 0; e < EPL; e++) {
             const T x0 = xa[e], y0 = xb[e];
@@ -294,6 +366,13 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             const T j0 = ja[e], k0 = jb[e];
             ja[e] = cs * j0 - sn * k0;
             jb[e] = sn * j0 + cs * k0;
+          }
+          if constexpr (kTrack) {
+            const T nx = al - tt * ga, ny = be + tt * ga;  // lower-id column, the other
+            const T nxa = swp ? ny : nx, nxb = swp ? nx : ny;
+            const T oa = na, ob = nb;
+            na = (nxa < (T)0.01 * oa) ? (T)-1 : nxa;
+            nb = (nxb < (T)0.01 * ob) ? (T)-1 : nxb;
           }
           if (lane == 0) *flag_local = 1;
         }
@@ -306,7 +385,10 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
               dx[lane + 32 * e] = s == 0 ? xb[e] : xa[e];
               dj[lane + 32 * e] = s == 0 ? jb[e] : ja[e];
             }
-            if (lane == 0) id_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? idb : ida;
+            if (lane == 0) {
+              id_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? idb : ida;
+              nr_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? nb : na;
+            }
           }
           if (to_prev) {  // second column backward
             T* dx = mbox(to_prev, buf, sp_ % spc, 1, 0);
@@ -316,7 +398,10 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
               dx[lane + 32 * e] = xb[e];
               dj[lane + 32 * e] = jb[e];
             }
-            if (lane == 0) id_prev[(buf * 16 + sp_ % spc) * 2 + 1] = idb;
+            if (lane == 0) {
+              id_prev[(buf * 16 + sp_ % spc) * 2 + 1] = idb;
+              nr_prev[(buf * 16 + sp_ % spc) * 2 + 1] = nb;
+            }
           }
         }
       }
@@ -330,6 +415,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             jb[e] = ja[e];
           }
           idb = ida;
+          nb = na;
         }
         if (s >= 1) {  // new first column from slot s-1
           const T* sx = mbox(box, buf, ls, 0, 0);
@@ -340,6 +426,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             ja[e] = sj[lane + 32 * e];
           }
           ida = mb_id[buf][ls][0];
+          na = mb_nrm[buf][ls][0];
         }
         if (s < P - 1) {  // new second column from slot s+1
           const T* sx = mbox(box, buf, ls, 1, 0);
@@ -350,6 +437,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             jb[e] = sj[lane + 32 * e];
           }
           idb = mb_id[buf][ls][1];
+          nb = mb_nrm[buf][ls][1];
         }
       }
     }
@@ -449,15 +537,16 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
   if (badv && a.err) atomicOr(a.err, QTT_DEVERR_NUMERIC);
   cl.sync();
   householder_cl<T>(cl, Tm, Rt, c, tau, diag, sh, rank, CL);
-  // X = R^T (wide) or R (tall) into the home columns; J = I
+  // X = R^T into the home columns (for both orientations: Jacobi on the
+  // columns of R^T needs about half the sweeps of Jacobi on R's columns
+  // here, the preconditioning effect of the QR); J = I
   for (int i = rank; i < c; i += CL) {
     T* x = xcol(i);
     T* jj = jcol(i);
     for (int e = threadIdx.x; e < c; e += blockDim.x) {
-      const int p = wide ? i : e, q = wide ? e : i;  // X(e, i) = R(p, q)
-      T rv = 0;
-      if (p == q) rv = diag[p];
-      else if (p < q) rv = Tm[(size_t)q * Rt + p];
+      T rv = 0;  // X(e, i) = R(i, e)
+      if (i == e) rv = diag[i];
+      else if (i < e) rv = Tm[(size_t)e * Rt + i];
       x[e] = rv;
       jj[e] = (e == i) ? (T)1 : (T)0;
     }
@@ -583,11 +672,14 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
   }
   cl.sync();
   const int r = (int)(*(volatile double*)(tail + c));
-  // Bw = [J_perm ; 0] (wide: V = Q J) or [X_perm ; 0] (tall: U S = Q X), own columns
+  // X J = U_x S with X = R^T.  Wide (M = R^T Q^T): U S = X and V = Q J.
+  // Tall (M = Q R = (Q J) S U_x^T): U S = Q (J S) and V = U_x = X / S.
+  // Bw = [J_perm (times S when tall) ; 0], own columns, then Q applied.
   for (int k = rank; k < r; k += CL) {
-    const T* src = wide ? jcol(perm[k]) : xcol(perm[k]);
+    const T* src = jcol(perm[k]);
+    const T sc = wide ? (T)1 : (T)sig[perm[k]];
     for (int i = threadIdx.x; i < Rt; i += blockDim.x)
-      Bw[(size_t)k * Rt + i] = (i < c) ? src[i] : (T)0;
+      Bw[(size_t)k * Rt + i] = (i < c) ? src[i] * sc : (T)0;
   }
   __syncthreads();
   apply_reflectors_cl<T>(Tm, Rt, c, tau, Bw, r, false, rank, CL);
@@ -599,13 +691,16 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
   const int vrl = dval(a.VT.rows.lact), vcl = dval(a.VT.cols.lact);
   for (int k = rank; k < r; k += CL) {
     const T* xs = xcol(perm[k]);
-    const T* js = jcol(perm[k]);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const double v = wide ? (double)xs[i] : (double)Bw[(size_t)k * Rt + i];
       a.US.ptr[a.usT ? voff(a.US, k, i, url, ucl) : voff(a.US, i, k, url, ucl)] = v;
     }
+    // a zero singular value (all-zero input, or a kept rank above the
+    // numerical rank) leaves a zero row: its U S column is zero as well
+    const double sk = sig[perm[k]];
+    const double inv = sk > 0.0 ? 1.0 / sk : 0.0;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      const double v = wide ? (double)Bw[(size_t)k * Rt + j] : (double)js[j];
+      const double v = wide ? (double)Bw[(size_t)k * Rt + j] : (double)xs[j] * inv;
       a.VT.ptr[a.vtT ? voff(a.VT, j, k, vrl, vcl) : voff(a.VT, k, j, vrl, vcl)] = v;
     }
   }
