@@ -72,6 +72,7 @@ struct SvdArgs {
   long long work_len;  // doubles available at work
   const int* skip;
   int* err;
+  int no_us;  // US is not wanted (cluster kernels skip the work only it needs)
 };
 size_t svd_work_doubles(int mcap, int ncap);
 void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);

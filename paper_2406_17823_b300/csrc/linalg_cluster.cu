@@ -255,7 +255,7 @@ __device__ __forceinline__ T warp_dot(const T (&u)[EPL], const T (&v)[EPL]) {
 
 template <typename T, int EPL, typename XC, typename JC>
 __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, T tol, T* box,
-                                int spc, int rank, int* flag_local) {
+                                int spc, int rank, int* flag_local, bool withJ) {
   constexpr bool kTrack = sizeof(T) == 8;  // FP64: tracked norms, shared scalars
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cp = c + (c & 1), P = cp / 2;
@@ -280,9 +280,9 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
       const int i = lane + 32 * e;
       const bool ok = i < c;
       xa[e] = (ok && ida < c) ? xcol(ida)[i] : (T)0;
-      ja[e] = (ok && ida < c) ? jcol(ida)[i] : (T)0;
+      ja[e] = (withJ && ok && ida < c) ? jcol(ida)[i] : (T)0;
       xb[e] = (ok && idb < c) ? xcol(idb)[i] : (T)0;
-      jb[e] = (ok && idb < c) ? jcol(idb)[i] : (T)0;
+      jb[e] = (withJ && ok && idb < c) ? jcol(idb)[i] : (T)0;
     }
   }
   // destinations are fixed per slot: next slot (as its first column) and
@@ -363,9 +363,14 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             const T x0 = xa[e], y0 = xb[e];
             xa[e] = cs * x0 - sn * y0;
             xb[e] = sn * x0 + cs * y0;
-            const T j0 = ja[e], k0 = jb[e];
-            ja[e] = cs * j0 - sn * k0;
-            jb[e] = sn * j0 + cs * k0;
+          }
+          if (withJ) {
+#pragma unroll
+            for (int e = 0; e < EPL; e++) {
+              const T j0 = ja[e], k0 = jb[e];
+              ja[e] = cs * j0 - sn * k0;
+              jb[e] = sn * j0 + cs * k0;
+            }
           }
           if constexpr (kTrack) {
             const T nx = al - tt * ga, ny = be + tt * ga;  // lower-id column, the other
@@ -381,9 +386,10 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             T* dx = mbox(to_next, buf, sn_ % spc, 0, 0);
             T* dj = mbox(to_next, buf, sn_ % spc, 0, 1);
 #pragma unroll
-            for (int e = 0; e < EPL; e++) {
-              dx[lane + 32 * e] = s == 0 ? xb[e] : xa[e];
-              dj[lane + 32 * e] = s == 0 ? jb[e] : ja[e];
+            for (int e = 0; e < EPL; e++) dx[lane + 32 * e] = s == 0 ? xb[e] : xa[e];
+            if (withJ) {
+#pragma unroll
+              for (int e = 0; e < EPL; e++) dj[lane + 32 * e] = s == 0 ? jb[e] : ja[e];
             }
             if (lane == 0) {
               id_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? idb : ida;
@@ -394,9 +400,10 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             T* dx = mbox(to_prev, buf, sp_ % spc, 1, 0);
             T* dj = mbox(to_prev, buf, sp_ % spc, 1, 1);
 #pragma unroll
-            for (int e = 0; e < EPL; e++) {
-              dx[lane + 32 * e] = xb[e];
-              dj[lane + 32 * e] = jb[e];
+            for (int e = 0; e < EPL; e++) dx[lane + 32 * e] = xb[e];
+            if (withJ) {
+#pragma unroll
+              for (int e = 0; e < EPL; e++) dj[lane + 32 * e] = jb[e];
             }
             if (lane == 0) {
               id_prev[(buf * 16 + sp_ % spc) * 2 + 1] = idb;
@@ -421,9 +428,10 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
           const T* sx = mbox(box, buf, ls, 0, 0);
           const T* sj = mbox(box, buf, ls, 0, 1);
 #pragma unroll
-          for (int e = 0; e < EPL; e++) {
-            xa[e] = sx[lane + 32 * e];
-            ja[e] = sj[lane + 32 * e];
+          for (int e = 0; e < EPL; e++) xa[e] = sx[lane + 32 * e];
+          if (withJ) {
+#pragma unroll
+            for (int e = 0; e < EPL; e++) ja[e] = sj[lane + 32 * e];
           }
           ida = mb_id[buf][ls][0];
           na = mb_nrm[buf][ls][0];
@@ -432,9 +440,10 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
           const T* sx = mbox(box, buf, ls, 1, 0);
           const T* sj = mbox(box, buf, ls, 1, 1);
 #pragma unroll
-          for (int e = 0; e < EPL; e++) {
-            xb[e] = sx[lane + 32 * e];
-            jb[e] = sj[lane + 32 * e];
+          for (int e = 0; e < EPL; e++) xb[e] = sx[lane + 32 * e];
+          if (withJ) {
+#pragma unroll
+            for (int e = 0; e < EPL; e++) jb[e] = sj[lane + 32 * e];
           }
           idb = mb_id[buf][ls][1];
           nb = mb_nrm[buf][ls][1];
@@ -454,11 +463,11 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
       if (i < c) {
         if (ida < c) {
           xcol(ida)[i] = xa[e];
-          jcol(ida)[i] = ja[e];
+          if (withJ) jcol(ida)[i] = ja[e];
         }
         if (idb < c) {
           xcol(idb)[i] = xb[e];
-          jcol(idb)[i] = jb[e];
+          if (withJ) jcol(idb)[i] = jb[e];
         }
       }
     }
@@ -554,13 +563,16 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
   cl.sync();
   const T tol = Prec<T>::cos_tol(c);
   const int cp = c + (c & 1);
+  // J is needed for V = Q J (wide) and for U S = Q J S (tall); a tall
+  // factorisation whose U S is not wanted needs neither J nor Q
+  const bool needJ = wide || !a.no_us;
   const int spc = ((cp / 2) + CL - 1) / CL;
   bool done = false;
   if constexpr (EPL > 0) {
     if (c <= 32 * EPL && spc <= nw && spc <= 16 && !use_smem) {
       // the homes are in global memory and the whole dynamic shared memory
       // holds the mailboxes (sized by the launcher for the capacity shape)
-      jacobi_systolic<T, EPL>(cl, xcol, jcol, c, tol, dsm, spc, rank, &flag_local);
+      jacobi_systolic<T, EPL>(cl, xcol, jcol, c, tol, dsm, spc, rank, &flag_local, needJ);
       done = true;
     }
   }
@@ -675,23 +687,25 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
   // X J = U_x S with X = R^T.  Wide (M = R^T Q^T): U S = X and V = Q J.
   // Tall (M = Q R = (Q J) S U_x^T): U S = Q (J S) and V = U_x = X / S.
   // Bw = [J_perm (times S when tall) ; 0], own columns, then Q applied.
-  for (int k = rank; k < r; k += CL) {
-    const T* src = jcol(perm[k]);
-    const T sc = wide ? (T)1 : (T)sig[perm[k]];
-    for (int i = threadIdx.x; i < Rt; i += blockDim.x)
-      Bw[(size_t)k * Rt + i] = (i < c) ? src[i] * sc : (T)0;
+  if (needJ) {
+    for (int k = rank; k < r; k += CL) {
+      const T* src = jcol(perm[k]);
+      const T sc = wide ? (T)1 : (T)sig[perm[k]];
+      for (int i = threadIdx.x; i < Rt; i += blockDim.x)
+        Bw[(size_t)k * Rt + i] = (i < c) ? src[i] * sc : (T)0;
+    }
+    __syncthreads();
+    apply_reflectors_cl<T>(Tm, Rt, c, tau, Bw, r, false, rank, CL);
   }
-  __syncthreads();
-  apply_reflectors_cl<T>(Tm, Rt, c, tau, Bw, r, false, rank, CL);
   cl.sync();
-  zero_view_cl(a.US, rank, CL);
+  if (!a.no_us) zero_view_cl(a.US, rank, CL);
   zero_view_cl(a.VT, rank, CL);
   cl.sync();
   const int url = dval(a.US.rows.lact), ucl = dval(a.US.cols.lact);
   const int vrl = dval(a.VT.rows.lact), vcl = dval(a.VT.cols.lact);
   for (int k = rank; k < r; k += CL) {
     const T* xs = xcol(perm[k]);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    for (int i = threadIdx.x; i < m && !a.no_us; i += blockDim.x) {
       const double v = wide ? (double)xs[i] : (double)Bw[(size_t)k * Rt + i];
       a.US.ptr[a.usT ? voff(a.US, k, i, url, ucl) : voff(a.US, i, k, url, ucl)] = v;
     }

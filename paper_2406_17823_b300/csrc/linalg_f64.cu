@@ -466,7 +466,11 @@ bool launch_svd_subspace_f32(const SvdArgs& a, int mcap, int ncap, cudaStream_t 
   check_range(a.VT.ptr, view_extent(a.VT), sizeof(double), "svd VT");
   check_range(a.work, (long long)svd_work_doubles(mcap, ncap), sizeof(double), "svd work");
   if ((mcap < ncap ? mcap : ncap) < cluster_threshold()) return false;
-  if (!launch_svd_cluster(a, mcap, ncap, s, true)) return false;
+  // the subspace search only ever wants V^T (both callers recompute the
+  // other factor in FP64)
+  SvdArgs b = a;
+  b.no_us = 1;
+  if (!launch_svd_cluster(b, mcap, ncap, s, true)) return false;
   post_launch("k_svd_cluster_f32", s, svd_flops(mcap, ncap));
   return true;
 }
