@@ -28,6 +28,7 @@ static inline GemmF64 gemm_plain(const double* A, const double* B, double* C, in
 }
 void launch_gemm_f64(const GemmF64& g, cudaStream_t s);
 void launch_scale(const GemmF64& g, cudaStream_t s);  // C = beta C
+void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, cudaStream_t s);
 
 // ---------------------------------------------------------------- QR
 // Householder QR of F = A (or A^T when inT): F = Q R, Q (m x r) with
@@ -73,6 +74,7 @@ struct SvdArgs {
   const int* skip;
   int* err;
   int no_us;  // US is not wanted (cluster kernels skip the work only it needs)
+  int gram;   // M is a Gram matrix B^T B: its singular values are the weights
 };
 size_t svd_work_doubles(int mcap, int ncap);
 void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);

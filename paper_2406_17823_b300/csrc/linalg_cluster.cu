@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) 
         tail[c] = 0.0;
         for (int j = c - 1; j >= 0; j--) {
           const double s = sig[perm[j]];
-          tail[j] = tail[j + 1] + s * s;
+          tail[j] = tail[j + 1] + (a.gram ? s : s * s);
         }
         if (a.total_weight) {  // weight outside M's subspace, counted as discarded
           const double extra = fmax(0.0, *a.total_weight - tail[0]);

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(512) k_svd_f64(SvdArgs a) {
       tail[c] = 0.0;
       for (int j = c - 1; j >= 0; j--) {
         const double s = sig[perm[j]];
-        tail[j] = tail[j + 1] + s * s;
+        tail[j] = tail[j + 1] + (a.gram ? s : s * s);
       }
       if (a.total_weight) {  // weight outside M's subspace, counted as discarded
         const double extra = fmax(0.0, *a.total_weight - tail[0]);
@@ -391,13 +391,13 @@ __global__ void __launch_bounds__(512) k_svd_f64(SvdArgs a) {
   }
   __syncthreads();
   apply_reflectors(T, Rt, Rt, c, tau, Bw, Rt, r, false);
-  zero_view(a.US);
+  if (!a.no_us) zero_view(a.US);
   zero_view(a.VT);
   __syncthreads();
   const int url = dval(a.US.rows.lact), ucl = dval(a.US.cols.lact);
   const int vrl = dval(a.VT.rows.lact), vcl = dval(a.VT.cols.lact);
   // U S (m x r)
-  for (long long e = threadIdx.x; e < (long long)m * r; e += blockDim.x) {
+  for (long long e = threadIdx.x; e < (long long)m * r && !a.no_us; e += blockDim.x) {
     const int i = (int)(e % m), k = (int)(e / m);
     const double v = wide ? X[(size_t)perm[k] * c + i] : Bw[(size_t)k * Rt + i];
     a.US.ptr[a.usT ? view_off(a.US, k, i, url, ucl) : view_off(a.US, i, k, url, ucl)] = v;

@@ -277,6 +277,44 @@ struct MpsPtr {
 
 void gemm(const GemmF64& g, cudaStream_t s) { launch_gemm_f64(g, s); }
 
+// One product whose output has few 64 x 64 tiles but a long K (a Gram
+// matrix of a wide factor): K is cut into slices of at least 128 that run
+// as one batched launch into scratch, summed afterwards in slice order
+// (deterministic).  Plain products only (alpha 1, beta 0, no batch).
+void gemm_splitk(const GemmF64& g, cudaStream_t s) {
+  const int tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  int S = 1;
+  while (tiles * S * 2 <= 2 * 148 && g.K / (S * 2) >= 128) S *= 2;
+  if (S == 1 || g.nb1 * g.nb2 != 1 || g.beta != 0.0 || g.alpha != 1.0) {
+    gemm(g, s);
+    return;
+  }
+  const int chunk = (g.K + S - 1) / S;
+  const int full = g.K / chunk, rem = g.K - full * chunk;
+  const int Sx = full + (rem > 0 ? 1 : 0);
+  DBuf<double> P((size_t)Sx * g.M * g.N, s);
+  GemmF64 b = g;
+  b.C = P.p;
+  b.ldc = g.N;
+  b.K = chunk;
+  b.nb1 = full;
+  b.nb2 = 1;
+  b.sA1 = g.tA ? (long long)chunk * g.lda : chunk;  // A stored K x M (tA) or M x K
+  b.sB1 = g.tB ? chunk : (long long)chunk * g.ldb;  // B stored N x K (tB) or K x N
+  b.sC1 = (long long)g.M * g.N;
+  gemm(b, s);
+  if (rem > 0) {
+    GemmF64 r = b;
+    r.K = rem;
+    r.nb1 = 1;
+    r.A = g.A + full * b.sA1;
+    r.B = g.B + full * b.sB1;
+    r.C = P.p + full * b.sC1;
+    gemm(r, s);
+  }
+  launch_sum_slices(P.p, Sx, g.M, g.N, g.C, g.ldc, s);
+}
+
 // --------------------------------------------------------------- MPO build
 // Carry tensor of App. A, Table "diff_mpo": C[p][so][si][q], p = alpha_m
 // (carry to the more significant site), q = alpha_{m+1} (request from the
@@ -618,11 +656,26 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
         g.tB = 1;
         gemm(g, s);
         launch_sumsq2(Mp, (long long)qcap[k] * 4 * ocap[k + 1], Mp, 0, wM.p, s);
+        // G = B^T B (rpo x rpo, into Rs, free after the gauge QR): its SVD
+        // gives V_B and the weights sigma_B^2 without factoring B itself
+        {
+          GemmF64 gg = gemm_plain(Bm.p, Bm.p, Rs.p, rpo, rpo, qcap[k], rpo, rpo, rpo);
+          gg.tA = 1;
+          gemm_splitk(gg, s);
+        }
         SvdArgs b64 = a;
-        b64.M = MatView{Bm.p, rpo, a.M.rows, axis_prefix(rpo, dref(rp.p))};
+        b64.M = MatView{Rs.p, rpo, axis_prefix(rpo, dref(rp.p)), axis_prefix(rpo, dref(rp.p))};
+        b64.gram = 1;
+        b64.no_us = 1;
         b64.VT = MatView{Vb.p, rpo, axis_prefix(ocap[k], dconst(1)), axis_prefix(rpo, dconst(1))};
         b64.total_weight = wM.p;
-        launch_svd_f64(b64, qcap[k], rpo, s);
+        launch_svd_f64(b64, rpo, rpo, s);
+        // carry U_B S_B = B V_B  (qcap x ocap[k])
+        {
+          GemmF64 gc = gemm_plain(Bm.p, Vb.p, USb.p, qcap[k], ocap[k], rpo, rpo, rpo, ocap[k]);
+          gc.tB = 1;
+          gemm(gc, s);
+        }
         // core = V_B^T V^T  (r x N)
         gemm(gemm_plain(Vb.p, Vt.p, Y->core(k), ocap[k], 4 * ocap[k + 1], rpo, rpo,
                         4 * ocap[k + 1], 4 * ocap[k + 1]), s);
@@ -821,14 +874,30 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
                                ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
         g.tA = 1;
         gemm(g, s);
-        // FP64 SVD of B^T: carry S V_B^T (written transposed), U_B into Ub
+        // G = B B^T (rpo x rpo, into Rs): its SVD gives U_B (into Ub) for
+        // the cap-chi cut without factoring the long B
+        {
+          GemmF64 gg = gemm_plain(Bt.p, Bt.p, Rs.p, rpo, rpo, ca[k + 1] * cb[k + 1],
+                                  ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1], rpo);
+          gg.tB = 1;
+          gemm_splitk(gg, s);
+        }
         SvdArgs b64 = a;
-        b64.M = MatView{Bt.p, ca[k + 1] * cb[k + 1], axis_prefix(rpo, dref(rp.p)), a.M.cols};
-        b64.inT = 1;
+        b64.M = MatView{Rs.p, rpo, axis_prefix(rpo, dref(rp.p)), axis_prefix(rpo, dref(rp.p))};
+        b64.inT = 0;
+        b64.gram = 1;
+        b64.no_us = 1;
         b64.VT = MatView{Ub.p, rcap[k + 1], axis_prefix(rpo, dconst(1)),
                          axis_prefix(rcap[k + 1], dconst(1))};
         b64.vtT = 1;
-        launch_svd_f64(b64, ca[k + 1] * cb[k + 1], rpo, s);
+        launch_svd_f64(b64, rpo, rpo, s);
+        // carry S_B V_B^T = U_B^T B  (r' x (a', b'))
+        {
+          GemmF64 gc = gemm_plain(Ub.p, Bt.p, Rn, rcap[k + 1], ca[k + 1] * cb[k + 1], rpo,
+                                  rcap[k + 1], ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
+          gc.tA = 1;
+          gemm(gc, s);
+        }
         // core = Q U_B  ((r, s) x r')
         gemm(gemm_plain(Ut.p, Ub.p, C->core(k), 4 * rcap[k], rcap[k + 1], rpo, rpo, rcap[k + 1],
                         rcap[k + 1]), s);
