@@ -117,11 +117,14 @@ def measured_peaks():
     return {}
 
 
-def fp64_dgemm_peak(torch, dev):
-    """FP64 peak for the roofline denominator: cuBLAS DGEMM 4096^3 on this GPU
-    (the measured-peaks file carries no FP64 figure); best of 3."""
-    a = torch.randn(4096, 4096, device=dev, dtype=torch.float64)
-    b = torch.randn(4096, 4096, device=dev, dtype=torch.float64)
+def gemm_peak(torch, dev, dtype):
+    """ALU peak for the roofline denominator, measured in this run: cuBLAS
+    GEMM 4096^3 in FP64 (DGEMM) or in FP32 with TF32 off (SGEMM on the FP32
+    pipe); the measured-peaks file carries neither figure.  Best of 3."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    a = torch.randn(4096, 4096, device=dev, dtype=dtype)
+    b = torch.randn(4096, 4096, device=dev, dtype=dtype)
     for _ in range(2):
         a @ b
     torch.cuda.synchronize()
@@ -134,6 +137,7 @@ def fp64_dgemm_peak(torch, dev):
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1) / 1e3)
     del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
     return 2 * 4096 ** 3 / best / 1e12
 
 
@@ -292,14 +296,18 @@ def main():
     dom, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
     tot_ms = sum(v["ms"] for v in prof.values())
     peaks = measured_peaks()
-    fp64_peak = fp64_dgemm_peak(torch, dev)
+    # the dominant kernel's arithmetic type decides the pipe it is bound by:
+    # the FP32 subspace search of the mixed form runs on the FP32 pipe
+    f32_kernel = dom.endswith("_f32")
+    peak = gemm_peak(torch, dev, torch.float32 if f32_kernel else torch.float64)
     avg_ms = rec["ms"] / rec["launches"]
     flops_per_launch = rec["flops"] / rec["launches"]
     achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
-    roofline = {"kernel": dom, "bound": "alu" if args.precision == "fp64" else "tensor",
-                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
-                "peak_source": "FP64 cuBLAS DGEMM 4096^3 measured in this run (of measured)",
+    roofline = {"kernel": dom, "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "peak_source": ("FP32 cuBLAS SGEMM (TF32 off) 4096^3" if f32_kernel else
+                                "FP64 cuBLAS DGEMM 4096^3") + " measured in this run (of measured)",
                 "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
                 "launches_timed": rec["launches"], "avg_launch_ms": avg_ms,
                 "flops_per_launch": flops_per_launch}
@@ -313,7 +321,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "tf32/f64",
+            "dtype": "f64" if args.precision == "fp64" else "f32/f64",
             "data": "synthetic (seeded shear-jet initial condition)",
             "config": {**w, "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)",
