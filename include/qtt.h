@@ -57,8 +57,26 @@ typedef enum {
 
 typedef enum {
   QTT_PREC_FP64 = 0,   /* every contraction and factorisation in FP64      */
-  QTT_PREC_MIXED = 1   /* tensor-core contractions, FP64 gauge / residual  */
+  QTT_PREC_MIXED = 1   /* FP32 subspace search; FP64 gauge QR, projection,
+                          truncation weights and projection residual        */
 } qtt_precision;
+
+/* Learned truncation modes (qtt_params.learned_trunc). */
+typedef enum {
+  QTT_LEARNED_OFF = 0,
+  QTT_LEARNED_LOG = 1,   /* plain FP64 cuts; log each cut's spectrum features  */
+  QTT_LEARNED_ON = 2     /* range-finder cuts of predicted width, plain FP64
+                            truncated SVD as the fallback; also logs           */
+} qtt_learned_mode;
+
+/* The rank predictor: 33 features -> 64 ReLU units -> 1 output (FP32),
+ * parameters packed as W1 (64 x 33, row-major), b1 (64), W2 (64), b2. */
+#define QTT_MLP_FEATURES 33
+#define QTT_MLP_HIDDEN 64
+#define QTT_MLP_PARAMS (QTT_MLP_HIDDEN * QTT_MLP_FEATURES + 2 * QTT_MLP_HIDDEN + 1)
+/* Cuts logged per step (one slot per compression call; later calls of a
+ * step are neither logged nor predicted). */
+#define QTT_LEARNED_SLOTS 512
 
 /* Solver parameters.  Paper defaults (Sec. II.C, App. B): mu = 2.5e5,
  * cg_tol = 1e-5, cg_maxit = 100, sweep_tol = 1e-5. */
@@ -73,6 +91,9 @@ typedef struct {
   double sweep_tol;   /* sweep stop: relative change of sum_i <v_i|v_i>   */
   int max_sweeps;     /* sweep cap per projection                         */
   int precision;      /* qtt_precision                                    */
+  int learned_trunc;  /* qtt_learned_mode; LOG needs QTT_PREC_FP64 (ON
+                         cuts every compression bond in FP64 either way) */
+  int rf_oversample;  /* range-finder width = predicted rank + this (>= 0) */
 } qtt_params;
 
 /* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,
@@ -173,6 +194,53 @@ qtt_status qtt_profile_end(qtt_ctx ctx, char* buf, size_t cap);
  * next synchronisation. */
 qtt_status qtt_to_dense_noalloc(const double* d_cores, const int* bonds, int n,
                                 double* d_field_out, void* cuda_stream);
+
+/* ---------------------------------------------------------------------
+ * Learned truncation (no counterpart in the paper's method; a systems
+ * extension of its compression, Sec. II.C).  Each compression call of a
+ * step gets a slot 0 .. QTT_LEARNED_SLOTS-1 in call order; slots restart at
+ * every qtt_rk4_step (or qtt_learned_next_step).  For every right-to-left
+ * cut the library records 33 features (the top 32 values of
+ * log10(sigma / sigma_1) clipped at -16 and scaled by 1/16, then bond / n)
+ * and the rank kept.  In QTT_LEARNED_ON mode the cut of bond b in slot s
+ * first runs a randomised range finder (Halko, Martinsson and Tropp 2011,
+ * Alg. 4.1) of width min(r + rf_oversample, ...) with r predicted by the
+ * perceptron from the PREVIOUS step's features of (s, b); when the weight
+ * outside the sketch, |M|^2 - |B|^2, exceeds 0.01 eps^2 |M|^2 (or no
+ * features exist yet) the plain truncated SVD overwrites the result.  The test
+ * matrix is SplitMix64 / Box-Muller with key (seed << 40) ^ (s << 8) ^ b,
+ * seed 0.
+ * --------------------------------------------------------------------- */
+
+/* Perceptron parameters (device, QTT_MLP_PARAMS floats) used by
+ * QTT_LEARNED_ON; copied, so the caller's buffer may be reused. */
+qtt_status qtt_learned_set(qtt_ctx ctx, const float* d_params);
+/* Start a new step's slots (qtt_rk4_step does this itself): the current
+ * features become the previous step's. */
+qtt_status qtt_learned_next_step(qtt_ctx ctx);
+/* Copy the current step's log to host memory: h_feat[slot][b][33] and
+ * h_rank[slot][b] for slots < max_slots and b = 0..n (entries without a
+ * cut have rank 0).  Synchronises; *n_slots = slots used so far. */
+qtt_status qtt_learned_log(qtt_ctx ctx, float* h_feat, int* h_rank, int max_slots,
+                           int* n_slots);
+/* Cuts served by the range finder / cuts that fell back, since creation. */
+qtt_status qtt_learned_stats(qtt_ctx ctx, long long* accepted, long long* fell_back);
+/* Gaussian test matrix of the range finder (device, 4*D x w doubles,
+ * row-major, entry (s*D + b, j)) for `key`; for tests of the generator. */
+qtt_status qtt_rf_omega(qtt_ctx ctx, unsigned long long key, int D, int w, double* d_out);
+
+/* Perceptron on device arrays: X (N x 33, row-major), y (N), params
+ * (QTT_MLP_PARAMS).  Forward: out (N).  Loss and gradient of the mean
+ * squared error: grad (QTT_MLP_PARAMS), loss (1 float); deterministic.
+ * Train: `iters` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8) from
+ * zero moments, updating params in place; loss_out (may be NULL) receives
+ * the loss before each step (iters floats). */
+qtt_status qtt_mlp_forward(qtt_ctx ctx, const float* d_params, const float* d_X, int N,
+                           float* d_out);
+qtt_status qtt_mlp_loss_grad(qtt_ctx ctx, const float* d_params, const float* d_X,
+                             const float* d_y, int N, float* d_grad, float* d_loss);
+qtt_status qtt_mlp_train(qtt_ctx ctx, float* d_params, const float* d_X, const float* d_y,
+                         int N, int iters, float lr, float* d_loss_out);
 
 #ifdef __cplusplus
 }

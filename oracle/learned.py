@@ -9,9 +9,10 @@ predicted rank is available, by a randomised range finder (Halko, Martinsson
 and Tropp, SIAM Review 53 (2011), Algorithm 4.1: Y = M Omega, Q = orth(Y),
 B = Q^T M, SVD of the small B) of width w = predicted rank + oversampling.
 The weight of M outside span(Q), |M|_F^2 - |B|_F^2 = |M - Q Q^T M|_F^2, is
-the error estimate: when it exceeds eps^2 |M|_F^2 the bond falls back to the
-full SVD; otherwise the eps rule runs on the singular values of B with that
-outside weight counted as discarded, and chi_max caps the rank.  The
+the error estimate: when it exceeds ACCEPT eps^2 |M|_F^2 (ACCEPT = 0.01: the
+sketch may miss at most 1% of the bond's truncation budget) the bond falls
+back to the full SVD; otherwise the eps rule runs on the singular values of
+B with that outside weight counted as discarded, and chi_max caps the rank.  The
 estimate is a difference of two sums of squares, so its rounding floor is
 about 1e-16 |M|_F^2: the rule is meaningful for eps above about 1e-7 (the
 learned form's workloads use eps = 1e-6).
@@ -49,6 +50,7 @@ N_FEAT = 33
 N_HID = 64
 N_PARAM = N_HID * N_FEAT + N_HID + N_HID + 1
 OMEGA_STRIDE = 1024
+ACCEPT = 0.01
 
 
 # ------------------------------------------------------------ generator
@@ -136,7 +138,7 @@ def compress_rf(cores: list, eps: float, chi_max: int, widths: dict, seed: int =
     b and b+1 counted from 1) with an entry widths[b] = w: there Algorithm
     4.1 runs on the D_b x (4 D_{b+1}) unfolding with key
     bond_key(seed, slot, b); if the outside weight
-    exceeds eps^2 |M|^2 the full SVD is used instead.  `info`, if given,
+    exceeds ACCEPT eps^2 |M|^2 the full SVD is used instead.  `info`, if given,
     receives (bond, used_range_finder, outside, |M|^2) per such bond.
     """
     A = [np.array(c, dtype=np.float64, copy=True) for c in cores]
@@ -154,7 +156,7 @@ def compress_rf(cores: list, eps: float, chi_max: int, widths: dict, seed: int =
         if bond in widths:
             Qm, B, outside = range_finder(M, int(widths[bond]), bond_key(seed, slot, bond))
             nM = float(np.sum(M * M))
-            if not outside > eps * eps * nM:
+            if not outside > ACCEPT * eps * eps * nM:
                 Ub, S, Vt = np.linalg.svd(B, full_matrices=False)
                 r = trunc_rank_total(S, outside, eps, chi_max)
                 A[k] = Vt[:r].reshape(r, d, Dr)

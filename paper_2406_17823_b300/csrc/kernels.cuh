@@ -122,3 +122,19 @@ void launch_cg_start(const CgVec& v, const double* b0, const double* b1, double*
 void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err, cudaStream_t s);
 void launch_sumsq2(const double* a, long long na, const double* b, long long nb, double* out,
                    cudaStream_t s);
+
+// ---------------------------------------------------------------- learned truncation
+void launch_rf_omega(double* O, int Dcap, const int* Dact, int wcap, const int* wact,
+                     unsigned long long key, cudaStream_t s);
+void launch_mlp_forward(const float* P, const float* X, int N, float* out, cudaStream_t s);
+void launch_mlp_grad(const float* P, const float* X, const float* y, int N, float* Z, float* dout,
+                     float* G, float* loss, cudaStream_t s);
+void launch_adam(float* P, const float* G, float* m, float* v, int t, float lr, cudaStream_t s);
+void launch_rf_predict(const float* P, const float* feat, const int* valid, int chi, int over,
+                       int wcap, const int* Dact, const int* Nact4, int* w_out, int* use_rf,
+                       cudaStream_t s);
+void launch_rf_decide(const double* nM, const double* nB, double eps, const int* use_rf,
+                      int* skip_full, double* total, long long* counters, cudaStream_t s);
+void launch_rf_features(const double* sv, const int* skip_full, const int* w, const int* Dact,
+                        const int* Nact4, const int* r, int bond, int n, float* feat, int* rank,
+                        int* valid, cudaStream_t s);

@@ -162,6 +162,18 @@ struct qtt_ctx_s {
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kWorkers] = {};
   cudaStream_t cur = nullptr;  // stream the current operation enqueues on
+  // learned truncation: features / ranks / flags of every cut of the
+  // previous (tab ^ 1) and the current (tab) step, [slot][bond][feature]
+  static constexpr int kSlots = QTT_LEARNED_SLOTS;
+  static constexpr int kBonds = 16;
+  float* d_feat[2] = {nullptr, nullptr};
+  int* d_rank[2] = {nullptr, nullptr};
+  int* d_valid[2] = {nullptr, nullptr};
+  int tab = 0;
+  int slot = 0;
+  float* d_mlp = nullptr;
+  bool mlp_set = false;
+  long long* d_rf_counts = nullptr;  // [0] cuts served by the range finder, [1] fallbacks
 };
 
 namespace {
@@ -571,6 +583,27 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   DBuf<double> Rs(mixed ? rsm : 0, s), Vt(mixed ? vtm : 0, s), Bm(mixed ? bmm : 0, s),
       Vb(mixed ? vbm : 0, s), wM(1, s);
   DBuf<int> rp(1, s);
+  // learned truncation: this call's slot, and the range finder's buffers
+  const int lmode = ctx->p.learned_trunc;
+  const int slot = lmode != QTT_LEARNED_OFF ? ctx->slot++ : -1;
+  const bool logged = slot >= 0 && slot < qtt_ctx_s::kSlots && n < qtt_ctx_s::kBonds;
+  const bool learn = logged && lmode == QTT_LEARNED_ON && ctx->mlp_set && eps > 0.0;
+  const int over = ctx->p.rf_oversample;
+  std::vector<int> wcap(n + 1, 1);
+  size_t om = 1, ym = 1, bbm = 1, ubm = 1, rrm = 1, svm = 1;
+  for (int k = 1; k < n; k++) {
+    wcap[k] = std::max(1, std::min({qcap[k], 4 * ocap[k + 1], chi + over}));
+    om = std::max(om, (size_t)4 * ocap[k + 1] * wcap[k]);
+    ym = std::max(ym, (size_t)qcap[k] * wcap[k]);
+    bbm = std::max(bbm, (size_t)wcap[k] * 4 * ocap[k + 1]);
+    ubm = std::max(ubm, (size_t)wcap[k] * ocap[k]);
+    rrm = std::max(rrm, (size_t)wcap[k] * wcap[k]);
+    svm = std::max(svm, (size_t)std::min(qcap[k], 4 * ocap[k + 1]));
+  }
+  DBuf<double> Om(learn ? om : 0, s), Yr(learn ? ym : 0, s), Qy(learn ? ym : 0, s),
+      Bb(learn ? bbm : 0, s), Ubr(learn ? ubm : 0, s), Rr(learn ? rrm : 0, s),
+      sv(logged ? svm : 0, s), rfd(learn ? 3 : 0, s);
+  DBuf<int> rfi(learn ? 3 : 0, s);  // width, use_rf, skip_full
   // left-to-right QR
   for (int k = 0; k < n - 1; k++) {
     const double* Tp;
@@ -626,8 +659,58 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     a.work = W.p;
     a.work_len = (long long)W.n;
     a.err = ctx->d_err;
+    if (logged) a.sv_out = sv.p;
     bool done = false;
-    if (mixed) {
+    if (learn) {
+      // range finder of predicted width (Halko et al. 2011, Alg. 4.1), then
+      // the plain SVD unless the sketch holds all but eps^2 of the weight
+      const int Wc = wcap[k];
+      const int N4 = 4 * ocap[k + 1];
+      const size_t cell = (size_t)slot * qtt_ctx_s::kBonds + k;
+      const int prev = ctx->tab ^ 1;
+      int* wdev = rfi.p;
+      int* use_rf = rfi.p + 1;
+      int* skip_full = rfi.p + 2;
+      launch_rf_predict(ctx->d_mlp, ctx->d_feat[prev] + cell * QTT_MLP_FEATURES,
+                        ctx->d_valid[prev] + cell, chi, over, Wc, qD.p + k, Y->dims + k + 1, wdev,
+                        use_rf, s);
+      const unsigned long long key = ((unsigned long long)slot << 8) ^ (unsigned long long)k;
+      launch_rf_omega(Om.p, ocap[k + 1], Y->dims + k + 1, Wc, wdev, key, s);
+      gemm(gemm_plain(Mp, Om.p, Yr.p, qcap[k], Wc, N4, N4, Wc, Wc), s);  // Y = M Omega
+      QrArgs q{};
+      q.A = MatView{Yr.p, Wc, axis_prefix(qcap[k], dref(qD.p + k)), axis_prefix(Wc, dref(wdev))};
+      q.Q = MatView{Qy.p, Wc, axis_prefix(qcap[k], dref(qD.p + k)), axis_prefix(Wc, dconst(1))};
+      q.R = MatView{Rr.p, Wc, axis_prefix(Wc, dconst(1)), axis_prefix(Wc, dconst(1))};
+      q.work = W.p;
+      q.work_len = (long long)W.n;
+      q.err = ctx->d_err;
+      launch_qr_f64(q, qcap[k], Wc, s);
+      {
+        GemmF64 g = gemm_plain(Qy.p, Mp, Bb.p, Wc, N4, qcap[k], Wc, N4, N4);  // B = Q^T M
+        g.tA = 1;
+        gemm(g, s);
+      }
+      launch_sumsq2(Mp, (long long)qcap[k] * N4, Mp, 0, rfd.p, s);
+      launch_sumsq2(Bb.p, (long long)Wc * N4, Bb.p, 0, rfd.p + 1, s);
+      launch_rf_decide(rfd.p, rfd.p + 1, eps, use_rf, skip_full, rfd.p + 2, ctx->d_rf_counts, s);
+      SvdArgs b = a;
+      b.M = MatView{Bb.p, N4, axis_prefix(Wc, dref(wdev)), a.M.cols};
+      b.US = MatView{Ubr.p, ocap[k], axis_prefix(Wc, dconst(1)), axis_prefix(ocap[k], dconst(1))};
+      b.total_weight = rfd.p + 2;
+      launch_svd_f64(b, Wc, N4, s);
+      gemm(gemm_plain(Qy.p, Ubr.p, USb.p, qcap[k], ocap[k], Wc, Wc, ocap[k], ocap[k]), s);
+      SvdArgs f = a;
+      f.skip = skip_full;
+      launch_svd_f64(f, qcap[k], N4, s);
+      if (logged) {
+        const int t = ctx->tab;
+        launch_rf_features(sv.p, skip_full, wdev, qD.p + k, Y->dims + k + 1, Y->dims + k, k, n,
+                           ctx->d_feat[t] + cell * QTT_MLP_FEATURES, ctx->d_rank[t] + cell,
+                           ctx->d_valid[t] + cell, s);
+      }
+      done = true;
+    }
+    if (!done && mixed) {
       // Rayleigh-Ritz: FP32 finds an oversampled subspace of right vectors,
       // FP64 orthonormalises it, projects B = M V exactly and makes the
       // (eps, chi) cut by an FP64 SVD of B, counting the weight of M outside
@@ -684,6 +767,13 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     }
     if (!done) {
       launch_svd_f64(a, qcap[k], 4 * ocap[k + 1], s);
+      if (logged) {
+        const size_t cell = (size_t)slot * qtt_ctx_s::kBonds + k;
+        const int t = ctx->tab;
+        launch_rf_features(sv.p, nullptr, nullptr, qD.p + k, Y->dims + k + 1, Y->dims + k, k, n,
+                           ctx->d_feat[t] + cell * QTT_MLP_FEATURES, ctx->d_rank[t] + cell,
+                           ctx->d_valid[t] + cell, s);
+      }
     }
   }
   // first core: Y_0 = Qcore_0 (4 x qcap[1]) * US (qcap[1] x ocap[1])
@@ -1375,9 +1465,20 @@ void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPt
   wk.join({w[0].get(), w[1].get()});
 }
 
+// A new step's slots: the current table becomes the previous one, the new
+// current table starts empty.
+void learned_next_step(qtt_ctx ctx) {
+  ctx->tab ^= 1;
+  ctx->slot = 0;
+  const size_t cells = (size_t)qtt_ctx_s::kSlots * qtt_ctx_s::kBonds;
+  QTT_CUDA_CHECK(cudaMemsetAsync(ctx->d_valid[ctx->tab], 0, cells * sizeof(int), stream_of(ctx)));
+  QTT_CUDA_CHECK(cudaMemsetAsync(ctx->d_rank[ctx->tab], 0, cells * sizeof(int), stream_of(ctx)));
+}
+
 void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
   static const double HS[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   static const double BC[4][2] = {{0, 0}, {3.0, 0.25}, {1.5, 0.625}, {3.0, 0.25}};
+  if (ctx->p.learned_trunc != QTT_LEARNED_OFF) learned_next_step(ctx);
   qtt_mps u[2] = {*u1, *u2};
   MpsPtr U[4][2];
   long long cg_total = 0, sw_total = 0;
@@ -1541,7 +1642,10 @@ qtt_status guarded(qtt_ctx ctx, F&& f) {
 bool valid_params(const qtt_params* p) {
   return p && p->n >= 1 && p->n <= 15 && p->L > 0 && p->eps >= 0 && p->chi_max >= 1 &&
          p->mu >= 0 && p->cg_tol >= 0 && p->cg_maxit >= 1 && p->sweep_tol >= 0 &&
-         p->max_sweeps >= 1 && (p->precision == QTT_PREC_FP64 || p->precision == QTT_PREC_MIXED);
+         p->max_sweeps >= 1 && (p->precision == QTT_PREC_FP64 || p->precision == QTT_PREC_MIXED) &&
+         p->learned_trunc >= QTT_LEARNED_OFF && p->learned_trunc <= QTT_LEARNED_ON &&
+         (p->learned_trunc != QTT_LEARNED_LOG || p->precision == QTT_PREC_FP64) &&
+         p->rf_oversample >= 0 && p->rf_oversample <= 256;
 }
 
 void check_mps(qtt_ctx ctx, qtt_mps m) {
@@ -1575,6 +1679,25 @@ qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* 
     }
     QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
     QTT_CUDA_CHECK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    {
+      const size_t cells = (size_t)qtt_ctx_s::kSlots * qtt_ctx_s::kBonds;
+      for (int t = 0; t < 2; t++) {
+        QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_feat[t], cells * QTT_MLP_FEATURES * sizeof(float)));
+        QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_rank[t], cells * sizeof(int)));
+        QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_valid[t], cells * sizeof(int)));
+        QTT_CUDA_CHECK(cudaMemset(ctx->d_rank[t], 0, cells * sizeof(int)));
+        QTT_CUDA_CHECK(cudaMemset(ctx->d_valid[t], 0, cells * sizeof(int)));
+        reg_alloc(ctx->d_feat[t], cells * QTT_MLP_FEATURES * sizeof(float));
+        reg_alloc(ctx->d_rank[t], cells * sizeof(int));
+        reg_alloc(ctx->d_valid[t], cells * sizeof(int));
+      }
+      QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_mlp, QTT_MLP_PARAMS * sizeof(float)));
+      QTT_CUDA_CHECK(cudaMemset(ctx->d_mlp, 0, QTT_MLP_PARAMS * sizeof(float)));
+      reg_alloc(ctx->d_mlp, QTT_MLP_PARAMS * sizeof(float));
+      QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_rf_counts, 2 * sizeof(long long)));
+      QTT_CUDA_CHECK(cudaMemset(ctx->d_rf_counts, 0, 2 * sizeof(long long)));
+      reg_alloc(ctx->d_rf_counts, 2 * sizeof(long long));
+    }
     const int n = params->n;
     const double dx = ctx->dx;
     HostMpo D1 = diff_mpo(n, 1, dx), D2 = diff_mpo(n, 2, dx);
@@ -1614,6 +1737,18 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) mpo_release(ctx->K[i][j]);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  for (int t = 0; t < 2; t++) {
+    for (void* q : {(void*)ctx->d_feat[t], (void*)ctx->d_rank[t], (void*)ctx->d_valid[t]})
+      if (q) {
+        reg_free(q);
+        cudaFree(q);
+      }
+  }
+  for (void* q : {(void*)ctx->d_mlp, (void*)ctx->d_rf_counts})
+    if (q) {
+      reg_free(q);
+      cudaFree(q);
+    }
   for (int k = 0; k < qtt_ctx_s::kWorkers; k++) {
     if (ctx->workers[k]) cudaStreamDestroy(ctx->workers[k]);
     if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
@@ -1869,6 +2004,113 @@ qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps, long l
   if (sweeps) *sweeps = ctx->sweeps;
   if (launches) *launches = ctx->launches.n;
   return QTT_OK;
+}
+
+// ------------------------------------------------------- learned truncation
+qtt_status qtt_learned_set(qtt_ctx ctx, const float* d_params) {
+  if (!ctx || !d_params) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    QTT_CUDA_CHECK(cudaMemcpyAsync(ctx->d_mlp, d_params, QTT_MLP_PARAMS * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->mlp_set = true;
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_learned_next_step(qtt_ctx ctx) {
+  return guarded(ctx, [&]() -> qtt_status {
+    learned_next_step(ctx);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_learned_log(qtt_ctx ctx, float* h_feat, int* h_rank, int max_slots, int* n_slots) {
+  if (!ctx || max_slots < 0 || (max_slots > 0 && (!h_feat || !h_rank))) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    const int ns = std::min(max_slots, (int)qtt_ctx_s::kSlots);
+    const int nb = ctx->p.n + 1;
+    std::vector<float> f((size_t)qtt_ctx_s::kSlots * qtt_ctx_s::kBonds * QTT_MLP_FEATURES);
+    std::vector<int> r((size_t)qtt_ctx_s::kSlots * qtt_ctx_s::kBonds);
+    const int t = ctx->tab;
+    QTT_CUDA_CHECK(cudaMemcpy(f.data(), ctx->d_feat[t], f.size() * sizeof(float),
+                              cudaMemcpyDeviceToHost));
+    QTT_CUDA_CHECK(cudaMemcpy(r.data(), ctx->d_rank[t], r.size() * sizeof(int),
+                              cudaMemcpyDeviceToHost));
+    for (int sl = 0; sl < ns; sl++)
+      for (int b = 0; b < nb; b++) {
+        const size_t src = (size_t)sl * qtt_ctx_s::kBonds + b, dst = (size_t)sl * nb + b;
+        h_rank[dst] = r[src];
+        for (int j = 0; j < QTT_MLP_FEATURES; j++)
+          h_feat[dst * QTT_MLP_FEATURES + j] = f[src * QTT_MLP_FEATURES + j];
+      }
+    if (n_slots) *n_slots = std::min(ctx->slot, (int)qtt_ctx_s::kSlots);
+    return check_device_errors(ctx);
+  });
+}
+
+qtt_status qtt_learned_stats(qtt_ctx ctx, long long* accepted, long long* fell_back) {
+  return guarded(ctx, [&]() -> qtt_status {
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    long long h[2] = {0, 0};
+    QTT_CUDA_CHECK(cudaMemcpy(h, ctx->d_rf_counts, sizeof h, cudaMemcpyDeviceToHost));
+    if (accepted) *accepted = h[0];
+    if (fell_back) *fell_back = h[1];
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_rf_omega(qtt_ctx ctx, unsigned long long key, int D, int w, double* d_out) {
+  if (!ctx || !d_out || D < 1 || w < 1 || w > 1024) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    reg_alloc(d_out, (size_t)4 * D * w * sizeof(double));  // caller's buffer, this launch only
+    try {
+      launch_rf_omega(d_out, D, nullptr, w, nullptr, key, ctx->stream);
+    } catch (...) {
+      reg_free(d_out);
+      throw;
+    }
+    reg_free(d_out);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_mlp_forward(qtt_ctx ctx, const float* d_params, const float* d_X, int N,
+                           float* d_out) {
+  if (!ctx || !d_params || !d_X || !d_out || N < 0) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    launch_mlp_forward(d_params, d_X, N, d_out, ctx->stream);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_mlp_loss_grad(qtt_ctx ctx, const float* d_params, const float* d_X,
+                             const float* d_y, int N, float* d_grad, float* d_loss) {
+  if (!ctx || !d_params || !d_X || !d_y || !d_grad || !d_loss || N < 1) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    cudaStream_t s = ctx->stream;
+    DBuf<float> Z((size_t)N * QTT_MLP_HIDDEN, s), dout(N, s);
+    launch_mlp_grad(d_params, d_X, d_y, N, Z.p, dout.p, d_grad, d_loss, s);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_mlp_train(qtt_ctx ctx, float* d_params, const float* d_X, const float* d_y, int N,
+                         int iters, float lr, float* d_loss_out) {
+  if (!ctx || !d_params || !d_X || !d_y || N < 1 || iters < 0 || !(lr > 0.0f)) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    cudaStream_t s = ctx->stream;
+    DBuf<float> Z((size_t)N * QTT_MLP_HIDDEN, s), dout(N, s), G(QTT_MLP_PARAMS, s),
+        m(QTT_MLP_PARAMS, s), v(QTT_MLP_PARAMS, s), L(1, s);
+    QTT_CUDA_CHECK(cudaMemsetAsync(m.p, 0, QTT_MLP_PARAMS * sizeof(float), s));
+    QTT_CUDA_CHECK(cudaMemsetAsync(v.p, 0, QTT_MLP_PARAMS * sizeof(float), s));
+    for (int t = 1; t <= iters; t++) {
+      float* lp = d_loss_out ? d_loss_out + (t - 1) : L.p;
+      launch_mlp_grad(d_params, d_X, d_y, N, Z.p, dout.p, G.p, lp, s);
+      launch_adam(d_params, G.p, m.p, v.p, t, lr, s);
+    }
+    return QTT_OK;
+  });
 }
 
 }  // extern "C"

@@ -16,6 +16,13 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqtt_b30
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+LEARNED_OFF = 0
+LEARNED_LOG = 1
+LEARNED_ON = 2
+MLP_FEATURES = 33
+MLP_HIDDEN = 64
+MLP_PARAMS = MLP_HIDDEN * MLP_FEATURES + 2 * MLP_HIDDEN + 1
+LEARNED_SLOTS = 512
 
 STATUS = {0: "QTT_OK", 1: "QTT_ERR_ARG", 2: "QTT_ERR_SHAPE", 3: "QTT_ERR_ALLOC",
           4: "QTT_ERR_CUDA", 5: "QTT_ERR_NOT_CONVERGED", 6: "QTT_ERR_TIMEOUT",
@@ -26,7 +33,9 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_from_dense", "qtt_to_dense", "qtt_mps_from_packed", "qtt_mps_to_packed",
            "qtt_mps_info", "qtt_free_mps", "qtt_mpo_get", "qtt_free_mpo", "qtt_apply_mpo",
            "qtt_add", "qtt_hadamard", "qtt_compress", "qtt_project", "qtt_rk4_step",
-           "qtt_stats", "qtt_profile_begin", "qtt_profile_end", "qtt_to_dense_noalloc")
+           "qtt_stats", "qtt_profile_begin", "qtt_profile_end", "qtt_to_dense_noalloc",
+           "qtt_learned_set", "qtt_learned_next_step", "qtt_learned_log", "qtt_learned_stats",
+           "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train")
 
 
 class QttError(RuntimeError):
@@ -38,7 +47,8 @@ class QttError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("n", c_int), ("L", c_double), ("eps", c_double), ("chi_max", c_int),
                 ("mu", c_double), ("cg_tol", c_double), ("cg_maxit", c_int),
-                ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int)]
+                ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int),
+                ("learned_trunc", c_int), ("rf_oversample", c_int)]
 
 
 _lib = None
@@ -79,6 +89,14 @@ def lib():
             "qtt_profile_begin": (c_int, [vp]),
             "qtt_profile_end": (c_int, [vp, ctypes.c_char_p, c_size_t]),
             "qtt_to_dense_noalloc": (c_int, [vp, ip, c_int, vp, vp]),
+            "qtt_learned_set": (c_int, [vp, vp]),
+            "qtt_learned_next_step": (c_int, [vp]),
+            "qtt_learned_log": (c_int, [vp, vp, vp, c_int, ip]),
+            "qtt_learned_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong)]),
+            "qtt_rf_omega": (c_int, [vp, ctypes.c_ulonglong, c_int, c_int, vp]),
+            "qtt_mlp_forward": (c_int, [vp, vp, vp, c_int, vp]),
+            "qtt_mlp_loss_grad": (c_int, [vp, vp, vp, vp, c_int, vp, vp]),
+            "qtt_mlp_train": (c_int, [vp, vp, vp, vp, c_int, c_int, ctypes.c_float, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -125,6 +143,7 @@ class Context:
     def __init__(self, n: int, L: float = 2 * np.pi, eps: float = 1e-8, chi_max: int = 64,
                  mu: float = 2.5e5, cg_tol: float = 1e-5, cg_maxit: int = 100,
                  sweep_tol: float = 1e-5, max_sweeps: int = 20, precision: int = PREC_FP64,
+                 learned_trunc: int = LEARNED_OFF, rf_oversample: int = 8,
                  device: int = 0, stream=None):
         torch = _torch()
         self.device = device
@@ -132,7 +151,7 @@ class Context:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         self.params = Params(n, L, eps, chi_max, mu, cg_tol, cg_maxit, sweep_tol, max_sweeps,
-                             precision)
+                             precision, learned_trunc, rf_oversample)
         h = c_void_p()
         st = lib().qtt_create(byref(h), device, c_void_p(stream.cuda_stream), byref(self.params))
         if st != 0:
@@ -279,3 +298,61 @@ class Context:
         a, b, c = c_longlong(), c_longlong(), c_longlong()
         self._check(lib().qtt_stats(self.h, byref(a), byref(b), byref(c)))
         return {"cg_iters": a.value, "sweeps": b.value, "launches": c.value}
+
+    # -------------------------------------------------- learned truncation
+    def learned_set(self, params):
+        """Install perceptron parameters (torch float32 tensor on the device)."""
+        self._check(lib().qtt_learned_set(self.h, c_void_p(params.data_ptr())))
+
+    def learned_next_step(self):
+        self._check(lib().qtt_learned_next_step(self.h))
+
+    def learned_log(self, max_slots: int = LEARNED_SLOTS):
+        """(features [slots, n+1, 33], ranks [slots, n+1], slots used)."""
+        nb = self.params.n + 1
+        f = np.zeros((max_slots, nb, MLP_FEATURES), np.float32)
+        r = np.zeros((max_slots, nb), np.int32)
+        ns = c_int()
+        self._check(lib().qtt_learned_log(self.h, c_void_p(f.ctypes.data), c_void_p(r.ctypes.data),
+                                          max_slots, byref(ns)))
+        return f, r, ns.value
+
+    def learned_stats(self):
+        a, b = c_longlong(), c_longlong()
+        self._check(lib().qtt_learned_stats(self.h, byref(a), byref(b)))
+        return a.value, b.value
+
+    def rf_omega(self, key: int, D: int, w: int):
+        torch = _torch()
+        out = torch.empty((4 * D, w), dtype=torch.float64, device=f"cuda:{self.device}")
+        self._check(lib().qtt_rf_omega(self.h, ctypes.c_ulonglong(key), D, w,
+                                       c_void_p(out.data_ptr())))
+        return out
+
+    def mlp_forward(self, params, X):
+        torch = _torch()
+        out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        self._check(lib().qtt_mlp_forward(self.h, c_void_p(params.data_ptr()),
+                                          c_void_p(X.data_ptr()), X.shape[0],
+                                          c_void_p(out.data_ptr())))
+        return out
+
+    def mlp_loss_grad(self, params, X, y):
+        torch = _torch()
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=X.device)
+        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        self._check(lib().qtt_mlp_loss_grad(self.h, c_void_p(params.data_ptr()),
+                                            c_void_p(X.data_ptr()), c_void_p(y.data_ptr()),
+                                            X.shape[0], c_void_p(g.data_ptr()),
+                                            c_void_p(L.data_ptr())))
+        return L, g
+
+    def mlp_train(self, params, X, y, iters: int, lr: float):
+        """Full-batch Adam in place on `params`; returns the loss before each step."""
+        torch = _torch()
+        losses = torch.empty(max(iters, 1), dtype=torch.float32, device=X.device)
+        self._check(lib().qtt_mlp_train(self.h, c_void_p(params.data_ptr()),
+                                        c_void_p(X.data_ptr()), c_void_p(y.data_ptr()),
+                                        X.shape[0], iters, ctypes.c_float(lr),
+                                        c_void_p(losses.data_ptr())))
+        return losses[:iters]

@@ -42,11 +42,13 @@ def test_params_layout_matches_header():
 #include <stddef.h>
 #include "qtt.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(qtt_params),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(qtt_params),
          offsetof(qtt_params, n), offsetof(qtt_params, L), offsetof(qtt_params, eps),
          offsetof(qtt_params, chi_max), offsetof(qtt_params, mu), offsetof(qtt_params, cg_tol),
          offsetof(qtt_params, cg_maxit), offsetof(qtt_params, sweep_tol),
-         offsetof(qtt_params, max_sweeps), offsetof(qtt_params, precision));
+         offsetof(qtt_params, max_sweeps), offsetof(qtt_params, precision),
+         offsetof(qtt_params, learned_trunc), offsetof(qtt_params, rf_oversample),
+         QTT_MLP_PARAMS);
   return 0;
 }
 """
@@ -56,8 +58,11 @@ int main(void) {
         open(c, "w").write(prog)
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         got = list(map(int, subprocess.check_output([exe]).split()))
+    from paper_2406_17823_b300.qtt import MLP_PARAMS
+    from oracle.learned import N_PARAM
     want = [ctypes.sizeof(Params)] + [getattr(Params, f).offset for f, _ in Params._fields_]
-    assert got == want
+    assert got == want + [MLP_PARAMS]
+    assert MLP_PARAMS == N_PARAM
 
 
 def test_null_arguments_are_rejected_without_gpu(libpath):

@@ -74,7 +74,7 @@ def test_fallback_when_the_sketch_misses_weight():
     P = Q.compress(A, 1e-8, 64)
     eps = 1e-8
     for (_, used, outside, nM) in info:
-        assert used == (not outside > eps * eps * nM)
+        assert used == (not outside > Lr.ACCEPT * eps * eps * nM)
     assert any(not u for (_, u, _, _) in info)
     # every bond here needs more than two directions: all fell back
     assert np.linalg.norm(Q.to_dense(R) - Q.to_dense(P)) <= 1e-12 * np.linalg.norm(Q.to_dense(P))
