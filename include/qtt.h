@@ -94,6 +94,8 @@ typedef struct {
   int learned_trunc;  /* qtt_learned_mode; LOG needs QTT_PREC_FP64 (ON
                          cuts every compression bond in FP64 either way) */
   int rf_oversample;  /* range-finder width = predicted rank + this (>= 0) */
+  int rf_min_width;   /* only cuts whose full factor is at least this wide
+                         (capacity) use the range finder (>= 1; 128)      */
 } qtt_params;
 
 /* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,
@@ -206,8 +208,10 @@ qtt_status qtt_to_dense_noalloc(const double* d_cores, const int* bonds, int n,
  * first runs a randomised range finder (Halko, Martinsson and Tropp 2011,
  * Alg. 4.1) of width min(r + rf_oversample, ...) with r predicted by the
  * perceptron from the PREVIOUS step's features of (s, b); when the weight
- * outside the sketch, |M|^2 - |B|^2, exceeds 0.01 eps^2 |M|^2 (or no
- * features exist yet) the plain truncated SVD overwrites the result.  The test
+ * outside the sketch, |M|^2 - |B|^2, exceeds 0.1 eps^2 |M|^2 (or no
+ * features exist yet) the plain truncated SVD overwrites the result.  Only
+ * cuts whose full factor is at least rf_min_width wide (capacity) take this
+ * path; narrower ones keep the plain SVD.  The test
  * matrix is SplitMix64 / Box-Muller with key (seed << 40) ^ (s << 8) ^ b,
  * seed 0.
  * --------------------------------------------------------------------- */

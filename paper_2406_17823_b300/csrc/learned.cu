@@ -165,13 +165,14 @@ __global__ void k_rf_predict(const float* P, const float* feat, const int* valid
 }
 
 // Accept the range finder when its outside weight |M|^2 - |B|^2 is at most
-// 0.01 eps^2 |M|^2 (the sketch misses at most 1% of the bond's truncation
-// budget); skip_full = 1 then (the full SVD that follows is skipped).
+// 0.1 eps^2 |M|^2 (the sketch misses at most a tenth of the bond's
+// truncation budget); skip_full = 1 then (the full SVD that follows is
+// skipped).
 __global__ void k_rf_decide(const double* nM, const double* nB, double eps, const int* use_rf,
                             int* skip_full, double* total, long long* counters) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double m = *nM, outside = fmax(m - *nB, 0.0);
-  const int accept = (*use_rf) && !(outside > 0.01 * eps * eps * m);
+  const int accept = (*use_rf) && !(outside > 0.1 * eps * eps * m);
   *skip_full = accept;
   *total = m;
   if (*use_rf) counters[accept ? 0 : 1] += 1;

@@ -661,7 +661,9 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     a.err = ctx->d_err;
     if (logged) a.sv_out = sv.p;
     bool done = false;
-    if (learn) {
+    // the range finder pays only where the full factor is wide: narrower
+    // cuts keep the plain SVD (and are still logged)
+    if (learn && std::min(qcap[k], 4 * ocap[k + 1]) >= ctx->p.rf_min_width) {
       // range finder of predicted width (Halko et al. 2011, Alg. 4.1), then
       // the plain SVD unless the sketch holds all but eps^2 of the weight
       const int Wc = wcap[k];
@@ -1645,7 +1647,7 @@ bool valid_params(const qtt_params* p) {
          p->max_sweeps >= 1 && (p->precision == QTT_PREC_FP64 || p->precision == QTT_PREC_MIXED) &&
          p->learned_trunc >= QTT_LEARNED_OFF && p->learned_trunc <= QTT_LEARNED_ON &&
          (p->learned_trunc != QTT_LEARNED_LOG || p->precision == QTT_PREC_FP64) &&
-         p->rf_oversample >= 0 && p->rf_oversample <= 256;
+         p->rf_oversample >= 0 && p->rf_oversample <= 256 && p->rf_min_width >= 1;
 }
 
 void check_mps(qtt_ctx ctx, qtt_mps m) {

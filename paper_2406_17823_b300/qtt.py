@@ -48,7 +48,7 @@ class Params(ctypes.Structure):
     _fields_ = [("n", c_int), ("L", c_double), ("eps", c_double), ("chi_max", c_int),
                 ("mu", c_double), ("cg_tol", c_double), ("cg_maxit", c_int),
                 ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int),
-                ("learned_trunc", c_int), ("rf_oversample", c_int)]
+                ("learned_trunc", c_int), ("rf_oversample", c_int), ("rf_min_width", c_int)]
 
 
 _lib = None
@@ -144,6 +144,7 @@ class Context:
                  mu: float = 2.5e5, cg_tol: float = 1e-5, cg_maxit: int = 100,
                  sweep_tol: float = 1e-5, max_sweeps: int = 20, precision: int = PREC_FP64,
                  learned_trunc: int = LEARNED_OFF, rf_oversample: int = 8,
+                 rf_min_width: int = 128,
                  device: int = 0, stream=None):
         torch = _torch()
         self.device = device
@@ -151,7 +152,7 @@ class Context:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         self.params = Params(n, L, eps, chi_max, mu, cg_tol, cg_maxit, sweep_tol, max_sweeps,
-                             precision, learned_trunc, rf_oversample)
+                             precision, learned_trunc, rf_oversample, rf_min_width)
         h = c_void_p()
         st = lib().qtt_create(byref(h), device, c_void_p(stream.cuda_stream), byref(self.params))
         if st != 0:

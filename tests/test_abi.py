@@ -42,13 +42,13 @@ def test_params_layout_matches_header():
 #include <stddef.h>
 #include "qtt.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(qtt_params),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(qtt_params),
          offsetof(qtt_params, n), offsetof(qtt_params, L), offsetof(qtt_params, eps),
          offsetof(qtt_params, chi_max), offsetof(qtt_params, mu), offsetof(qtt_params, cg_tol),
          offsetof(qtt_params, cg_maxit), offsetof(qtt_params, sweep_tol),
          offsetof(qtt_params, max_sweeps), offsetof(qtt_params, precision),
          offsetof(qtt_params, learned_trunc), offsetof(qtt_params, rf_oversample),
-         QTT_MLP_PARAMS);
+         offsetof(qtt_params, rf_min_width), QTT_MLP_PARAMS);
   return 0;
 }
 """

@@ -102,7 +102,8 @@ def test_range_finder_compress_vs_oracle(P, torch, rank):
     n, chi, eps = 7, 32, 1e-6
     u, _ = I.decaying_turbulence(n, 4, seed=1)
     A = Q.from_dense(u[0] + 1e-3 * I.white_field(n, seed=2), 0.0, 64)
-    ctx = P.Context(n, eps=eps, chi_max=chi, learned_trunc=P.LEARNED_ON, rf_oversample=6)
+    ctx = P.Context(n, eps=eps, chi_max=chi, learned_trunc=P.LEARNED_ON, rf_oversample=6,
+                    rf_min_width=1)
     pc = constant_predictor(rank, chi)
     ctx.learned_set(torch.tensor(pc, dtype=torch.float32, device="cuda"))
     # first call: no features yet -> every cut is the full SVD (slot 0)
@@ -183,7 +184,8 @@ def test_trained_predictor_gain(P, torch):
     a, t_plain, _ = run(plain)
     res = {}
     for name, prm in (("trained", pt), ("untrained", p_untrained)):
-        ctx = P.Context(n, eps=eps, chi_max=chi, learned_trunc=P.LEARNED_ON, rf_oversample=8)
+        ctx = P.Context(n, eps=eps, chi_max=chi, learned_trunc=P.LEARNED_ON, rf_oversample=8,
+                        rf_min_width=1)
         ctx.learned_set(prm)
         b, t, served = run(ctx)
         err = max(rel(ctx.to_dense(b[i]).cpu().numpy(), plain.to_dense(a[i]).cpu().numpy())
