@@ -246,6 +246,27 @@ qtt_status qtt_mlp_loss_grad(qtt_ctx ctx, const float* d_params, const float* d_
 qtt_status qtt_mlp_train(qtt_ctx ctx, float* d_params, const float* d_X, const float* d_y,
                          int N, int iters, float lr, float* d_loss_out);
 
+/* ---------------------------------------------------------------------
+ * Batched trajectories (no counterpart in the paper: an ensemble of
+ * independent flows stepped together on one GPU).  A batch owns B contexts,
+ * each with its own parameters (n, chi_max, ... may differ) and its own
+ * non-blocking CUDA stream; qtt_rk4_step_batched runs one RK4 step of every
+ * trajectory at once, one host thread per trajectory, so that the
+ * factorisations of different trajectories occupy the GPU's SMs together.
+ * --------------------------------------------------------------------- */
+typedef struct qtt_batch_s* qtt_batch;
+qtt_status qtt_batch_create(qtt_batch* out, int device, int B, const qtt_params* per_traj);
+qtt_status qtt_batch_destroy(qtt_batch batch);
+/* The context of trajectory i (0 <= i < B), for I/O calls; owned by the
+ * batch (do not destroy).  NULL for an invalid index. */
+qtt_ctx qtt_batch_context(qtt_batch batch, int i);
+/* One RK4 step of every trajectory, in place as qtt_rk4_step: u1s[i],
+ * u2s[i] belong to context i and are replaced by new handles.  Waits for
+ * all trajectories; returns the first status that is not QTT_OK in
+ * trajectory order (QTT_ERR_NOT_CONVERGED included), all results kept. */
+qtt_status qtt_rk4_step_batched(qtt_batch batch, qtt_mps* u1s, qtt_mps* u2s, const double* dts,
+                                const double* nus);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,7 +68,7 @@ struct LaunchCounter {
   long long n = 0;
 };
 extern thread_local LaunchCounter* g_launch_counter;
-extern int* g_dev_err;
+extern thread_local int* g_dev_err;
 // Called after every kernel launch: counts it and, when the environment
 // variable QTT_DEBUG_SYNC is set, waits for it and reports a failure by
 // kernel name (a debugging aid that localises device-side faults).

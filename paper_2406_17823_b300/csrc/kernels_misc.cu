@@ -9,7 +9,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
-int* g_dev_err = nullptr;  // error flag of the context issuing the launch
+thread_local int* g_dev_err = nullptr;  // error flag of the context issuing the launch
 
 namespace {
 

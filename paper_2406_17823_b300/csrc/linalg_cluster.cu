@@ -18,6 +18,8 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -737,8 +739,14 @@ void for_each_svd_kernel(F f) {
   f((const void*)k_svd_cluster_t<float, 8>);
 }
 
+int pick_cluster_size_once();
 int pick_cluster_size() {
-  if (g_cluster_size >= 0) return g_cluster_size;
+  static std::once_flag once;
+  std::call_once(once, [] { pick_cluster_size_once(); });
+  return g_cluster_size;
+}
+
+int pick_cluster_size_once() {
   g_cluster_size = 0;
   const int want[2] = {16, 8};
   for (int w : want) {

@@ -12,7 +12,10 @@
 
 #include <algorithm>
 #include <initializer_list>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -23,6 +26,7 @@ thread_local LaunchCounter* g_launch_counter = nullptr;
 #include <iterator>
 #include <map>
 #include <mutex>
+#include <thread>
 
 namespace {
 std::mutex g_reg_mu;
@@ -39,12 +43,16 @@ struct ProfRec {
   cudaEvent_t e0, e1;
   double flops;
 };
+// Per-launch CUDA events of every context in the process (the recording is
+// shared by host threads under a mutex; each thread keeps its own pending
+// start event, so contexts stepped from different threads do not mix).
 struct Profiler {
   bool on = false;
+  std::mutex mu;
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
-  cudaEvent_t pending = nullptr;
   cudaEvent_t get() {
+    std::lock_guard<std::mutex> g(mu);
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
       pool.pop_back();
@@ -56,21 +64,25 @@ struct Profiler {
   }
 };
 Profiler g_prof;
+thread_local cudaEvent_t t_pending = nullptr;
 }  // namespace
 
 void pre_launch(cudaStream_t s) {
   if (!g_prof.on) return;
-  g_prof.pending = g_prof.get();
-  QTT_CUDA_CHECK(cudaEventRecord(g_prof.pending, s));
+  t_pending = g_prof.get();
+  QTT_CUDA_CHECK(cudaEventRecord(t_pending, s));
 }
 
 void post_launch(const char* name, cudaStream_t s, double flops) {
   count_launch();
-  if (g_prof.on && g_prof.pending) {
+  if (g_prof.on && t_pending) {
     cudaEvent_t e1 = g_prof.get();
     QTT_CUDA_CHECK(cudaEventRecord(e1, s));
-    g_prof.recs.push_back(ProfRec{name, g_prof.pending, e1, flops});
-    g_prof.pending = nullptr;
+    {
+      std::lock_guard<std::mutex> g(g_prof.mu);
+      g_prof.recs.push_back(ProfRec{name, t_pending, e1, flops});
+    }
+    t_pending = nullptr;
   }
   static const bool dbg = getenv("QTT_DEBUG_SYNC") != nullptr;
   if (!dbg) return;
@@ -1956,6 +1968,7 @@ qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
 qtt_status qtt_profile_begin(qtt_ctx ctx) {
   return guarded(ctx, [&]() -> qtt_status {
     QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    std::lock_guard<std::mutex> g(g_prof.mu);
     for (auto& r : g_prof.recs) {
       g_prof.pool.push_back(r.e0);
       g_prof.pool.push_back(r.e1);
@@ -1971,6 +1984,7 @@ qtt_status qtt_profile_end(qtt_ctx ctx, char* buf, size_t cap) {
   return guarded(ctx, [&]() -> qtt_status {
     g_prof.on = false;
     QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    std::lock_guard<std::mutex> g(g_prof.mu);
     struct Agg { long long n = 0; double ms = 0, flops = 0; };
     std::map<std::string, Agg> agg;
     for (auto& r : g_prof.recs) {
@@ -2113,6 +2127,78 @@ qtt_status qtt_mlp_train(qtt_ctx ctx, float* d_params, const float* d_X, const f
     }
     return QTT_OK;
   });
+}
+
+// ---------------------------------------------------------- batched steps
+}  // extern "C"
+
+struct qtt_batch_s {
+  int device = 0;
+  std::vector<qtt_ctx> ctx;
+  std::vector<cudaStream_t> streams;
+};
+
+extern "C" {
+
+qtt_status qtt_batch_create(qtt_batch* out, int device, int B, const qtt_params* per_traj) {
+  if (!out || B < 1 || !per_traj) return QTT_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < B; i++)
+    if (!valid_params(per_traj + i)) return QTT_ERR_ARG;
+  auto b = new qtt_batch_s;
+  b->device = device;
+  qtt_status st = QTT_OK;
+  if (cudaSetDevice(device) != cudaSuccess) st = QTT_ERR_CUDA;
+  for (int i = 0; i < B && st == QTT_OK; i++) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      st = QTT_ERR_CUDA;
+      break;
+    }
+    b->streams.push_back(s);
+    qtt_ctx c = nullptr;
+    st = qtt_create(&c, device, s, per_traj + i);
+    if (st == QTT_OK) b->ctx.push_back(c);
+  }
+  if (st != QTT_OK) {
+    qtt_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return QTT_OK;
+}
+
+qtt_status qtt_batch_destroy(qtt_batch b) {
+  if (!b) return QTT_ERR_ARG;
+  for (qtt_ctx c : b->ctx) qtt_destroy(c);
+  cudaSetDevice(b->device);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  delete b;
+  return QTT_OK;
+}
+
+qtt_ctx qtt_batch_context(qtt_batch b, int i) {
+  if (!b || i < 0 || i >= (int)b->ctx.size()) return nullptr;
+  return b->ctx[i];
+}
+
+qtt_status qtt_rk4_step_batched(qtt_batch b, qtt_mps* u1s, qtt_mps* u2s, const double* dts,
+                                const double* nus) {
+  if (!b || !u1s || !u2s || !dts || !nus) return QTT_ERR_ARG;
+  const int B = (int)b->ctx.size();
+  for (int i = 0; i < B; i++)
+    if (!u1s[i] || !u2s[i] || u1s[i]->ctx != b->ctx[i] || u2s[i]->ctx != b->ctx[i])
+      return QTT_ERR_ARG;
+  std::vector<qtt_status> st(B, QTT_OK);
+  std::vector<std::thread> th;
+  th.reserve(B > 1 ? B - 1 : 0);
+  for (int i = 1; i < B; i++)
+    th.emplace_back([&, i] { st[i] = qtt_rk4_step(b->ctx[i], &u1s[i], &u2s[i], dts[i], nus[i]); });
+  st[0] = qtt_rk4_step(b->ctx[0], &u1s[0], &u2s[0], dts[0], nus[0]);
+  for (auto& t : th) t.join();
+  for (int i = 0; i < B; i++)
+    if (st[i] != QTT_OK) return st[i];
+  return QTT_OK;
 }
 
 }  // extern "C"

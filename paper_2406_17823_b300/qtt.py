@@ -35,7 +35,8 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_add", "qtt_hadamard", "qtt_compress", "qtt_project", "qtt_rk4_step",
            "qtt_stats", "qtt_profile_begin", "qtt_profile_end", "qtt_to_dense_noalloc",
            "qtt_learned_set", "qtt_learned_next_step", "qtt_learned_log", "qtt_learned_stats",
-           "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train")
+           "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
+           "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched")
 
 
 class QttError(RuntimeError):
@@ -97,6 +98,11 @@ def lib():
             "qtt_mlp_forward": (c_int, [vp, vp, vp, c_int, vp]),
             "qtt_mlp_loss_grad": (c_int, [vp, vp, vp, vp, c_int, vp, vp]),
             "qtt_mlp_train": (c_int, [vp, vp, vp, vp, c_int, c_int, ctypes.c_float, vp]),
+            "qtt_batch_create": (c_int, [POINTER(vp), c_int, c_int, POINTER(Params)]),
+            "qtt_batch_destroy": (c_int, [vp]),
+            "qtt_batch_context": (vp, [vp, c_int]),
+            "qtt_rk4_step_batched": (c_int, [vp, POINTER(vp), POINTER(vp), POINTER(c_double),
+                                             POINTER(c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -357,3 +363,65 @@ class Context:
                                         X.shape[0], iters, ctypes.c_float(lr),
                                         c_void_p(losses.data_ptr())))
         return losses[:iters]
+
+
+class _BatchMember(Context):
+    """A context owned by a Batch (created and destroyed by the library)."""
+
+    def __init__(self, batch, handle, params, device):
+        self.batch = batch        # the batch owns the C context: keep it alive
+        self.device = device
+        self.params = params
+        self.h = c_void_p(handle)
+
+    def close(self):
+        self.h = c_void_p(None)   # the batch destroys it
+
+
+class Batch:
+    """B independent trajectories with their own parameters, stepped
+    together by qtt_rk4_step_batched (one host thread per trajectory)."""
+
+    def __init__(self, params_list, device: int = 0):
+        B = len(params_list)
+        arr = (Params * B)()
+        for i, kw in enumerate(params_list):
+            kw = dict(kw)
+            arr[i] = Params(kw.pop("n"), kw.pop("L", 2 * np.pi), kw.pop("eps", 1e-8),
+                            kw.pop("chi_max", 64), kw.pop("mu", 2.5e5), kw.pop("cg_tol", 1e-5),
+                            kw.pop("cg_maxit", 100), kw.pop("sweep_tol", 1e-5),
+                            kw.pop("max_sweeps", 20), kw.pop("precision", PREC_FP64),
+                            kw.pop("learned_trunc", LEARNED_OFF), kw.pop("rf_oversample", 8),
+                            kw.pop("rf_min_width", 128))
+            if kw:
+                raise TypeError(f"unknown parameters {sorted(kw)}")
+        h = c_void_p()
+        st = lib().qtt_batch_create(byref(h), device, B, arr)
+        if st != 0:
+            raise QttError(st, "qtt_batch_create failed")
+        self.h = h
+        self.contexts = [_BatchMember(self, lib().qtt_batch_context(h, i), arr[i], device)
+                         for i in range(B)]
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().qtt_batch_destroy(self.h)
+            self.h = c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rk4_step(self, u1s, u2s, dts, nus):
+        """In place on the MPS objects (u1s[i], u2s[i] of context i)."""
+        B = len(self.contexts)
+        a = (c_void_p * B)(*[m.h.value for m in u1s])
+        b = (c_void_p * B)(*[m.h.value for m in u2s])
+        st = lib().qtt_rk4_step_batched(self.h, a, b, (c_double * B)(*dts), (c_double * B)(*nus))
+        for i in range(B):
+            u1s[i].h, u2s[i].h = c_void_p(a[i]), c_void_p(b[i])
+        if st not in (0, NOT_CONVERGED):
+            raise QttError(st, "qtt_rk4_step_batched failed")
+        return st == 0
