@@ -205,6 +205,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     ap.add_argument("--n", type=int, default=None, help="override grid bits (testing only)")
+    ap.add_argument("--batched", type=int, default=1,
+                    help="B > 1: B trajectories (seeds seed..seed+B-1) stepped together by "
+                         "qtt_rk4_step_batched; value = aggregate steps/s")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -226,10 +229,27 @@ def main():
         w["n"] = args.n
         w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
     prec = P.PREC_FP64 if args.precision == "fp64" else P.PREC_MIXED
-    u, dx, dt = workload_state(w["n"], w["seed"] + rank)
     nu = 1.0 / w["Re"]
-    ctx = P.Context(w["n"], precision=prec, device=local, **solver_kwargs(w))
-    state = [ctx.from_dense(f) for f in u]
+    B = max(1, args.batched)
+    if B > 1:
+        w["workload"] = f"{w['workload']}_x{B}_trajectories"
+        batch = P.Batch([dict(n=w["n"], precision=prec, **solver_kwargs(w)) for _ in range(B)],
+                        device=local)
+        ctxs = batch.contexts
+    else:
+        ctxs = [P.Context(w["n"], precision=prec, device=local, **solver_kwargs(w))]
+    states, dts = [], []
+    for i, c in enumerate(ctxs):
+        u, dx, dt_i = workload_state(w["n"], w["seed"] + rank * B + i)
+        states.append([c.from_dense(f) for f in u])
+        dts.append(dt_i)
+    ctx = ctxs[0]
+
+    def step():
+        if B > 1:
+            return batch.rk4_step([s[0] for s in states], [s[1] for s in states], dts, [nu] * B)
+        return ctx.rk4_step(states[0][0], states[0][1], dts[0], nu)
+
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -238,9 +258,9 @@ def main():
             dist.barrier()
 
     for _ in range(args.warmup):
-        ctx.rk4_step(state[0], state[1], dt, nu)
+        step()
     barrier()
-    launches0 = ctx.stats()["launches"]
+    launches0 = sum(c.stats()["launches"] for c in ctxs)
     ctx.profile_begin()
     times = []
     converged = True
@@ -249,43 +269,53 @@ def main():
         wall0 = time.perf_counter()
         for _ in range(args.steps):
             flush.zero_()  # evict the L2 between timed steps
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            converged &= ctx.rk4_step(state[0], state[1], dt, nu)
-            e1.record()
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
+            if B > 1:
+                # the trajectories run on library-owned streams: device-wide
+                # synchronisation on both sides of the step, host clock
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                converged &= step()
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            else:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                converged &= step()
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
         barrier()
         wall = time.perf_counter() - wall0
+    torch.cuda.synchronize()
     prof = ctx.profile_end()
-    gpu_launches = ctx.stats()["launches"] - launches0
+    gpu_launches = sum(c.stats()["launches"] for c in ctxs) - launches0
     t_local = sum(times)
     t_max = t_local
     if dist is not None:
         tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
-    value = world * args.steps / t_max
+    value = world * B * args.steps / t_max
 
-    # e2e through the C ABI with host buffers: upload the packed state from
-    # pinned memory, one step, download the packed result
-    cores = [ctx.to_cores(s) for s in state]
+    # e2e through the C ABI with host buffers: upload the packed states from
+    # host memory, one step, download the packed results
+    cores = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
     e2e_times, h2d, d2h = [], 0, 0
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
-        host = [c for c in cores]
+        host = cores
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        g = [ctx.from_cores(c) for c in host]
-        ctx.rk4_step(g[0], g[1], dt, nu)
-        out = [ctx.to_cores(x) for x in g]
+        states = [[c.from_cores(x) for x in hc] for c, hc in zip(ctxs, host)]
+        step()
+        out = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
-        h2d = sum(a.nbytes for c in host for a in c)
-        d2h = sum(a.nbytes for c in out for a in c)
+        h2d = sum(a.nbytes for hc in host for cc in hc for a in cc)
+        d2h = sum(a.nbytes for oc in out for cc in oc for a in cc)
         cores = out
-    e2e_value = world * len(e2e_times) / sum(e2e_times) if e2e_times else None
+    e2e_value = world * B * len(e2e_times) / sum(e2e_times) if e2e_times else None
 
     if rank != 0:
         if dist is not None:
@@ -323,7 +353,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32/f64",
             "data": "synthetic (seeded shear-jet initial condition)",
+            "timing": ("CUDA events on the stepping stream" if B == 1 else
+                       "host clock between device-wide synchronisations (library-owned streams)"),
             "config": {**w, "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "trajectories": B,
                        "l2": "flushed between timed steps (256 MB write)",
                        "all_projections_converged": bool(converged)},
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
