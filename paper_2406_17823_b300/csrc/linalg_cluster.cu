@@ -229,14 +229,19 @@ __device__ __forceinline__ int rr_pos_c(int k, int t, int cp) {
 // The circle has period cp-1, so after each sweep every column is back in
 // its starting slot.  Rows at and beyond c are zero in every register.
 //
-// FP64 (about two FMAs per clock per SM on this GPU) takes two shortcuts
+// FP64 (about two FMAs per clock per SM on this GPU) takes three shortcuts
 // that keep the arithmetic but cut the instruction count: the squared
 // column norms travel with the columns and are updated by the exact Jacobi
 // identities |x'|^2 = |x|^2 - t g, |y'|^2 = |y|^2 + t g (recomputed at the
 // start of every sweep and whenever an update cancels more than 99%), so a
-// round computes one dot product instead of three; and the rotation
-// scalars of all pairs of a CTA are computed by one warp, one pair per
-// lane, instead of redundantly by all 32 lanes of every pair's warp.
+// round computes one dot product instead of three; the rotation scalars of
+// all pairs of a CTA are computed by one warp, one pair per lane, instead
+// of redundantly by all 32 lanes of every pair's warp; and the rotations
+// are scaled ("fast" Givens, as in LAPACK's one-sided Jacobi): a column is
+// held as d * x, a rotation updates x by two FMAs per element pair,
+// x_a -= t (d_b / d_a) x_b, x_b += t (d_a / d_b) x_a, and multiplies both
+// scales by cos; the scales (at least cos^(c-1) >= 2^-128 within a sweep)
+// are folded into the columns at every sweep start.
 template <typename T>
 __device__ __forceinline__ bool jacobi_angle(T al, T be, T ga, T tol, T& cs, T& sn, T& tt) {
   if (!(ga != (T)0 && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
@@ -266,8 +271,9 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
   const int nact = max(0, min(spc, P - rank * spc));  // active slots of this CTA
   __shared__ int mb_id[2][16][2];
   __shared__ T mb_nrm[2][16][2];
-  __shared__ T sc_in[16][3];   // (alpha, beta, gamma) per slot, FP64 only
-  __shared__ T sc_out[16][3];  // (cs, sn, t) per slot; t = 0 means no rotation
+  __shared__ T mb_scl[2][16][2];
+  __shared__ T sc_in[16][5];   // (alpha, beta, gamma, d_a, d_b) per slot, FP64 only
+  __shared__ T sc_out[16][4];  // (cs, t d_b / d_a, t d_a / d_b, t); t = 0: no rotation
   constexpr int L = 32 * EPL;  // mailbox column length
   // box[buf][lslot][which][xj][L]; which 0 = new first column, 1 = new second
   auto mbox = [&](T* base, int buf, int ls, int which, int xj) -> T* {
@@ -276,6 +282,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
   T xa[EPL], xb[EPL], ja[EPL], jb[EPL];
   int ida = 2 * s, idb = 2 * s + 1;
   T na = -1, nb = -1;  // tracked squared norms (negative: recompute)
+  T da = 1, db = 1;    // column scales (FP64: the column is d * x)
   if (active) {
 #pragma unroll
     for (int e = 0; e < EPL; e++) {
@@ -296,9 +303,27 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
   int* id_prev = (active && s >= 1) ? cl.map_shared_rank(&mb_id[0][0][0], sp_ / spc) : nullptr;
   T* nr_next = (active && sn_ < P) ? cl.map_shared_rank(&mb_nrm[0][0][0], sn_ / spc) : nullptr;
   T* nr_prev = (active && s >= 1) ? cl.map_shared_rank(&mb_nrm[0][0][0], sp_ / spc) : nullptr;
+  T* sc_next = (active && sn_ < P) ? cl.map_shared_rank(&mb_scl[0][0][0], sn_ / spc) : nullptr;
+  T* sc_prev = (active && s >= 1) ? cl.map_shared_rank(&mb_scl[0][0][0], sp_ / spc) : nullptr;
+  // fold the scales into the columns (FP64)
+  auto fold = [&]() {
+    if constexpr (kTrack) {
+      if (active && (da != (T)1 || db != (T)1)) {
+#pragma unroll
+        for (int e = 0; e < EPL; e++) {
+          xa[e] *= da;
+          xb[e] *= db;
+          ja[e] *= da;
+          jb[e] *= db;
+        }
+      }
+      da = db = (T)1;
+    }
+  };
   cl.sync();  // every CTA has read its homes before anything is rotated
   for (int sweep = 0; sweep < 80 && c > 1; sweep++) {
     if (threadIdx.x == 0) *flag_local = 0;
+    fold();
     na = nb = (T)-1;  // exact norms at the start of every sweep
     __syncthreads();
     for (int t = 0; t < cp - 1; t++) {
@@ -308,9 +333,9 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
       if (active) {
         swp = ida > idb;  // orientation: lower column id is "x"
         if constexpr (kTrack) {
-          if (na < (T)0) na = warp_dot<T, EPL>(xa, xa);
-          if (nb < (T)0) nb = warp_dot<T, EPL>(xb, xb);
-          ga = warp_dot<T, EPL>(xa, xb);
+          if (na < (T)0) na = warp_dot<T, EPL>(xa, xa) * (da * da);
+          if (nb < (T)0) nb = warp_dot<T, EPL>(xb, xb) * (db * db);
+          ga = warp_dot<T, EPL>(xa, xb) * (da * db);
         } else {
           T saa = 0, sbb = 0, sab = 0;
 #pragma unroll
@@ -337,21 +362,29 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
           sc_in[warp][0] = al;
           sc_in[warp][1] = be;
           sc_in[warp][2] = ga;
+          sc_in[warp][3] = da;
+          sc_in[warp][4] = db;
         }
         __syncthreads();
         if (warp == 0 && lane < nact) {
-          T c_ = 1, s_ = 0, t_ = 0;
-          if (!jacobi_angle<T>(sc_in[lane][0], sc_in[lane][1], sc_in[lane][2], tol, c_, s_, t_))
+          T c_ = 1, s_ = 0, t_ = 0, r1 = 0, r2 = 0;
+          if (!jacobi_angle<T>(sc_in[lane][0], sc_in[lane][1], sc_in[lane][2], tol, c_, s_, t_)) {
             t_ = 0;
+          } else {
+            const T d_a = sc_in[lane][3], d_b = sc_in[lane][4];
+            r1 = t_ * (d_b / d_a);
+            r2 = t_ * (d_a / d_b);
+          }
           sc_out[lane][0] = c_;
-          sc_out[lane][1] = s_;
-          sc_out[lane][2] = t_;
+          sc_out[lane][1] = r1;
+          sc_out[lane][2] = r2;
+          sc_out[lane][3] = t_;
         }
         __syncthreads();
         if (active) {
           cs = sc_out[warp][0];
-          sn = sc_out[warp][1];
-          tt = sc_out[warp][2];
+          sn = sc_out[warp][1];  // t d_b / d_a (FP64 scaled form)
+          tt = sc_out[warp][3];
           rot = tt != (T)0;
         }
       } else {
@@ -359,19 +392,41 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
       }
       if (active) {
         if (rot) {
-          if (swp) sn = -sn;
-#pragma unroll
-          for (int e = 0; e < EPL; e++) {
-            const T x0 = xa[e], y0 = xb[e];
-            xa[e] = cs * x0 - sn * y0;
-            xb[e] = sn * x0 + cs * y0;
-          }
-          if (withJ) {
+          if constexpr (kTrack) {
+            // scaled rotation: x_a -= f1 x_b, x_b += f2 x_a (old x_a)
+            const T f1 = swp ? -sn : sn;
+            const T f2 = swp ? -sc_out[warp][2] : sc_out[warp][2];
 #pragma unroll
             for (int e = 0; e < EPL; e++) {
-              const T j0 = ja[e], k0 = jb[e];
-              ja[e] = cs * j0 - sn * k0;
-              jb[e] = sn * j0 + cs * k0;
+              const T x0 = xa[e], y0 = xb[e];
+              xa[e] = fma(-f1, y0, x0);
+              xb[e] = fma(f2, x0, y0);
+            }
+            if (withJ) {
+#pragma unroll
+              for (int e = 0; e < EPL; e++) {
+                const T j0 = ja[e], k0 = jb[e];
+                ja[e] = fma(-f1, k0, j0);
+                jb[e] = fma(f2, j0, k0);
+              }
+            }
+            da *= cs;
+            db *= cs;
+          } else {
+            if (swp) sn = -sn;
+#pragma unroll
+            for (int e = 0; e < EPL; e++) {
+              const T x0 = xa[e], y0 = xb[e];
+              xa[e] = cs * x0 - sn * y0;
+              xb[e] = sn * x0 + cs * y0;
+            }
+            if (withJ) {
+#pragma unroll
+              for (int e = 0; e < EPL; e++) {
+                const T j0 = ja[e], k0 = jb[e];
+                ja[e] = cs * j0 - sn * k0;
+                jb[e] = sn * j0 + cs * k0;
+              }
             }
           }
           if constexpr (kTrack) {
@@ -396,6 +451,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             if (lane == 0) {
               id_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? idb : ida;
               nr_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? nb : na;
+              sc_next[(buf * 16 + sn_ % spc) * 2 + 0] = s == 0 ? db : da;
             }
           }
           if (to_prev) {  // second column backward
@@ -410,6 +466,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
             if (lane == 0) {
               id_prev[(buf * 16 + sp_ % spc) * 2 + 1] = idb;
               nr_prev[(buf * 16 + sp_ % spc) * 2 + 1] = nb;
+              sc_prev[(buf * 16 + sp_ % spc) * 2 + 1] = db;
             }
           }
         }
@@ -425,6 +482,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
           }
           idb = ida;
           nb = na;
+          db = da;
         }
         if (s >= 1) {  // new first column from slot s-1
           const T* sx = mbox(box, buf, ls, 0, 0);
@@ -437,6 +495,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
           }
           ida = mb_id[buf][ls][0];
           na = mb_nrm[buf][ls][0];
+          da = mb_scl[buf][ls][0];
         }
         if (s < P - 1) {  // new second column from slot s+1
           const T* sx = mbox(box, buf, ls, 1, 0);
@@ -449,6 +508,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
           }
           idb = mb_id[buf][ls][1];
           nb = mb_nrm[buf][ls][1];
+          db = mb_scl[buf][ls][1];
         }
       }
     }
@@ -458,6 +518,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
     cl.sync();  // nobody resets its flag before all have read it
     if (!any) break;
   }
+  fold();
   if (active) {
 #pragma unroll
     for (int e = 0; e < EPL; e++) {
@@ -481,7 +542,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
 // working precision: double for the FP64 path; float for the mixed path,
 // whose callers re-orthonormalise the returned factor in FP64.
 template <typename T, int EPL>
-__global__ void __launch_bounds__(512) k_svd_cluster_t(SvdArgs a, int use_smem) {
+__global__ void __launch_bounds__(512, 1) k_svd_cluster_t(SvdArgs a, int use_smem) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
   extern __shared__ double dsm_raw[];
