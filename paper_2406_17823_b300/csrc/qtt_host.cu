@@ -780,7 +780,17 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       }
     }
     if (!done) {
+      // only V^T from the factorisation (for a tall unfolding it needs
+      // neither the rotation accumulator nor Q); the carry U S = M V is an
+      // FP64 product
+      a.no_us = 1;
       launch_svd_f64(a, qcap[k], 4 * ocap[k + 1], s);
+      {
+        GemmF64 gc = gemm_plain(Mp, Y->core(k), USb.p, qcap[k], ocap[k], 4 * ocap[k + 1],
+                                4 * ocap[k + 1], 4 * ocap[k + 1], ocap[k]);
+        gc.tB = 1;
+        gemm(gc, s);
+      }
       if (logged) {
         const size_t cell = (size_t)slot * qtt_ctx_s::kBonds + k;
         const int t = ctx->tab;
@@ -1008,7 +1018,16 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
         done = true;
       }
     }
-    if (!done) launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+    if (!done) {
+      // only the core from the factorisation; the carry S V_T^T = U^T T is
+      // an FP64 product ((r' x (r, s)) x ((r, s) x (a', b')))
+      a.no_us = 1;
+      launch_svd_f64(a, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+      GemmF64 gc = gemm_plain(C->core(k), Tb.p, Rn, rcap[k + 1], ca[k + 1] * cb[k + 1], 4 * rcap[k],
+                              rcap[k + 1], ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
+      gc.tA = 1;
+      gemm(gc, s);
+    }
     std::swap(Rc, Rn);
   }
   return compress_impl(ctx, C.get(), eps, chi);
