@@ -299,7 +299,11 @@ struct MpsPtr {
   qtt_mps operator->() const { return m; }
 };
 
-void gemm(const GemmF64& g, cudaStream_t s) { launch_gemm_f64(g, s); }
+void gemm_splitk(const GemmF64& g, cudaStream_t s);
+
+// Every single product goes through gemm_splitk, which cuts K when the
+// output has too few 64 x 64 tiles to occupy the GPU.
+void gemm(const GemmF64& g, cudaStream_t s) { gemm_splitk(g, s); }
 
 // One product whose output has few 64 x 64 tiles but a long K (a Gram
 // matrix of a wide factor): K is cut into slices of at least 128 that run
@@ -309,8 +313,8 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s) {
   const int tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
   int S = 1;
   while (tiles * S * 2 <= 2 * 148 && g.K / (S * 2) >= 128) S *= 2;
-  if (S == 1 || g.nb1 * g.nb2 != 1 || g.beta != 0.0 || g.alpha != 1.0) {
-    gemm(g, s);
+  if (S == 1 || g.nb1 * g.nb2 != 1 || g.beta != 0.0 || g.alpha != 1.0 || g.skip) {
+    launch_gemm_f64(g, s);
     return;
   }
   const int chunk = (g.K + S - 1) / S;
@@ -326,7 +330,7 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s) {
   b.sA1 = g.tA ? (long long)chunk * g.lda : chunk;  // A stored K x M (tA) or M x K
   b.sB1 = g.tB ? chunk : (long long)chunk * g.ldb;  // B stored N x K (tB) or K x N
   b.sC1 = (long long)g.M * g.N;
-  gemm(b, s);
+  launch_gemm_f64(b, s);
   if (rem > 0) {
     GemmF64 r = b;
     r.K = rem;
@@ -334,7 +338,7 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s) {
     r.A = g.A + full * b.sA1;
     r.B = g.B + full * b.sB1;
     r.C = P.p + full * b.sC1;
-    gemm(r, s);
+    launch_gemm_f64(r, s);
   }
   launch_sum_slices(P.p, Sx, g.M, g.N, g.C, g.ldc, s);
 }
