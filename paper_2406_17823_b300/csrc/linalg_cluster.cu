@@ -252,6 +252,40 @@ __device__ __forceinline__ bool jacobi_angle(T al, T be, T ga, T tol, T& cs, T& 
   return true;
 }
 
+// FP32 (the mixed form's subspace search, latency-bound per round): the
+// same angle with the hardware's approximate reciprocal and reciprocal
+// square root, measured at about a third of the IEEE divide / square-root
+// chain.  The test compares squares (no square roots); one Newton-Raphson
+// step on rsqrt restores cos to full precision, so that cos^2 + sin^2 = 1
+// to rounding and the rotation stays orthogonal (the angle itself only
+// needs to be near the optimum).  Columns below 1e-30 in squared norm, and
+// angles whose zeta would overflow, take the IEEE path.
+template <>
+__device__ __forceinline__ bool jacobi_angle<float>(float al, float be, float ga, float tol,
+                                                   float& cs, float& sn, float& tt) {
+  if (!(ga != 0.0f)) return false;
+  if (al < 1e-30f || be < 1e-30f) {
+    if (!(fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
+  } else if (!(ga * ga > (tol * tol) * (al * be))) {
+    return false;
+  }
+  const float zeta = __fdividef(be - al, 2.0f * ga);
+  const float az = fabsf(zeta);
+  if (az > 1e15f) {
+    tt = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.0f);
+    const float root = q * rsqrtf(q);  // sqrt(1 + zeta^2)
+    tt = copysignf(__fdividef(1.0f, az + root), zeta);
+  }
+  const float x = fmaf(tt, tt, 1.0f);
+  float r = rsqrtf(x);
+  r = r * fmaf(-0.5f * x * r, r, 1.5f);  // Newton-Raphson step for 1/sqrt(x)
+  cs = r;
+  sn = r * tt;
+  return true;
+}
+
 template <typename T, int EPL>
 __device__ __forceinline__ T warp_dot(const T (&u)[EPL], const T (&v)[EPL]) {
   T s = 0;
