@@ -37,6 +37,11 @@ WORKLOAD = dict(workload="shear_jet_2^10_chi64", n=10, chi_max=64, eps=1e-8, Re=
                 cg_tol=1e-5, cg_maxit=100, sweep_tol=1e-5, max_sweeps=20, seed=0,
                 dt_rule="0.1*dx/max|u0|")
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu
+# capture of the widest launch at n = 8 (the same factor shapes as this
+# workload; cold, serialised): profiles/ncu_k_svd_cluster_shear_jet_n8.md.
+# To be re-taken whenever those kernels change.
+NCU_TRAFFIC = {"k_svd_cluster": 520448 + 118272, "k_svd_cluster_f32": 8479232 + 444672}
 
 
 def workload_state(n, seed):
@@ -335,7 +340,10 @@ def main():
     achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
     roofline = {"kernel": dom, "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None,
+                "traffic": NCU_TRAFFIC.get(dom),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the widest "
+                                  "launch (factor 256 wide) at n = 8, same shapes; see profiles/",
                 "peak_source": ("FP32 cuBLAS SGEMM (TF32 off) 4096^3" if f32_kernel else
                                 "FP64 cuBLAS DGEMM 4096^3") + " measured in this run (of measured)",
                 "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
