@@ -28,7 +28,8 @@ static inline GemmF64 gemm_plain(const double* A, const double* B, double* C, in
 }
 void launch_gemm_f64(const GemmF64& g, cudaStream_t s);
 void launch_scale(const GemmF64& g, cudaStream_t s);  // C = beta C
-void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, cudaStream_t s);
+void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, double alpha,
+                       double beta, const int* skip, cudaStream_t s);
 
 // ---------------------------------------------------------------- QR
 // Householder QR of F = A (or A^T when inT): F = Q R, Q (m x r) with

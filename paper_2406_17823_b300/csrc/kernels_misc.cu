@@ -239,15 +239,19 @@ __global__ void __launch_bounds__(1024) k_cg_step(CgVec v, double* scal, int* is
   }
 }
 
-// C = sum over S slices of P (slice z at P + z * M * N, row-major M x N),
-// added in slice order (deterministic), written to C (ld ldc).
-__global__ void k_sum_slices(const double* P, int S, int M, int N, double* C, int ldc) {
+// C = alpha * (sum over S slices of P) + beta * C (slice z at P + z * M * N,
+// row-major M x N), the slices added in order (deterministic); C has ld ldc
+// and is not read when beta == 0.
+__global__ void k_sum_slices(const double* P, int S, int M, int N, double* C, int ldc,
+                             double alpha, double beta, const int* skip) {
+  if (skip && *skip) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)M * N) return;
   const int i = (int)(e / N), j = (int)(e % N);
   double v = 0.0;
   for (int z = 0; z < S; z++) v += P[(long long)z * M * N + e];
-  C[(long long)i * ldc + j] = v;
+  double* c = C + (long long)i * ldc + j;
+  *c = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *c);
 }
 
 __global__ void __launch_bounds__(1024) k_sumsq2(const double* a, long long na, const double* b,
@@ -416,13 +420,15 @@ void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err,
   k_cg_step<<<1, 1024, 0, s>>>(v, scal, ist, maxit, err);
   post_launch("k_cg_step", s);
 }
-void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, cudaStream_t s) {
+void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, double alpha,
+                       double beta, const int* skip, cudaStream_t s) {
   if (M <= 0 || N <= 0 || S <= 0) return;
   check_range(P, (long long)S * M * N, sizeof(double), "sum_slices P");
   check_range(C, (long long)(M - 1) * ldc + N, sizeof(double), "sum_slices C");
   const long long tot = (long long)M * N;
   pre_launch(s);
-  k_sum_slices<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, S, M, N, C, ldc);
+  k_sum_slices<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, S, M, N, C, ldc, alpha, beta,
+                                                                skip);
   post_launch("k_sum_slices", s);
 }
 

@@ -306,14 +306,16 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s);
 void gemm(const GemmF64& g, cudaStream_t s) { gemm_splitk(g, s); }
 
 // One product whose output has few 64 x 64 tiles but a long K (a Gram
-// matrix of a wide factor): K is cut into slices of at least 128 that run
-// as one batched launch into scratch, summed afterwards in slice order
-// (deterministic).  Plain products only (alpha 1, beta 0, no batch).
+// matrix of a wide factor, an environment contraction of the projection):
+// K is cut into slices of at least 128 that run as one batched launch into
+// scratch, then C = alpha * (sum of the slices, in slice order:
+// deterministic) + beta * C.  Single products only (no batch); a skip flag
+// skips both launches.
 void gemm_splitk(const GemmF64& g, cudaStream_t s) {
   const int tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
   int S = 1;
   while (tiles * S * 2 <= 2 * 148 && g.K / (S * 2) >= 128) S *= 2;
-  if (S == 1 || g.nb1 * g.nb2 != 1 || g.beta != 0.0 || g.alpha != 1.0 || g.skip) {
+  if (S == 1 || g.nb1 * g.nb2 != 1) {
     launch_gemm_f64(g, s);
     return;
   }
@@ -324,6 +326,8 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s) {
   GemmF64 b = g;
   b.C = P.p;
   b.ldc = g.N;
+  b.alpha = 1.0;
+  b.beta = 0.0;
   b.K = chunk;
   b.nb1 = full;
   b.nb2 = 1;
@@ -340,7 +344,7 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s) {
     r.C = P.p + full * b.sC1;
     launch_gemm_f64(r, s);
   }
-  launch_sum_slices(P.p, Sx, g.M, g.N, g.C, g.ldc, s);
+  launch_sum_slices(P.p, Sx, g.M, g.N, g.C, g.ldc, g.alpha, g.beta, g.skip, s);
 }
 
 // --------------------------------------------------------------- MPO build
