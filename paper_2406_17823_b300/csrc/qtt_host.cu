@@ -307,14 +307,14 @@ void gemm(const GemmF64& g, cudaStream_t s) { gemm_splitk(g, s); }
 
 // One product whose output has few 64 x 64 tiles but a long K (a Gram
 // matrix of a wide factor, an environment contraction of the projection):
-// K is cut into slices of at least 128 that run as one batched launch into
+// K is cut into slices of at least 32 that run as one batched launch into
 // scratch, then C = alpha * (sum of the slices, in slice order:
 // deterministic) + beta * C.  Single products only (no batch); a skip flag
 // skips both launches.
 void gemm_splitk(const GemmF64& g, cudaStream_t s) {
   const int tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
   int S = 1;
-  while (tiles * S * 2 <= 2 * 148 && g.K / (S * 2) >= 128) S *= 2;
+  while (tiles * S * 2 <= 2 * 148 && g.K / (S * 2) >= 32) S *= 2;
   if (S == 1 || g.nb1 * g.nb2 != 1) {
     launch_gemm_f64(g, s);
     return;
@@ -1061,6 +1061,7 @@ struct Projector {
   // environments per block, per bond
   std::vector<DBuf<double>> LE[2][2], RE[2][2], LW[2], RW[2];
   DBuf<double> t1, t2, rb, tmp, work, vt_i, vt_j, wt;
+  DBuf<double> t1b, t2b;  // scratch of component 1's matvec row (runs beside row 0)
   DBuf<double> cg_r[2], cg_p[2], cg_ap[2], rhs[2];
   DBuf<double> scal;
   DBuf<int> ist;
@@ -1113,6 +1114,8 @@ struct Projector {
     maxcore = cm;
     t1 = DBuf<double>(t1m, s);
     t2 = DBuf<double>(t2m, s);
+    t1b = DBuf<double>(t1m, s);
+    t2b = DBuf<double>(t2m, s);
     int cmax = 1;
     for (int i = 0; i < 2; i++)
       for (int b = 0; b <= n; b++) cmax = std::max(cmax, cap(i)[b]);
@@ -1222,18 +1225,30 @@ struct Projector {
   }
 
   // Y = (1 + c sum_j K_ij) X at site d; X, Y two-component local tensors.
+  // Y_i = X_i + c sum_j (D_i^T D_j block applied to X_j); the two rows i run
+  // on two worker streams (own scratch), joined back into the projection
+  // stream.
   void matvec(int d, double* const X[2], double* const Y[2], const int* skip) {
+    cudaStream_t ps = s;
+    const bool par = ctx->workers[0] != nullptr && ctx->workers[1] != nullptr;
+    if (par) {
+      QTT_CUDA_CHECK(cudaEventRecord(ctx->fork_ev, ps));
+      for (int i = 0; i < 2; i++) QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[i], ctx->fork_ev, 0));
+    }
     for (int i = 0; i < 2; i++) {
+      const cudaStream_t s = par ? ctx->workers[i] : ps;
+      double* const t1p = i == 0 ? t1.p : t1b.p;
+      double* const t2p = i == 0 ? t2.p : t2b.p;
       launch_copy(Y[i], X[i], V[i]->core_size(d), s);
       for (int j = 0; j < 2; j++) {
         qtt_mpo Kij = K[i][j];
         const int wl = Kij->w[d], wr = Kij->w[d + 1];
         const int ci = cap(i)[d], cj = cap(j)[d], ci1 = cap(i)[d + 1], cj1 = cap(j)[d + 1];
-        GemmF64 g1 = gemm_plain(LE[i][j][d].p, X[j], t1.p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1);
+        GemmF64 g1 = gemm_plain(LE[i][j][d].p, X[j], t1p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1);
         g1.skip = skip;
         gemm(g1, s);
         GemmF64 g{};
-        g.A = Kij->k2(d); g.B = t1.p; g.C = t2.p;
+        g.A = Kij->k2(d); g.B = t1p; g.C = t2p;
         g.M = 4 * wr; g.N = cj1; g.K = 4 * wl;
         g.lda = 4 * wl; g.ldb = cj1; g.ldc = cj1;
         g.nb1 = ci; g.nb2 = 1;
@@ -1242,13 +1257,19 @@ struct Projector {
         g.skip = skip;
         gemm(g, s);
         // Y[(a s)][b] += c * T2[(a s)][(q z)] * RE[d+1][b][(q z)]^T
-        GemmF64 g3 = gemm_plain(t2.p, RE[i][j][d + 1].p, Y[i], 4 * ci, ci1, wr * cj1, wr * cj1,
+        GemmF64 g3 = gemm_plain(t2p, RE[i][j][d + 1].p, Y[i], 4 * ci, ci1, wr * cj1, wr * cj1,
                                 wr * cj1, ci1);
         g3.tB = 1;
         g3.alpha = c;
         g3.beta = 1.0;
         g3.skip = skip;
         gemm(g3, s);
+      }
+    }
+    if (par) {
+      for (int i = 0; i < 2; i++) {
+        QTT_CUDA_CHECK(cudaEventRecord(ctx->join_ev[i], ctx->workers[i]));
+        QTT_CUDA_CHECK(cudaStreamWaitEvent(ps, ctx->join_ev[i], 0));
       }
     }
   }
