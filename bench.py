@@ -346,6 +346,13 @@ def main():
                                   "launch (factor 256 wide) at n = 8, same shapes; see profiles/",
                 "peak_source": ("FP32 cuBLAS SGEMM (TF32 off) 4096^3" if f32_kernel else
                                 "FP64 cuBLAS DGEMM 4096^3") + " measured in this run (of measured)",
+                # one launch of the cluster SVD holds a 16-CTA cluster (16 of the 148 SMs)
+                "cluster_sms": 16 if dom.startswith("k_svd_cluster") else None,
+                "frac_of_cluster_peak": (achieved / (peak * 16 / 148)
+                                         if peak and dom.startswith("k_svd_cluster") else None),
+                "flops_source": ("counted on the device (QR, Jacobi dots and rotations, Q "
+                                 "application)" if dom.startswith("k_svd_cluster") else
+                                 "host model"),
                 "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
                 "launches_timed": rec["launches"], "avg_launch_ms": avg_ms,
                 "flops_per_launch": flops_per_launch}

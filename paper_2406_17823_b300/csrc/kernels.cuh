@@ -78,6 +78,9 @@ struct SvdArgs {
   int gram;   // M is a Gram matrix B^T B: its singular values are the weights
 };
 size_t svd_work_doubles(int mcap, int ncap);
+// FLOPs performed by the cluster SVDs since the last reset ([0] FP64, [1] FP32)
+void svd_work_reset();
+void svd_work_read(unsigned long long out[2]);
 void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);
 bool launch_svd_subspace_f32(const SvdArgs& a, int mcap, int ncap, cudaStream_t s);
 

@@ -25,6 +25,19 @@
 
 namespace cg = cooperative_groups;
 
+// Arithmetic actually performed by the cluster SVDs (FLOPs: Householder QR,
+// Jacobi dot products and rotations counted per visit / per rotation, Q
+// application), [0] FP64, [1] FP32; read by the profiler.
+__device__ unsigned long long g_svd_work[2];
+
+void svd_work_reset() {
+  const unsigned long long z[2] = {0, 0};
+  cudaMemcpyToSymbol(g_svd_work, z, sizeof z);
+}
+void svd_work_read(unsigned long long out[2]) {
+  cudaMemcpyFromSymbol(out, g_svd_work, 2 * sizeof(unsigned long long));
+}
+
 namespace {
 
 template <typename T>
@@ -315,6 +328,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
   };
   T xa[EPL], xb[EPL], ja[EPL], jb[EPL];
   int ida = 2 * s, idb = 2 * s + 1;
+  unsigned long long n_dot = 0, n_rot = 0;  // dot products and rotations done
   T na = -1, nb = -1;  // tracked squared norms (negative: recompute)
   T da = 1, db = 1;    // column scales (FP64: the column is d * x)
   if (active) {
@@ -367,10 +381,12 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
       if (active) {
         swp = ida > idb;  // orientation: lower column id is "x"
         if constexpr (kTrack) {
-          if (na < (T)0) na = warp_dot<T, EPL>(xa, xa) * (da * da);
-          if (nb < (T)0) nb = warp_dot<T, EPL>(xb, xb) * (db * db);
+          if (na < (T)0) { na = warp_dot<T, EPL>(xa, xa) * (da * da); n_dot++; }
+          if (nb < (T)0) { nb = warp_dot<T, EPL>(xb, xb) * (db * db); n_dot++; }
           ga = warp_dot<T, EPL>(xa, xb) * (da * db);
+          n_dot++;
         } else {
+          n_dot += 3;
           T saa = 0, sbb = 0, sab = 0;
 #pragma unroll
           for (int e = 0; e < EPL; e++) {
@@ -426,6 +442,7 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
       }
       if (active) {
         if (rot) {
+          n_rot++;
           if constexpr (kTrack) {
             // scaled rotation: x_a -= f1 x_b, x_b += f2 x_a (old x_a)
             const T f1 = swp ? -sn : sn;
@@ -553,6 +570,11 @@ __device__ void jacobi_systolic(cg::cluster_group& cl, XC xcol, JC jcol, int c, 
     if (!any) break;
   }
   fold();
+  if (active && lane == 0) {
+    // per dot 2c; per rotation of X (and J) 4c scaled (FP64) or 6c
+    const unsigned long long rotf = (kTrack ? 4ull : 6ull) * (unsigned long long)c * (withJ ? 2 : 1);
+    atomicAdd(&g_svd_work[sizeof(T) == 4], n_dot * 2ull * c + n_rot * rotf);
+  }
   if (active) {
 #pragma unroll
     for (int e = 0; e < EPL; e++) {
@@ -784,6 +806,12 @@ __global__ void __launch_bounds__(512, 1) k_svd_cluster_t(SvdArgs a, int use_sme
   // X J = U_x S with X = R^T.  Wide (M = R^T Q^T): U S = X and V = Q J.
   // Tall (M = Q R = (Q J) S U_x^T): U S = Q (J S) and V = U_x = X / S.
   // Bw = [J_perm (times S when tall) ; 0], own columns, then Q applied.
+  if (rank == 0 && threadIdx.x == 0) {
+    const double R_ = Rt, c_ = c;
+    double f = 2.0 * R_ * c_ * c_ - 2.0 / 3.0 * c_ * c_ * c_;  // Householder QR
+    if (needJ) f += 4.0 * R_ * c_ * r;                          // Q applied to r columns
+    atomicAdd(&g_svd_work[sizeof(T) == 4], (unsigned long long)f);
+  }
   if (needJ) {
     for (int k = rank; k < r; k += CL) {
       const T* src = jcol(perm[k]);

@@ -2022,6 +2022,7 @@ qtt_status qtt_profile_begin(qtt_ctx ctx) {
       g_prof.pool.push_back(r.e1);
     }
     g_prof.recs.clear();
+    svd_work_reset();
     g_prof.on = true;
     return QTT_OK;
   });
@@ -2046,6 +2047,12 @@ qtt_status qtt_profile_end(qtt_ctx ctx, char* buf, size_t cap) {
       g_prof.pool.push_back(r.e1);
     }
     g_prof.recs.clear();
+    // the cluster SVDs count the arithmetic they actually did (sweeps are
+    // data-dependent); that replaces the host's capacity-shape estimate
+    unsigned long long work[2] = {0, 0};
+    svd_work_read(work);
+    if (agg.count("k_svd_cluster")) agg["k_svd_cluster"].flops = (double)work[0];
+    if (agg.count("k_svd_cluster_f32")) agg["k_svd_cluster_f32"].flops = (double)work[1];
     std::string out = "{";
     bool first = true;
     for (auto& kv : agg) {
