@@ -169,10 +169,12 @@ struct qtt_ctx_s {
   int last_not_converged = 0;
   // worker streams for independent operations of a stage (non-blocking, so
   // the legacy default stream does not serialise them), joined by events
-  static constexpr int kWorkers = 9;
+  static constexpr int kWorkers = 12;
   cudaStream_t workers[kWorkers] = {};
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[kWorkers] = {};
+  static constexpr int kFlowEvents = 16;
+  cudaEvent_t flow_ev[kFlowEvents] = {};  // cross-stream dependencies inside a stage
   cudaStream_t cur = nullptr;  // stream the current operation enqueues on
   // learned truncation: features / ranks / flags of every cut of the
   // previous (tab ^ 1) and the current (tab) step, [slot][bond][feature]
@@ -1465,6 +1467,16 @@ struct Workers {
     ctx->cur = nullptr;
     return out;
   }
+  // cross-stream dependency: worker `to` waits for everything enqueued so far
+  // on worker `from` (an event of the context's pool, reused stage by stage)
+  int nflow = 0;
+  void after(int to, int from) {
+    if (serial || to == from) return;
+    if (nflow >= qtt_ctx_s::kFlowEvents) throw QttError(QTT_ERR_ARG, "flow event pool exhausted");
+    cudaEvent_t e = ctx->flow_ev[nflow++];
+    QTT_CUDA_CHECK(cudaEventRecord(e, ctx->workers[from % qtt_ctx_s::kWorkers]));
+    QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[to % qtt_ctx_s::kWorkers], e, 0));
+  }
   void join(std::initializer_list<qtt_mps> outs) {
     if (serial) return;
     for (int k = 0; k < qtt_ctx_s::kWorkers; k++) {
@@ -1481,50 +1493,56 @@ void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPt
   const int chi = ctx->p.chi_max;
   Workers wk(ctx);
   MpsPtr Db[2][2], P[2][2], Q[2][2], DQ[2][2], Lb[2];
-  // wave 1: D_j b_i, b_j (.) b_i, Lap b_i are independent
+  MpsPtr ca[2], cb[2], conv[2], B[2];
+  // Dataflow over the worker streams: every operation starts as soon as its
+  // own inputs are done (an operation on its input's stream is ordered by
+  // the stream, others wait on an event), instead of wave by wave.
+  //   streams 0-3  D_j b_i -> b_j (.) D_j b_i -> (i: sum over j -> conv -> B -> w)
+  //   streams 4-6  b_j (.) b_i -> D_j (b_j (.) b_i)
+  //   stream  9    D_1 (b_1 (.) b_0) (waits for stream 5)
+  //   streams 7-8  Lap b_i
+  auto sDb = [](int j, int i) { return 2 * i + j; };
   wk.fork();
-  int k = 0;
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++)
-      Db[j][i] = MpsPtr(wk.run(k++, [&] { return apply_impl(ctx, ctx->D[j], b[i], eps, chi); }));
-  Q[0][0] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[0], b[0], eps, chi); }));
-  Q[0][1] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[0], b[1], eps, chi); }));
-  Q[1][1] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[1], b[1], eps, chi); }));
+      Db[j][i] = MpsPtr(wk.run(sDb(j, i), [&] { return apply_impl(ctx, ctx->D[j], b[i], eps, chi); }));
+  Q[0][0] = MpsPtr(wk.run(4, [&] { return hadamard_impl(ctx, b[0], b[0], eps, chi); }));
+  Q[0][1] = MpsPtr(wk.run(5, [&] { return hadamard_impl(ctx, b[0], b[1], eps, chi); }));
+  Q[1][1] = MpsPtr(wk.run(6, [&] { return hadamard_impl(ctx, b[1], b[1], eps, chi); }));
   for (int i = 0; i < 2; i++)
-    Lb[i] = MpsPtr(wk.run(k++, [&] { return apply_impl(ctx, ctx->lap, b[i], eps, chi); }));
-  wk.join({Db[0][0].get(), Db[0][1].get(), Db[1][0].get(), Db[1][1].get(), Q[0][0].get(),
-           Q[0][1].get(), Q[1][1].get(), Lb[0].get(), Lb[1].get()});
-  auto q = [&](int j, int i) { return (j == 1 && i == 0) ? Q[0][1].get() : Q[j][i].get(); };
-  // wave 2: b_j (.) D_j b_i and D_j (b_j (.) b_i)
-  wk.fork();
-  k = 0;
+    Lb[i] = MpsPtr(wk.run(7 + i, [&] { return apply_impl(ctx, ctx->lap, b[i], eps, chi); }));
+  // b_j (.) D_j b_i on the stream of D_j b_i
   for (int i = 0; i < 2; i++)
-    for (int j = 0; j < 2; j++) {
-      P[j][i] = MpsPtr(wk.run(k++, [&] { return hadamard_impl(ctx, b[j], Db[j][i].get(), eps, chi); }));
-      DQ[j][i] = MpsPtr(wk.run(k++, [&] { return apply_impl(ctx, ctx->D[j], q(j, i), eps, chi); }));
-    }
-  wk.join({P[0][0].get(), P[0][1].get(), P[1][0].get(), P[1][1].get(), DQ[0][0].get(),
-           DQ[0][1].get(), DQ[1][0].get(), DQ[1][1].get()});
-  // wave 3: the sums, per component
-  MpsPtr ca[2], cb[2], conv[2], B[2];
-  wk.fork();
+    for (int j = 0; j < 2; j++)
+      P[j][i] = MpsPtr(wk.run(sDb(j, i), [&] { return hadamard_impl(ctx, b[j], Db[j][i].get(), eps, chi); }));
+  // D_j (b_j (.) b_i): q(j, i) is Q00, Q01 (for (0,1) and (1,0)) or Q11
+  wk.after(9, 5);  // before D_0 Q01 is queued on stream 5: waits for Q01 only
+  DQ[0][0] = MpsPtr(wk.run(4, [&] { return apply_impl(ctx, ctx->D[0], Q[0][0].get(), eps, chi); }));
+  DQ[0][1] = MpsPtr(wk.run(5, [&] { return apply_impl(ctx, ctx->D[0], Q[0][1].get(), eps, chi); }));
+  DQ[1][0] = MpsPtr(wk.run(9, [&] { return apply_impl(ctx, ctx->D[1], Q[0][1].get(), eps, chi); }));
+  DQ[1][1] = MpsPtr(wk.run(6, [&] { return apply_impl(ctx, ctx->D[1], Q[1][1].get(), eps, chi); }));
+  // the sums of component i on stream sDb(0, i)
+  const int sDQ[2][2] = {{4, 5}, {9, 6}};  // stream of DQ[j][i]
   for (int i = 0; i < 2; i++) {
-    ca[i] = MpsPtr(wk.run(2 * i, [&] { return add2(ctx, 1.0, P[0][i].get(), 1.0, P[1][i].get()); }));
-    cb[i] = MpsPtr(wk.run(2 * i + 1, [&] { return add2(ctx, 1.0, DQ[0][i].get(), 1.0, DQ[1][i].get()); }));
+    const int si = sDb(0, i);
+    wk.after(si, sDb(1, i));
+    ca[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 1.0, P[0][i].get(), 1.0, P[1][i].get()); }));
+    // D_0 q + D_1 q on the stream of DQ[0][i], after DQ[1][i]
+    wk.after(sDQ[0][i], sDQ[1][i]);
+    cb[i] = MpsPtr(wk.run(sDQ[0][i], [&] { return add2(ctx, 1.0, DQ[0][i].get(), 1.0, DQ[1][i].get()); }));
+    wk.after(si, sDQ[0][i]);
+    conv[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 0.5, ca[i].get(), 0.5, cb[i].get()); }));
+    wk.after(si, 7 + i);
+    B[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 1.0, conv[i].get(), -nu, Lb[i].get()); }));
+    w[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 0.25, u[i], -h, B[i].get()); }));
   }
-  wk.join({ca[0].get(), ca[1].get(), cb[0].get(), cb[1].get()});
-  wk.fork();
-  for (int i = 0; i < 2; i++)
-    conv[i] = MpsPtr(wk.run(i, [&] { return add2(ctx, 0.5, ca[i].get(), 0.5, cb[i].get()); }));
-  wk.join({conv[0].get(), conv[1].get()});
-  wk.fork();
-  for (int i = 0; i < 2; i++)
-    B[i] = MpsPtr(wk.run(i, [&] { return add2(ctx, 1.0, conv[i].get(), -nu, Lb[i].get()); }));
-  wk.join({B[0].get(), B[1].get()});
-  wk.fork();
-  for (int i = 0; i < 2; i++)
-    w[i] = MpsPtr(wk.run(i, [&] { return add2(ctx, 0.25, u[i], -h, B[i].get()); }));
-  wk.join({w[0].get(), w[1].get()});
+  // every worker joins the context stream; all outputs and intermediates
+  // are then released on it
+  wk.join({Db[0][0].get(), Db[0][1].get(), Db[1][0].get(), Db[1][1].get(), Q[0][0].get(),
+           Q[0][1].get(), Q[1][1].get(), Lb[0].get(), Lb[1].get(), P[0][0].get(), P[0][1].get(),
+           P[1][0].get(), P[1][1].get(), DQ[0][0].get(), DQ[0][1].get(), DQ[1][0].get(),
+           DQ[1][1].get(), ca[0].get(), ca[1].get(), cb[0].get(), cb[1].get(), conv[0].get(),
+           conv[1].get(), B[0].get(), B[1].get(), w[0].get(), w[1].get()});
 }
 
 // A new step's slots: the current table becomes the previous one, the new
@@ -1740,6 +1758,8 @@ qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* 
       QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming));
     }
     QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+    for (int e = 0; e < qtt_ctx_s::kFlowEvents; e++)
+      QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->flow_ev[e], cudaEventDisableTiming));
     QTT_CUDA_CHECK(cudaMemset(ctx->d_err, 0, sizeof(int)));
     {
       const size_t cells = (size_t)qtt_ctx_s::kSlots * qtt_ctx_s::kBonds;
@@ -1816,6 +1836,8 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
     if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (int e = 0; e < qtt_ctx_s::kFlowEvents; e++)
+    if (ctx->flow_ev[e]) cudaEventDestroy(ctx->flow_ev[e]);
   delete ctx;
   return QTT_OK;
 }
