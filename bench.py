@@ -174,12 +174,27 @@ def _oracle_stage_child(wjson):
     print(time.perf_counter() - t)
 
 
+# ------------------------------------------------------------------ ranks
+def reduce_max_time(t_local, dist=None, device="cpu"):
+    """The timed region of a multi-rank run: the maximum over ranks of each
+    rank's own time (seconds); the local time when there is one rank."""
+    if dist is None:
+        return t_local
+    import torch
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     w = dict(WORKLOAD)
+    if args.n:
+        w["n"] = args.n
+        w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
     total = 0.0
     for _ in range(args.steps):  # no warm-up: the CPU oracle has no warm-up effects
         total += oracle_stage_seconds(w)
@@ -209,7 +224,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
-    ap.add_argument("--n", type=int, default=None, help="override grid bits (testing only)")
+    ap.add_argument("--grid-bits", "--n", dest="n", type=int, default=None,
+                    help="override grid bits (testing only; under torchrun use --grid-bits)")
     ap.add_argument("--batched", type=int, default=1,
                     help="B > 1: B trajectories (seeds seed..seed+B-1) stepped together by "
                          "qtt_rk4_step_batched; value = aggregate steps/s")
@@ -296,11 +312,7 @@ def main():
     prof = ctx.profile_end()
     gpu_launches = sum(c.stats()["launches"] for c in ctxs) - launches0
     t_local = sum(times)
-    t_max = t_local
-    if dist is not None:
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = reduce_max_time(t_local, dist, dev)
     value = world * B * args.steps / t_max
 
     # e2e through the C ABI with host buffers: upload the packed states from
