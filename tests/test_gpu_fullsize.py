@@ -1,0 +1,62 @@
+"""Parity at the bench's full size (2^10 x 2^10, chi = 64, eps = 1e-8), op by op.
+
+A whole RK4 step of the oracle at this size takes minutes, so the step's
+operations are compared one at a time on the bench workload's own state
+(the seeded shear jet): the TT-SVD of the initial field, the derivative and
+Laplacian MPO applications, the Hadamard product of the convection term and
+a block-diagonal sum, each against the FP64 oracle to 1e-10 relative L2 on
+the reconstructed dense fields.
+"""
+import numpy as np
+import pytest
+
+import qtt_inputs as I
+from oracle import qtt as Q
+
+pytestmark = pytest.mark.gpu
+N_BITS, CHI, EPS, TOL = 10, 64, 1e-8, 1e-10
+
+
+@pytest.fixture(scope="module")
+def state():
+    import paper_2406_17823_b300 as P
+    (u, v), dx = I.shear_jet(N_BITS, seed=0)
+    ctx = P.Context(N_BITS, eps=EPS, chi_max=CHI)
+    A = Q.from_dense(u, EPS, CHI)
+    B = Q.from_dense(v, EPS, CHI)
+    ops = Q.build_operators(N_BITS, dx)
+    return ctx, (u, v), A, B, ops
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_from_dense_full_size(state):
+    ctx, (u, v), A, B, ops = state
+    g = ctx.from_dense(u)
+    assert rel(ctx.to_dense(g).cpu().numpy(), Q.to_dense(A)) <= TOL
+    assert max(g.bonds) <= CHI
+
+
+@pytest.mark.parametrize("which", [1, 3])
+def test_apply_full_size(state, which):
+    ctx, _, A, B, ops = state
+    W = ops.D[0] if which == 1 else ops.lap
+    g = ctx.apply_mpo(which, ctx.from_cores(A))
+    o = Q.apply_mpo(W, A, EPS, CHI)
+    assert rel(ctx.to_dense(g).cpu().numpy(), Q.to_dense(o)) <= TOL
+
+
+def test_hadamard_full_size(state):
+    ctx, _, A, B, ops = state
+    g = ctx.hadamard(ctx.from_cores(A), ctx.from_cores(B))
+    o = Q.hadamard(A, B, EPS, CHI)
+    assert rel(ctx.to_dense(g).cpu().numpy(), Q.to_dense(o)) <= TOL
+
+
+def test_add_full_size(state):
+    ctx, _, A, B, ops = state
+    g = ctx.add([0.25, -3e-4], [ctx.from_cores(A), ctx.from_cores(B)])
+    o = Q.add([0.25, -3e-4], [A, B], EPS, CHI)
+    assert rel(ctx.to_dense(g).cpu().numpy(), Q.to_dense(o)) <= TOL
