@@ -126,7 +126,11 @@ class MPS:
 
     def free(self):
         if self.h and self.h.value:
-            lib().qtt_free_mps(self.h)
+            # after its context is gone (interpreter shutdown tears objects
+            # down in any order) the device memory went with the context
+            ctx_h = getattr(self.ctx, "h", None)
+            if ctx_h is not None and ctx_h.value:
+                lib().qtt_free_mps(self.h)
             self.h = c_void_p(None)
 
     def __del__(self):
@@ -405,6 +409,8 @@ class Batch:
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
+            for c in getattr(self, "contexts", []):
+                c.h = c_void_p(None)   # MPS of these contexts no longer free themselves
             lib().qtt_batch_destroy(self.h)
             self.h = c_void_p(None)
 
