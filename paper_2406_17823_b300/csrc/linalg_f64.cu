@@ -421,7 +421,7 @@ size_t qr_work_doubles(int mcap, int ccap) {
   return (size_t)mcap * ccap + (size_t)mcap * r + 2 * (size_t)ccap + 8;
 }
 
-bool launch_qr_cluster(const QrArgs& a, cudaStream_t s);
+bool launch_qr_cluster(const QrArgs& a, int mcap, cudaStream_t s);
 bool launch_svd_cluster(const SvdArgs& a, int mcap, int ncap, cudaStream_t s, bool fp32);
 
 // Problems at least this large (capacity of the square factor) go to the
@@ -442,7 +442,7 @@ void launch_qr_f64(const QrArgs& a, int mcap, int ccap, cudaStream_t s) {
   check_range(a.work, (long long)qr_work_doubles(mcap, ccap), sizeof(double), "qr work");
   const double fm = mcap, fc = ccap < mcap ? ccap : mcap;
   const double flops = 4.0 * fm * fc * fc - 4.0 / 3.0 * fc * fc * fc;
-  if ((ccap < mcap ? ccap : mcap) >= cluster_threshold() && launch_qr_cluster(a, s)) {
+  if ((ccap < mcap ? ccap : mcap) >= cluster_threshold() && launch_qr_cluster(a, mcap, s)) {
     post_launch("k_qr_cluster", s, flops);
     return;
   }
