@@ -226,6 +226,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     ap.add_argument("--grid-bits", "--n", dest="n", type=int, default=None,
                     help="override grid bits (testing only; under torchrun use --grid-bits)")
+    ap.add_argument("--tight", action="store_true",
+                    help="CG and sweep tolerances 1e-12, CG cap 500, instead of the paper's "
+                         "1e-5 / 1e-5 / 100")
     ap.add_argument("--batched", type=int, default=1,
                     help="B > 1: B trajectories (seeds seed..seed+B-1) stepped together by "
                          "qtt_rk4_step_batched; value = aggregate steps/s")
@@ -249,6 +252,9 @@ def main():
     if args.n:
         w["n"] = args.n
         w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
+    if args.tight:
+        w.update(cg_tol=1e-12, sweep_tol=1e-12, cg_maxit=500)
+        w["workload"] += "_tight"
     prec = P.PREC_FP64 if args.precision == "fp64" else P.PREC_MIXED
     nu = 1.0 / w["Re"]
     B = max(1, args.batched)

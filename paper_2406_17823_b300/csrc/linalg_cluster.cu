@@ -1082,22 +1082,6 @@ int pick_cluster_size_once() {
   return g_cluster_size;
 }
 
-template <typename K, typename Args>
-void launch_cluster(K kern, int CL, size_t smem, cudaStream_t s, Args a) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CL);
-  cfg.blockDim = dim3(512);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  QTT_CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, a));
-}
 
 // shared-memory scratch of the blocked Householder: up to 16 panel columns
 // of mcap rows, within the 200 KB the kernels are configured for
