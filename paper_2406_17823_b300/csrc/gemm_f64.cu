@@ -3,8 +3,9 @@
 // op = optional transpose, batch z = z1 * nb2 + z2 with two stride levels
 // (the site contractions of the zip-up batch over (carry row, omega)).
 //
-// Tiling: 64 x 64 output tile per 256-thread CTA, K staged 16 at a time in
-// shared memory, 4 x 4 register accumulators per thread.  FP64 on this GPU
+// Tiling: 64 x 64 (256 threads) or 32 x 32 (64 threads) output tile per CTA,
+// K staged 16 at a time in shared memory, 4 x 4 register accumulators per
+// thread; the host picks the tile and a split of K per product shape.  FP64 on this GPU
 // runs on the CUDA-core DFMA pipe (no FP64 tensor-core rate worth using), so
 // the kernel is DFMA-bound once tiles are full.
 #include "common.cuh"
@@ -12,20 +13,25 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 
-__global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
+// TBM x TBN output tile per CTA of (TBM / 4) * (TBN / 4) threads, 4 x 4
+// accumulators per thread: 64 x 64 (256 threads) for large outputs, 32 x 32
+// (64 threads) to spread small outputs over more SMs.
+template <int TBM, int TBN>
+__global__ void __launch_bounds__((TBM / 4) * (TBN / 4)) k_gemm_f64(GemmF64 g) {
+  constexpr int TX = TBN / 4, TY = TBM / 4, NT = TX * TY;
   if (g.skip && *g.skip) return;
   const int z = blockIdx.z;
   const int z1 = z / g.nb2, z2 = z % g.nb2;
   const double* A = g.A + z1 * g.sA1 + z2 * g.sA2;
   const double* B = g.B + z1 * g.sB1 + z2 * g.sB2;
   double* C = g.C + z1 * g.sC1 + z2 * g.sC2;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  __shared__ double As[BK][TBM + 1];
+  __shared__ double Bs[BK][TBN + 1];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tx = tid % TX, ty = tid / TX;
   double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; i++)
@@ -33,19 +39,18 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
     for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
 
   for (int k0 = 0; k0 < g.K; k0 += BK) {
-#pragma unroll
-    for (int t = 0; t < 4; t++) {
-      int idx = tid + t * 256;
+    for (int idx = tid; idx < BK * TBM; idx += NT) {
       int mm, kk;
-      if (!g.tA) { mm = idx / BK; kk = idx % BK; } else { kk = idx / BM; mm = idx % BM; }
-      int gm = m0 + mm, gk = k0 + kk;
+      if (!g.tA) { mm = idx / BK; kk = idx % BK; } else { kk = idx / TBM; mm = idx % TBM; }
+      const int gm = m0 + mm, gk = k0 + kk;
       double v = 0.0;
       if (gm < g.M && gk < g.K) v = g.tA ? A[(long long)gk * g.lda + gm] : A[(long long)gm * g.lda + gk];
       As[kk][mm] = v;
-      int nn;
-      if (!g.tB) { kk = idx / BN; nn = idx % BN; } else { nn = idx / BK; kk = idx % BK; }
-      int gn = n0 + nn;
-      gk = k0 + kk;
+    }
+    for (int idx = tid; idx < BK * TBN; idx += NT) {
+      int nn, kk;
+      if (!g.tB) { kk = idx / TBN; nn = idx % TBN; } else { nn = idx / BK; kk = idx % BK; }
+      const int gn = n0 + nn, gk = k0 + kk;
       double w = 0.0;
       if (gn < g.N && gk < g.K) w = g.tB ? B[(long long)gn * g.ldb + gk] : B[(long long)gk * g.ldb + gn];
       Bs[kk][nn] = w;
@@ -55,9 +60,9 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
     for (int kk = 0; kk < BK; kk++) {
       double a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + TY * i];
 #pragma unroll
-      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + TX * j];
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
@@ -67,11 +72,11 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
   }
 #pragma unroll
   for (int i = 0; i < 4; i++) {
-    int gm = m0 + ty + 16 * i;
+    const int gm = m0 + ty + TY * i;
     if (gm >= g.M) continue;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-      int gn = n0 + tx + 16 * j;
+      const int gn = n0 + tx + TX * j;
       if (gn >= g.N) continue;
       double* c = C + (long long)gm * g.ldc + gn;
       double v = g.alpha * acc[i][j];
@@ -83,7 +88,9 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
 
 }  // namespace
 
-void launch_gemm_f64(const GemmF64& g, cudaStream_t s) {
+void launch_gemm_f64(const GemmF64& g, cudaStream_t s) { launch_gemm_f64_tile(g, 0, s); }
+
+void launch_gemm_f64_tile(const GemmF64& g, int tile, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 * g.nb2 <= 0) return;
   {
     const long long zb1 = g.nb1 - 1, zb2 = g.nb2 - 1;
@@ -99,8 +106,13 @@ void launch_gemm_f64(const GemmF64& g, cudaStream_t s) {
     launch_scale(g, s);
     return;
   }
-  dim3 grid(ceil_div(g.N, BN), ceil_div(g.M, BM), g.nb1 * g.nb2);
   pre_launch(s);
-  k_gemm_f64<<<grid, 256, 0, s>>>(g);
+  if (tile == 1) {
+    dim3 grid(ceil_div(g.N, 32), ceil_div(g.M, 32), g.nb1 * g.nb2);
+    k_gemm_f64<32, 32><<<grid, 64, 0, s>>>(g);
+  } else {
+    dim3 grid(ceil_div(g.N, 64), ceil_div(g.M, 64), g.nb1 * g.nb2);
+    k_gemm_f64<64, 64><<<grid, 256, 0, s>>>(g);
+  }
   post_launch("k_gemm_f64", s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
 }

@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -301,24 +302,13 @@ struct MpsPtr {
   qtt_mps operator->() const { return m; }
 };
 
-void gemm_splitk(const GemmF64& g, cudaStream_t s);
-
-// Every single product goes through gemm_splitk, which cuts K when the
-// output has too few 64 x 64 tiles to occupy the GPU.
-void gemm(const GemmF64& g, cudaStream_t s) { gemm_splitk(g, s); }
-
-// One product whose output has few 64 x 64 tiles but a long K (a Gram
-// matrix of a wide factor, an environment contraction of the projection):
-// K is cut into slices of at least 32 that run as one batched launch into
-// scratch, then C = alpha * (sum of the slices, in slice order:
-// deterministic) + beta * C.  Single products only (no batch); a skip flag
-// skips both launches.
-void gemm_splitk(const GemmF64& g, cudaStream_t s) {
-  const int tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
-  int S = 1;
-  while (tiles * S * 2 <= 2 * 148 && g.K / (S * 2) >= 32) S *= 2;
-  if (S == 1 || g.nb1 * g.nb2 != 1) {
-    launch_gemm_f64(g, s);
+// One product with a given tile (0: 64 x 64, 1: 32 x 32) and K cut into S
+// slices (S > 1: single products only): the slices run as one batched
+// launch into scratch, then C = alpha * (sum of the slices, in slice order:
+// deterministic) + beta * C; a skip flag skips both launches.
+void gemm_run(const GemmF64& g, int tile, int S, cudaStream_t s) {
+  if (S <= 1 || g.nb1 * g.nb2 != 1 || g.K < 2) {
+    launch_gemm_f64_tile(g, tile, s);
     return;
   }
   const int chunk = (g.K + S - 1) / S;
@@ -336,7 +326,7 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s) {
   b.sA1 = g.tA ? (long long)chunk * g.lda : chunk;  // A stored K x M (tA) or M x K
   b.sB1 = g.tB ? chunk : (long long)chunk * g.ldb;  // B stored N x K (tB) or K x N
   b.sC1 = (long long)g.M * g.N;
-  launch_gemm_f64(b, s);
+  launch_gemm_f64_tile(b, tile, s);
   if (rem > 0) {
     GemmF64 r = b;
     r.K = rem;
@@ -344,10 +334,112 @@ void gemm_splitk(const GemmF64& g, cudaStream_t s) {
     r.A = g.A + full * b.sA1;
     r.B = g.B + full * b.sB1;
     r.C = P.p + full * b.sC1;
-    launch_gemm_f64(r, s);
+    launch_gemm_f64_tile(r, tile, s);
   }
   launch_sum_slices(P.p, Sx, g.M, g.N, g.C, g.ldc, g.alpha, g.beta, g.skip, s);
 }
+
+// The fixed rule: 64 x 64 tiles, K cut into slices of at least 32 while the
+// output has too few tiles to occupy the GPU.
+int split_rule(const GemmF64& g) {
+  const int tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  int S = 1;
+  while (g.nb1 * g.nb2 == 1 && tiles * S * 2 <= 2 * 148 && g.K / (S * 2) >= 32) S *= 2;
+  return S;
+}
+
+// Autotuner: the first time a process meets a product shape (M, N, K,
+// transposes, batch) it times every (tile, K split) candidate on the
+// caller's stream, writing into scratch, and keeps the fastest for the rest
+// of the process (so repeated runs use the same summation order).
+// QTT_AUTOTUNE=0 keeps the fixed rule.
+struct GemmKey {
+  int M, N, K, tA, tB, nb;
+  bool operator<(const GemmKey& o) const {
+    return std::tie(M, N, K, tA, tB, nb) < std::tie(o.M, o.N, o.K, o.tA, o.tB, o.nb);
+  }
+};
+struct GemmChoice {
+  int tile, S;
+};
+std::mutex g_tune_mu;
+std::map<GemmKey, GemmChoice>& tune_map() {
+  static std::map<GemmKey, GemmChoice> m;
+  return m;
+}
+
+GemmChoice gemm_tune(const GemmF64& g, cudaStream_t s) {
+  const int nb = g.nb1 * g.nb2;
+  // scratch output, compact layout (the candidates' results are discarded)
+  DBuf<double> Cs((size_t)g.M * g.N * nb, s);
+  GemmF64 t = g;
+  t.C = Cs.p;
+  t.ldc = g.N;
+  t.sC2 = (long long)g.M * g.N;
+  t.sC1 = t.sC2 * g.nb2;
+  t.alpha = 1.0;
+  t.beta = 0.0;
+  t.skip = nullptr;
+  cudaEvent_t e0, e1;
+  QTT_CUDA_CHECK(cudaEventCreate(&e0));
+  QTT_CUDA_CHECK(cudaEventCreate(&e1));
+  GemmChoice best{0, split_rule(g)};
+  float tbest = 1e30f;
+  for (int tile = 0; tile < 2; tile++)
+    for (int S = 1; S <= 16; S *= 2) {
+      if (S > 1 && (nb != 1 || g.K / S < 32)) break;
+      gemm_run(t, tile, S, s);  // warm
+      QTT_CUDA_CHECK(cudaEventRecord(e0, s));
+      gemm_run(t, tile, S, s);
+      QTT_CUDA_CHECK(cudaEventRecord(e1, s));
+      QTT_CUDA_CHECK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      QTT_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < tbest) {
+        tbest = ms;
+        best = GemmChoice{tile, S};
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+void gemm(const GemmF64& g, cudaStream_t s) {
+  static const bool tune = [] {
+    const char* e = getenv("QTT_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nb1 * g.nb2 <= 0) {
+    launch_gemm_f64(g, s);  // empty product or C = beta C
+    return;
+  }
+  if (!tune) {
+    gemm_run(g, 0, split_rule(g), s);
+    return;
+  }
+  const GemmKey key{g.M, g.N, g.K, g.tA, g.tB, g.nb1 * g.nb2};
+  GemmChoice ch;
+  bool found = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = tune_map().find(key);
+    if (it != tune_map().end()) {
+      ch = it->second;
+      found = true;
+    }
+  }
+  if (!found) {
+    ch = gemm_tune(g, s);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto ins = tune_map().emplace(key, ch);  // another thread may have tuned it first
+    ch = ins.first->second;
+  }
+  gemm_run(g, ch.tile, ch.S, s);
+}
+
+// Split-K product with the fixed rule (Gram matrices of long factors).
+void gemm_splitk(const GemmF64& g, cudaStream_t s) { gemm(g, s); }
 
 // --------------------------------------------------------------- MPO build
 // Carry tensor of App. A, Table "diff_mpo": C[p][so][si][q], p = alpha_m
