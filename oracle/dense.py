@@ -82,3 +82,18 @@ def rk4_step(u, dt, nu, mu, dx):
         w = [0.25 * u[i] - h * B[i] for i in range(2)]
         U.append(project(w, h, mu, dx))
     return [U[0][i] + U[1][i] + U[2][i] + U[3][i] for i in range(2)]
+
+
+def euler_step(u, dt, nu, mu, dx):
+    """Projected explicit Euler (App. B, Eq. "euler"): P(u - dt B(u))."""
+    B = rhs_B(u, nu, dx)
+    return project([u[i] - dt * B[i] for i in range(2)], dt, mu, dx)
+
+
+def rk2_step(u, dt, nu, mu, dx):
+    """Projected midpoint RK2 (App. B, Eqs. "midpoint_calc", "full_calc")."""
+    B = rhs_B(u, nu, dx)
+    um = project([u[i] - 0.5 * dt * B[i] for i in range(2)], 0.5 * dt, mu, dx)
+    B = rhs_B(um, nu, dx)
+    return project([u[i] - dt * B[i] for i in range(2)], dt, mu, dx)
+

@@ -615,8 +615,9 @@ def conjugate_gradient(matvec, b, x, tol, maxit) -> int:
 # --------------------------------------------------------------------------
 # Right-hand side and RK4 (App. B, Eq. for B_i, Table RK4, Eqs. U1-U4)
 # --------------------------------------------------------------------------
-def stage_w(u, b, h, nu, params: Params, ops: Operators):
-    """w_i = u_i / 4 - h B_i(b) with the skew-symmetric convection term
+def stage_w(u, b, h, nu, params: Params, ops: Operators, a_scale: float = 0.25):
+    """w_i = a_scale u_i - h B_i(b) (a_scale = 1/4 for the RK4 stages, 1 for
+    the Euler and RK2 minimisations) with the skew-symmetric convection term
     B_i = sum_j 1/2 (b_j (.) D_j b_i + D_j (b_j (.) b_i)) - nu D_j^2 b_i
     (App. B, Eq. for B_i).  Every intermediate is compressed to
     (eps, chi_max); the sums are taken pairwise in the order below.
@@ -637,7 +638,7 @@ def stage_w(u, b, h, nu, params: Params, ops: Operators):
         cb = add([1.0, 1.0], [DQ[(0, i)], DQ[(1, i)]], eps, chi)
         conv = add([0.5, 0.5], [ca, cb], eps, chi)
         B = add([1.0, -nu], [conv, Lb[i]], eps, chi)
-        w.append(add([0.25, -h], [u[i], B], eps, chi))
+        w.append(add([a_scale, -h], [u[i], B], eps, chi))
     return w
 
 
@@ -669,3 +670,23 @@ def rk4_step(u, dt: float, nu: float, params: Params, ops: Operators, stats=None
         acc = add([1.0, 1.0], [acc, U[3][i]], eps, chi)
         out.append(acc)
     return out
+
+
+def euler_step(u, dt: float, nu: float, params: Params, ops: Operators):
+    """One explicit Euler (RK1) step (App. B, Eq. "euler" in the cost
+    function): u^{s+1} = argmin Theta(v, a = u^s, b = u^s, h = dt)."""
+    w = stage_w(u, u, dt, nu, params, ops, a_scale=1.0)
+    v, _ = project(w, dt, params, ops)
+    return v
+
+
+def rk2_step(u, dt: float, nu: float, params: Params, ops: Operators):
+    """One midpoint RK2 step (App. B, Eqs. "midpoint_calc", "full_calc"):
+    u^{s+1/2} = argmin Theta(v, u^s, u^s, dt/2), then
+    u^{s+1} = argmin Theta(v, u^s, u^{s+1/2}, dt)."""
+    w = stage_w(u, u, 0.5 * dt, nu, params, ops, a_scale=1.0)
+    um, _ = project(w, 0.5 * dt, params, ops)
+    w = stage_w(u, um, dt, nu, params, ops, a_scale=1.0)
+    v, _ = project(w, dt, params, ops)
+    return v
+

@@ -354,3 +354,43 @@ def test_initial_conditions_are_discretely_divergence_free():
         assert np.abs(div).max() < 1e-10 * max(np.abs(Dn.d(u[0], 1, dx)).max(), 1.0)
     u, dx = I.decaying_turbulence(7, seed=1)
     assert abs(0.5 * np.mean(u[0] ** 2 + u[1] ** 2) - 1.0) < 1e-12
+
+
+def test_qtt_euler_and_rk2_equal_dense():
+    """Untruncated QTT Euler and midpoint-RK2 steps == the dense projected
+    schemes (App. B: Eq. "euler"; Eqs. "midpoint_calc", "full_calc")."""
+    n = 4
+    X1, X2, dx = I.grid(n)
+    ops = Q.build_operators(n, dx)
+    u0, _ = I.taylor_green(n)
+    u = [u0[0] + 0.1 * I.random_field(n, seed=5), u0[1] + 0.1 * I.random_field(n, seed=6)]
+    uq = [Q.from_dense(f, 0.0, FULL) for f in u]
+    p = Q.Params(eps=0.0, chi_max=FULL, **TIGHT)
+    for qstep, dstep in ((Q.euler_step, Dn.euler_step), (Q.rk2_step, Dn.rk2_step)):
+        out = qstep(uq, 1e-2, 0.01, p, ops)
+        ref = dstep(u, 1e-2, 0.01, p.mu, dx)
+        for i in range(2):
+            assert rel(Q.to_dense(out[i]), ref[i]) < 1e-10
+
+
+def test_euler_rk2_amplification_factors():
+    """On the Taylor-Green mode the convection is energy-neutral and, with a
+    strong penalty, the pressure part is projected out, so one step
+    multiplies the mode amplitude by the scheme's amplification factor for
+    y' = -lam y, lam = 2 nu c^2: 1 - lam dt (Euler), 1 - lam dt + (lam dt)^2 / 2
+    (midpoint RK2), the Taylor polynomial of order 4 (RK4)."""
+    n, nu, dt, steps = 6, 0.1, 1e-2, 10
+    u0, dx = I.taylor_green(n)
+    lam = 2 * nu * (math.sin(dx) / dx) ** 2
+    z = lam * dt
+    norm0 = sum(np.vdot(x, x) for x in u0)
+    amp = lambda u: sum(np.vdot(u[i], u0[i]) for i in range(2)) / norm0
+    factors = {Dn.euler_step: 1 - z, Dn.rk2_step: 1 - z + z * z / 2,
+               Dn.rk4_step: 1 - z + z * z / 2 - z ** 3 / 6 + z ** 4 / 24}
+    for step, g in factors.items():
+        v = [x.copy() for x in u0]
+        for _ in range(steps):
+            v = step(v, dt, nu, 1e12, dx)
+        assert abs(amp(v) / g ** steps - 1) < 1e-9, step.__name__
+    # the three schemes are told apart at this step size
+    assert abs((1 - z) ** steps / (1 - z + z * z / 2) ** steps - 1) > 1e-5
