@@ -162,6 +162,14 @@ qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v
  * *u1, *u2 are replaced by new handles (the old ones are released).
  * nu = 1 / Re.  Synchronises (the projections do). */
 qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu);
+/* The lower-order steps of App. B, in place like qtt_rk4_step (same
+ * ownership, synchronisation and status rules): explicit Euler,
+ * u^{s+1} = argmin Theta(v, a = u^s, b = u^s, h = dt) (Eq. "euler"), and the
+ * midpoint RK2, u^{s+1/2} = argmin Theta(v, u^s, u^s, dt/2) then
+ * u^{s+1} = argmin Theta(v, u^s, u^{s+1/2}, dt) (Eqs. "midpoint_calc",
+ * "full_calc"). */
+qtt_status qtt_euler_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu);
+qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu);
 
 /* Counters of the last qtt_project / qtt_rk4_step: total CG iterations,
  * sweeps, kernel launches enqueued by the library since context creation. */

@@ -1580,7 +1580,8 @@ struct Workers {
   }
 };
 
-void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2]) {
+void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2],
+             double a_scale = 0.25) {
   const double eps = ctx->p.eps;
   const int chi = ctx->p.chi_max;
   Workers wk(ctx);
@@ -1626,7 +1627,7 @@ void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPt
     conv[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 0.5, ca[i].get(), 0.5, cb[i].get()); }));
     wk.after(si, 7 + i);
     B[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 1.0, conv[i].get(), -nu, Lb[i].get()); }));
-    w[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 0.25, u[i], -h, B[i].get()); }));
+    w[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, a_scale, u[i], -h, B[i].get()); }));
   }
   // every worker joins the context stream; all outputs and intermediates
   // are then released on it
@@ -1698,6 +1699,48 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
   ctx->last_not_converged = nc;
   (void)cg_total;
   (void)sw_total;
+}
+
+// One penalised minimisation with a = u (scale 1) and the given b, h.
+void euler_min(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr v[2]) {
+  MpsPtr w[2];
+  stage_w(ctx, u, b, h, nu, w, 1.0);
+  qtt_mps v1, v2;
+  int cg = 0, sw = 0;
+  project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+  v[0] = MpsPtr(v1);
+  v[1] = MpsPtr(v2);
+}
+
+// Explicit Euler (App. B, Eq. "euler"): u^{s+1} = argmin Theta(v, u, u, dt).
+void euler_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+  if (ctx->p.learned_trunc != QTT_LEARNED_OFF) learned_next_step(ctx);
+  qtt_mps u[2] = {*u1, *u2};
+  MpsPtr v[2];
+  euler_min(ctx, u, u, dt, nu, v);
+  const int nc = ctx->last_not_converged;
+  free_mps(*u1);
+  free_mps(*u2);
+  *u1 = v[0].release();
+  *u2 = v[1].release();
+  ctx->last_not_converged = nc;
+}
+
+// Midpoint RK2 (App. B, Eqs. "midpoint_calc", "full_calc").
+void rk2_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+  if (ctx->p.learned_trunc != QTT_LEARNED_OFF) learned_next_step(ctx);
+  qtt_mps u[2] = {*u1, *u2};
+  MpsPtr um[2], v[2];
+  euler_min(ctx, u, u, 0.5 * dt, nu, um);
+  int nc = ctx->last_not_converged;
+  qtt_mps b[2] = {um[0].get(), um[1].get()};
+  euler_min(ctx, u, b, dt, nu, v);
+  nc |= ctx->last_not_converged;
+  free_mps(*u1);
+  free_mps(*u2);
+  *u1 = v[0].release();
+  *u2 = v[1].release();
+  ctx->last_not_converged = nc;
 }
 
 // ---------------------------------------------------------------- dense I/O
@@ -2117,6 +2160,38 @@ qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
     check_mps(ctx, *u1);
     check_mps(ctx, *u2);
     rk4_impl(ctx, u1, u2, dt, nu);
+    qtt_status st = check_device_errors(ctx);
+    if (st != QTT_OK) return st;
+    if (ctx->last_not_converged) {
+      ctx->err = "a projection reached its CG or sweep cap";
+      return QTT_ERR_NOT_CONVERGED;
+    }
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_euler_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+  if (!u1 || !u2 || !(dt > 0) || nu < 0) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, *u1);
+    check_mps(ctx, *u2);
+    euler_impl(ctx, u1, u2, dt, nu);
+    qtt_status st = check_device_errors(ctx);
+    if (st != QTT_OK) return st;
+    if (ctx->last_not_converged) {
+      ctx->err = "a projection reached its CG or sweep cap";
+      return QTT_ERR_NOT_CONVERGED;
+    }
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+  if (!u1 || !u2 || !(dt > 0) || nu < 0) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, *u1);
+    check_mps(ctx, *u2);
+    rk2_impl(ctx, u1, u2, dt, nu);
     qtt_status st = check_device_errors(ctx);
     if (st != QTT_OK) return st;
     if (ctx->last_not_converged) {

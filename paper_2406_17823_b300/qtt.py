@@ -36,7 +36,8 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_stats", "qtt_profile_begin", "qtt_profile_end", "qtt_to_dense_noalloc",
            "qtt_learned_set", "qtt_learned_next_step", "qtt_learned_log", "qtt_learned_stats",
            "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
-           "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched")
+           "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
+           "qtt_euler_step", "qtt_rk2_step")
 
 
 class QttError(RuntimeError):
@@ -85,6 +86,8 @@ def lib():
             "qtt_compress": (c_int, [vp, vp, c_double, c_int]),
             "qtt_project": (c_int, [vp, vp, vp, c_double, POINTER(vp), POINTER(vp), ip, ip]),
             "qtt_rk4_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
+            "qtt_euler_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
+            "qtt_rk2_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong),
                                   POINTER(c_longlong)]),
             "qtt_profile_begin": (c_int, [vp]),
@@ -295,6 +298,21 @@ class Context:
         u1.h, u2.h = h1, h2
         self._check(st, allow_not_converged=True)
         return st == 0
+
+    def _step(self, fn, u1: MPS, u2: MPS, dt: float, nu: float):
+        h1, h2 = c_void_p(u1.h.value), c_void_p(u2.h.value)
+        st = fn(self.h, byref(h1), byref(h2), dt, nu)
+        u1.h, u2.h = h1, h2
+        self._check(st, allow_not_converged=True)
+        return st == 0
+
+    def euler_step(self, u1: MPS, u2: MPS, dt: float, nu: float):
+        """Explicit Euler in place (App. B); True if the projection converged."""
+        return self._step(lib().qtt_euler_step, u1, u2, dt, nu)
+
+    def rk2_step(self, u1: MPS, u2: MPS, dt: float, nu: float):
+        """Midpoint RK2 in place (App. B); True if both projections converged."""
+        return self._step(lib().qtt_rk2_step, u1, u2, dt, nu)
 
     def profile_begin(self):
         self._check(lib().qtt_profile_begin(self.h))
