@@ -121,6 +121,11 @@ qtt_status qtt_to_dense(qtt_ctx ctx, qtt_mps mps, double* d_field_out);
  * selects whether `cores` is a device or a host pointer; bonds[0..n]. */
 qtt_status qtt_mps_from_packed(qtt_ctx ctx, const double* cores, int cores_are_device,
                                const int* bonds, qtt_mps* out);
+/* <a|b> = sum over the grid of a(x) b(x) (the MPS inner product, used by
+ * the paper's fidelity and kinetic-energy diagnostics, Sec. III): left
+ * transfer matrices in FP64 on the context stream; synchronises and writes
+ * the value to *out (host). */
+qtt_status qtt_inner(qtt_ctx ctx, qtt_mps a, qtt_mps b, double* out);
 /* Copy an MPS out in packed layout.  Synchronises; writes bonds[0..n] and
  * at most `capacity` doubles to `cores` (device or host). */
 qtt_status qtt_mps_to_packed(qtt_ctx ctx, qtt_mps mps, double* cores, int cores_are_device,

@@ -1743,6 +1743,35 @@ void rk2_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
   ctx->last_not_converged = nc;
 }
 
+// <a|b> by the left transfer matrices E_k = sum_s A_k[s]^T E_{k-1} B_k[s]
+// (capacity shapes; the zero padding contributes nothing); the 1 x 1 E_n is
+// copied to the host (synchronises).
+double inner_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B) {
+  const int n = A->n;
+  cudaStream_t s = stream_of(ctx);
+  size_t emax = 1, tmax = 1;
+  for (int k = 0; k <= n; k++) emax = std::max(emax, (size_t)A->cap[k] * B->cap[k]);
+  for (int k = 0; k < n; k++) tmax = std::max(tmax, (size_t)A->cap[k] * 4 * B->cap[k + 1]);
+  DBuf<double> E0(emax, s), E1(emax, s), Tb(tmax, s);
+  launch_fill(E0.p, 1, 1.0, s);
+  double* Ec = E0.p;
+  double* En = E1.p;
+  for (int k = 0; k < n; k++) {
+    const int al = A->cap[k], ar = A->cap[k + 1], bl = B->cap[k], br = B->cap[k + 1];
+    // T ((al x 4) x br) = E (al x bl) * B_k (bl x 4 br)
+    gemm(gemm_plain(Ec, B->core(k), Tb.p, al, 4 * br, bl, bl, 4 * br, 4 * br), s);
+    // E' (ar x br) = A_k^T ((al 4) x ar)^T * T ((al 4) x br)
+    GemmF64 g = gemm_plain(A->core(k), Tb.p, En, ar, br, 4 * al, ar, br, br);
+    g.tA = 1;
+    gemm(g, s);
+    std::swap(Ec, En);
+  }
+  double h = 0.0;
+  QTT_CUDA_CHECK(cudaMemcpyAsync(&h, Ec, sizeof(double), cudaMemcpyDeviceToHost, s));
+  QTT_CUDA_CHECK(cudaStreamSynchronize(s));
+  return h;
+}
+
 // ---------------------------------------------------------------- dense I/O
 qtt_mps from_dense_impl(qtt_ctx ctx, const double* F, double eps, int chi) {
   const int n = ctx->p.n;
@@ -2199,6 +2228,16 @@ qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
       return QTT_ERR_NOT_CONVERGED;
     }
     return QTT_OK;
+  });
+}
+
+qtt_status qtt_inner(qtt_ctx ctx, qtt_mps a, qtt_mps b, double* out) {
+  if (!out) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, a);
+    check_mps(ctx, b);
+    *out = inner_impl(ctx, a, b);
+    return check_device_errors(ctx);
   });
 }
 

@@ -37,7 +37,7 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_learned_set", "qtt_learned_next_step", "qtt_learned_log", "qtt_learned_stats",
            "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
            "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
-           "qtt_euler_step", "qtt_rk2_step")
+           "qtt_euler_step", "qtt_rk2_step", "qtt_inner")
 
 
 class QttError(RuntimeError):
@@ -87,6 +87,7 @@ def lib():
             "qtt_project": (c_int, [vp, vp, vp, c_double, POINTER(vp), POINTER(vp), ip, ip]),
             "qtt_rk4_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_euler_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
+            "qtt_inner": (c_int, [vp, vp, vp, POINTER(c_double)]),
             "qtt_rk2_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong),
                                   POINTER(c_longlong)]),
@@ -298,6 +299,22 @@ class Context:
         u1.h, u2.h = h1, h2
         self._check(st, allow_not_converged=True)
         return st == 0
+
+    # -------------------------------------------------------- diagnostics
+    def inner(self, a: MPS, b: MPS) -> float:
+        """<a|b>, the sum over the grid of a(x) b(x)."""
+        v = c_double()
+        self._check(lib().qtt_inner(self.h, a.h, b.h, byref(v)))
+        return v.value
+
+    def fidelity(self, a: MPS, b: MPS) -> float:
+        """|<a|b>|^2 / (<a|a> <b|b>) (Sec. III's fidelity of two states)."""
+        ab, aa, bb = self.inner(a, b), self.inner(a, a), self.inner(b, b)
+        return ab * ab / (aa * bb) if aa > 0 and bb > 0 else 0.0
+
+    def kinetic_energy(self, u1: MPS, u2: MPS) -> float:
+        """1/2 mean(u1^2 + u2^2) over the grid."""
+        return 0.5 * (self.inner(u1, u1) + self.inner(u2, u2)) / float(self.N) ** 2
 
     def _step(self, fn, u1: MPS, u2: MPS, dt: float, nu: float):
         h1, h2 = c_void_p(u1.h.value), c_void_p(u2.h.value)
