@@ -75,3 +75,36 @@ def test_null_arguments_are_rejected_without_gpu(libpath):
     lib.qtt_last_error.restype = ctypes.c_char_p
     lib.qtt_last_error.argtypes = [ctypes.c_void_p]
     assert lib.qtt_last_error(None) == b"null context"
+
+
+def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
+    """Argument checks happen before any CUDA call: the learned-truncation,
+    perceptron, batch, lower-order step and inner-product entry points all
+    return QTT_ERR_ARG for null handles or pointers, on a machine without a
+    GPU."""
+    lib = ctypes.CDLL(libpath)
+    vp = ctypes.c_void_p
+    calls = [
+        ("qtt_learned_set", [vp, vp], (None, None)),
+        ("qtt_learned_next_step", [vp], (None,)),
+        ("qtt_learned_stats", [vp, vp, vp], (None, None, None)),
+        ("qtt_rf_omega", [vp, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int, vp], (None, 0, 1, 1, None)),
+        ("qtt_mlp_forward", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 1, None)),
+        ("qtt_mlp_loss_grad", [vp, vp, vp, vp, ctypes.c_int, vp, vp], (None,) * 4 + (1, None, None)),
+        ("qtt_mlp_train", [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_float, vp],
+         (None,) * 4 + (1, 1, 1e-3, None)),
+        ("qtt_batch_create", [vp, ctypes.c_int, ctypes.c_int, vp], (None, 0, 1, None)),
+        ("qtt_batch_destroy", [vp], (None,)),
+        ("qtt_rk4_step_batched", [vp, vp, vp, vp, vp], (None,) * 5),
+        ("qtt_euler_step", [vp, vp, vp, ctypes.c_double, ctypes.c_double], (None, None, None, 1e-3, 0.0)),
+        ("qtt_rk2_step", [vp, vp, vp, ctypes.c_double, ctypes.c_double], (None, None, None, 1e-3, 0.0)),
+        ("qtt_inner", [vp, vp, vp, vp], (None,) * 4),
+    ]
+    for name, argtypes, args in calls:
+        f = getattr(lib, name)
+        f.argtypes = argtypes
+        f.restype = ctypes.c_int
+        assert f(*args) == 1, name
+    lib.qtt_batch_context.argtypes = [vp, ctypes.c_int]
+    lib.qtt_batch_context.restype = vp
+    assert lib.qtt_batch_context(None, 0) is None
