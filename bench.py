@@ -1,7 +1,8 @@
 """Benchmark: QTT RK4 steps per second on a 2^10 x 2^10 shear jet at chi = 64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
-                    [--impl reference]
+                    [--impl reference] [--batched B] [--tight] [--grid-bits n]
+                    [--no-cpu-baseline] [--no-e2e]
 
 Workload (default): decaying double shear layer, periodic [0, 2 pi)^2 with
 N = 2^10, u = tanh((y - pi/2)/delta) - tanh((y - 3 pi/2)/delta),
@@ -15,6 +16,17 @@ velocity components; the state advances from step to step.
 One JSON line is printed by rank 0.  With torchrun (N > 1) every rank runs
 its own trajectory on its own GPU (replicas: the method has no exchange
 step), value = all ranks' steps / the slowest rank's time.
+
+--batched B steps B jets (seeds seed .. seed+B-1) together through the
+batched C ABI (value = aggregate steps/s); --tight runs CG and sweeps to
+1e-12 (CG cap 500) instead of the paper's settings; --grid-bits overrides n
+(smaller test cases); --impl reference times the CPU oracle instead (one
+core, a bounded sample of the same workload).  Timing: 3 warm-up steps by
+default, the L2 flushed (256 MB write) before every timed step, CUDA events
+on the stepping stream (host clock between device-wide synchronisations for
+a batch), SM clocks and throttle reasons sampled during the timed region;
+the roofline of the dominant kernel uses the arithmetic it counts on the
+device and a peak measured in the same run.
 """
 from __future__ import annotations
 
