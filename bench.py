@@ -1,8 +1,8 @@
 """Benchmark: QTT RK4 steps per second on a 2^10 x 2^10 shear jet at chi = 64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
-                    [--impl reference] [--batched B] [--tight] [--grid-bits n]
-                    [--no-cpu-baseline] [--no-e2e]
+                    [--impl reference] [--batched B] [--eager] [--tight]
+                    [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
 
 Workload (default): decaying double shear layer, periodic [0, 2 pi)^2 with
 N = 2^10, u = tanh((y - pi/2)/delta) - tanh((y - 3 pi/2)/delta),
@@ -18,15 +18,19 @@ its own trajectory on its own GPU (replicas: the method has no exchange
 step), value = all ranks' steps / the slowest rank's time.
 
 --batched B steps B jets (seeds seed .. seed+B-1) together through the
-batched C ABI (value = aggregate steps/s); --tight runs CG and sweeps to
-1e-12 (CG cap 500) instead of the paper's settings; --grid-bits overrides n
+batched C ABI (value = aggregate steps/s); --eager launches every stage
+eagerly instead of replaying its right-hand side as a CUDA graph (the
+default: a stage's graph is captured the second time its shapes occur, so
+the warm-up steps capture and the timed steps replay); --tight runs CG and sweeps to 1e-12 (CG cap 500)
+instead of the paper's settings; --grid-bits / --chi override n / chi_max
 (smaller test cases); --impl reference times the CPU oracle instead (one
 core, a bounded sample of the same workload).  Timing: 3 warm-up steps by
 default, the L2 flushed (256 MB write) before every timed step, CUDA events
 on the stepping stream (host clock between device-wide synchronisations for
 a batch), SM clocks and throttle reasons sampled during the timed region;
 the roofline of the dominant kernel uses the arithmetic it counts on the
-device and a peak measured in the same run.
+device, its launch times from one more step under the library's launch
+profiler (outside the timed region) and a peak measured in the same run.
 """
 from __future__ import annotations
 
@@ -244,6 +248,10 @@ def main():
     ap.add_argument("--batched", type=int, default=1,
                     help="B > 1: B trajectories (seeds seed..seed+B-1) stepped together by "
                          "qtt_rk4_step_batched; value = aggregate steps/s")
+    ap.add_argument("--chi", type=int, default=None, help="override chi_max (testing only)")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every stage eagerly instead of replaying its right-hand side "
+                         "as a CUDA graph")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -264,19 +272,24 @@ def main():
     if args.n:
         w["n"] = args.n
         w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
+    if args.chi:
+        w["chi_max"] = args.chi
+        w["workload"] = f"shear_jet_2^{w['n']}_chi{args.chi}"
     if args.tight:
         w.update(cg_tol=1e-12, sweep_tol=1e-12, cg_maxit=500)
         w["workload"] += "_tight"
+    graphs = 0 if args.eager else 1
     prec = P.PREC_FP64 if args.precision == "fp64" else P.PREC_MIXED
     nu = 1.0 / w["Re"]
     B = max(1, args.batched)
     if B > 1:
         w["workload"] = f"{w['workload']}_x{B}_trajectories"
-        batch = P.Batch([dict(n=w["n"], precision=prec, **solver_kwargs(w)) for _ in range(B)],
-                        device=local)
+        batch = P.Batch([dict(n=w["n"], precision=prec, graphs=graphs,
+                              **solver_kwargs(w)) for _ in range(B)], device=local)
         ctxs = batch.contexts
     else:
-        ctxs = [P.Context(w["n"], precision=prec, device=local, **solver_kwargs(w))]
+        ctxs = [P.Context(w["n"], precision=prec, device=local, graphs=graphs,
+                          **solver_kwargs(w))]
     states, dts = [], []
     for i, c in enumerate(ctxs):
         u, dx, dt_i = workload_state(w["n"], w["seed"] + rank * B + i)
@@ -300,7 +313,6 @@ def main():
         step()
     barrier()
     launches0 = sum(c.stats()["launches"] for c in ctxs)
-    ctx.profile_begin()
     times = []
     converged = True
     with ClockSampler(local) as clk:
@@ -327,14 +339,22 @@ def main():
         barrier()
         wall = time.perf_counter() - wall0
     torch.cuda.synchronize()
-    prof = ctx.profile_end()
     gpu_launches = sum(c.stats()["launches"] for c in ctxs) - launches0
+    replays = sum(c.graph_stats()[1] for c in ctxs)
+    # per-kernel device times for the roofline: one more step under the
+    # launch profiler (CUDA events around every launch, which also makes the
+    # stages launch eagerly), outside the timed region
+    ctx.profile_begin()
+    step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_end()
     t_local = sum(times)
     t_max = reduce_max_time(t_local, dist, dev)
     value = world * B * args.steps / t_max
 
     # e2e through the C ABI with host buffers: upload the packed states from
-    # host memory, one step, download the packed results
+    # host memory (into the state objects, whose capacities the stage graphs
+    # are keyed on), one step, download the packed results
     cores = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
     e2e_times, h2d, d2h = [], 0, 0
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
@@ -342,7 +362,9 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        states = [[c.from_cores(x) for x in hc] for c, hc in zip(ctxs, host)]
+        for c, st, hc in zip(ctxs, states, host):
+            for x, cc in zip(st, hc):
+                c.upload_cores(x, cc)
         step()
         out = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
         torch.cuda.synchronize()
@@ -386,6 +408,8 @@ def main():
                 "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
                 "launches_timed": rec["launches"], "avg_launch_ms": avg_ms,
                 "flops_per_launch": flops_per_launch}
+    roofline["timing_source"] = ("one step after the timed region, launched eagerly under the "
+                                 "library's launch profiler")
     cpu = None
     if not args.no_cpu_baseline:
         st = oracle_stage_seconds(w)
@@ -401,7 +425,8 @@ def main():
             "timing": ("CUDA events on the stepping stream" if B == 1 else
                        "host clock between device-wide synchronisations (library-owned streams)"),
             "config": {**w, "precision": args.precision, "parallelism": f"replicas x{world}",
-                       "trajectories": B,
+                       "trajectories": B, "stage_graphs": bool(graphs),
+                       "stage_graph_replays": replays,
                        "l2": "flushed between timed steps (256 MB write)",
                        "all_projections_converged": bool(converged)},
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,

@@ -96,6 +96,13 @@ typedef struct {
   int rf_oversample;  /* range-finder width = predicted rank + this (>= 0) */
   int rf_min_width;   /* only cuts whose full factor is at least this wide
                          (capacity) use the range finder (>= 1; 128)      */
+  int graphs;         /* 1: a stage's right-hand side w = a u - h B(b) runs
+                         as a replayed CUDA graph (captured the first time
+                         its input capacities, h, nu and a occur; inputs and
+                         outputs copied through graph-owned buffers); 0:
+                         launched eagerly.  Either way the same kernels in
+                         the same order per stream: results are identical.
+                         Ignored while profiling or with learned truncation. */
 } qtt_params;
 
 /* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,
@@ -121,6 +128,14 @@ qtt_status qtt_to_dense(qtt_ctx ctx, qtt_mps mps, double* d_field_out);
  * selects whether `cores` is a device or a host pointer; bonds[0..n]. */
 qtt_status qtt_mps_from_packed(qtt_ctx ctx, const double* cores, int cores_are_device,
                                const int* bonds, qtt_mps* out);
+/* Overwrite an existing MPS with packed cores (see conventions), keeping its
+ * storage and capacities, so that a stepped state can be refreshed from the
+ * host without new shapes (a stage graph keyed on those capacities stays
+ * valid).  Requires bonds[0] = bonds[n] = 1 and 1 <= bonds[b] <= the MPS's
+ * capacity at bond b (QTT_ERR_SHAPE otherwise); the padding is zeroed.
+ * `cores_are_device` as in qtt_mps_from_packed.  Synchronises. */
+qtt_status qtt_mps_upload_packed(qtt_ctx ctx, qtt_mps dst, const double* cores,
+                                 int cores_are_device, const int* bonds);
 /* <a|b> = sum over the grid of a(x) b(x) (the MPS inner product, used by
  * the paper's fidelity and kinetic-energy diagnostics, Sec. III): left
  * transfer matrices in FP64 on the context stream; synchronises and writes
@@ -180,6 +195,13 @@ qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
  * sweeps, kernel launches enqueued by the library since context creation. */
 qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps,
                      long long* launches);
+
+/* Stage graphs (qtt_params.graphs): graphs captured and kept by the context
+ * (at most 16; cleared by qtt_set_params) and replays since creation.  A
+ * stage whose key (input capacities, aliasing of b and u, h, nu, a) occurs
+ * for the second time runs eagerly and is captured; from the third time on
+ * it is replayed.  QTT_ERR_ARG for null arguments. */
+qtt_status qtt_graph_stats(qtt_ctx ctx, long long* captured, long long* replays);
 
 /* Per-kernel timing of the work enqueued between qtt_profile_begin and
  * qtt_profile_end: CUDA events are recorded on the context stream around

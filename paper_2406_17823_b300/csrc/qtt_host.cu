@@ -155,6 +155,18 @@ struct qtt_mpo_s {
   double* kr2(int k) const { return dev_kr2 + off[k]; }
 };
 
+// A stage's right-hand side captured as a CUDA graph: graph-owned input
+// buffers (u_0, u_1, b_0, b_1; b unused when it aliases u) and outputs
+// (w_0, w_1) with the capacities of the occurrence it was captured from.
+struct StageGraph {
+  cudaGraphExec_t exec = nullptr;
+  qtt_mps in[4] = {nullptr, nullptr, nullptr, nullptr};
+  qtt_mps out[2] = {nullptr, nullptr};
+  long long launches = 0;  // kernels per replay
+  int seen = 0;            // eager occurrences so far
+  bool failed = false;     // not capturable: launched eagerly from then on
+};
+
 struct qtt_ctx_s {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -189,6 +201,12 @@ struct qtt_ctx_s {
   float* d_mlp = nullptr;
   bool mlp_set = false;
   long long* d_rf_counts = nullptr;  // [0] cuts served by the range finder, [1] fallbacks
+  // stage graphs (params.graphs), keyed by input capacities, aliasing, h,
+  // nu and a; captured on a private non-blocking stream
+  cudaStream_t gstream = nullptr;
+  std::map<std::string, std::unique_ptr<StageGraph>> graphs;
+  static constexpr int kMaxGraphs = 16;  // captured graphs kept per context
+  long long graphs_captured = 0, graph_replays = 0;
 };
 
 namespace {
@@ -1638,6 +1656,153 @@ void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPt
            conv[1].get(), B[0].get(), B[1].get(), w[0].get(), w[1].get()});
 }
 
+// ------------------------------------------------ stage graphs (params.graphs)
+// The right-hand side of a stage issues thousands of launches over the
+// worker streams and never waits for the device, so it can be captured once
+// and replayed: a key's first occurrence runs eagerly (one-off shapes, such
+// as a state just read from host memory, are never captured); the second
+// runs eagerly (every product shape is then tuned) and is captured into a
+// graph on graph-owned buffers; later occurrences copy their inputs in,
+// launch the graph and copy the outputs out (device-to-device, a few MB).
+// The kernels, their per-stream order and their arguments are those of the
+// eager run, so the results are the same bit for bit.  h is part of the key:
+// replays pay off with a fixed time step.
+std::string stage_key(qtt_mps u[2], qtt_mps b[2], bool alias, double h, double nu, double a) {
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  put(&alias, sizeof alias);
+  put(&h, sizeof h);
+  put(&nu, sizeof nu);
+  put(&a, sizeof a);
+  for (int i = 0; i < (alias ? 2 : 4); i++) {
+    const qtt_mps m = i < 2 ? u[i] : b[i - 2];
+    put(m->cap.data(), m->cap.size() * sizeof(int));
+  }
+  return k;
+}
+
+void copy_mps_d2d(qtt_mps dst, qtt_mps src, cudaStream_t s) {
+  if (dst->cap != src->cap) throw QttError(QTT_ERR_SHAPE, "stage graph: capacity mismatch");
+  QTT_CUDA_CHECK(cudaMemcpyAsync(dst->data, src->data, src->off[src->n] * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+  QTT_CUDA_CHECK(cudaMemcpyAsync(dst->dims, src->dims, (src->n + 1) * sizeof(int),
+                                 cudaMemcpyDeviceToDevice, s));
+}
+
+void graph_release(StageGraph& G) {
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
+  for (qtt_mps& m : G.in) {
+    free_mps(m);
+    m = nullptr;
+  }
+  for (qtt_mps& m : G.out) {
+    free_mps(m);
+    m = nullptr;
+  }
+}
+
+void graphs_clear(qtt_ctx ctx) {
+  if (ctx->graphs.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->graphs) graph_release(*kv.second);
+  ctx->graphs.clear();
+  ctx->graphs_captured = 0;
+}
+
+// Capture stage_w on graph-owned buffers shaped like this occurrence's
+// inputs and outputs.  Any failure leaves the key marked `failed` (eager
+// from then on) and the context as it was.
+void capture_stage(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], qtt_mps b[2], bool alias, double h,
+                   double nu, double a_scale, MpsPtr w_eager[2]) {
+  const int n = u[0]->n;
+  G.in[0] = new_mps(ctx, n, u[0]->cap);
+  G.in[1] = new_mps(ctx, n, u[1]->cap);
+  if (!alias) {
+    G.in[2] = new_mps(ctx, n, b[0]->cap);
+    G.in[3] = new_mps(ctx, n, b[1]->cap);
+  }
+  G.out[0] = new_mps(ctx, n, w_eager[0]->cap);
+  G.out[1] = new_mps(ctx, n, w_eager[1]->cap);
+  if (!ctx->gstream)
+    QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+  // nothing is executed by the capture; the buffers exist before any replay
+  // because replays are ordered after this point on the context stream
+  const cudaStream_t orig = ctx->stream;
+  const long long n0 = ctx->launches.n;
+  cudaGraph_t graph = nullptr;
+  QTT_CUDA_CHECK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+  ctx->stream = ctx->gstream;
+  try {
+    qtt_mps gu[2] = {G.in[0], G.in[1]};
+    qtt_mps gb[2] = {alias ? G.in[0] : G.in[2], alias ? G.in[1] : G.in[3]};
+    MpsPtr w[2];
+    stage_w(ctx, gu, gb, h, nu, w, a_scale);
+    for (int i = 0; i < 2; i++) copy_mps_d2d(G.out[i], w[i].get(), ctx->stream);
+  } catch (...) {
+    cudaStreamEndCapture(ctx->gstream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    ctx->stream = orig;
+    ctx->launches.n = n0;
+    (void)cudaGetLastError();
+    graph_release(G);
+    G.failed = true;
+    return;
+  }
+  const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
+  ctx->stream = orig;
+  G.launches = ctx->launches.n - n0;
+  ctx->launches.n = n0;
+  cudaError_t ei = ec;
+  if (ec == cudaSuccess) ei = cudaGraphInstantiate(&G.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    (void)cudaGetLastError();
+    G.exec = nullptr;
+    graph_release(G);
+    G.failed = true;
+  }
+}
+
+void stage_w_run(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2],
+                 double a_scale) {
+  if (!ctx->p.graphs || g_prof.on || ctx->p.learned_trunc != QTT_LEARNED_OFF) {
+    stage_w(ctx, u, b, h, nu, w, a_scale);
+    return;
+  }
+  const bool alias = b[0] == u[0] && b[1] == u[1];
+  const std::string key = stage_key(u, b, alias, h, nu, a_scale);
+  if (ctx->graphs.size() > 256) {  // keys seen but never captured (a varying h)
+    for (auto it = ctx->graphs.begin(); it != ctx->graphs.end();)
+      it = it->second->exec ? std::next(it) : ctx->graphs.erase(it);
+  }
+  std::unique_ptr<StageGraph>& slot = ctx->graphs[key];
+  if (!slot) slot.reset(new StageGraph);
+  StageGraph& G = *slot;
+  if (!G.exec) {
+    stage_w(ctx, u, b, h, nu, w, a_scale);
+    if (G.seen++ >= 1 && !G.failed && ctx->graphs_captured < qtt_ctx_s::kMaxGraphs) {
+      capture_stage(ctx, G, u, b, alias, h, nu, a_scale, w);
+      if (!G.failed) ctx->graphs_captured++;
+    }
+    return;
+  }
+  const int n = u[0]->n;
+  copy_mps_d2d(G.in[0], u[0], ctx->stream);
+  copy_mps_d2d(G.in[1], u[1], ctx->stream);
+  if (!alias) {
+    copy_mps_d2d(G.in[2], b[0], ctx->stream);
+    copy_mps_d2d(G.in[3], b[1], ctx->stream);
+  }
+  QTT_CUDA_CHECK(cudaGraphLaunch(G.exec, ctx->stream));
+  ctx->launches.n += G.launches;
+  ctx->graph_replays++;
+  for (int i = 0; i < 2; i++) {
+    w[i] = MpsPtr(new_mps(ctx, n, G.out[i]->cap));
+    copy_mps_d2d(w[i].get(), G.out[i], ctx->stream);
+  }
+}
+
 // A new step's slots: the current table becomes the previous one, the new
 // current table starts empty.
 void learned_next_step(qtt_ctx ctx) {
@@ -1670,7 +1835,7 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
     }
     const double h = HS[st] * dt;
     MpsPtr w[2];
-    stage_w(ctx, u, b, h, nu, w);
+    stage_w_run(ctx, u, b, h, nu, w, 0.25);
     qtt_mps v1, v2;
     int cg = 0, sw = 0;
     project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
@@ -1704,7 +1869,7 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
 // One penalised minimisation with a = u (scale 1) and the given b, h.
 void euler_min(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr v[2]) {
   MpsPtr w[2];
-  stage_w(ctx, u, b, h, nu, w, 1.0);
+  stage_w_run(ctx, u, b, h, nu, w, 1.0);
   qtt_mps v1, v2;
   int cg = 0, sw = 0;
   project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
@@ -1889,7 +2054,8 @@ bool valid_params(const qtt_params* p) {
          p->max_sweeps >= 1 && (p->precision == QTT_PREC_FP64 || p->precision == QTT_PREC_MIXED) &&
          p->learned_trunc >= QTT_LEARNED_OFF && p->learned_trunc <= QTT_LEARNED_ON &&
          (p->learned_trunc != QTT_LEARNED_LOG || p->precision == QTT_PREC_FP64) &&
-         p->rf_oversample >= 0 && p->rf_oversample <= 256 && p->rf_min_width >= 1;
+         p->rf_oversample >= 0 && p->rf_oversample <= 256 && p->rf_min_width >= 1 &&
+         (p->graphs == 0 || p->graphs == 1);
 }
 
 void check_mps(qtt_ctx ctx, qtt_mps m) {
@@ -1978,6 +2144,8 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
   if (!ctx) return QTT_ERR_ARG;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  graphs_clear(ctx);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   for (int i = 0; i < 2; i++) mpo_release(ctx->D[i]);
   mpo_release(ctx->lap);
   for (int i = 0; i < 2; i++)
@@ -2008,8 +2176,11 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
 
 qtt_status qtt_set_params(qtt_ctx ctx, const qtt_params* p) {
   if (!ctx || !valid_params(p) || p->n != ctx->p.n || p->L != ctx->p.L) return QTT_ERR_ARG;
-  ctx->p = *p;
-  return QTT_OK;
+  return guarded(ctx, [&]() -> qtt_status {
+    graphs_clear(ctx);  // captured with the previous eps / chi / precision
+    ctx->p = *p;
+    return QTT_OK;
+  });
 }
 
 qtt_status qtt_sync(qtt_ctx ctx) {
@@ -2052,6 +2223,36 @@ qtt_status qtt_mps_from_packed(qtt_ctx ctx, const double* cores, int cores_are_d
                                    cudaMemcpyHostToDevice, ctx->stream));
     QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
     *out = m.release();
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_mps_upload_packed(qtt_ctx ctx, qtt_mps dst, const double* cores,
+                                 int cores_are_device, const int* bonds) {
+  if (!dst || !cores || !bonds) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, dst);
+    const int n = dst->n;
+    std::vector<int> d(bonds, bonds + n + 1);
+    if (d[0] != 1 || d[n] != 1) throw QttError(QTT_ERR_SHAPE, "end bonds must be 1");
+    for (int b = 1; b < n; b++)
+      if (d[b] < 1 || d[b] > dst->cap[b])
+        throw QttError(QTT_ERR_SHAPE, "bond dimension above the MPS's capacity");
+    cudaStream_t s = ctx->stream;
+    // capacity storage: rows (a, s) of length cap[k+1], the actual block in
+    // the leading rows and columns, zero elsewhere
+    QTT_CUDA_CHECK(cudaMemsetAsync(dst->data, 0, dst->off[n] * sizeof(double), s));
+    const cudaMemcpyKind kind = cores_are_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t o = 0;
+    for (int k = 0; k < n; k++) {
+      QTT_CUDA_CHECK(cudaMemcpy2DAsync(dst->core(k), dst->cap[k + 1] * sizeof(double), cores + o,
+                                       d[k + 1] * sizeof(double), d[k + 1] * sizeof(double),
+                                       (size_t)d[k] * 4, kind, s));
+      o += (size_t)d[k] * 4 * d[k + 1];
+    }
+    QTT_CUDA_CHECK(cudaMemcpyAsync(dst->dims, d.data(), (n + 1) * sizeof(int),
+                                   cudaMemcpyHostToDevice, s));
+    QTT_CUDA_CHECK(cudaStreamSynchronize(s));
     return QTT_OK;
   });
 }
@@ -2239,6 +2440,13 @@ qtt_status qtt_inner(qtt_ctx ctx, qtt_mps a, qtt_mps b, double* out) {
     *out = inner_impl(ctx, a, b);
     return check_device_errors(ctx);
   });
+}
+
+qtt_status qtt_graph_stats(qtt_ctx ctx, long long* captured, long long* replays) {
+  if (!ctx || !captured || !replays) return QTT_ERR_ARG;
+  *captured = ctx->graphs_captured;
+  *replays = ctx->graph_replays;
+  return QTT_OK;
 }
 
 qtt_status qtt_profile_begin(qtt_ctx ctx) {

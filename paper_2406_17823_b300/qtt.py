@@ -37,7 +37,8 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_learned_set", "qtt_learned_next_step", "qtt_learned_log", "qtt_learned_stats",
            "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
            "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
-           "qtt_euler_step", "qtt_rk2_step", "qtt_inner")
+           "qtt_euler_step", "qtt_rk2_step", "qtt_inner", "qtt_graph_stats",
+           "qtt_mps_upload_packed")
 
 
 class QttError(RuntimeError):
@@ -50,7 +51,8 @@ class Params(ctypes.Structure):
     _fields_ = [("n", c_int), ("L", c_double), ("eps", c_double), ("chi_max", c_int),
                 ("mu", c_double), ("cg_tol", c_double), ("cg_maxit", c_int),
                 ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int),
-                ("learned_trunc", c_int), ("rf_oversample", c_int), ("rf_min_width", c_int)]
+                ("learned_trunc", c_int), ("rf_oversample", c_int), ("rf_min_width", c_int),
+                ("graphs", c_int)]
 
 
 _lib = None
@@ -91,6 +93,8 @@ def lib():
             "qtt_rk2_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong),
                                   POINTER(c_longlong)]),
+            "qtt_graph_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong)]),
+            "qtt_mps_upload_packed": (c_int, [vp, vp, vp, c_int, ip]),
             "qtt_profile_begin": (c_int, [vp]),
             "qtt_profile_end": (c_int, [vp, ctypes.c_char_p, c_size_t]),
             "qtt_to_dense_noalloc": (c_int, [vp, ip, c_int, vp, vp]),
@@ -158,7 +162,7 @@ class Context:
                  mu: float = 2.5e5, cg_tol: float = 1e-5, cg_maxit: int = 100,
                  sweep_tol: float = 1e-5, max_sweeps: int = 20, precision: int = PREC_FP64,
                  learned_trunc: int = LEARNED_OFF, rf_oversample: int = 8,
-                 rf_min_width: int = 128,
+                 rf_min_width: int = 128, graphs: int = 0,
                  device: int = 0, stream=None):
         torch = _torch()
         self.device = device
@@ -166,7 +170,7 @@ class Context:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         self.params = Params(n, L, eps, chi_max, mu, cg_tol, cg_maxit, sweep_tol, max_sweeps,
-                             precision, learned_trunc, rf_oversample, rf_min_width)
+                             precision, learned_trunc, rf_oversample, rf_min_width, graphs)
         h = c_void_p()
         st = lib().qtt_create(byref(h), device, c_void_p(stream.cuda_stream), byref(self.params))
         if st != 0:
@@ -229,6 +233,15 @@ class Context:
         self._check(lib().qtt_mps_from_packed(self.h, c_void_p(flat.ctypes.data), 0, b,
                                               byref(out)))
         return MPS(self, out.value)
+
+    def upload_cores(self, mps: MPS, cores):
+        """Overwrite `mps` with numpy cores (host buffer path), keeping its
+        capacities (each bond at most the MPS's capacity)."""
+        bonds = [1] + [int(c.shape[2]) for c in cores]
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(c, np.float64).reshape(-1)
+                                                    for c in cores]))
+        b = (c_int * len(bonds))(*bonds)
+        self._check(lib().qtt_mps_upload_packed(self.h, mps.h, c_void_p(flat.ctypes.data), 0, b))
 
     def to_cores(self, mps: MPS):
         n = self.params.n
@@ -345,6 +358,12 @@ class Context:
         self._check(lib().qtt_stats(self.h, byref(a), byref(b), byref(c)))
         return {"cg_iters": a.value, "sweeps": b.value, "launches": c.value}
 
+    def graph_stats(self):
+        """(stage graphs captured and kept, stage replays) of this context."""
+        a, b = c_longlong(), c_longlong()
+        self._check(lib().qtt_graph_stats(self.h, byref(a), byref(b)))
+        return a.value, b.value
+
     # -------------------------------------------------- learned truncation
     def learned_set(self, params):
         """Install perceptron parameters (torch float32 tensor on the device)."""
@@ -431,7 +450,7 @@ class Batch:
                             kw.pop("cg_maxit", 100), kw.pop("sweep_tol", 1e-5),
                             kw.pop("max_sweeps", 20), kw.pop("precision", PREC_FP64),
                             kw.pop("learned_trunc", LEARNED_OFF), kw.pop("rf_oversample", 8),
-                            kw.pop("rf_min_width", 128))
+                            kw.pop("rf_min_width", 128), kw.pop("graphs", 0))
             if kw:
                 raise TypeError(f"unknown parameters {sorted(kw)}")
         h = c_void_p()

@@ -42,13 +42,13 @@ def test_params_layout_matches_header():
 #include <stddef.h>
 #include "qtt.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(qtt_params),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(qtt_params),
          offsetof(qtt_params, n), offsetof(qtt_params, L), offsetof(qtt_params, eps),
          offsetof(qtt_params, chi_max), offsetof(qtt_params, mu), offsetof(qtt_params, cg_tol),
          offsetof(qtt_params, cg_maxit), offsetof(qtt_params, sweep_tol),
          offsetof(qtt_params, max_sweeps), offsetof(qtt_params, precision),
          offsetof(qtt_params, learned_trunc), offsetof(qtt_params, rf_oversample),
-         offsetof(qtt_params, rf_min_width), QTT_MLP_PARAMS);
+         offsetof(qtt_params, rf_min_width), offsetof(qtt_params, graphs), QTT_MLP_PARAMS);
   return 0;
 }
 """
@@ -79,9 +79,9 @@ def test_null_arguments_are_rejected_without_gpu(libpath):
 
 def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
     """Argument checks happen before any CUDA call: the learned-truncation,
-    perceptron, batch, lower-order step and inner-product entry points all
-    return QTT_ERR_ARG for null handles or pointers, on a machine without a
-    GPU."""
+    perceptron, batch, lower-order step, inner-product, graph-statistics and
+    upload entry points all return QTT_ERR_ARG for null handles or pointers, on a
+    machine without a GPU."""
     lib = ctypes.CDLL(libpath)
     vp = ctypes.c_void_p
     calls = [
@@ -99,6 +99,8 @@ def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
         ("qtt_euler_step", [vp, vp, vp, ctypes.c_double, ctypes.c_double], (None, None, None, 1e-3, 0.0)),
         ("qtt_rk2_step", [vp, vp, vp, ctypes.c_double, ctypes.c_double], (None, None, None, 1e-3, 0.0)),
         ("qtt_inner", [vp, vp, vp, vp], (None,) * 4),
+        ("qtt_graph_stats", [vp, vp, vp], (None,) * 3),
+        ("qtt_mps_upload_packed", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 0, None)),
     ]
     for name, argtypes, args in calls:
         f = getattr(lib, name)
