@@ -313,6 +313,7 @@ def main():
         step()
     barrier()
     launches0 = sum(c.stats()["launches"] for c in ctxs)
+    replays0 = sum(c.graph_stats()[1] for c in ctxs)
     times = []
     converged = True
     with ClockSampler(local) as clk:
@@ -340,7 +341,7 @@ def main():
         wall = time.perf_counter() - wall0
     torch.cuda.synchronize()
     gpu_launches = sum(c.stats()["launches"] for c in ctxs) - launches0
-    replays = sum(c.graph_stats()[1] for c in ctxs)
+    replays = sum(c.graph_stats()[1] for c in ctxs) - replays0
     # per-kernel device times for the roofline: one more step under the
     # launch profiler (CUDA events around every launch, which also makes the
     # stages launch eagerly), outside the timed region
@@ -426,7 +427,7 @@ def main():
                        "host clock between device-wide synchronisations (library-owned streams)"),
             "config": {**w, "precision": args.precision, "parallelism": f"replicas x{world}",
                        "trajectories": B, "stage_graphs": bool(graphs),
-                       "stage_graph_replays": replays,
+                       "stage_graph_replays_timed": replays,
                        "l2": "flushed between timed steps (256 MB write)",
                        "all_projections_converged": bool(converged)},
             "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
