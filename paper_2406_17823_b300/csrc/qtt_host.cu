@@ -846,9 +846,10 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     }
     if (!done && mixed) {
       // Rayleigh-Ritz: FP32 finds an oversampled subspace of right vectors,
-      // FP64 orthonormalises it, projects B = M V exactly and makes the
-      // (eps, chi) cut by an FP64 SVD of B, counting the weight of M outside
-      // the subspace (|M|^2 - |B|^2, FP64) as discarded.
+      // one FP64 subspace iteration refines it and orthonormalises it, B =
+      // M V is projected exactly and the (eps, chi) cut is made by an FP64
+      // SVD of B, counting the weight of M outside the subspace
+      // (|M|^2 - |B|^2, FP64) as discarded.
       const int rpo = std::min({qcap[k], 4 * ocap[k + 1], chi + kOver});
       SvdArgs a32 = a;
       a32.eps = -1.0;
@@ -866,12 +867,24 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
         q.work = W.p;
         q.work_len = (long long)W.n;
         q.err = ctx->d_err;
-        launch_qr_f64(q, 4 * ocap[k + 1], rpo, s);
-        // B = M V  (qcap x rpo), and |M|_F^2
+        // one FP64 subspace iteration from the FP32 vectors V_32:
+        // V = orth(M^T M V_32) = orth((B_0^T M)^T) with B_0 = M V_32.  The
+        // FP32 search leaves every kept direction off by about the FP32
+        // rounding of M (relative to |M|); the iteration shrinks that by
+        // (sigma_{p+1} / sigma_i)^2, p = rpo, and its Householder QR makes V
+        // orthonormal in FP64.  Then B = M V (qcap x rpo), and |M|_F^2.
         GemmF64 g = gemm_plain(Mp, Vt.p, Bm.p, qcap[k], rpo, 4 * ocap[k + 1], 4 * ocap[k + 1],
                                4 * ocap[k + 1], rpo);
         g.tB = 1;
         gemm(g, s);
+        {
+          GemmF64 gz = gemm_plain(Bm.p, Mp, Vt.p, rpo, 4 * ocap[k + 1], qcap[k], rpo,
+                                  4 * ocap[k + 1], 4 * ocap[k + 1]);
+          gz.tA = 1;
+          gemm(gz, s);
+          launch_qr_f64(q, 4 * ocap[k + 1], rpo, s);
+          gemm(g, s);
+        }
         launch_sumsq2(Mp, (long long)qcap[k] * 4 * ocap[k + 1], Mp, 0, wM.p, s);
         // G = B^T B (rpo x rpo, into Rs, free after the gauge QR): its SVD
         // gives V_B and the weights sigma_B^2 without factoring B itself
@@ -1086,8 +1099,9 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
     bool done = false;
     if (mixed) {
       // Rayleigh-Ritz: FP32 finds an oversampled subspace (chi + kOver
-      // directions), FP64 orthonormalises it (Householder), projects
-      // B = Q^T T exactly and makes the cap-chi cut by an FP64 SVD of B.
+      // directions), one FP64 subspace iteration refines it and
+      // orthonormalises it (Householder), B = Q^T T is projected exactly
+      // and the cap-chi cut is made by an FP64 SVD of B.
       const int rpo = std::min({4 * rcap[k], ca[k + 1] * cb[k + 1], chi + kOver});
       SvdArgs a32 = a;
       a32.chi = chi + kOver;
@@ -1102,12 +1116,23 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
         q.work = W.p;
         q.work_len = (long long)W.n;
         q.err = ctx->d_err;
-        launch_qr_f64(q, 4 * rcap[k], rpo, s);
-        // B = Q^T T  (rpo x (a', b'))
+        // one FP64 subspace iteration from the FP32 vectors U_32:
+        // Q = orth(T T^T U_32) = orth(T B_0^T) with B_0 = U_32^T T (the FP32
+        // search's error shrinks by (sigma_{p+1} / sigma_i)^2; the
+        // Householder QR makes Q orthonormal in FP64); then B = Q^T T
+        // (rpo x (a', b'))
         GemmF64 g = gemm_plain(Ut.p, Tb.p, Bt.p, rpo, ca[k + 1] * cb[k + 1], 4 * rcap[k], rpo,
                                ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
         g.tA = 1;
         gemm(g, s);
+        {
+          GemmF64 gy = gemm_plain(Tb.p, Bt.p, Ut.p, 4 * rcap[k], rpo, ca[k + 1] * cb[k + 1],
+                                  ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1], rpo);
+          gy.tB = 1;
+          gemm(gy, s);
+          launch_qr_f64(q, 4 * rcap[k], rpo, s);
+          gemm(g, s);
+        }
         // G = B B^T (rpo x rpo, into Rs): its SVD gives U_B (into Ub) for
         // the cap-chi cut without factoring the long B
         {

@@ -1,11 +1,12 @@
-"""Parity at the bench's full size (2^10 x 2^10, chi = 64, eps = 1e-8), op by op.
+"""Parity at the bench's full size (2^10 x 2^10, chi = 64, eps = 1e-8).
 
-A whole RK4 step of the oracle at this size takes minutes, so the step's
-operations are compared one at a time on the bench workload's own state
-(the seeded shear jet): the TT-SVD of the initial field, the derivative and
+The step's operations one at a time on the bench workload's own state (the
+seeded shear jet): the TT-SVD of the initial field, the derivative and
 Laplacian MPO applications, the Hadamard product of the convection term and
-a block-diagonal sum, each against the FP64 oracle to 1e-10 relative L2 on
-the reconstructed dense fields.
+a block-diagonal sum; then one whole RK4 step at the bench's settings (about
+half a minute of oracle time), with the stage graphs the bench replays.
+Each against the FP64 oracle to 1e-10 relative L2 on the reconstructed
+dense fields.
 """
 import numpy as np
 import pytest
@@ -60,3 +61,25 @@ def test_add_full_size(state):
     g = ctx.add([0.25, -3e-4], [ctx.from_cores(A), ctx.from_cores(B)])
     o = Q.add([0.25, -3e-4], [A, B], EPS, CHI)
     assert rel(ctx.to_dense(g).cpu().numpy(), Q.to_dense(o)) <= TOL
+
+
+def test_rk4_step_full_size(state):
+    """One RK4 step of the bench workload (paper solver settings, Re = 2e5,
+    dt = 0.1 dx / max|u0|), twice on the GPU so that the second step runs
+    from replayed stage graphs, against two oracle steps."""
+    import paper_2406_17823_b300 as P
+    _, (u, v), A, B, ops = state
+    dx = 2 * np.pi / 2 ** N_BITS
+    dt, nu = 0.1 * dx / float(np.abs(u).max()), 1 / 2e5
+    ctx = P.Context(N_BITS, eps=EPS, chi_max=CHI, graphs=1)
+    g = [ctx.from_cores(c) for c in (A, B)]
+    o = [A, B]
+    prm = Q.Params(eps=EPS, chi_max=CHI)
+    for _ in range(2):
+        ctx.rk4_step(g[0], g[1], dt, nu)
+        o = Q.rk4_step(o, dt, nu, prm, ops)
+    assert ctx.graph_stats()[1] >= 2
+    for got, ref in zip(g, o):
+        r = rel(ctx.to_dense(got).cpu().numpy(), Q.to_dense(ref))
+        print(f"full-size RK4, two steps: relative L2 {r:.2e}")
+        assert r <= TOL

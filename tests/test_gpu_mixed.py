@@ -98,3 +98,24 @@ def test_mixed_matches_fp64_at_full_size(P):
     mix.rk4_step(gmx[0], gmx[1], dt, 1 / 2e5)
     for i in range(2):
         assert rel(dense(mix, gmx[i]), dense(f64, g64[i])) < TOL
+
+
+def test_mixed_stays_within_bar_over_steps(P):
+    """Six RK4 steps, mixed against FP64 on the GPU (2^7 jet, chi 64, which
+    is the natural bound there): the per-cut error of the FP32 subspace
+    search is shrunk by one FP64 subspace iteration, so the difference does
+    not build up past the bar."""
+    n = 7
+    u, dx = I.shear_jet(n, seed=0)
+    dt = 0.1 * dx / np.abs(u[0]).max()
+    f64 = P.Context(n, eps=1e-8, chi_max=64)
+    mix = P.Context(n, eps=1e-8, chi_max=64, precision=P.PREC_MIXED)
+    gf = [f64.from_dense(f) for f in u]
+    gm = [mix.from_cores(f64.to_cores(x)) for x in gf]
+    errs = []
+    for _ in range(6):
+        f64.rk4_step(gf[0], gf[1], dt, 1 / 2e5)
+        mix.rk4_step(gm[0], gm[1], dt, 1 / 2e5)
+        errs.append(max(rel(dense(mix, gm[i]), dense(f64, gf[i])) for i in range(2)))
+    print("mixed vs FP64 after 1..6 steps:", ["%.1e" % e for e in errs])
+    assert max(errs) < TOL
