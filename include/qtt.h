@@ -57,8 +57,9 @@ typedef enum {
 
 typedef enum {
   QTT_PREC_FP64 = 0,   /* every contraction and factorisation in FP64      */
-  QTT_PREC_MIXED = 1   /* FP32 subspace search; FP64 gauge QR, projection,
-                          truncation weights and projection residual        */
+  QTT_PREC_MIXED = 1   /* FP32 subspace search refined by one FP64
+                          subspace iteration; FP64 projection, truncation
+                          weights and projection residual                    */
 } qtt_precision;
 
 /* Learned truncation modes (qtt_params.learned_trunc). */
