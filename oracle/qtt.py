@@ -620,7 +620,10 @@ def stage_w(u, b, h, nu, params: Params, ops: Operators, a_scale: float = 0.25):
     the Euler and RK2 minimisations) with the skew-symmetric convection term
     B_i = sum_j 1/2 (b_j (.) D_j b_i + D_j (b_j (.) b_i)) - nu D_j^2 b_i
     (App. B, Eq. for B_i).  Every intermediate is compressed to
-    (eps, chi_max); the sums are taken pairwise in the order below.
+    (eps, chi_max); the sums are taken pairwise in the order below (the
+    paper fixes none): c_a = P_0 + P_1, c_b = DQ_0 + DQ_1, conv =
+    (c_a + c_b) / 2, e = a_scale u + h nu Lap b, w = e - h conv, i.e.
+    w = a_scale u - h (conv - nu Lap b) with the viscous term folded into e.
     """
     eps, chi = params.eps, params.chi_max
     Db = {(j, i): apply_mpo(ops.D[j], b[i], eps, chi) for i in range(2) for j in range(2)}
@@ -636,9 +639,9 @@ def stage_w(u, b, h, nu, params: Params, ops: Operators, a_scale: float = 0.25):
     for i in range(2):
         ca = add([1.0, 1.0], [P[(0, i)], P[(1, i)]], eps, chi)
         cb = add([1.0, 1.0], [DQ[(0, i)], DQ[(1, i)]], eps, chi)
+        e = add([a_scale, h * nu], [u[i], Lb[i]], eps, chi)
         conv = add([0.5, 0.5], [ca, cb], eps, chi)
-        B = add([1.0, -nu], [conv, Lb[i]], eps, chi)
-        w.append(add([a_scale, -h], [u[i], B], eps, chi))
+        w.append(add([1.0, -h], [e, conv], eps, chi))
     return w
 
 

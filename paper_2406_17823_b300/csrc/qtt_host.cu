@@ -1629,14 +1629,16 @@ void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPt
   const int chi = ctx->p.chi_max;
   Workers wk(ctx);
   MpsPtr Db[2][2], P[2][2], Q[2][2], DQ[2][2], Lb[2];
-  MpsPtr ca[2], cb[2], conv[2], B[2];
+  MpsPtr ca[2], cb[2], conv[2], e[2];
   // Dataflow over the worker streams: every operation starts as soon as its
   // own inputs are done (an operation on its input's stream is ordered by
   // the stream, others wait on an event), instead of wave by wave.
-  //   streams 0-3  D_j b_i -> b_j (.) D_j b_i -> (i: sum over j -> conv -> B -> w)
+  //   streams 0-3  D_j b_i -> b_j (.) D_j b_i -> (i: sum over j -> conv -> w)
   //   streams 4-6  b_j (.) b_i -> D_j (b_j (.) b_i)
   //   stream  9    D_1 (b_1 (.) b_0) (waits for stream 5)
-  //   streams 7-8  Lap b_i
+  //   streams 7-8  Lap b_i -> e_i = a u_i + h nu Lap b_i
+  // The viscous term is folded into e (w = e - h conv), off the chain of
+  // sums that follows the last Hadamard product.
   auto sDb = [](int j, int i) { return 2 * i + j; };
   wk.fork();
   for (int i = 0; i < 2; i++)
@@ -1666,11 +1668,11 @@ void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPt
     // D_0 q + D_1 q on the stream of DQ[0][i], after DQ[1][i]
     wk.after(sDQ[0][i], sDQ[1][i]);
     cb[i] = MpsPtr(wk.run(sDQ[0][i], [&] { return add2(ctx, 1.0, DQ[0][i].get(), 1.0, DQ[1][i].get()); }));
+    e[i] = MpsPtr(wk.run(7 + i, [&] { return add2(ctx, a_scale, u[i], h * nu, Lb[i].get()); }));
     wk.after(si, sDQ[0][i]);
     conv[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 0.5, ca[i].get(), 0.5, cb[i].get()); }));
     wk.after(si, 7 + i);
-    B[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 1.0, conv[i].get(), -nu, Lb[i].get()); }));
-    w[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, a_scale, u[i], -h, B[i].get()); }));
+    w[i] = MpsPtr(wk.run(si, [&] { return add2(ctx, 1.0, e[i].get(), -h, conv[i].get()); }));
   }
   // every worker joins the context stream; all outputs and intermediates
   // are then released on it
@@ -1678,7 +1680,7 @@ void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPt
            Q[0][1].get(), Q[1][1].get(), Lb[0].get(), Lb[1].get(), P[0][0].get(), P[0][1].get(),
            P[1][0].get(), P[1][1].get(), DQ[0][0].get(), DQ[0][1].get(), DQ[1][0].get(),
            DQ[1][1].get(), ca[0].get(), ca[1].get(), cb[0].get(), cb[1].get(), conv[0].get(),
-           conv[1].get(), B[0].get(), B[1].get(), w[0].get(), w[1].get()});
+           conv[1].get(), e[0].get(), e[1].get(), w[0].get(), w[1].get()});
 }
 
 // ------------------------------------------------ stage graphs (params.graphs)
