@@ -126,6 +126,13 @@ struct CgVec {
 void launch_cg_start(const CgVec& v, const double* b0, const double* b1, double* scal, int* ist,
                      double tol, int* err, cudaStream_t s);
 void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err, cudaStream_t s);
+// device-driven loops of a captured step (see kernels_misc.cu)
+void launch_loop_cond(cudaGraphConditionalHandle h, int* counter, const int* stop, int cap,
+                      int first, cudaStream_t s);
+void launch_cg_account(const int* ist, long long* stats, int maxit, cudaStream_t s);
+void launch_sweep_check(double* scal, int* stop, long long* stats, double tol, int init,
+                        cudaStream_t s);
+void launch_sweep_final(const int* stop, long long* stats, cudaStream_t s);
 void launch_sumsq2(const double* a, long long na, const double* b, long long nb, double* out,
                    cudaStream_t s);
 

@@ -420,6 +420,71 @@ void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err,
   k_cg_step<<<1, 1024, 0, s>>>(v, scal, ist, maxit, err);
   post_launch("k_cg_step", s);
 }
+// ---- device-driven loops of a captured step (WHILE graph nodes)
+// The loop condition of a WHILE node: iteration `counter` (0 on the first
+// call) continues while counter < cap and *stop == 0.  The counter makes
+// every loop end after at most cap iterations whatever the stop word holds.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, int* counter, const int* stop, int cap,
+                            int first) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int c = first ? 0 : *counter + 1;
+  *counter = c;
+  cudaGraphSetConditional(h, (c < cap && !(stop && *stop)) ? 1u : 0u);
+}
+void launch_loop_cond(cudaGraphConditionalHandle h, int* counter, const int* stop, int cap,
+                      int first, cudaStream_t s) {
+  pre_launch(s);
+  k_loop_cond<<<1, 32, 0, s>>>(h, counter, stop, cap, first);
+  post_launch("k_loop_cond", s);
+}
+
+// After a device-driven CG solve: stats[0] += iterations; a solve that hit
+// the iteration cap marks the step not converged (stats[2]).
+__global__ void k_cg_account(const int* ist, long long* stats, int maxit) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  stats[0] += ist[1];
+  if (ist[1] >= maxit) stats[2] = 1;
+}
+void launch_cg_account(const int* ist, long long* stats, int maxit, cudaStream_t s) {
+  pre_launch(s);
+  k_cg_account<<<1, 32, 0, s>>>(ist, stats, maxit);
+  post_launch("k_cg_account", s);
+}
+
+// Sweep convergence on the device, the host rule restated: with N = scal[6]
+// (sum of <v_i|v_i> after the sweep) and N_prev = scal[7], stop when N == 0
+// or |N - N_prev| <= tol N; N_prev <- N; stats[1] counts sweeps.  init: only
+// N_prev <- N and stop <- 0 (before the first sweep).
+__global__ void k_sweep_check(double* scal, int* stop, long long* stats, double tol, int init) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double nn = scal[6];
+  if (!init) {
+    const double np = scal[7];
+    *stop = (nn == 0.0 || fabs(nn - np) <= tol * nn) ? 1 : 0;
+    stats[1] += 1;
+  } else {
+    *stop = 0;
+  }
+  scal[7] = nn;
+}
+void launch_sweep_check(double* scal, int* stop, long long* stats, double tol, int init,
+                        cudaStream_t s) {
+  pre_launch(s);
+  k_sweep_check<<<1, 32, 0, s>>>(scal, stop, stats, tol, init);
+  post_launch("k_sweep_check", s);
+}
+// After the sweep loop: a loop that ended without the stop word set ran into
+// its cap (stats[2] = 1).
+__global__ void k_sweep_final(const int* stop, long long* stats) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!*stop) stats[2] = 1;
+}
+void launch_sweep_final(const int* stop, long long* stats, cudaStream_t s) {
+  pre_launch(s);
+  k_sweep_final<<<1, 32, 0, s>>>(stop, stats);
+  post_launch("k_sweep_final", s);
+}
+
 void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, double alpha,
                        double beta, const int* skip, cudaStream_t s) {
   if (M <= 0 || N <= 0 || S <= 0) return;

@@ -207,6 +207,15 @@ struct qtt_ctx_s {
   std::map<std::string, std::unique_ptr<StageGraph>> graphs;
   static constexpr int kMaxGraphs = 16;  // captured graphs kept per context
   long long graphs_captured = 0, graph_replays = 0;
+  // whole-step graphs (params.graphs = 2): the projection's CG and sweep
+  // loops run as WHILE nodes, captured on the body streams; their counters
+  // and the step statistics live on the device until the next sync
+  std::map<std::string, std::unique_ptr<StageGraph>> step_graphs;
+  cudaStream_t bstream[2] = {nullptr, nullptr};
+  bool dev_loops = false;      // set while a step is being captured
+  long long* d_stats = nullptr;  // [0] CG iterations, [1] sweeps, [2] not converged
+  int* d_loop = nullptr;         // [0..1] loop counters, [2] sweep stop word
+  bool stats_pending = false;
 };
 
 namespace {
@@ -324,6 +333,14 @@ struct MpsPtr {
 // slices (S > 1: single products only): the slices run as one batched
 // launch into scratch, then C = alpha * (sum of the slices, in slice order:
 // deterministic) + beta * C; a skip flag skips both launches.
+// Split-K scratch supplied by the caller (a buffer made before a capture
+// whose conditional bodies may not allocate); null: allocate per product.
+thread_local double* t_gemm_scratch = nullptr;
+thread_local size_t t_gemm_scratch_n = 0;
+// set while a graph is being captured: products of a shape not met before
+// take the fixed rule instead of being timed (timing waits for the device)
+thread_local bool t_capturing = false;
+
 void gemm_run(const GemmF64& g, int tile, int S, cudaStream_t s) {
   if (S <= 1 || g.nb1 * g.nb2 != 1 || g.K < 2) {
     launch_gemm_f64_tile(g, tile, s);
@@ -332,9 +349,17 @@ void gemm_run(const GemmF64& g, int tile, int S, cudaStream_t s) {
   const int chunk = (g.K + S - 1) / S;
   const int full = g.K / chunk, rem = g.K - full * chunk;
   const int Sx = full + (rem > 0 ? 1 : 0);
-  DBuf<double> P((size_t)Sx * g.M * g.N, s);
+  const size_t need = (size_t)Sx * g.M * g.N;
+  DBuf<double> Pown;
+  double* Pp = t_gemm_scratch;
+  if (Pp) {
+    if (need > t_gemm_scratch_n) throw QttError(QTT_ERR_SHAPE, "split-K scratch too small");
+  } else {
+    Pown = DBuf<double>(need, s);
+    Pp = Pown.p;
+  }
   GemmF64 b = g;
-  b.C = P.p;
+  b.C = Pp;
   b.ldc = g.N;
   b.alpha = 1.0;
   b.beta = 0.0;
@@ -351,10 +376,10 @@ void gemm_run(const GemmF64& g, int tile, int S, cudaStream_t s) {
     r.nb1 = 1;
     r.A = g.A + full * b.sA1;
     r.B = g.B + full * b.sB1;
-    r.C = P.p + full * b.sC1;
+    r.C = Pp + full * b.sC1;
     launch_gemm_f64_tile(r, tile, s);
   }
-  launch_sum_slices(P.p, Sx, g.M, g.N, g.C, g.ldc, g.alpha, g.beta, g.skip, s);
+  launch_sum_slices(Pp, Sx, g.M, g.N, g.C, g.ldc, g.alpha, g.beta, g.skip, s);
 }
 
 // The fixed rule: 64 x 64 tiles, K cut into slices of at least 32 while the
@@ -446,6 +471,10 @@ void gemm(const GemmF64& g, cudaStream_t s) {
       ch = it->second;
       found = true;
     }
+  }
+  if (!found && t_capturing) {
+    gemm_run(g, 0, split_rule(g), s);
+    return;
   }
   if (!found) {
     ch = gemm_tune(g, s);
@@ -1187,6 +1216,47 @@ struct Env {
   std::vector<DBuf<double>> b;  // per bond
 };
 
+// Appends to the graph that stream s is capturing a WHILE node whose body
+// is captured from body(bs) on stream bs, followed by the loop condition:
+// iteration i (0 on entry) runs while i < cap and *stop == 0, so the loop
+// ends after at most cap iterations whatever the stop word does.
+template <typename F>
+void capture_while(cudaStream_t s, cudaStream_t bs, int* counter, const int* stop, int cap,
+                   F&& body) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  QTT_CUDA_CHECK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) throw QttError(QTT_ERR_CUDA, "device loop outside a capture");
+  cudaGraphConditionalHandle h;
+  QTT_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  launch_loop_cond(h, counter, stop, cap, 1, s);
+  QTT_CUDA_CHECK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  QTT_CUDA_CHECK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp));
+  cudaGraph_t body_graph = cp.conditional.phGraph_out[0];
+  QTT_CUDA_CHECK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                                     cudaStreamSetCaptureDependencies));
+  QTT_CUDA_CHECK(cudaStreamBeginCaptureToGraph(bs, body_graph, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+  try {
+    body(bs);
+    launch_loop_cond(h, counter, stop, cap, 0, bs);
+  } catch (...) {
+    cudaGraph_t x = nullptr;
+    cudaStreamEndCapture(bs, &x);
+    throw;
+  }
+  cudaGraph_t done = nullptr;
+  QTT_CUDA_CHECK(cudaStreamEndCapture(bs, &done));
+}
+
 struct Projector {
   qtt_ctx ctx;
   cudaStream_t s;
@@ -1203,6 +1273,7 @@ struct Projector {
   DBuf<double> scal;
   DBuf<int> ist;
   size_t maxcore = 0;
+  size_t maxout = 1;  // largest product output of the projection (split-K scratch sizing)
 
   const std::vector<int>& cap(int i) const { return V[i]->cap; }
 
@@ -1249,6 +1320,12 @@ struct Projector {
         qrw = std::max(qrw, qr_work_doubles(4 * cap(i)[k + 1], cap(i)[k]));
       }
     maxcore = cm;
+    maxout = std::max({t1m, t2m, cm});
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++)
+        for (int b = 0; b <= n; b++) maxout = std::max(maxout, LE[i][j][b].n);
+    for (int i = 0; i < 2; i++)
+      for (int b = 0; b <= n; b++) maxout = std::max(maxout, LW[i][b].n);
     t1 = DBuf<double>(t1m, s);
     t2 = DBuf<double>(t2m, s);
     t1b = DBuf<double>(t1m, s);
@@ -1257,6 +1334,7 @@ struct Projector {
     for (int i = 0; i < 2; i++)
       for (int b = 0; b <= n; b++) cmax = std::max(cmax, cap(i)[b]);
     rb = DBuf<double>((size_t)cmax * cmax, s);
+    maxout = std::max(maxout, (size_t)cmax * cmax);
     tmp = DBuf<double>(cm, s);
     work = DBuf<double>(qrw, s);
     vt_i = DBuf<double>(cm, s);
@@ -1367,7 +1445,9 @@ struct Projector {
   // stream.
   void matvec(int d, double* const X[2], double* const Y[2], const int* skip) {
     cudaStream_t ps = s;
-    const bool par = ctx->workers[0] != nullptr && ctx->workers[1] != nullptr;
+    // a captured step's loop bodies stay on their own stream (the worker
+    // streams belong to the enclosing capture)
+    const bool par = !ctx->dev_loops && ctx->workers[0] != nullptr && ctx->workers[1] != nullptr;
     if (par) {
       QTT_CUDA_CHECK(cudaEventRecord(ctx->fork_ev, ps));
       for (int i = 0; i < 2; i++) QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[i], ctx->fork_ev, 0));
@@ -1438,6 +1518,20 @@ struct Projector {
     matvec(d, X, AP, nullptr);
     launch_cg_start(v, rhs[0].p, rhs[1].p, scal.p, ist.p, ctx->p.cg_tol, ctx->d_err, s);
     const int maxit = ctx->p.cg_maxit;
+    if (ctx->dev_loops) {
+      // a WHILE node of at most maxit iterations, ended by the CG's own stop
+      // word (converged, iteration cap, breakdown): the host loop below
+      // without its reads, iterations counted on the device
+      const cudaStream_t outer = s;
+      capture_while(outer, ctx->bstream[1], ctx->d_loop + 1, ist.p, maxit, [&](cudaStream_t bs) {
+        s = bs;
+        matvec(d, P, AP, ist.p);
+        launch_cg_step(v, scal.p, ist.p, maxit, ctx->d_err, s);
+        s = outer;
+      });
+      launch_cg_account(ist.p, ctx->d_stats, maxit, s);
+      return 0;
+    }
     int done_iters = 0;
     const int chunk = 8;
     for (int it = 0; it < maxit; it += chunk) {
@@ -1533,9 +1627,57 @@ void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qt
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
   P.alloc();
+  DBuf<double> arena(ctx->dev_loops ? 16 * P.maxout : 0, P.s);
+  struct ScratchScope {  // split-K scratch of a captured step's loop bodies
+    explicit ScratchScope(DBuf<double>& a) {
+      t_gemm_scratch = a.p;
+      t_gemm_scratch_n = a.n;
+    }
+    ~ScratchScope() {
+      t_gemm_scratch = nullptr;
+      t_gemm_scratch_n = 0;
+    }
+  };
+  std::unique_ptr<ScratchScope> scope(ctx->dev_loops ? new ScratchScope(arena) : nullptr);
   // right-canonical initial guess (centre at site 1)
   for (int d = n - 1; d >= 1; d--) P.shift_left(d);
   for (int k = n - 1; k >= 1; k--) P.build_right(k);
+  if (ctx->dev_loops) {
+    // the sweep loop as a WHILE node (each solve a nested one): the host
+    // loop below with its convergence test on the device
+    launch_sumsq2(P.V[0]->core(0), (long long)P.V[0]->core_size(0), P.V[1]->core(0),
+                  (long long)P.V[1]->core_size(0), P.scal.p + 6, P.s);
+    launch_sweep_check(P.scal.p, ctx->d_loop + 2, ctx->d_stats, ctx->p.sweep_tol, 1, P.s);
+    if (n > 1) {
+      const cudaStream_t outer = P.s;
+      capture_while(outer, ctx->bstream[0], ctx->d_loop + 0, ctx->d_loop + 2, ctx->p.max_sweeps,
+                    [&](cudaStream_t bs) {
+                      P.s = bs;
+                      for (int d = 0; d < n - 1; d++) {
+                        P.solve(d);
+                        P.shift_right(d);
+                        P.build_left(d);
+                      }
+                      for (int d = n - 1; d >= 1; d--) {
+                        P.solve(d);
+                        P.shift_left(d);
+                        P.build_right(d);
+                      }
+                      launch_sumsq2(P.V[0]->core(0), (long long)P.V[0]->core_size(0),
+                                    P.V[1]->core(0), (long long)P.V[1]->core_size(0),
+                                    P.scal.p + 6, P.s);
+                      launch_sweep_check(P.scal.p, ctx->d_loop + 2, ctx->d_stats,
+                                         ctx->p.sweep_tol, 0, P.s);
+                      P.s = outer;
+                    });
+      launch_sweep_final(ctx->d_loop + 2, ctx->d_stats, P.s);
+    }
+    if (cg_out) *cg_out = 0;
+    if (sw_out) *sw_out = 0;
+    *v1 = V0.release();
+    *v2 = V1.release();
+    return;
+  }
   long long cg = 0;
   int sweeps = 0;
   ctx->last_not_converged = 0;
@@ -1730,10 +1872,12 @@ void graph_release(StageGraph& G) {
 }
 
 void graphs_clear(qtt_ctx ctx) {
-  if (ctx->graphs.empty()) return;
+  if (ctx->graphs.empty() && ctx->step_graphs.empty()) return;
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->graphs) graph_release(*kv.second);
+  for (auto& kv : ctx->step_graphs) graph_release(*kv.second);
   ctx->graphs.clear();
+  ctx->step_graphs.clear();
   ctx->graphs_captured = 0;
 }
 
@@ -1760,13 +1904,16 @@ void capture_stage(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], qtt_mps b[2], bool 
   cudaGraph_t graph = nullptr;
   QTT_CUDA_CHECK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
   ctx->stream = ctx->gstream;
+  t_capturing = true;
   try {
     qtt_mps gu[2] = {G.in[0], G.in[1]};
     qtt_mps gb[2] = {alias ? G.in[0] : G.in[2], alias ? G.in[1] : G.in[3]};
     MpsPtr w[2];
     stage_w(ctx, gu, gb, h, nu, w, a_scale);
     for (int i = 0; i < 2; i++) copy_mps_d2d(G.out[i], w[i].get(), ctx->stream);
+    t_capturing = false;
   } catch (...) {
+    t_capturing = false;
     cudaStreamEndCapture(ctx->gstream, &graph);
     if (graph) cudaGraphDestroy(graph);
     ctx->stream = orig;
@@ -1793,7 +1940,7 @@ void capture_stage(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], qtt_mps b[2], bool 
 
 void stage_w_run(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2],
                  double a_scale) {
-  if (!ctx->p.graphs || g_prof.on || ctx->p.learned_trunc != QTT_LEARNED_OFF) {
+  if (!ctx->p.graphs || g_prof.on || ctx->p.learned_trunc != QTT_LEARNED_OFF || ctx->dev_loops) {
     stage_w(ctx, u, b, h, nu, w, a_scale);
     return;
   }
@@ -1840,14 +1987,14 @@ void learned_next_step(qtt_ctx ctx) {
   QTT_CUDA_CHECK(cudaMemsetAsync(ctx->d_rank[ctx->tab], 0, cells * sizeof(int), stream_of(ctx)));
 }
 
-void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+// The four stages and the final sum (Eqs. U1-U4); the inputs are left
+// alone.  *nc: a projection of the step reached its CG or sweep cap (host
+// loops; device-driven loops report on the device).
+void rk4_core(qtt_ctx ctx, qtt_mps u[2], double dt, double nu, MpsPtr out[2], int* nc) {
   static const double HS[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
   static const double BC[4][2] = {{0, 0}, {3.0, 0.25}, {1.5, 0.625}, {3.0, 0.25}};
-  if (ctx->p.learned_trunc != QTT_LEARNED_OFF) learned_next_step(ctx);
-  qtt_mps u[2] = {*u1, *u2};
   MpsPtr U[4][2];
-  long long cg_total = 0, sw_total = 0;
-  int nc = 0;
+  *nc = 0;
   for (int st = 0; st < 4; st++) {
     MpsPtr bown[2];
     qtt_mps b[2] = {u[0], u[1]};
@@ -1866,31 +2013,132 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
     qtt_mps v1, v2;
     int cg = 0, sw = 0;
     project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
-    nc |= ctx->last_not_converged;
-    cg_total += cg;
-    sw_total += sw;
+    *nc |= ctx->last_not_converged;
     U[st][0] = MpsPtr(v1);
     U[st][1] = MpsPtr(v2);
   }
+  Workers wk(ctx);
+  wk.fork();
+  for (int i = 0; i < 2; i++)
+    out[i] = MpsPtr(wk.run(i, [&] {
+      MpsPtr acc(add2(ctx, 1.0, U[0][i].get(), 1.0, U[1][i].get()));
+      acc = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[2][i].get()));
+      return add2(ctx, 1.0, acc.get(), 1.0, U[3][i].get());
+    }));
+  wk.join({out[0].get(), out[1].get()});
+}
+
+// Whole-step graph (params.graphs = 2): stages as in stage graphs, the
+// projection's loops as WHILE nodes (capture_while), inputs and outputs
+// through graph-owned buffers; key = the capacities of u_1, u_2 and dt, nu.
+void capture_step(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], double dt, double nu,
+                  MpsPtr out_eager[2]) {
+  const int n = u[0]->n;
+  if (!ctx->d_stats) {
+    QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_stats, 3 * sizeof(long long)));
+    QTT_CUDA_CHECK(cudaMemset(ctx->d_stats, 0, 3 * sizeof(long long)));
+    reg_alloc(ctx->d_stats, 3 * sizeof(long long));
+    QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_loop, 4 * sizeof(int)));
+    QTT_CUDA_CHECK(cudaMemset(ctx->d_loop, 0, 4 * sizeof(int)));
+    reg_alloc(ctx->d_loop, 4 * sizeof(int));
+  }
+  for (int k = 0; k < 2; k++)
+    if (!ctx->bstream[k])
+      QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->bstream[k], cudaStreamNonBlocking));
+  if (!ctx->gstream)
+    QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+  G.in[0] = new_mps(ctx, n, u[0]->cap);
+  G.in[1] = new_mps(ctx, n, u[1]->cap);
+  G.out[0] = new_mps(ctx, n, out_eager[0]->cap);
+  G.out[1] = new_mps(ctx, n, out_eager[1]->cap);
+  const cudaStream_t orig = ctx->stream;
+  const long long n0 = ctx->launches.n;
+  cudaGraph_t graph = nullptr;
+  QTT_CUDA_CHECK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+  ctx->stream = ctx->gstream;
+  ctx->dev_loops = true;
+  t_capturing = true;
+  try {
+    qtt_mps gu[2] = {G.in[0], G.in[1]};
+    MpsPtr o[2];
+    int nc = 0;
+    rk4_core(ctx, gu, dt, nu, o, &nc);
+    for (int i = 0; i < 2; i++) copy_mps_d2d(G.out[i], o[i].get(), ctx->stream);
+    t_capturing = false;
+    ctx->dev_loops = false;
+  } catch (...) {
+    t_capturing = false;
+    ctx->dev_loops = false;
+    cudaStreamEndCapture(ctx->gstream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    ctx->stream = orig;
+    ctx->launches.n = n0;
+    (void)cudaGetLastError();
+    graph_release(G);
+    G.failed = true;
+    return;
+  }
+  const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
+  ctx->stream = orig;
+  G.launches = ctx->launches.n - n0;
+  ctx->launches.n = n0;
+  cudaError_t ei = ec;
+  if (ec == cudaSuccess) ei = cudaGraphInstantiate(&G.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    (void)cudaGetLastError();
+    G.exec = nullptr;
+    graph_release(G);
+    G.failed = true;
+  }
+}
+
+void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
+  if (ctx->p.learned_trunc != QTT_LEARNED_OFF) learned_next_step(ctx);
+  qtt_mps u[2] = {*u1, *u2};
   MpsPtr out[2];
-  {
-    Workers wk(ctx);
-    wk.fork();
-    for (int i = 0; i < 2; i++)
-      out[i] = MpsPtr(wk.run(i, [&] {
-        MpsPtr acc(add2(ctx, 1.0, U[0][i].get(), 1.0, U[1][i].get()));
-        acc = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[2][i].get()));
-        return add2(ctx, 1.0, acc.get(), 1.0, U[3][i].get());
-      }));
-    wk.join({out[0].get(), out[1].get()});
+  const bool step_graphs = ctx->p.graphs == 2 && !g_prof.on && ctx->p.learned_trunc == QTT_LEARNED_OFF;
+  StageGraph* G = nullptr;
+  if (step_graphs) {
+    std::string key;
+    auto put = [&](const void* p, size_t k) { key.append((const char*)p, k); };
+    put(&dt, sizeof dt);
+    put(&nu, sizeof nu);
+    for (int i = 0; i < 2; i++) put(u[i]->cap.data(), u[i]->cap.size() * sizeof(int));
+    if (ctx->step_graphs.size() > 64) {
+      for (auto it = ctx->step_graphs.begin(); it != ctx->step_graphs.end();)
+        it = it->second->exec ? std::next(it) : ctx->step_graphs.erase(it);
+    }
+    std::unique_ptr<StageGraph>& slot = ctx->step_graphs[key];
+    if (!slot) slot.reset(new StageGraph);
+    G = slot.get();
+  }
+  if (G && G->exec) {
+    const int n = u[0]->n;
+    copy_mps_d2d(G->in[0], u[0], ctx->stream);
+    copy_mps_d2d(G->in[1], u[1], ctx->stream);
+    QTT_CUDA_CHECK(cudaGraphLaunch(G->exec, ctx->stream));
+    ctx->launches.n += G->launches;
+    ctx->graph_replays++;
+    ctx->stats_pending = true;
+    for (int i = 0; i < 2; i++) {
+      out[i] = MpsPtr(new_mps(ctx, n, G->out[i]->cap));
+      copy_mps_d2d(out[i].get(), G->out[i], ctx->stream);
+    }
+    ctx->last_not_converged = 0;  // the device flag is read at the next sync
+  } else {
+    int nc = 0;
+    rk4_core(ctx, u, dt, nu, out, &nc);
+    if (G && G->seen++ >= 1 && !G->failed && ctx->graphs_captured < qtt_ctx_s::kMaxGraphs) {
+      capture_step(ctx, *G, u, dt, nu, out);
+      if (!G->failed) ctx->graphs_captured++;
+    }
+    ctx->last_not_converged = nc;
   }
   free_mps(*u1);
   free_mps(*u2);
   *u1 = out[0].release();
   *u2 = out[1].release();
-  ctx->last_not_converged = nc;
-  (void)cg_total;
-  (void)sw_total;
 }
 
 // One penalised minimisation with a = u (scale 1) and the given b, h.
@@ -2036,8 +2284,20 @@ void to_dense_impl(qtt_ctx ctx, qtt_mps A, double* F) {
 // --------------------------------------------------------------- errors
 qtt_status check_device_errors(qtt_ctx ctx) {
   int h = 0;
+  long long st[3] = {0, 0, 0};
   QTT_CUDA_CHECK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  const bool pending = ctx->stats_pending && ctx->d_stats;
+  if (pending)
+    QTT_CUDA_CHECK(cudaMemcpyAsync(st, ctx->d_stats, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
   QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  if (pending) {
+    // counters of replayed steps whose projection loops ran on the device
+    ctx->cg_iters += st[0];
+    ctx->sweeps += st[1];
+    if (st[2]) ctx->last_not_converged = 1;
+    QTT_CUDA_CHECK(cudaMemsetAsync(ctx->d_stats, 0, sizeof st, ctx->stream));
+    ctx->stats_pending = false;
+  }
   if (h) {
     QTT_CUDA_CHECK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
     if (h & QTT_DEVERR_NUMERIC) {
@@ -2082,7 +2342,7 @@ bool valid_params(const qtt_params* p) {
          p->learned_trunc >= QTT_LEARNED_OFF && p->learned_trunc <= QTT_LEARNED_ON &&
          (p->learned_trunc != QTT_LEARNED_LOG || p->precision == QTT_PREC_FP64) &&
          p->rf_oversample >= 0 && p->rf_oversample <= 256 && p->rf_min_width >= 1 &&
-         (p->graphs == 0 || p->graphs == 1);
+         p->graphs >= 0 && p->graphs <= 2;
 }
 
 void check_mps(qtt_ctx ctx, qtt_mps m) {
@@ -2173,6 +2433,13 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   graphs_clear(ctx);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  for (cudaStream_t b : ctx->bstream)
+    if (b) cudaStreamDestroy(b);
+  for (void* q : {(void*)ctx->d_stats, (void*)ctx->d_loop})
+    if (q) {
+      reg_free(q);
+      cudaFree(q);
+    }
   for (int i = 0; i < 2; i++) mpo_release(ctx->D[i]);
   mpo_release(ctx->lap);
   for (int i = 0; i < 2; i++)

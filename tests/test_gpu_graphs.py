@@ -186,3 +186,64 @@ def test_upload_rejects_bond_above_capacity(P):
     wide = [np.zeros((bonds[k], 4, bonds[k + 1])) for k in range(5)]
     with pytest.raises(P.QttError):
         ctx.upload_cores(a, wide)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_graph_equals_eager(P, precision):
+    """graphs = 2: the whole RK4 step (stages, projection with its CG and
+    sweep loops as device-driven WHILE nodes, final sum) is one replayed
+    graph from the third step on; fields, converged flags and CG iteration
+    counts equal the eager run's."""
+    res = []
+    for graphs in (0, 2):
+        (u, v), dx = I.shear_jet(7, seed=5)
+        dt, nu = 0.1 * dx / float(np.abs(u).max()), 1e-4
+        ctx = P.Context(7, eps=1e-8, chi_max=32, precision=precision, graphs=graphs)
+        a, b = ctx.from_dense(u), ctx.from_dense(v)
+        conv, cg = [], []
+        for _ in range(4):
+            before = ctx.stats()["cg_iters"]
+            conv.append(ctx.rk4_step(a, b, dt, nu))
+            cg.append(ctx.stats()["cg_iters"] - before)
+        res.append((dense(ctx, a), dense(ctx, b), conv, cg, ctx.graph_stats()))
+    (a0, b0, c0, g0, _), (a1, b1, c1, g1, gs) = res
+    assert gs[1] >= 2  # steps 3 and 4 replayed
+    assert np.array_equal(a0, a1) and np.array_equal(b0, b1)
+    assert c0 == c1 and g0 == g1
+
+
+def test_step_graph_reports_caps(P):
+    """A CG cap of one iteration: every replayed step reports that a
+    projection reached its cap, as the eager step does."""
+    (u, v), dx = I.shear_jet(6, seed=6)
+    dt, nu = 0.1 * dx / float(np.abs(u).max()), 1e-4
+    out = []
+    for graphs in (0, 2):
+        ctx = P.Context(6, eps=1e-8, chi_max=16, cg_tol=1e-14, cg_maxit=1, graphs=graphs)
+        a, b = ctx.from_dense(u), ctx.from_dense(v)
+        out.append([ctx.rk4_step(a, b, dt, nu) for _ in range(4)])
+        if graphs:
+            assert ctx.graph_stats()[1] >= 2
+    assert out[0] == out[1] == [False] * 4
+
+
+def test_step_graph_timing(P):
+    """2^7 jet, chi 32: steps per second with stage graphs and with whole-step
+    graphs (printed)."""
+    import torch
+    res = {}
+    for graphs in (1, 2):
+        (u, v), dx = I.shear_jet(7, seed=7)
+        dt, nu = 0.1 * dx / float(np.abs(u).max()), 1e-4
+        ctx = P.Context(7, eps=1e-8, chi_max=32, graphs=graphs)
+        a, b = ctx.from_dense(u), ctx.from_dense(v)
+        for _ in range(3):
+            ctx.rk4_step(a, b, dt, nu)
+        ctx.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            ctx.rk4_step(a, b, dt, nu)
+        ctx.sync()
+        res[graphs] = 5 / (time.perf_counter() - t0)
+    print(f"2^7 jet, chi 32: stage graphs {res[1]:.2f} steps/s, step graphs {res[2]:.2f} steps/s")
