@@ -1,7 +1,7 @@
 """Benchmark: QTT RK4 steps per second on a 2^10 x 2^10 shear jet at chi = 64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
-                    [--impl reference] [--batched B] [--eager] [--tight]
+                    [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight]
                     [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
 
 Workload (default): decaying double shear layer, periodic [0, 2 pi)^2 with
@@ -18,10 +18,12 @@ its own trajectory on its own GPU (replicas: the method has no exchange
 step), value = all ranks' steps / the slowest rank's time.
 
 --batched B steps B jets (seeds seed .. seed+B-1) together through the
-batched C ABI (value = aggregate steps/s); --eager launches every stage
-eagerly instead of replaying its right-hand side as a CUDA graph (the
-default: a stage's graph is captured the second time its shapes occur, so
-the warm-up steps capture and the timed steps replay); --tight runs CG and sweeps to 1e-12 (CG cap 500)
+batched C ABI (value = aggregate steps/s).  By default every RK4 step is
+replayed as one CUDA graph (the projection's CG and sweep loops as
+device-driven WHILE nodes), captured the second time its shapes occur, so
+the warm-up steps capture and the timed steps replay; --stage-graphs
+replays only the stages' right-hand sides, --eager launches everything from
+the host; --tight runs CG and sweeps to 1e-12 (CG cap 500)
 instead of the paper's settings; --grid-bits / --chi override n / chi_max
 (smaller test cases); --impl reference times the CPU oracle instead (one
 core, a bounded sample of the same workload).  Timing: 3 warm-up steps by
@@ -249,9 +251,10 @@ def main():
                     help="B > 1: B trajectories (seeds seed..seed+B-1) stepped together by "
                          "qtt_rk4_step_batched; value = aggregate steps/s")
     ap.add_argument("--chi", type=int, default=None, help="override chi_max (testing only)")
-    ap.add_argument("--eager", action="store_true",
-                    help="launch every stage eagerly instead of replaying its right-hand side "
-                         "as a CUDA graph")
+    ap.add_argument("--eager", action="store_true", help="launch every kernel from the host")
+    ap.add_argument("--stage-graphs", action="store_true",
+                    help="replay only each stage's right-hand side as a CUDA graph (the "
+                         "projection launched from the host)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -278,7 +281,7 @@ def main():
     if args.tight:
         w.update(cg_tol=1e-12, sweep_tol=1e-12, cg_maxit=500)
         w["workload"] += "_tight"
-    graphs = 0 if args.eager else 1
+    graphs = 0 if args.eager else (1 if args.stage_graphs else 2)
     prec = P.PREC_FP64 if args.precision == "fp64" else P.PREC_MIXED
     nu = 1.0 / w["Re"]
     B = max(1, args.batched)
@@ -427,6 +430,7 @@ def main():
                        "host clock between device-wide synchronisations (library-owned streams)"),
             "config": {**w, "precision": args.precision, "parallelism": f"replicas x{world}",
                        "trajectories": B, "stage_graphs": bool(graphs),
+                       "step_graphs": graphs == 2,
                        "stage_graph_replays_timed": replays,
                        "l2": "flushed between timed steps (256 MB write)",
                        "all_projections_converged": bool(converged)},

@@ -97,13 +97,20 @@ typedef struct {
   int rf_oversample;  /* range-finder width = predicted rank + this (>= 0) */
   int rf_min_width;   /* only cuts whose full factor is at least this wide
                          (capacity) use the range finder (>= 1; 128)      */
-  int graphs;         /* 1: a stage's right-hand side w = a u - h B(b) runs
-                         as a replayed CUDA graph (captured the first time
-                         its input capacities, h, nu and a occur; inputs and
-                         outputs copied through graph-owned buffers); 0:
-                         launched eagerly.  Either way the same kernels in
-                         the same order per stream: results are identical.
-                         Ignored while profiling or with learned truncation. */
+  int graphs;         /* 0: every kernel launched from the host.
+                         1: a stage's right-hand side w = a u - h B(b) runs
+                         as a replayed CUDA graph (key: input capacities,
+                         h, nu, a); the projection from the host.
+                         2: as 1, and a whole RK4 step runs as one replayed
+                         graph (key: capacities of u_1, u_2 and dt, nu), the
+                         projection's CG and sweep loops as device-driven
+                         WHILE nodes capped at cg_maxit / max_sweeps passes.
+                         A key is captured at its second occurrence and
+                         replayed from its third; inputs and outputs pass
+                         through graph-owned buffers.  The kernels and their
+                         per-stream order are those of the eager run, so
+                         results are identical.  Ignored while profiling or
+                         with learned truncation. */
 } qtt_params;
 
 /* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,
@@ -197,11 +204,12 @@ qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
 qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps,
                      long long* launches);
 
-/* Stage graphs (qtt_params.graphs): graphs captured and kept by the context
- * (at most 16; cleared by qtt_set_params) and replays since creation.  A
- * stage whose key (input capacities, aliasing of b and u, h, nu, a) occurs
- * for the second time runs eagerly and is captured; from the third time on
- * it is replayed.  QTT_ERR_ARG for null arguments. */
+/* Stage and step graphs (qtt_params.graphs): graphs captured and kept by
+ * the context (at most 16 of the two kinds together; cleared by
+ * qtt_set_params) and
+ * replays of either kind since creation.  A key occurring for the second
+ * time runs eagerly and is captured; from the third time on it is
+ * replayed.  QTT_ERR_ARG for null arguments. */
 qtt_status qtt_graph_stats(qtt_ctx ctx, long long* captured, long long* replays);
 
 /* Per-kernel timing of the work enqueued between qtt_profile_begin and

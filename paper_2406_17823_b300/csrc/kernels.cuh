@@ -128,7 +128,8 @@ void launch_cg_start(const CgVec& v, const double* b0, const double* b1, double*
 void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err, cudaStream_t s);
 // device-driven loops of a captured step (see kernels_misc.cu)
 void launch_loop_cond(cudaGraphConditionalHandle h, int* counter, const int* stop, int cap,
-                      int first, cudaStream_t s);
+                      int first, cudaStream_t s, long long body_launches = 0,
+                      long long* launched = nullptr);
 void launch_cg_account(const int* ist, long long* stats, int maxit, cudaStream_t s);
 void launch_sweep_check(double* scal, int* stop, long long* stats, double tol, int init,
                         cudaStream_t s);

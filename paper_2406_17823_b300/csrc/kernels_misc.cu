@@ -424,17 +424,20 @@ void launch_cg_step(const CgVec& v, double* scal, int* ist, int maxit, int* err,
 // The loop condition of a WHILE node: iteration `counter` (0 on the first
 // call) continues while counter < cap and *stop == 0.  The counter makes
 // every loop end after at most cap iterations whatever the stop word holds.
+// At the end of each pass (first == 0) `body_launches` kernels of the body
+// have run; they are added to *launched (the step's launch count).
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, int* counter, const int* stop, int cap,
-                            int first) {
+                            int first, long long body_launches, long long* launched) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int c = first ? 0 : *counter + 1;
   *counter = c;
+  if (!first && launched) *launched += body_launches;
   cudaGraphSetConditional(h, (c < cap && !(stop && *stop)) ? 1u : 0u);
 }
 void launch_loop_cond(cudaGraphConditionalHandle h, int* counter, const int* stop, int cap,
-                      int first, cudaStream_t s) {
+                      int first, cudaStream_t s, long long body_launches, long long* launched) {
   pre_launch(s);
-  k_loop_cond<<<1, 32, 0, s>>>(h, counter, stop, cap, first);
+  k_loop_cond<<<1, 32, 0, s>>>(h, counter, stop, cap, first, body_launches, launched);
   post_launch("k_loop_cond", s);
 }
 

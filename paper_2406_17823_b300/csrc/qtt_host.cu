@@ -212,8 +212,12 @@ struct qtt_ctx_s {
   // and the step statistics live on the device until the next sync
   std::map<std::string, std::unique_ptr<StageGraph>> step_graphs;
   cudaStream_t bstream[2] = {nullptr, nullptr};
+  // the two matvec rows inside loop body k run on bworkers[k][0..1] (a
+  // stream joined to one capture cannot serve another)
+  cudaStream_t bworkers[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool dev_loops = false;      // set while a step is being captured
-  long long* d_stats = nullptr;  // [0] CG iterations, [1] sweeps, [2] not converged
+  long long* d_stats = nullptr;  // [0] CG iterations, [1] sweeps, [2] not converged,
+                                 // [3] kernels run by loop bodies
   int* d_loop = nullptr;         // [0..1] loop counters, [2] sweep stop word
   bool stats_pending = false;
 };
@@ -1216,13 +1220,20 @@ struct Env {
   std::vector<DBuf<double>> b;  // per bond
 };
 
+// Launches captured inside WHILE bodies (nested ones included) since the
+// enclosing capture began: they run once per pass, counted on the device.
+thread_local long long t_body_launches = 0;
+long long launches_now() { return g_launch_counter ? g_launch_counter->n : 0; }
+
 // Appends to the graph that stream s is capturing a WHILE node whose body
 // is captured from body(bs) on stream bs, followed by the loop condition:
 // iteration i (0 on entry) runs while i < cap and *stop == 0, so the loop
-// ends after at most cap iterations whatever the stop word does.
+// ends after at most cap iterations whatever the stop word does.  Each pass
+// adds the kernels of this body (not of nested bodies, which count their
+// own passes) to *launched.
 template <typename F>
 void capture_while(cudaStream_t s, cudaStream_t bs, int* counter, const int* stop, int cap,
-                   F&& body) {
+                   long long* launched, F&& body) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -1245,14 +1256,19 @@ void capture_while(cudaStream_t s, cudaStream_t bs, int* counter, const int* sto
                                                      cudaStreamSetCaptureDependencies));
   QTT_CUDA_CHECK(cudaStreamBeginCaptureToGraph(bs, body_graph, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal));
+  const long long before = launches_now(), nested0 = t_body_launches;
+  t_body_launches = 0;
   try {
     body(bs);
-    launch_loop_cond(h, counter, stop, cap, 0, bs);
+    const long long own = launches_now() - before - t_body_launches + 1;  // + the condition
+    launch_loop_cond(h, counter, stop, cap, 0, bs, own, launched);
   } catch (...) {
+    t_body_launches = nested0;
     cudaGraph_t x = nullptr;
     cudaStreamEndCapture(bs, &x);
     throw;
   }
+  t_body_launches = nested0 + (launches_now() - before);
   cudaGraph_t done = nullptr;
   QTT_CUDA_CHECK(cudaStreamEndCapture(bs, &done));
 }
@@ -1445,15 +1461,29 @@ struct Projector {
   // stream.
   void matvec(int d, double* const X[2], double* const Y[2], const int* skip) {
     cudaStream_t ps = s;
-    // a captured step's loop bodies stay on their own stream (the worker
-    // streams belong to the enclosing capture)
-    const bool par = !ctx->dev_loops && ctx->workers[0] != nullptr && ctx->workers[1] != nullptr;
-    if (par) {
-      QTT_CUDA_CHECK(cudaEventRecord(ctx->fork_ev, ps));
-      for (int i = 0; i < 2; i++) QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[i], ctx->fork_ev, 0));
+    // inside a captured step's loop body the rows run on that body's own
+    // pair of streams (the context's workers belong to the enclosing capture)
+    cudaStream_t rowst[2] = {ctx->workers[0], ctx->workers[1]};
+    if (ctx->dev_loops) {
+      const int lvl = ps == ctx->bstream[1] ? 1 : ps == ctx->bstream[0] ? 0 : -1;
+      rowst[0] = lvl >= 0 ? ctx->bworkers[lvl][0] : nullptr;
+      rowst[1] = lvl >= 0 ? ctx->bworkers[lvl][1] : nullptr;
     }
+    const bool par = rowst[0] != nullptr && rowst[1] != nullptr;
+    cudaEvent_t fe = ctx->dev_loops ? ctx->flow_ev[12] : ctx->fork_ev;
+    if (par) {
+      QTT_CUDA_CHECK(cudaEventRecord(fe, ps));
+      for (int i = 0; i < 2; i++) QTT_CUDA_CHECK(cudaStreamWaitEvent(rowst[i], fe, 0));
+    }
+    // concurrent rows take separate halves of the split-K scratch
+    double* const scr = t_gemm_scratch;
+    const size_t scr_n = t_gemm_scratch_n;
     for (int i = 0; i < 2; i++) {
-      const cudaStream_t s = par ? ctx->workers[i] : ps;
+      const cudaStream_t s = par ? rowst[i] : ps;
+      if (scr && par) {
+        t_gemm_scratch = scr + i * (scr_n / 2);
+        t_gemm_scratch_n = scr_n / 2;
+      }
       double* const t1p = i == 0 ? t1.p : t1b.p;
       double* const t2p = i == 0 ? t2.p : t2b.p;
       launch_copy(Y[i], X[i], V[i]->core_size(d), s);
@@ -1483,10 +1513,13 @@ struct Projector {
         gemm(g3, s);
       }
     }
+    t_gemm_scratch = scr;
+    t_gemm_scratch_n = scr_n;
     if (par) {
       for (int i = 0; i < 2; i++) {
-        QTT_CUDA_CHECK(cudaEventRecord(ctx->join_ev[i], ctx->workers[i]));
-        QTT_CUDA_CHECK(cudaStreamWaitEvent(ps, ctx->join_ev[i], 0));
+        cudaEvent_t je = ctx->dev_loops ? ctx->flow_ev[13 + i] : ctx->join_ev[i];
+        QTT_CUDA_CHECK(cudaEventRecord(je, rowst[i]));
+        QTT_CUDA_CHECK(cudaStreamWaitEvent(ps, je, 0));
       }
     }
   }
@@ -1523,7 +1556,8 @@ struct Projector {
       // word (converged, iteration cap, breakdown): the host loop below
       // without its reads, iterations counted on the device
       const cudaStream_t outer = s;
-      capture_while(outer, ctx->bstream[1], ctx->d_loop + 1, ist.p, maxit, [&](cudaStream_t bs) {
+      capture_while(outer, ctx->bstream[1], ctx->d_loop + 1, ist.p, maxit, ctx->d_stats + 3,
+                    [&](cudaStream_t bs) {
         s = bs;
         matvec(d, P, AP, ist.p);
         launch_cg_step(v, scal.p, ist.p, maxit, ctx->d_err, s);
@@ -1627,7 +1661,7 @@ void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qt
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
   P.alloc();
-  DBuf<double> arena(ctx->dev_loops ? 16 * P.maxout : 0, P.s);
+  DBuf<double> arena(ctx->dev_loops ? 2 * 16 * P.maxout : 0, P.s);  // a half per matvec row
   struct ScratchScope {  // split-K scratch of a captured step's loop bodies
     explicit ScratchScope(DBuf<double>& a) {
       t_gemm_scratch = a.p;
@@ -1651,7 +1685,7 @@ void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qt
     if (n > 1) {
       const cudaStream_t outer = P.s;
       capture_while(outer, ctx->bstream[0], ctx->d_loop + 0, ctx->d_loop + 2, ctx->p.max_sweeps,
-                    [&](cudaStream_t bs) {
+                    ctx->d_stats + 3, [&](cudaStream_t bs) {
                       P.s = bs;
                       for (int d = 0; d < n - 1; d++) {
                         P.solve(d);
@@ -1925,7 +1959,10 @@ void capture_stage(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], qtt_mps b[2], bool 
   }
   const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
   ctx->stream = orig;
-  G.launches = ctx->launches.n - n0;
+  // kernels outside the loop bodies run once per replay; the bodies' count
+  // their passes on the device
+  G.launches = ctx->launches.n - n0 - t_body_launches;
+  t_body_launches = 0;
   ctx->launches.n = n0;
   cudaError_t ei = ec;
   if (ec == cudaSuccess) ei = cudaGraphInstantiate(&G.exec, graph, 0);
@@ -2035,16 +2072,20 @@ void capture_step(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], double dt, double nu
                   MpsPtr out_eager[2]) {
   const int n = u[0]->n;
   if (!ctx->d_stats) {
-    QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_stats, 3 * sizeof(long long)));
-    QTT_CUDA_CHECK(cudaMemset(ctx->d_stats, 0, 3 * sizeof(long long)));
-    reg_alloc(ctx->d_stats, 3 * sizeof(long long));
+    QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_stats, 4 * sizeof(long long)));
+    QTT_CUDA_CHECK(cudaMemset(ctx->d_stats, 0, 4 * sizeof(long long)));
+    reg_alloc(ctx->d_stats, 4 * sizeof(long long));
     QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_loop, 4 * sizeof(int)));
     QTT_CUDA_CHECK(cudaMemset(ctx->d_loop, 0, 4 * sizeof(int)));
     reg_alloc(ctx->d_loop, 4 * sizeof(int));
   }
-  for (int k = 0; k < 2; k++)
+  for (int k = 0; k < 2; k++) {
     if (!ctx->bstream[k])
       QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->bstream[k], cudaStreamNonBlocking));
+    for (int i = 0; i < 2; i++)
+      if (!ctx->bworkers[k][i])
+        QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->bworkers[k][i], cudaStreamNonBlocking));
+  }
   if (!ctx->gstream)
     QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
   G.in[0] = new_mps(ctx, n, u[0]->cap);
@@ -2058,6 +2099,7 @@ void capture_step(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], double dt, double nu
   ctx->stream = ctx->gstream;
   ctx->dev_loops = true;
   t_capturing = true;
+  t_body_launches = 0;
   try {
     qtt_mps gu[2] = {G.in[0], G.in[1]};
     MpsPtr o[2];
@@ -2284,7 +2326,7 @@ void to_dense_impl(qtt_ctx ctx, qtt_mps A, double* F) {
 // --------------------------------------------------------------- errors
 qtt_status check_device_errors(qtt_ctx ctx) {
   int h = 0;
-  long long st[3] = {0, 0, 0};
+  long long st[4] = {0, 0, 0, 0};
   QTT_CUDA_CHECK(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   const bool pending = ctx->stats_pending && ctx->d_stats;
   if (pending)
@@ -2294,6 +2336,7 @@ qtt_status check_device_errors(qtt_ctx ctx) {
     // counters of replayed steps whose projection loops ran on the device
     ctx->cg_iters += st[0];
     ctx->sweeps += st[1];
+    ctx->launches.n += st[3];
     if (st[2]) ctx->last_not_converged = 1;
     QTT_CUDA_CHECK(cudaMemsetAsync(ctx->d_stats, 0, sizeof st, ctx->stream));
     ctx->stats_pending = false;
@@ -2435,6 +2478,9 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   for (cudaStream_t b : ctx->bstream)
     if (b) cudaStreamDestroy(b);
+  for (auto& pr : ctx->bworkers)
+    for (cudaStream_t b : pr)
+      if (b) cudaStreamDestroy(b);
   for (void* q : {(void*)ctx->d_stats, (void*)ctx->d_loop})
     if (q) {
       reg_free(q);
