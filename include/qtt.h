@@ -206,10 +206,9 @@ qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps,
 
 /* Stage and step graphs (qtt_params.graphs): graphs captured and kept by
  * the context (at most 16 of the two kinds together; cleared by
- * qtt_set_params) and
- * replays of either kind since creation.  A key occurring for the second
- * time runs eagerly and is captured; from the third time on it is
- * replayed.  QTT_ERR_ARG for null arguments. */
+ * qtt_set_params) and replays of either kind since creation.  A key
+ * occurring for the second time runs eagerly and is captured; from the
+ * third time on it is replayed.  QTT_ERR_ARG for null arguments. */
 qtt_status qtt_graph_stats(qtt_ctx ctx, long long* captured, long long* replays);
 
 /* Per-kernel timing of the work enqueued between qtt_profile_begin and
