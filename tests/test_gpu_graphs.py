@@ -106,8 +106,10 @@ def test_graphs_follow_parameter_changes(P):
     assert g.graph_stats()[0] >= 1
 
 
-def test_batched_graphs_equal_sequential(P):
-    cases = [dict(n=5, chi_max=8, eps=1e-10, graphs=1), dict(n=6, chi_max=16, eps=1e-8, graphs=1)]
+@pytest.mark.parametrize("graphs", [1, 2])
+def test_batched_graphs_equal_sequential(P, graphs):
+    cases = [dict(n=5, chi_max=8, eps=1e-10, graphs=graphs),
+             dict(n=6, chi_max=16, eps=1e-8, graphs=graphs)]
     fields, dts = [], []
     for i, c in enumerate(cases):
         (u, v), dx = I.shear_jet(c["n"], seed=10 + i)
