@@ -458,7 +458,8 @@ void launch_qr_f64(const QrArgs& a, int mcap, int ccap, cudaStream_t s) {
 double svd_flops(int mcap, int ncap);
 
 // FP32 working precision for the subspace search of the mixed path; the
-// caller re-orthonormalises the returned factor in FP64.  Returns false when
+// caller refines the returned subspace in FP64 (one subspace iteration with
+// a Householder QR).  Returns false when
 // no cluster launch is possible or the problem is small (FP64 is used then).
 bool launch_svd_subspace_f32(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
   check_range(a.M.ptr, view_extent(a.M), sizeof(double), "svd M");

@@ -919,7 +919,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
           gemm(g, s);
         }
         launch_sumsq2(Mp, (long long)qcap[k] * 4 * ocap[k + 1], Mp, 0, wM.p, s);
-        // G = B^T B (rpo x rpo, into Rs, free after the gauge QR): its SVD
+        // G = B^T B (rpo x rpo, into Rs, free after the subspace QR): its SVD
         // gives V_B and the weights sigma_B^2 without factoring B itself
         {
           GemmF64 gg = gemm_plain(Bm.p, Bm.p, Rs.p, rpo, rpo, qcap[k], rpo, rpo, rpo);
