@@ -43,6 +43,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -82,10 +83,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, path: str = None):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = path or os.path.join(tempfile.gettempdir(), f"qtt_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -252,6 +253,9 @@ def main():
                          "qtt_rk4_step_batched; value = aggregate steps/s")
     ap.add_argument("--chi", type=int, default=None, help="override chi_max (testing only)")
     ap.add_argument("--eager", action="store_true", help="launch every kernel from the host")
+    ap.add_argument("--clocks-file", default=None,
+                    help="where the nvidia-smi clock samples of the timed region go (CSV; "
+                         "default: a file in the temporary directory)")
     ap.add_argument("--stage-graphs", action="store_true",
                     help="replay only each stage's right-hand side as a CUDA graph (the "
                          "projection launched from the host)")
@@ -319,7 +323,7 @@ def main():
     replays0 = sum(c.graph_stats()[1] for c in ctxs)
     times = []
     converged = True
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_file) as clk:
         barrier()
         wall0 = time.perf_counter()
         for _ in range(args.steps):
