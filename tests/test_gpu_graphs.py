@@ -138,7 +138,7 @@ def test_graph_timing_small_grid(P):
     by more than noise)."""
     import torch
     res = {}
-    for graphs in (0, 1):
+    for graphs in (0, 1, 2):
         (u, v), dx = I.taylor_green(6)
         ctx = P.Context(6, eps=1e-12, chi_max=16, graphs=graphs)
         a, b = ctx.from_dense(u), ctx.from_dense(v)
@@ -151,8 +151,9 @@ def test_graph_timing_small_grid(P):
             ctx.rk4_step(a, b, 1e-3, 0.01)
         ctx.sync()
         res[graphs] = 10 / (time.perf_counter() - t0)
-    print(f"Taylor-Green 2^6, chi 16: eager {res[0]:.1f} steps/s, graphs {res[1]:.1f} steps/s")
-    assert res[1] >= 0.8 * res[0]
+    print(f"Taylor-Green 2^6, chi 16: eager {res[0]:.1f} steps/s, stage graphs {res[1]:.1f}, "
+          f"step graphs {res[2]:.1f}")
+    assert res[1] >= 0.8 * res[0] and res[2] >= 0.8 * res[0]
 
 
 def test_upload_keeps_capacities_and_replays(P):
