@@ -1285,6 +1285,7 @@ struct Projector {
   std::vector<DBuf<double>> LE[2][2], RE[2][2], LW[2], RW[2];
   DBuf<double> t1, t2, rb, tmp, work, vt_i, vt_j, wt;
   DBuf<double> t1b, t2b;  // scratch of component 1's matvec row (runs beside row 0)
+  DBuf<double> rb2, tmp2, work2, wt2;  // component 1's copies of rb, tmp, work, wt
   DBuf<double> cg_r[2], cg_p[2], cg_ap[2], rhs[2];
   DBuf<double> scal;
   DBuf<int> ist;
@@ -1353,6 +1354,10 @@ struct Projector {
     maxout = std::max(maxout, (size_t)cmax * cmax);
     tmp = DBuf<double>(cm, s);
     work = DBuf<double>(qrw, s);
+    rb2 = DBuf<double>((size_t)cmax * cmax, s);
+    tmp2 = DBuf<double>(cm, s);
+    work2 = DBuf<double>(qrw, s);
+    wt2 = DBuf<double>(cm, s);
     vt_i = DBuf<double>(cm, s);
     vt_j = DBuf<double>(cm, s);
     wt = DBuf<double>(cm, s);
@@ -1381,7 +1386,9 @@ struct Projector {
       // transposed copy of V_j[k] ([b][s][a]) into vt_j; reused for every i
       launch_core_transpose(V[j]->core(k), cap(j)[k], cap(j)[k + 1], j == 0 ? vt_i.p : vt_j.p, s);
     }
-    for (int i = 0; i < 2; i++) {
+    by_component([&](int i) {
+      double* const t1p = i == 0 ? t1.p : t1b.p;
+      double* const t2p = i == 0 ? t2.p : t2b.p;
       const double* ViT = (i == 0) ? vt_i.p : vt_j.p;
       for (int j = 0; j < 2; j++) {
         const double* VjT = (j == 0) ? vt_i.p : vt_j.p;
@@ -1389,10 +1396,10 @@ struct Projector {
         const int wl = Kij->w[k], wr = Kij->w[k + 1];
         const int ci = cap(i)[k], cj = cap(j)[k], ci1 = cap(i)[k + 1], cj1 = cap(j)[k + 1];
         // T1[(b q)][(t x)] = RE[k+1][(b q)][z] * VjT[z][(t x)]
-        gemm(gemm_plain(RE[i][j][k + 1].p, VjT, t1.p, ci1 * wr, 4 * cj, cj1, cj1, 4 * cj, 4 * cj), s);
+        gemm(gemm_plain(RE[i][j][k + 1].p, VjT, t1p, ci1 * wr, 4 * cj, cj1, cj1, 4 * cj, 4 * cj), s);
         // T2[b][(s p)][x] = KR2[(s p)][(q t)] * T1[b][(q t)][x]
         GemmF64 g{};
-        g.A = Kij->kr2(k); g.B = t1.p; g.C = t2.p;
+        g.A = Kij->kr2(k); g.B = t1p; g.C = t2p;
         g.M = 4 * wl; g.N = cj; g.K = wr * 4;
         g.lda = wr * 4; g.ldb = cj; g.ldc = cj;
         g.nb1 = ci1; g.nb2 = 1;
@@ -1400,37 +1407,37 @@ struct Projector {
         g.alpha = 1.0;
         gemm(g, s);
         // RE[k][a][(p x)] = ViT[(b s)][a]^T * T2[(b s)][(p x)]
-        GemmF64 g3 = gemm_plain(ViT, t2.p, RE[i][j][k].p, ci, wl * cj, ci1 * 4, ci, wl * cj, wl * cj);
+        GemmF64 g3 = gemm_plain(ViT, t2p, RE[i][j][k].p, ci, wl * cj, ci1 * 4, ci, wl * cj, wl * cj);
         g3.tA = 1;
         gemm(g3, s);
       }
-    }
-    for (int i = 0; i < 2; i++) {
-      const double* ViT = (i == 0) ? vt_i.p : vt_j.p;
+      double* const wtp = i == 0 ? wt.p : wt2.p;
       const int ci = cap(i)[k], ci1 = cap(i)[k + 1];
       const int cw = W[i]->cap[k], cw1 = W[i]->cap[k + 1];
-      launch_core_transpose(W[i]->core(k), cw, cw1, wt.p, s);
+      launch_core_transpose(W[i]->core(k), cw, cw1, wtp, s);
       // T1[b][(s c)] = RW[k+1][b][d] * WiT[d][(s c)]
-      gemm(gemm_plain(RW[i][k + 1].p, wt.p, t1.p, ci1, 4 * cw, cw1, cw1, 4 * cw, 4 * cw), s);
+      gemm(gemm_plain(RW[i][k + 1].p, wtp, t1p, ci1, 4 * cw, cw1, cw1, 4 * cw, 4 * cw), s);
       // RW[k][a][c] = ViT[(b s)][a]^T * T1[(b s)][c]
-      GemmF64 g = gemm_plain(ViT, t1.p, RW[i][k].p, ci, cw, ci1 * 4, ci, cw, cw);
+      GemmF64 g = gemm_plain(ViT, t1p, RW[i][k].p, ci, cw, ci1 * 4, ci, cw, cw);
       g.tA = 1;
       gemm(g, s);
-    }
+    });
   }
 
   // LE[k+1] from LE[k] and site k.
   void build_left(int k) {
-    for (int i = 0; i < 2; i++)
+    by_component([&](int i) {
+      double* const t1p = i == 0 ? t1.p : t1b.p;
+      double* const t2p = i == 0 ? t2.p : t2b.p;
       for (int j = 0; j < 2; j++) {
         qtt_mpo Kij = K[i][j];
         const int wl = Kij->w[k], wr = Kij->w[k + 1];
         const int ci = cap(i)[k], cj = cap(j)[k], ci1 = cap(i)[k + 1], cj1 = cap(j)[k + 1];
         // T1[(a p)][(t z)] = LE[k][(a p)][x] * Vj[k][x][(t z)]
-        gemm(gemm_plain(LE[i][j][k].p, V[j]->core(k), t1.p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1), s);
+        gemm(gemm_plain(LE[i][j][k].p, V[j]->core(k), t1p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1), s);
         // T2[a][(s q)][z] = K2[(s q)][(p t)] * T1[a][(p t)][z]
         GemmF64 g{};
-        g.A = Kij->k2(k); g.B = t1.p; g.C = t2.p;
+        g.A = Kij->k2(k); g.B = t1p; g.C = t2p;
         g.M = 4 * wr; g.N = cj1; g.K = 4 * wl;
         g.lda = 4 * wl; g.ldb = cj1; g.ldc = cj1;
         g.nb1 = ci; g.nb2 = 1;
@@ -1438,21 +1445,20 @@ struct Projector {
         g.alpha = 1.0;
         gemm(g, s);
         // LE[k+1][b][(q z)] = Vi[(a s)][b]^T * T2[(a s)][(q z)]
-        GemmF64 g3 = gemm_plain(V[i]->core(k), t2.p, LE[i][j][k + 1].p, ci1, wr * cj1, 4 * ci, ci1,
+        GemmF64 g3 = gemm_plain(V[i]->core(k), t2p, LE[i][j][k + 1].p, ci1, wr * cj1, 4 * ci, ci1,
                                 wr * cj1, wr * cj1);
         g3.tA = 1;
         gemm(g3, s);
       }
-    for (int i = 0; i < 2; i++) {
       const int ci = cap(i)[k], ci1 = cap(i)[k + 1];
       const int cw = W[i]->cap[k], cw1 = W[i]->cap[k + 1];
       // T1[a][(s d)] = LW[k][a][c] * Wi[c][(s d)]
-      gemm(gemm_plain(LW[i][k].p, W[i]->core(k), t1.p, ci, 4 * cw1, cw, cw, 4 * cw1, 4 * cw1), s);
+      gemm(gemm_plain(LW[i][k].p, W[i]->core(k), t1p, ci, 4 * cw1, cw, cw, 4 * cw1, 4 * cw1), s);
       // LW[k+1][b][d] = Vi[(a s)][b]^T * T1[(a s)][d]
-      GemmF64 g = gemm_plain(V[i]->core(k), t1.p, LW[i][k + 1].p, ci1, cw1, 4 * ci, ci1, cw1, cw1);
+      GemmF64 g = gemm_plain(V[i]->core(k), t1p, LW[i][k + 1].p, ci1, cw1, 4 * ci, ci1, cw1, cw1);
       g.tA = 1;
       gemm(g, s);
-    }
+    });
   }
 
   // Y = (1 + c sum_j K_ij) X at site d; X, Y two-component local tensors.
@@ -1585,28 +1591,92 @@ struct Projector {
   }
 
   // centre moves right: V_i[d] = Q, V_i[d+1] = R V_i[d+1]
+  // The two components' streams for work that splits by component: the
+  // context's workers (eagerly, or in the enclosing capture of a step), or
+  // the stream pair of the loop body being captured (a stream joined to one
+  // capture cannot serve another).  Null: run on s.
+  void row_streams(cudaStream_t out[2]) const {
+    out[0] = ctx->workers[0];
+    out[1] = ctx->workers[1];
+    if (ctx->dev_loops) {
+      const int lvl = s == ctx->bstream[1] ? 1 : s == ctx->bstream[0] ? 0 : -1;
+      if (lvl >= 0) {
+        out[0] = ctx->bworkers[lvl][0];
+        out[1] = ctx->bworkers[lvl][1];
+      }
+    }
+  }
+  // f(i) for the two components, concurrently on the row streams (s is the
+  // component's stream while f runs; each takes its own half of a split-K
+  // scratch), joined back into s
+  template <typename F>
+  void by_component(F&& f) {
+    const cudaStream_t ps = s;
+    cudaStream_t rs[2];
+    row_streams(rs);
+    const bool par = rs[0] != nullptr && rs[1] != nullptr;
+    cudaEvent_t fe = ctx->dev_loops ? ctx->flow_ev[12] : ctx->fork_ev;
+    if (par) {
+      QTT_CUDA_CHECK(cudaEventRecord(fe, ps));
+      for (int i = 0; i < 2; i++) QTT_CUDA_CHECK(cudaStreamWaitEvent(rs[i], fe, 0));
+    }
+    double* const scr = t_gemm_scratch;
+    const size_t scr_n = t_gemm_scratch_n;
+    try {
+      for (int i = 0; i < 2; i++) {
+        s = par ? rs[i] : ps;
+        if (scr && par) {
+          t_gemm_scratch = scr + i * (scr_n / 2);
+          t_gemm_scratch_n = scr_n / 2;
+        }
+        f(i);
+      }
+    } catch (...) {
+      s = ps;
+      t_gemm_scratch = scr;
+      t_gemm_scratch_n = scr_n;
+      throw;
+    }
+    s = ps;
+    t_gemm_scratch = scr;
+    t_gemm_scratch_n = scr_n;
+    if (par) {
+      for (int i = 0; i < 2; i++) {
+        cudaEvent_t je = ctx->dev_loops ? ctx->flow_ev[13 + i] : ctx->join_ev[i];
+        QTT_CUDA_CHECK(cudaEventRecord(je, rs[i]));
+        QTT_CUDA_CHECK(cudaStreamWaitEvent(ps, je, 0));
+      }
+    }
+  }
+
   void shift_right(int d) {
-    for (int i = 0; i < 2; i++) {
+    by_component([&](int i) {
+      double* const rbp = i == 0 ? rb.p : rb2.p;
+      double* const tmpp = i == 0 ? tmp.p : tmp2.p;
+      DBuf<double>& wk = i == 0 ? work : work2;
       const int cl = cap(i)[d], cr = cap(i)[d + 1], cr2 = cap(i)[d + 2];
       QrArgs a{};
       a.A = MatView{V[i]->core(d), cr, axis_pair(cl, dref(V[i]->dims + d), 4, dconst(4)),
                     axis_prefix(cr, dref(V[i]->dims + d + 1))};
       a.Q = MatView{V[i]->core(d), cr, axis_pair(cl, dref(V[i]->dims + d), 4, dconst(4)),
                     axis_prefix(cr, dconst(1))};
-      a.R = MatView{rb.p, cr, axis_prefix(cr, dconst(1)), axis_prefix(cr, dref(V[i]->dims + d + 1))};
+      a.R = MatView{rbp, cr, axis_prefix(cr, dconst(1)), axis_prefix(cr, dref(V[i]->dims + d + 1))};
       a.r_out = V[i]->dims + d + 1;
-      a.work = work.p;
-      a.work_len = (long long)work.n;
+      a.work = wk.p;
+      a.work_len = (long long)wk.n;
       a.err = ctx->d_err;
       launch_qr_f64(a, 4 * cl, cr, s);
-      gemm(gemm_plain(rb.p, V[i]->core(d + 1), tmp.p, cr, 4 * cr2, cr, cr, 4 * cr2, 4 * cr2), s);
-      launch_copy(V[i]->core(d + 1), tmp.p, V[i]->core_size(d + 1), s);
-    }
+      gemm(gemm_plain(rbp, V[i]->core(d + 1), tmpp, cr, 4 * cr2, cr, cr, 4 * cr2, 4 * cr2), s);
+      launch_copy(V[i]->core(d + 1), tmpp, V[i]->core_size(d + 1), s);
+    });
   }
 
   // centre moves left: V_i[d] = Q^T (right isometry), V_i[d-1] = V_i[d-1] R^T
   void shift_left(int d) {
-    for (int i = 0; i < 2; i++) {
+    by_component([&](int i) {
+      double* const rbp = i == 0 ? rb.p : rb2.p;
+      double* const tmpp = i == 0 ? tmp.p : tmp2.p;
+      DBuf<double>& wk = i == 0 ? work : work2;
       const int cl = cap(i)[d], cr = cap(i)[d + 1], cl0 = cap(i)[d - 1];
       QrArgs a{};
       a.A = MatView{V[i]->core(d), 4 * cr, axis_prefix(cl, dref(V[i]->dims + d)),
@@ -1615,16 +1685,16 @@ struct Projector {
       a.Q = MatView{V[i]->core(d), 4 * cr, axis_prefix(cl, dconst(1)),
                     axis_pair(4, dconst(4), cr, dref(V[i]->dims + d + 1))};
       a.qT = 1;
-      a.R = MatView{rb.p, cl, axis_prefix(cl, dref(V[i]->dims + d)), axis_prefix(cl, dconst(1))};
+      a.R = MatView{rbp, cl, axis_prefix(cl, dref(V[i]->dims + d)), axis_prefix(cl, dconst(1))};
       a.rT = 1;
       a.r_out = V[i]->dims + d;
-      a.work = work.p;
-      a.work_len = (long long)work.n;
+      a.work = wk.p;
+      a.work_len = (long long)wk.n;
       a.err = ctx->d_err;
       launch_qr_f64(a, 4 * cr, cl, s);
-      gemm(gemm_plain(V[i]->core(d - 1), rb.p, tmp.p, 4 * cl0, cl, cl, cl, cl, cl), s);
-      launch_copy(V[i]->core(d - 1), tmp.p, V[i]->core_size(d - 1), s);
-    }
+      gemm(gemm_plain(V[i]->core(d - 1), rbp, tmpp, 4 * cl0, cl, cl, cl, cl, cl), s);
+      launch_copy(V[i]->core(d - 1), tmpp, V[i]->core_size(d - 1), s);
+    });
   }
 
   double norm_total() {
