@@ -1531,14 +1531,15 @@ struct Projector {
   }
 
   void local_rhs(int d) {
-    for (int i = 0; i < 2; i++) {
+    by_component([&](int i) {
+      double* const t1p = i == 0 ? t1.p : t1b.p;
       const int ci = cap(i)[d], ci1 = cap(i)[d + 1];
       const int cw = W[i]->cap[d], cw1 = W[i]->cap[d + 1];
-      gemm(gemm_plain(LW[i][d].p, W[i]->core(d), t1.p, ci, 4 * cw1, cw, cw, 4 * cw1, 4 * cw1), s);
-      GemmF64 g = gemm_plain(t1.p, RW[i][d + 1].p, rhs[i].p, 4 * ci, ci1, cw1, cw1, cw1, ci1);
+      gemm(gemm_plain(LW[i][d].p, W[i]->core(d), t1p, ci, 4 * cw1, cw, cw, 4 * cw1, 4 * cw1), s);
+      GemmF64 g = gemm_plain(t1p, RW[i][d + 1].p, rhs[i].p, 4 * ci, ci1, cw1, cw1, cw1, ci1);
       g.tB = 1;
       gemm(g, s);
-    }
+    });
   }
 
   int solve(int d) {
