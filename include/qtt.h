@@ -82,7 +82,7 @@ typedef enum {
 /* Solver parameters.  Paper defaults (Sec. II.C, App. B): mu = 2.5e5,
  * cg_tol = 1e-5, cg_maxit = 100, sweep_tol = 1e-5. */
 typedef struct {
-  int n;              /* bits per axis, 1 <= n <= 16                      */
+  int n;              /* bits per axis, 1 <= n <= 15                      */
   double L;           /* domain length (dx = L / 2^n)                     */
   double eps;         /* relative truncation per bond (Sec. III.E)        */
   int chi_max;        /* bond cap                                         */

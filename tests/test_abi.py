@@ -110,3 +110,28 @@ def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
     lib.qtt_batch_context.argtypes = [vp, ctypes.c_int]
     lib.qtt_batch_context.restype = vp
     assert lib.qtt_batch_context(None, 0) is None
+
+
+def test_parameter_validation_without_gpu(libpath):
+    """qtt_create checks its parameters before any CUDA call: out-of-range
+    graph modes, learned-truncation modes and range-finder settings are
+    QTT_ERR_ARG on a machine without a GPU."""
+    from paper_2406_17823_b300.qtt import Params
+    lib = ctypes.CDLL(libpath)
+    lib.qtt_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.qtt_create.restype = ctypes.c_int
+
+    def params(**kw):
+        p = Params(5, 6.283185307179586, 1e-8, 16, 2.5e5, 1e-5, 100, 1e-5, 20, 0, 0, 8, 128, 0)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    bad = [dict(graphs=3), dict(graphs=-1), dict(learned_trunc=3), dict(precision=2),
+           dict(learned_trunc=1, precision=1), dict(rf_oversample=257), dict(rf_min_width=0),
+           dict(n=0), dict(n=16), dict(chi_max=0), dict(cg_maxit=0), dict(max_sweeps=0),
+           dict(eps=-1.0), dict(L=0.0)]
+    h = ctypes.c_void_p()
+    for kw in bad:
+        p = params(**kw)
+        assert lib.qtt_create(ctypes.byref(h), 0, None, ctypes.byref(p)) == 1, kw
