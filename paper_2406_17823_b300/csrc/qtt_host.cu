@@ -212,9 +212,10 @@ struct qtt_ctx_s {
   // and the step statistics live on the device until the next sync
   std::map<std::string, std::unique_ptr<StageGraph>> step_graphs;
   cudaStream_t bstream[2] = {nullptr, nullptr};
-  // the two matvec rows inside loop body k run on bworkers[k][0..1] (a
-  // stream joined to one capture cannot serve another)
-  cudaStream_t bworkers[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  // the matvec chains inside loop body k run on bworkers[k][0..3] (a stream
+  // joined to one capture cannot serve another)
+  cudaStream_t bworkers[2][4] = {{nullptr, nullptr, nullptr, nullptr},
+                                  {nullptr, nullptr, nullptr, nullptr}};
   bool dev_loops = false;      // set while a step is being captured
   long long* d_stats = nullptr;  // [0] CG iterations, [1] sweeps, [2] not converged,
                                  // [3] kernels run by loop bodies
@@ -1286,6 +1287,8 @@ struct Projector {
   DBuf<double> t1, t2, rb, tmp, work, vt_i, vt_j, wt;
   DBuf<double> t1b, t2b;  // scratch of component 1's matvec row (runs beside row 0)
   DBuf<double> rb2, tmp2, work2, wt2;  // component 1's copies of rb, tmp, work, wt
+  DBuf<double> t1c, t2c, t1d, t2d;     // scratch of the matvec's (i, j = 1) chains
+  DBuf<double> zb[2];                   // row i's j = 1 block, added to Y_i at the end
   DBuf<double> cg_r[2], cg_p[2], cg_ap[2], rhs[2];
   DBuf<double> scal;
   DBuf<int> ist;
@@ -1354,6 +1357,11 @@ struct Projector {
     maxout = std::max(maxout, (size_t)cmax * cmax);
     tmp = DBuf<double>(cm, s);
     work = DBuf<double>(qrw, s);
+    t1c = DBuf<double>(t1m, s);
+    t2c = DBuf<double>(t2m, s);
+    t1d = DBuf<double>(t1m, s);
+    t2d = DBuf<double>(t2m, s);
+    for (int i = 0; i < 2; i++) zb[i] = DBuf<double>(cm, s);
     rb2 = DBuf<double>((size_t)cmax * cmax, s);
     tmp2 = DBuf<double>(cm, s);
     work2 = DBuf<double>(qrw, s);
@@ -1466,66 +1474,86 @@ struct Projector {
   // on two worker streams (own scratch), joined back into the projection
   // stream.
   void matvec(int d, double* const X[2], double* const Y[2], const int* skip) {
-    cudaStream_t ps = s;
-    // inside a captured step's loop body the rows run on that body's own
-    // pair of streams (the context's workers belong to the enclosing capture)
-    cudaStream_t rowst[2] = {ctx->workers[0], ctx->workers[1]};
+    // four chains, one per block (i, j): Y_i = X_i + c K_i0-block(X_0) on
+    // chain (i, 0), Z_i = c K_i1-block(X_1) on chain (i, 1), then Y_i += Z_i;
+    // eagerly on the context's workers 0..3, inside a captured loop body on
+    // that body's four streams (the workers belong to the enclosing capture)
+    const cudaStream_t ps = s;
+    cudaStream_t ch[4] = {ctx->workers[0], ctx->workers[1], ctx->workers[2], ctx->workers[3]};
     if (ctx->dev_loops) {
       const int lvl = ps == ctx->bstream[1] ? 1 : ps == ctx->bstream[0] ? 0 : -1;
-      rowst[0] = lvl >= 0 ? ctx->bworkers[lvl][0] : nullptr;
-      rowst[1] = lvl >= 0 ? ctx->bworkers[lvl][1] : nullptr;
+      for (int q = 0; q < 4; q++) ch[q] = lvl >= 0 ? ctx->bworkers[lvl][q] : nullptr;
     }
-    const bool par = rowst[0] != nullptr && rowst[1] != nullptr;
-    cudaEvent_t fe = ctx->dev_loops ? ctx->flow_ev[12] : ctx->fork_ev;
+    const bool par = ch[0] && ch[1] && ch[2] && ch[3];
+    // events: fork, block (i, 1) done (i = 0, 1), rows joined (i = 0, 1)
+    cudaEvent_t ev[5];
+    for (int q = 0; q < 5; q++)
+      ev[q] = ctx->dev_loops ? ctx->flow_ev[11 + q] : (q == 0 ? ctx->fork_ev : ctx->join_ev[q - 1]);
     if (par) {
-      QTT_CUDA_CHECK(cudaEventRecord(fe, ps));
-      for (int i = 0; i < 2; i++) QTT_CUDA_CHECK(cudaStreamWaitEvent(rowst[i], fe, 0));
+      QTT_CUDA_CHECK(cudaEventRecord(ev[0], ps));
+      for (int q = 0; q < 4; q++) QTT_CUDA_CHECK(cudaStreamWaitEvent(ch[q], ev[0], 0));
     }
-    // concurrent rows take separate halves of the split-K scratch
+    // each chain takes a quarter of the split-K scratch
     double* const scr = t_gemm_scratch;
     const size_t scr_n = t_gemm_scratch_n;
-    for (int i = 0; i < 2; i++) {
-      const cudaStream_t s = par ? rowst[i] : ps;
+    double* const t1s[4] = {t1.p, t1b.p, t1c.p, t1d.p};
+    double* const t2s[4] = {t2.p, t2b.p, t2c.p, t2d.p};
+    auto block = [&](int i, int j, double* out, double beta, cudaStream_t cs) {
+      const int q = 2 * j + i;  // chain index
       if (scr && par) {
-        t_gemm_scratch = scr + i * (scr_n / 2);
-        t_gemm_scratch_n = scr_n / 2;
+        t_gemm_scratch = scr + q * (scr_n / 4);
+        t_gemm_scratch_n = scr_n / 4;
       }
-      double* const t1p = i == 0 ? t1.p : t1b.p;
-      double* const t2p = i == 0 ? t2.p : t2b.p;
-      launch_copy(Y[i], X[i], V[i]->core_size(d), s);
-      for (int j = 0; j < 2; j++) {
-        qtt_mpo Kij = K[i][j];
-        const int wl = Kij->w[d], wr = Kij->w[d + 1];
-        const int ci = cap(i)[d], cj = cap(j)[d], ci1 = cap(i)[d + 1], cj1 = cap(j)[d + 1];
-        GemmF64 g1 = gemm_plain(LE[i][j][d].p, X[j], t1p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1);
-        g1.skip = skip;
-        gemm(g1, s);
-        GemmF64 g{};
-        g.A = Kij->k2(d); g.B = t1p; g.C = t2p;
-        g.M = 4 * wr; g.N = cj1; g.K = 4 * wl;
-        g.lda = 4 * wl; g.ldb = cj1; g.ldc = cj1;
-        g.nb1 = ci; g.nb2 = 1;
-        g.sA1 = 0; g.sB1 = (long long)wl * 4 * cj1; g.sC1 = (long long)4 * wr * cj1;
-        g.alpha = 1.0;
-        g.skip = skip;
-        gemm(g, s);
-        // Y[(a s)][b] += c * T2[(a s)][(q z)] * RE[d+1][b][(q z)]^T
-        GemmF64 g3 = gemm_plain(t2p, RE[i][j][d + 1].p, Y[i], 4 * ci, ci1, wr * cj1, wr * cj1,
-                                wr * cj1, ci1);
-        g3.tB = 1;
-        g3.alpha = c;
-        g3.beta = 1.0;
-        g3.skip = skip;
-        gemm(g3, s);
+      double* const t1p = t1s[q];
+      double* const t2p = t2s[q];
+      qtt_mpo Kij = K[i][j];
+      const int wl = Kij->w[d], wr = Kij->w[d + 1];
+      const int ci = cap(i)[d], cj = cap(j)[d], ci1 = cap(i)[d + 1], cj1 = cap(j)[d + 1];
+      GemmF64 g1 = gemm_plain(LE[i][j][d].p, X[j], t1p, ci * wl, 4 * cj1, cj, cj, 4 * cj1, 4 * cj1);
+      g1.skip = skip;
+      gemm(g1, cs);
+      GemmF64 g{};
+      g.A = Kij->k2(d); g.B = t1p; g.C = t2p;
+      g.M = 4 * wr; g.N = cj1; g.K = 4 * wl;
+      g.lda = 4 * wl; g.ldb = cj1; g.ldc = cj1;
+      g.nb1 = ci; g.nb2 = 1;
+      g.sA1 = 0; g.sB1 = (long long)wl * 4 * cj1; g.sC1 = (long long)4 * wr * cj1;
+      g.alpha = 1.0;
+      g.skip = skip;
+      gemm(g, cs);
+      // out[(a s)][b] (+)= c * T2[(a s)][(q z)] * RE[d+1][b][(q z)]^T
+      GemmF64 g3 = gemm_plain(t2p, RE[i][j][d + 1].p, out, 4 * ci, ci1, wr * cj1, wr * cj1,
+                              wr * cj1, ci1);
+      g3.tB = 1;
+      g3.alpha = c;
+      g3.beta = beta;
+      g3.skip = skip;
+      gemm(g3, cs);
+    };
+    try {
+      for (int i = 0; i < 2; i++) {
+        const cudaStream_t c0 = par ? ch[i] : ps, c1 = par ? ch[2 + i] : ps;
+        block(i, 1, zb[i].p, 0.0, c1);
+        launch_copy(Y[i], X[i], V[i]->core_size(d), c0);
+        block(i, 0, Y[i], 1.0, c0);
+        if (par) {
+          QTT_CUDA_CHECK(cudaEventRecord(ev[1 + i], c1));
+          QTT_CUDA_CHECK(cudaStreamWaitEvent(c0, ev[1 + i], 0));
+        }
+        const int ci = cap(i)[d], ci1 = cap(i)[d + 1];
+        launch_sum_slices(zb[i].p, 1, 4 * ci, ci1, Y[i], ci1, 1.0, 1.0, skip, c0);
       }
+    } catch (...) {
+      t_gemm_scratch = scr;
+      t_gemm_scratch_n = scr_n;
+      throw;
     }
     t_gemm_scratch = scr;
     t_gemm_scratch_n = scr_n;
     if (par) {
       for (int i = 0; i < 2; i++) {
-        cudaEvent_t je = ctx->dev_loops ? ctx->flow_ev[13 + i] : ctx->join_ev[i];
-        QTT_CUDA_CHECK(cudaEventRecord(je, rowst[i]));
-        QTT_CUDA_CHECK(cudaStreamWaitEvent(ps, je, 0));
+        QTT_CUDA_CHECK(cudaEventRecord(ev[3 + i], ch[i]));
+        QTT_CUDA_CHECK(cudaStreamWaitEvent(ps, ev[3 + i], 0));
       }
     }
   }
@@ -1732,7 +1760,7 @@ void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qt
   for (int i = 0; i < 2; i++)
     for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
   P.alloc();
-  DBuf<double> arena(ctx->dev_loops ? 2 * 16 * P.maxout : 0, P.s);  // a half per matvec row
+  DBuf<double> arena(ctx->dev_loops ? 4 * 16 * P.maxout : 0, P.s);  // a quarter per matvec chain
   struct ScratchScope {  // split-K scratch of a captured step's loop bodies
     explicit ScratchScope(DBuf<double>& a) {
       t_gemm_scratch = a.p;
@@ -2153,7 +2181,7 @@ void capture_step(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], double dt, double nu
   for (int k = 0; k < 2; k++) {
     if (!ctx->bstream[k])
       QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->bstream[k], cudaStreamNonBlocking));
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < 4; i++)
       if (!ctx->bworkers[k][i])
         QTT_CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->bworkers[k][i], cudaStreamNonBlocking));
   }
