@@ -3,6 +3,7 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
                     [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight]
                     [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
+                    [--clocks-file PATH]
 
 Workload (default): decaying double shear layer, periodic [0, 2 pi)^2 with
 N = 2^10, u = tanh((y - pi/2)/delta) - tanh((y - 3 pi/2)/delta),
@@ -33,6 +34,9 @@ a batch), SM clocks and throttle reasons sampled during the timed region;
 the roofline of the dominant kernel uses the arithmetic it counts on the
 device, its launch times from one more step under the library's launch
 profiler (outside the timed region) and a peak measured in the same run.
+gpu_launches counts the library's kernels run in the timed region: kernels
+of a replayed graph once per replay, those of its WHILE bodies once per
+pass (tallied on the device).  --clocks-file keeps the clock samples.
 """
 from __future__ import annotations
 
