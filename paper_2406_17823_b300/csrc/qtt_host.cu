@@ -183,8 +183,10 @@ struct qtt_ctx_s {
   // worker streams for independent operations of a stage (non-blocking, so
   // the legacy default stream does not serialise them), joined by events
   static constexpr int kWorkers = 12;
+  static constexpr int kStageWorkers = 10;  // the rest: the running sum of RK4 stages
   cudaStream_t workers[kWorkers] = {};
   cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t sum_ev = nullptr;  // hands a finished RK4 stage to the running sum
   cudaEvent_t join_ev[kWorkers] = {};
   static constexpr int kFlowEvents = 16;
   cudaEvent_t flow_ev[kFlowEvents] = {};  // cross-stream dependencies inside a stage
@@ -1849,7 +1851,9 @@ void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qt
 // Concurrency of independent operations: fork() makes every worker stream
 // wait for the context stream, run(k, f) enqueues operation f on worker k,
 // join() makes the context stream wait for every worker and hands the
-// outputs (allocated on workers) to the context stream for release.
+// outputs (allocated on workers) to the context stream for release.  These
+// are the first kStageWorkers streams; the last two carry the running sum
+// of the RK4 stages (rk4_core) and are forked and joined there.
 struct Workers {
   qtt_ctx ctx;
   bool serial;
@@ -1860,13 +1864,14 @@ struct Workers {
   void fork() {
     if (serial) return;
     QTT_CUDA_CHECK(cudaEventRecord(ctx->fork_ev, ctx->stream));
-    for (int k = 0; k < qtt_ctx_s::kWorkers; k++)
+    for (int k = 0; k < qtt_ctx_s::kStageWorkers; k++)
       QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[k], ctx->fork_ev, 0));
   }
   template <typename F>
   qtt_mps run(int k, F&& f) {
     if (serial) return f();
-    ctx->cur = ctx->workers[k % qtt_ctx_s::kWorkers];
+    if (k < 0 || k >= qtt_ctx_s::kStageWorkers) throw QttError(QTT_ERR_ARG, "worker index");
+    ctx->cur = ctx->workers[k];
     qtt_mps out = nullptr;
     try {
       out = f();
@@ -1883,13 +1888,15 @@ struct Workers {
   void after(int to, int from) {
     if (serial || to == from) return;
     if (nflow >= qtt_ctx_s::kFlowEvents) throw QttError(QTT_ERR_ARG, "flow event pool exhausted");
+    if (to >= qtt_ctx_s::kStageWorkers || from >= qtt_ctx_s::kStageWorkers)
+      throw QttError(QTT_ERR_ARG, "worker index");
     cudaEvent_t e = ctx->flow_ev[nflow++];
-    QTT_CUDA_CHECK(cudaEventRecord(e, ctx->workers[from % qtt_ctx_s::kWorkers]));
-    QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[to % qtt_ctx_s::kWorkers], e, 0));
+    QTT_CUDA_CHECK(cudaEventRecord(e, ctx->workers[from]));
+    QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[to], e, 0));
   }
   void join(std::initializer_list<qtt_mps> outs) {
     if (serial) return;
-    for (int k = 0; k < qtt_ctx_s::kWorkers; k++) {
+    for (int k = 0; k < qtt_ctx_s::kStageWorkers; k++) {
       QTT_CUDA_CHECK(cudaEventRecord(ctx->join_ev[k], ctx->workers[k]));
       QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[k], 0));
     }
@@ -2131,6 +2138,30 @@ void rk4_core(qtt_ctx ctx, qtt_mps u[2], double dt, double nu, MpsPtr out[2], in
   static const double BC[4][2] = {{0, 0}, {3.0, 0.25}, {1.5, 0.625}, {3.0, 0.25}};
   MpsPtr U[4][2];
   *nc = 0;
+  // the running sum ((U_1 + U_2) + U_3) + U_4 is built on workers 10 and 11
+  // (no stage uses them) as soon as each U_s exists, beside the later
+  // stages: the same sums in the same order, one of them left after the
+  // last projection instead of three
+  static const bool ser = getenv("QTT_SERIAL") != nullptr;
+  const bool side = !ser && ctx->workers[qtt_ctx_s::kWorkers - 1] != nullptr;
+  MpsPtr acc[2];
+  auto accumulate = [&](int st) {
+    if (side) {
+      QTT_CUDA_CHECK(cudaEventRecord(ctx->sum_ev, ctx->stream));
+      for (int i = 0; i < 2; i++) QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->workers[10 + i], ctx->sum_ev, 0));
+    }
+    for (int i = 0; i < 2; i++) {
+      ctx->cur = side ? ctx->workers[10 + i] : nullptr;
+      try {
+        const qtt_mps prev = st == 1 ? U[0][i].get() : acc[i].get();
+        acc[i] = MpsPtr(add2(ctx, 1.0, prev, 1.0, U[st][i].get()));
+      } catch (...) {
+        ctx->cur = nullptr;
+        throw;
+      }
+      ctx->cur = nullptr;
+    }
+  };
   for (int st = 0; st < 4; st++) {
     MpsPtr bown[2];
     qtt_mps b[2] = {u[0], u[1]};
@@ -2152,16 +2183,18 @@ void rk4_core(qtt_ctx ctx, qtt_mps u[2], double dt, double nu, MpsPtr out[2], in
     *nc |= ctx->last_not_converged;
     U[st][0] = MpsPtr(v1);
     U[st][1] = MpsPtr(v2);
+    if (st >= 1) accumulate(st);
   }
-  Workers wk(ctx);
-  wk.fork();
-  for (int i = 0; i < 2; i++)
-    out[i] = MpsPtr(wk.run(i, [&] {
-      MpsPtr acc(add2(ctx, 1.0, U[0][i].get(), 1.0, U[1][i].get()));
-      acc = MpsPtr(add2(ctx, 1.0, acc.get(), 1.0, U[2][i].get()));
-      return add2(ctx, 1.0, acc.get(), 1.0, U[3][i].get());
-    }));
-  wk.join({out[0].get(), out[1].get()});
+  if (side) {
+    for (int i = 0; i < 2; i++) {
+      QTT_CUDA_CHECK(cudaEventRecord(ctx->join_ev[10 + i], ctx->workers[10 + i]));
+      QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[10 + i], 0));
+    }
+  }
+  for (int i = 0; i < 2; i++) {
+    acc[i]->stream = ctx->stream;
+    out[i] = std::move(acc[i]);
+  }
 }
 
 // Whole-step graph (params.graphs = 2): stages as in stage graphs, the
@@ -2517,6 +2550,7 @@ qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* 
       QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->join_ev[k], cudaEventDisableTiming));
     }
     QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+    QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->sum_ev, cudaEventDisableTiming));
     for (int e = 0; e < qtt_ctx_s::kFlowEvents; e++)
       QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->flow_ev[e], cudaEventDisableTiming));
     QTT_CUDA_CHECK(cudaMemset(ctx->d_err, 0, sizeof(int)));
@@ -2607,6 +2641,7 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
     if (ctx->join_ev[k]) cudaEventDestroy(ctx->join_ev[k]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->sum_ev) cudaEventDestroy(ctx->sum_ev);
   for (int e = 0; e < qtt_ctx_s::kFlowEvents; e++)
     if (ctx->flow_ev[e]) cudaEventDestroy(ctx->flow_ev[e]);
   delete ctx;
