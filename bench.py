@@ -1,6 +1,6 @@
 """Benchmark: QTT RK4 steps per second on a 2^10 x 2^10 shear jet at chi = 64.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|mixed|fp64]
                     [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight]
                     [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
                     [--clocks-file PATH]
@@ -14,29 +14,48 @@ CG tolerance 1e-5 with at most 100 iterations, sweep tolerance 1e-5).
 A step is one full RK4 step (four penalised Euler minimisations) of both
 velocity components; the state advances from step to step.
 
+The metric compares the plain FP64 form with the mixed form.  By default
+(--precision both) one run times both on the same initial state: W warm-up
+steps of each, then K timed steps of the mixed form (the line's value,
+ms_per_step, e2e and roofline) and K timed steps of the FP64 form (the
+line's "fp64" object).  Both forms then take the same further steps (the
+profiled step, the e2e steps), after which "mixed_vs_fp64_rel_l2" is the
+relative L2 distance of their dense fields (both components).
+--precision mixed | fp64 times one form only.
+
 One JSON line is printed by rank 0.  With torchrun (N > 1) every rank runs
 its own trajectory on its own GPU (replicas: the method has no exchange
 step), value = all ranks' steps / the slowest rank's time.
 
 --batched B steps B jets (seeds seed .. seed+B-1) together through the
-batched C ABI (value = aggregate steps/s).  By default every RK4 step is
-replayed as one CUDA graph (the projection's CG and sweep loops as
-device-driven WHILE nodes), captured the second time its shapes occur, so
-the warm-up steps capture and the timed steps replay; --stage-graphs
-replays only the stages' right-hand sides, --eager launches everything from
-the host; --tight runs CG and sweeps to 1e-12 (CG cap 500)
+batched C ABI (value = aggregate steps/s; one precision, mixed when "both").
+By default every RK4 step is replayed as one CUDA graph (the projection's
+CG and sweep loops as device-driven WHILE nodes), captured the second time
+its shapes occur, so the warm-up steps capture and the timed steps replay;
+--stage-graphs replays only the stages' right-hand sides, --eager launches
+everything from the host; --tight runs CG and sweeps to 1e-12 (CG cap 500)
 instead of the paper's settings; --grid-bits / --chi override n / chi_max
-(smaller test cases); --impl reference times the CPU oracle instead (one
-core, a bounded sample of the same workload).  Timing: 3 warm-up steps by
-default, the L2 flushed (256 MB write) before every timed step, CUDA events
-on the stepping stream (host clock between device-wide synchronisations for
-a batch), SM clocks and throttle reasons sampled during the timed region;
-the roofline of the dominant kernel uses the arithmetic it counts on the
-device, its launch times from one more step under the library's launch
-profiler (outside the timed region) and a peak measured in the same run.
-gpu_launches counts the library's kernels run in the timed region: kernels
-of a replayed graph once per replay, those of its WHILE bodies once per
-pass (tallied on the device).  --clocks-file keeps the clock samples.
+(smaller test cases).
+
+CPU oracle: cpu_baseline times one whole RK4 step of the same workload
+from its initial state with the oracle on one core (a subprocess with one
+BLAS thread), counting the algorithmic FLOPs of that step as it runs
+(matrix products 2MNK, Householder QR with explicit Q 4mn^2 - 4n^3/3, thin
+SVD 6mn^2 + 20n^3 for m >= n); the count is the numerator of the line's
+aggregate roofline.  --impl reference times the oracle as the reference
+arm: one untimed RK4 step, then min(K, 3) consecutive whole steps, timed
+(the line's "steps" is the number timed).
+
+Timing: 3 warm-up steps by default, the L2 flushed (256 MB write) before
+every timed step, CUDA events on the stepping stream (host clock between
+device-wide synchronisations for a batch), SM clocks and throttle reasons
+sampled during the timed regions; the roofline of the dominant kernel uses
+the arithmetic it counts on the device, its launch times from one more step
+under the library's launch profiler (outside the timed region) and a peak
+measured in the same run.  gpu_launches counts the library's kernels run in
+the timed region: kernels of a replayed graph once per replay, those of its
+WHILE bodies once per pass (tallied on the device).  --clocks-file keeps
+the clock samples.
 """
 from __future__ import annotations
 
@@ -170,31 +189,114 @@ def gemm_peak(torch, dev, dtype):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_stage_seconds(w):
-    """Time the CPU oracle on a bounded sample: RK4 stage 1 (stage_w plus the
-    projection) of the workload, in a fresh interpreter whose BLAS is held to
-    one thread; a full step is four such stages, so steps/s = 1 / (4 t)."""
+def oracle_steps(w, warm, timed):
+    """Run the CPU oracle on the workload in a fresh interpreter whose BLAS is
+    held to one thread: `warm` untimed RK4 steps from the initial state, then
+    `timed` consecutive whole steps, each timed.  Returns the list of step
+    times (s) and the algorithmic FLOPs of the timed steps (per step)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-stage",
-                        json.dumps(w)], env=env, capture_output=True, text=True, timeout=900)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-steps",
+                        json.dumps(dict(w, warm=warm, timed=timed))], env=env,
+                       capture_output=True, text=True, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError("oracle timing failed:\n" + r.stderr[-2000:])
-    return float(r.stdout.strip().splitlines()[-1])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["times"], out["flops"]
 
 
-def _oracle_stage_child(wjson):
+class FlopCounter:
+    """Counts the algorithmic FLOPs of numpy's contraction and factorisation
+    calls while installed (the oracle's matrix products go through
+    tensordot / einsum / matmul; its factorisations through linalg.qr and
+    linalg.svd).  Models: a product 2 x (output size) x (contracted size);
+    Householder QR with explicit Q 4mn^2 - 4n^3/3 (m >= n); thin SVD
+    6mn^2 + 20n^3 (R-SVD, U_1, Sigma and V; m >= n)."""
+
+    def __init__(self):
+        self.total = 0.0
+        self._saved = []
+
+    def install(self):
+        import numpy
+        import numpy.linalg
+        c = self
+
+        def wrap(mod, name, count):
+            orig = getattr(mod, name)
+
+            def f(*a, **k):
+                out = orig(*a, **k)
+                c.total += count(out, *a, **k)
+                return out
+            self._saved.append((mod, name, orig))
+            setattr(mod, name, f)
+
+        def td(out, A, B, axes=2, **_):
+            A, B = numpy.asarray(A), numpy.asarray(B)
+            if isinstance(axes, int):
+                kdims = A.shape[A.ndim - axes:]
+            else:
+                ax = axes[0] if isinstance(axes[0], (list, tuple)) else [axes[0]]
+                kdims = [A.shape[i] for i in ax]
+            return 2.0 * numpy.asarray(out).size * float(numpy.prod(kdims))
+
+        def ein(out, spec, *ops, **_):
+            # every index of a two-operand contraction appears once in the loop nest
+            ins = spec.split("->")[0].split(",")
+            ext = {}
+            for sub, op in zip(ins, ops):
+                for ch, n in zip(sub, numpy.shape(op)):
+                    ext[ch] = n
+            return 2.0 * float(numpy.prod(list(ext.values()))) if len(ops) > 1 else 0.0
+
+        def mm(out, A, B, **_):
+            A = numpy.asarray(A)
+            return 2.0 * numpy.asarray(out).size * A.shape[-1]
+
+        def qr(out, A, *a, **k):
+            m, n = numpy.shape(A)[-2:]
+            m, n = max(m, n), min(m, n)
+            return 4.0 * m * n * n - 4.0 / 3.0 * n ** 3
+
+        def svd(out, A, *a, **k):
+            m, n = numpy.shape(A)[-2:]
+            m, n = max(m, n), min(m, n)
+            return 6.0 * m * n * n + 20.0 * n ** 3
+
+        wrap(numpy, "tensordot", td)
+        wrap(numpy, "einsum", ein)
+        wrap(numpy, "matmul", mm)
+        wrap(numpy.linalg, "qr", qr)
+        wrap(numpy.linalg, "svd", svd)
+        return self
+
+    def uninstall(self):
+        for mod, name, orig in reversed(self._saved):
+            setattr(mod, name, orig)
+        self._saved = []
+
+
+def _oracle_steps_child(wjson):
     w = json.loads(wjson)
+    counter = FlopCounter().install()  # before the oracle binds numpy's functions
     from oracle import qtt as Q
     u, dx, dt = workload_state(w["n"], w["seed"])
     p = Q.Params(eps=w["eps"], chi_max=w["chi_max"], mu=w["mu"], cg_tol=w["cg_tol"],
                  cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"])
     uq = [Q.from_dense(f, p.eps, p.chi_max) for f in u]
     ops = Q.build_operators(w["n"], dx)
-    t = time.perf_counter()
-    wv = Q.stage_w(uq, uq, dt / 6.0, 1.0 / w["Re"], p, ops)
-    Q.project(wv, dt / 6.0, p, ops)
-    print(time.perf_counter() - t)
+    nu = 1.0 / w["Re"]
+    for _ in range(w["warm"]):
+        uq = Q.rk4_step(uq, dt, nu, p, ops)
+    times, flops = [], []
+    for _ in range(w["timed"]):
+        f0 = counter.total
+        t = time.perf_counter()
+        uq = Q.rk4_step(uq, dt, nu, p, ops)
+        times.append(time.perf_counter() - t)
+        flops.append(counter.total - f0)
+    print(json.dumps({"times": times, "flops": flops}))
 
 
 # ------------------------------------------------------------------ ranks
@@ -218,19 +320,20 @@ def run_reference(args):
     if args.n:
         w["n"] = args.n
         w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
-    total = 0.0
-    for _ in range(args.steps):  # no warm-up: the CPU oracle has no warm-up effects
-        total += oracle_stage_seconds(w)
-    steps_done = 0.25 * args.steps
-    value = steps_done / total
+    timed = max(1, min(args.steps, 3))
+    times, flops = oracle_steps(w, 1, timed)
+    total = sum(times)
+    value = timed / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / steps_done, "higher_is_better": True,
+            "n_gpus": args.gpus, "steps": timed, "steps_requested": args.steps,
+            "warmup": 1, "ms_per_step": 1e3 * total / timed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {**w, "parallelism": "none (CPU oracle)"},
+            "algorithmic_flops_per_step": statistics.mean(flops),
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": "RK4 stage 1 of the workload per step, x4 for a full "
-                                       "step, numpy FP64 on one BLAS thread"},
+                             "sample": f"one untimed RK4 step, then {timed} consecutive whole "
+                                       "RK4 steps of the workload, timed; numpy FP64 oracle on "
+                                       "one BLAS thread"},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -238,13 +341,150 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ main arm
+def make_form(P, w, prec, graphs, B, local, rank):
+    """Contexts and initial states of one precision (same seeds for every form)."""
+    B = max(1, B)
+    if B > 1:
+        batch = P.Batch([dict(n=w["n"], precision=prec, graphs=graphs,
+                              **solver_kwargs(w)) for _ in range(B)], device=local)
+        ctxs = batch.contexts
+    else:
+        batch = None
+        ctxs = [P.Context(w["n"], precision=prec, device=local, graphs=graphs,
+                          **solver_kwargs(w))]
+    states, dts = [], []
+    for i, c in enumerate(ctxs):
+        u, dx, dt_i = workload_state(w["n"], w["seed"] + rank * B + i)
+        states.append([c.from_dense(f) for f in u])
+        dts.append(dt_i)
+    nu = 1.0 / w["Re"]
+
+    def step():
+        if B > 1:
+            return batch.rk4_step([s[0] for s in states], [s[1] for s in states], dts, [nu] * B)
+        return ctxs[0].rk4_step(states[0][0], states[0][1], dts[0], nu)
+
+    return dict(batch=batch, ctxs=ctxs, states=states, step=step, B=B)
+
+
+def time_steps(torch, form, K, flush):
+    """K timed steps: L2 flushed before each, CUDA events on the stepping
+    stream (host clock between device-wide synchronisations for a batch)."""
+    step, B = form["step"], form["B"]
+    times, converged = [], True
+    launches0 = sum(c.stats()["launches"] for c in form["ctxs"])
+    replays0 = sum(c.graph_stats()[1] for c in form["ctxs"])
+    tc0 = [c.tc_stats() for c in form["ctxs"]]
+    for _ in range(K):
+        flush.zero_()  # evict the L2 between timed steps
+        if B > 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            converged &= step()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        else:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            converged &= step()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize()
+    launches = sum(c.stats()["launches"] for c in form["ctxs"]) - launches0
+    replays = sum(c.graph_stats()[1] for c in form["ctxs"]) - replays0
+    tc1 = [c.tc_stats() for c in form["ctxs"]]
+    tc = {"accepted": sum(b[0] - a[0] for a, b in zip(tc0, tc1)),
+          "fell_back": sum(b[1] - a[1] for a, b in zip(tc0, tc1))}
+    return times, bool(converged), launches, replays, tc
+
+
+def profile_step(torch, form):
+    """Per-kernel device times: one more step under the launch profiler (CUDA
+    events around every launch, which also makes the stages launch eagerly),
+    outside the timed region."""
+    ctx = form["ctxs"][0]
+    ctx.profile_begin()
+    form["step"]()
+    torch.cuda.synchronize()
+    return ctx.profile_end()
+
+
+def e2e_steps(torch, form, n_steps, flush, world):
+    """The same metric through the C ABI with host buffers: upload the packed
+    states from host memory (into the state objects, whose capacities the
+    step graphs are keyed on), one step, download the packed results."""
+    ctxs, states = form["ctxs"], form["states"]
+    cores = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
+    times, h2d, d2h = [], 0, 0
+    for _ in range(n_steps):
+        host = cores
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, st, hc in zip(ctxs, states, host):
+            for x, cc in zip(st, hc):
+                c.upload_cores(x, cc)
+        form["step"]()
+        out = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        h2d = sum(a.nbytes for hc in host for cc in hc for a in cc)
+        d2h = sum(a.nbytes for oc in out for cc in oc for a in cc)
+        cores = out
+    value = world * form["B"] * len(times) / sum(times) if times else None
+    return {"value": value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def roofline_of(torch, dev, prof):
+    """Roofline of the kernel with the largest share of device time."""
+    dom, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    tot_ms = sum(v["ms"] for v in prof.values())
+    # the dominant kernel's arithmetic type decides the pipe it is bound by:
+    # the FP32 subspace search of the mixed form runs on the FP32 pipe
+    f32_kernel = dom.endswith("_f32")
+    peak = gemm_peak(torch, dev, torch.float32 if f32_kernel else torch.float64)
+    avg_ms = rec["ms"] / rec["launches"]
+    flops_per_launch = rec["flops"] / rec["launches"]
+    achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
+    cluster = dom.startswith("k_svd_cluster")
+    return {"kernel": dom, "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None,
+            "traffic": NCU_TRAFFIC.get(dom),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the widest "
+                              "launch (factor 256 wide) at n = 8, same shapes; see profiles/",
+            "peak_source": ("FP32 cuBLAS SGEMM (TF32 off) 4096^3" if f32_kernel else
+                            "FP64 cuBLAS DGEMM 4096^3") + " measured in this run (of measured)",
+            # one launch of the cluster SVD holds a 16-CTA cluster (16 of the 148 SMs)
+            "cluster_sms": 16 if cluster else None,
+            "frac_of_cluster_peak": achieved / (peak * 16 / 148) if peak and cluster else None,
+            "flops_source": ("counted on the device (QR, Jacobi dots and rotations, Q "
+                             "application)" if cluster else "host model"),
+            "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
+            "launches_timed": rec["launches"], "avg_launch_ms": avg_ms,
+            "flops_per_launch": flops_per_launch,
+            "timing_source": "one step after the timed region, launched eagerly under the "
+                             "library's launch profiler",
+            "kernel_shares": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items()}}
+
+
+def rel_l2(fa, fb):
+    """sqrt(sum_i |a_i - b_i|^2) / sqrt(sum_i |b_i|^2) over the components."""
+    num = sum(float(((a - b) ** 2).sum()) for a, b in zip(fa, fb))
+    den = sum(float((b ** 2).sum()) for b in fb)
+    return math.sqrt(num / den) if den > 0 else None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     ap.add_argument("--grid-bits", "--n", dest="n", type=int, default=None,
@@ -290,29 +530,14 @@ def main():
         w.update(cg_tol=1e-12, sweep_tol=1e-12, cg_maxit=500)
         w["workload"] += "_tight"
     graphs = 0 if args.eager else (1 if args.stage_graphs else 2)
-    prec = P.PREC_FP64 if args.precision == "fp64" else P.PREC_MIXED
-    nu = 1.0 / w["Re"]
     B = max(1, args.batched)
     if B > 1:
         w["workload"] = f"{w['workload']}_x{B}_trajectories"
-        batch = P.Batch([dict(n=w["n"], precision=prec, graphs=graphs,
-                              **solver_kwargs(w)) for _ in range(B)], device=local)
-        ctxs = batch.contexts
-    else:
-        ctxs = [P.Context(w["n"], precision=prec, device=local, graphs=graphs,
-                          **solver_kwargs(w))]
-    states, dts = [], []
-    for i, c in enumerate(ctxs):
-        u, dx, dt_i = workload_state(w["n"], w["seed"] + rank * B + i)
-        states.append([c.from_dense(f) for f in u])
-        dts.append(dt_i)
-    ctx = ctxs[0]
-
-    def step():
-        if B > 1:
-            return batch.rk4_step([s[0] for s in states], [s[1] for s in states], dts, [nu] * B)
-        return ctx.rk4_step(states[0][0], states[0][1], dts[0], nu)
-
+    names = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
+    if B > 1:
+        names = names[:1]
+    precs = {"mixed": P.PREC_MIXED, "fp64": P.PREC_FP64}
+    forms = {nm: make_form(P, w, precs[nm], graphs, B, local, rank) for nm in names}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -320,134 +545,100 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        step()
+    for nm in names:
+        for _ in range(args.warmup):
+            forms[nm]["step"]()
     barrier()
-    launches0 = sum(c.stats()["launches"] for c in ctxs)
-    replays0 = sum(c.graph_stats()[1] for c in ctxs)
-    times = []
-    converged = True
+    res = {}
     with ClockSampler(local, args.clocks_file) as clk:
-        barrier()
-        wall0 = time.perf_counter()
-        for _ in range(args.steps):
-            flush.zero_()  # evict the L2 between timed steps
-            if B > 1:
-                # the trajectories run on library-owned streams: device-wide
-                # synchronisation on both sides of the step, host clock
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                converged &= step()
-                torch.cuda.synchronize()
-                times.append(time.perf_counter() - t0)
-            else:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                converged &= step()
-                e1.record()
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1) / 1e3)
-        barrier()
-        wall = time.perf_counter() - wall0
+        for nm in names:
+            barrier()
+            wall0 = time.perf_counter()
+            times, conv, launches, replays, tc = time_steps(torch, forms[nm], args.steps, flush)
+            barrier()
+            t_max = reduce_max_time(sum(times), dist, dev)
+            res[nm] = dict(t_max=t_max, converged=conv, launches=launches, replays=replays,
+                           wall=time.perf_counter() - wall0, tc=tc)
+    for nm in names:
+        res[nm]["prof"] = profile_step(torch, forms[nm])
+    n_e2e = 0 if args.no_e2e else max(1, min(args.steps, 2))
+    head = names[0]
+    e2e = e2e_steps(torch, forms[head], n_e2e, flush, world)
+    for nm in names[1:]:  # the same number of steps, so the states can be compared
+        for _ in range(n_e2e):
+            forms[nm]["step"]()
     torch.cuda.synchronize()
-    gpu_launches = sum(c.stats()["launches"] for c in ctxs) - launches0
-    replays = sum(c.graph_stats()[1] for c in ctxs) - replays0
-    # per-kernel device times for the roofline: one more step under the
-    # launch profiler (CUDA events around every launch, which also makes the
-    # stages launch eagerly), outside the timed region
-    ctx.profile_begin()
-    step()
-    torch.cuda.synchronize()
-    prof = ctx.profile_end()
-    t_local = sum(times)
-    t_max = reduce_max_time(t_local, dist, dev)
-    value = world * B * args.steps / t_max
-
-    # e2e through the C ABI with host buffers: upload the packed states from
-    # host memory (into the state objects, whose capacities the stage graphs
-    # are keyed on), one step, download the packed results
-    cores = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
-    e2e_times, h2d, d2h = [], 0, 0
-    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
-        host = cores
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for c, st, hc in zip(ctxs, states, host):
-            for x, cc in zip(st, hc):
-                c.upload_cores(x, cc)
-        step()
-        out = [[c.to_cores(x) for x in st] for c, st in zip(ctxs, states)]
-        torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
-        h2d = sum(a.nbytes for hc in host for cc in hc for a in cc)
-        d2h = sum(a.nbytes for oc in out for cc in oc for a in cc)
-        cores = out
-    e2e_value = world * B * len(e2e_times) / sum(e2e_times) if e2e_times else None
+    cmp = None
+    if len(names) == 2:
+        fields = {nm: [forms[nm]["ctxs"][0].to_dense(x).cpu().numpy()
+                       for x in forms[nm]["states"][0]] for nm in names}
+        cmp = rel_l2(fields["mixed"], fields["fp64"])
+    steps_taken = args.warmup + args.steps + 1 + n_e2e
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (largest share of device time)
-    dom, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    tot_ms = sum(v["ms"] for v in prof.values())
-    peaks = measured_peaks()
-    # the dominant kernel's arithmetic type decides the pipe it is bound by:
-    # the FP32 subspace search of the mixed form runs on the FP32 pipe
-    f32_kernel = dom.endswith("_f32")
-    peak = gemm_peak(torch, dev, torch.float32 if f32_kernel else torch.float64)
-    avg_ms = rec["ms"] / rec["launches"]
-    flops_per_launch = rec["flops"] / rec["launches"]
-    achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
-    roofline = {"kernel": dom, "bound": "alu",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None,
-                "traffic": NCU_TRAFFIC.get(dom),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the widest "
-                                  "launch (factor 256 wide) at n = 8, same shapes; see profiles/",
-                "peak_source": ("FP32 cuBLAS SGEMM (TF32 off) 4096^3" if f32_kernel else
-                                "FP64 cuBLAS DGEMM 4096^3") + " measured in this run (of measured)",
-                # one launch of the cluster SVD holds a 16-CTA cluster (16 of the 148 SMs)
-                "cluster_sms": 16 if dom.startswith("k_svd_cluster") else None,
-                "frac_of_cluster_peak": (achieved / (peak * 16 / 148)
-                                         if peak and dom.startswith("k_svd_cluster") else None),
-                "flops_source": ("counted on the device (QR, Jacobi dots and rotations, Q "
-                                 "application)" if dom.startswith("k_svd_cluster") else
-                                 "host model"),
-                "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
-                "launches_timed": rec["launches"], "avg_launch_ms": avg_ms,
-                "flops_per_launch": flops_per_launch}
-    roofline["timing_source"] = ("one step after the timed region, launched eagerly under the "
-                                 "library's launch profiler")
-    cpu = None
+    def summary(nm):
+        r = res[nm]
+        return {"value": world * B * args.steps / r["t_max"],
+                "ms_per_step": 1e3 * r["t_max"] / args.steps,
+                "gpu_launches": r["launches"], "step_graph_replays_timed": r["replays"],
+                "all_projections_converged": r["converged"], "wall_s": r["wall"],
+                "tc_subspace_searches_timed": r["tc"],
+                "roofline": roofline_of(torch, dev, r["prof"])}
+
+    sums = {nm: summary(nm) for nm in names}
+    cpu, oracle_flops = None, None
     if not args.no_cpu_baseline:
-        st = oracle_stage_seconds(w)
-        cpu = {"value": 1.0 / (4.0 * st), "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": "RK4 stage 1 of the same workload (stage_w + projection), x4 for a "
-                         "full step, numpy FP64 oracle on one BLAS thread"}
+        times, flops = oracle_steps(w, 0, 1)
+        oracle_flops = flops[0]
+        cpu = {"value": 1.0 / times[0], "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": "one whole RK4 step of the same workload from its initial state, "
+                         "numpy FP64 oracle on one BLAS thread",
+               "algorithmic_flops_per_step": oracle_flops}
+    fp64_peak = None
+    for nm in names:
+        rf = sums[nm]["roofline"]
+        if rf["peak_source"].startswith("FP64"):
+            fp64_peak = rf["peak"]
+    if oracle_flops:
+        if fp64_peak is None:
+            fp64_peak = gemm_peak(torch, dev, torch.float64)
+        for nm in names:
+            ach = oracle_flops * sums[nm]["value"] / world / B / 1e12
+            sums[nm]["roofline"]["aggregate"] = {
+                "flops_per_step": oracle_flops, "achieved": ach, "unit": "TFLOP/s",
+                "peak": fp64_peak, "frac": ach / fp64_peak,
+                "source": "algorithmic FLOPs of one RK4 step counted in the CPU oracle (FP64 "
+                          "algorithm) x steps/s; peak = FP64 cuBLAS DGEMM measured in this run "
+                          "(of measured)"}
     clocks = clk.summary()
-    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+    peaks = measured_peaks()
+    hs = sums[head]
+    line = {"metric": METRIC, "value": hs["value"], "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": hs["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32/f64",
+            "dtype": "f64" if head == "fp64" else "f32/f64",
             "data": "synthetic (seeded shear-jet initial condition)",
             "timing": ("CUDA events on the stepping stream" if B == 1 else
                        "host clock between device-wide synchronisations (library-owned streams)"),
-            "config": {**w, "precision": args.precision, "parallelism": f"replicas x{world}",
+            "config": {**w, "precision": head, "parallelism": f"replicas x{world}",
                        "trajectories": B, "stage_graphs": bool(graphs),
                        "step_graphs": graphs == 2,
-                       "stage_graph_replays_timed": replays,
+                       "stage_graph_replays_timed": hs["step_graph_replays_timed"],
                        "l2": "flushed between timed steps (256 MB write)",
-                       "all_projections_converged": bool(converged)},
-            "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": gpu_launches, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": clocks, "wall_s": wall,
-            "kernel_shares": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items()},
-            "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}}
+                       "all_projections_converged": hs["all_projections_converged"]},
+            "e2e": e2e, "gpu_launches": hs["gpu_launches"], "roofline": hs["roofline"],
+            "tc_subspace_searches_timed": hs["tc_subspace_searches_timed"],
+            "cpu_baseline": cpu, "clocks": clocks, "wall_s": hs["wall_s"]}
+    if len(names) == 2:
+        line["fp64"] = sums["fp64"]
+        line["mixed_vs_fp64_rel_l2"] = cmp
+        line["mixed_vs_fp64_after_steps"] = steps_taken
+        line["mixed_over_fp64"] = hs["value"] / sums["fp64"]["value"]
+    line["peaks_file"] = {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -455,7 +646,7 @@ def main():
 
 
 if __name__ == "__main__":
-    if len(sys.argv) == 3 and sys.argv[1] == "--oracle-stage":
-        _oracle_stage_child(sys.argv[2])
+    if len(sys.argv) == 3 and sys.argv[1] == "--oracle-steps":
+        _oracle_steps_child(sys.argv[2])
         sys.exit(0)
     sys.exit(main())

@@ -199,6 +199,26 @@ qtt_status qtt_rk4_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
 qtt_status qtt_euler_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu);
 qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu);
 
+/* The mixed form's dense product on the tensor cores (spec precision
+ * option; no counterpart in the paper, which contracts in FP64 through
+ * cuTensorNet): C = op(A) op(B) with op(A) M x K (A row-major M x K with
+ * leading dimension lda, or its transpose when tA: A stored K x M), op(B)
+ * K x N (B stored K x N, or N x K when tB), C M x N row-major (ldc), all
+ * FP64 device buffers.  Both operands are split into two TF32 planes
+ * (hi = tf32(x), lo = tf32(x - hi)) and multiplied by tcgen05 tensor-core
+ * instructions as hi*hi + hi*lo + lo*hi with FP32 accumulation ("3xTF32");
+ * the error is below about (K + 3) 2^-23 (|op(A)| |op(B)|)_ij.  Enqueued
+ * on the context stream; scratch comes from the stream-ordered pool.
+ * QTT_ERR_ARG for null pointers, sizes < 1 or leading dimensions below the
+ * row length. */
+qtt_status qtt_gemm_tf32x3(qtt_ctx ctx, int M, int N, int K, const double* A, int lda, int tA,
+                           const double* B, int ldb, int tB, double* C, int ldc);
+
+/* Subspace searches of the mixed form (QTT_PREC_MIXED) served by the
+ * tensor cores since creation, and those whose acceptance test failed so
+ * that the FP32 cluster SVD recomputed the subspace.  Synchronises. */
+qtt_status qtt_tc_stats(qtt_ctx ctx, long long* accepted, long long* fell_back);
+
 /* Counters of the last qtt_project / qtt_rk4_step: total CG iterations,
  * sweeps, kernel launches enqueued by the library since context creation. */
 qtt_status qtt_stats(qtt_ctx ctx, long long* cg_iters, long long* sweeps,
@@ -231,8 +251,11 @@ qtt_status qtt_profile_end(qtt_ctx ctx, char* buf, size_t cap);
  * Intermediates live in a static 4 MiB device array: n <= 9 and every
  * partial contraction 4^k * bonds[k] (k < n) at most 2^18 doubles, else
  * QTT_ERR_SHAPE; QTT_ERR_ARG for null pointers or n outside 1..9.  The
- * first call on a device looks up the array's address with that device
- * current, so make it before any stream capture.  All calls share the
+ * array's device address is looked up once per device, with that device
+ * current: qtt_create does it for its device, otherwise the first call on a
+ * device does, so a caller without a context makes one call before any
+ * stream capture.  The cached address assumes the device's primary context
+ * lives as long as the process (no cudaDeviceReset).  All calls share the
  * array: calls whose work overlaps on the GPU race and must be ordered by
  * the caller.  Uses no cudaMalloc / cudaFree.  Asynchronous: launch errors
  * are returned (QTT_ERR_CUDA), execution errors surface at the caller's

@@ -85,7 +85,29 @@ __global__ void __launch_bounds__(1024) k_to_dense_noalloc(NoallocArgs g) {
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {nullptr};
 
+// The array's device address on device `dev` (which must be current),
+// looked up once and cached; null if the lookup fails.
+void* noalloc_address(int dev) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
 }  // namespace
+
+// Called by qtt_create with its device current, so that a caller who made a
+// context first never reaches the lookup inside a stream capture.
+void noalloc_prepare_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) noalloc_address(dev);
+}
 
 extern "C" qtt_status qtt_to_dense_noalloc(const double* d_cores, const int* bonds, int n,
                                            double* d_field_out, void* cuda_stream) {
@@ -110,18 +132,12 @@ extern "C" qtt_status qtt_to_dense_noalloc(const double* d_cores, const int* bon
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QTT_ERR_CUDA;
-  void* scratch = nullptr;
-  {
-    // first call on a device: look up the array's device address (with that
-    // device current); this must happen before any stream capture
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return QTT_ERR_CUDA;
-      g_noalloc_ptr[dev] = p;
-    }
-    scratch = g_noalloc_ptr[dev];
-  }
+  // the array's device address, looked up with this device current the
+  // first time the device is seen (qtt_create does it for its device); the
+  // cached address stays valid while the device's primary context lives,
+  // i.e. until the process exits or resets the device
+  void* scratch = noalloc_address(dev);
+  if (!scratch) return QTT_ERR_CUDA;
   g.scratch = (double*)scratch;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   k_to_dense_noalloc<<<1, 1024, 0, s>>>(g);

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc.cuh"
 
 thread_local LaunchCounter* g_launch_counter = nullptr;
 
@@ -38,6 +39,10 @@ std::map<uintptr_t, size_t>& reg_map() {
 }  // namespace
 
 // ---- launch profiler (events around every launch while a context profiles)
+// noalloc.cu: resolve the allocation-free readout's static array on the
+// current device (outside any stream capture)
+void noalloc_prepare_current_device();
+
 namespace {
 struct ProfRec {
   const char* name;
@@ -202,7 +207,9 @@ struct qtt_ctx_s {
   int slot = 0;
   float* d_mlp = nullptr;
   bool mlp_set = false;
-  long long* d_rf_counts = nullptr;  // [0] cuts served by the range finder, [1] fallbacks
+  // [0] cuts served by the range finder, [1] its fallbacks; [2] tensor-core
+  // subspace searches accepted, [3] searches that fell back to the FP32 SVD
+  long long* d_rf_counts = nullptr;
   // stage graphs (params.graphs), keyed by input capacities, aliasing, h,
   // nu and a; captured on a private non-blocking stream
   cudaStream_t gstream = nullptr;
@@ -704,6 +711,51 @@ HostMpo mpo_scaled(HostMpo m, double s) {
 }
 
 // ------------------------------------------------------------ compression
+// The mixed form's subspace search on the tensor cores (QTT_TC_SEARCH=0
+// selects the FP32 cluster Jacobi search instead) and its power iterations
+// after the sketch (QTT_TC_ITERS, default 6).
+// QTT_TC_SEARCH: 0 off, z zip-up cuts only (default), c compression cuts
+// only, a all.
+int tc_search_mode() {
+  static const int m = [] {
+    const char* e = getenv("QTT_TC_SEARCH");
+    if (!e) return 1;
+    return e[0] == '0' ? 0 : e[0] == 'z' ? 1 : e[0] == 'c' ? 2 : 3;
+  }();
+  return m;
+}
+bool tc_search_enabled() { return tc_search_mode() != 0; }
+bool tc_search_zipup() { return tc_search_mode() & 1; }
+bool tc_search_compress() { return tc_search_mode() & 2; }
+// Largest accepted contraction rho = (sigma_p / sigma_keep)^2 of a
+// tensor-core search (QTT_TC_RHO, default 1e-1): after the FP64 subspace
+// iteration the kept directions' error is about the search's FP32-level floor
+// times rho (about 1e-8 of the factor's norm at 1e-1).
+double tc_rho_max() {
+  static const double r = [] {
+    const char* e = getenv("QTT_TC_RHO");
+    return e ? atof(e) : 1e-1;
+  }();
+  return r;
+}
+// FP64 subspace iterations after the search (QTT_FP64_ITERS, default 1)
+int mixed_fp64_iters() {
+  static const int it = [] {
+    const char* e = getenv("QTT_FP64_ITERS");
+    const int v = e ? atoi(e) : 1;
+    return v < 1 ? 1 : v > 4 ? 4 : v;
+  }();
+  return it;
+}
+int tc_search_iters() {
+  static const int it = [] {
+    const char* e = getenv("QTT_TC_ITERS");
+    const int v = e ? atoi(e) : 6;
+    return v < 0 ? 0 : v > 16 ? 16 : v;
+  }();
+  return it;
+}
+
 // compress X -> new MPS with caps ocap; X unchanged.
 qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   const int n = X->n;
@@ -748,6 +800,16 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       vbm = std::max(vbm, (size_t)ocap[k] * rpo);
       rsm = std::max(rsm, rpo * rpo);
     }
+  // tensor-core subspace search of the mixed form: scratch for the widest cut
+  size_t tcm = 0;
+  if (mixed && tc_search_compress())
+    for (int k = 1; k < n; k++) {
+      const int rpo = std::min({qcap[k], 4 * ocap[k + 1], chi + kOver});
+      if (tc_search_supported(4 * ocap[k + 1], qcap[k], rpo))
+        tcm = std::max(tcm, tc_search_scratch_floats(4 * ocap[k + 1], qcap[k], rpo));
+    }
+  DBuf<float> TCs(tcm, s);
+  DBuf<int> tca(tcm ? 2 : 0, s);  // accept flag, stop word
   DBuf<double> Rs(mixed ? rsm : 0, s), Vt(mixed ? vtm : 0, s), Bm(mixed ? bmm : 0, s),
       Vb(mixed ? vbm : 0, s), wM(1, s);
   DBuf<int> rp(1, s);
@@ -893,7 +955,40 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       a32.US = MatView{Bm.p, rpo, a.US.rows, axis_prefix(rpo, dconst(1))};
       a32.VT = MatView{Vt.p, 4 * ocap[k + 1], axis_prefix(rpo, dconst(1)), a.VT.cols};
       a32.r_out = rp.p;
-      if (launch_svd_subspace_f32(a32, qcap[k], 4 * ocap[k + 1], s)) {
+      bool found = false;
+      if (TCs.p && tc_search_supported(4 * ocap[k + 1], qcap[k], rpo)) {
+        // right vectors of M: the subspace is on the column side (4 D_{k+1})
+        TcSearch t{};
+        t.X = Mp;
+        t.ld = 4 * ocap[k + 1];
+        t.rows = qcap[k];
+        t.cols = 4 * ocap[k + 1];
+        t.small_is_rows = 0;
+        t.sact = DimRef{Y->dims + k + 1, 4};
+        t.lact = dref(qD.p + k);
+        t.lact2 = dconst(1);
+        t.lact2.p = nullptr;
+        t.p = rpo;
+        t.iters = tc_search_iters();
+        t.key = 0x51ED0000ull + (unsigned long long)k;
+        t.out = Vt.p;
+        t.ldo = 4 * ocap[k + 1];
+        t.outT = 1;
+        t.r_out = rp.p;
+        t.keep = std::min(chi, rpo);
+        t.rho_max = tc_rho_max();
+        t.accept = tca.p;
+        t.stop = tca.p + 1;
+        t.counts = ctx->d_rf_counts + 2;
+        tc_search(t, TCs.p, TCs.n, ctx->d_err, s);
+        // the FP32 cluster SVD overwrites the result unless it was accepted
+        SvdArgs f32 = a32;
+        f32.skip = tca.p;
+        launch_svd_subspace_f32(f32, qcap[k], 4 * ocap[k + 1], s);
+        found = true;
+      }
+      if (!found) found = launch_svd_subspace_f32(a32, qcap[k], 4 * ocap[k + 1], s);
+      if (found) {
         QrArgs q{};
         q.A = MatView{Vt.p, 4 * ocap[k + 1], axis_prefix(rpo, dref(rp.p)), a.VT.cols};
         q.inT = 1;
@@ -913,7 +1008,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
                                4 * ocap[k + 1], rpo);
         g.tB = 1;
         gemm(g, s);
-        {
+        for (int it = 0; it < mixed_fp64_iters(); it++) {
           GemmF64 gz = gemm_plain(Bm.p, Mp, Vt.p, rpo, 4 * ocap[k + 1], qcap[k], rpo,
                                   4 * ocap[k + 1], 4 * ocap[k + 1]);
           gz.tA = 1;
@@ -1079,6 +1174,15 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
     }
   }
   DBuf<double> R0(rmax, s), R1(rmax, s), Xb(xmax, s), Tb(tmax, s), W(std::max(svw, qrw), s);
+  size_t tcm = 0;
+  if (mixed && tc_search_zipup())
+    for (int k = 0; k < n - 1; k++) {
+      const int rpo = std::min({4 * rcap[k], ca[k + 1] * cb[k + 1], chi + kOver});
+      if (tc_search_supported(4 * rcap[k], ca[k + 1] * cb[k + 1], rpo))
+        tcm = std::max(tcm, tc_search_scratch_floats(4 * rcap[k], ca[k + 1] * cb[k + 1], rpo));
+    }
+  DBuf<float> TCs(tcm, s);
+  DBuf<int> tca(tcm ? 2 : 0, s);  // accept flag, stop word
   DBuf<double> Rs(mixed ? rsm : 0, s), Ut(mixed ? utm : 0, s), Bt(mixed ? btm : 0, s),
       Ub(mixed ? ubm : 0, s);
   DBuf<int> rp(1, s);
@@ -1144,7 +1248,39 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
       a32.US = MatView{Bt.p, ca[k + 1] * cb[k + 1], axis_prefix(rpo, dconst(1)), a.US.cols};
       a32.VT = MatView{Ut.p, rpo, a.VT.rows, axis_prefix(rpo, dconst(1))};
       a32.r_out = rp.p;
-      if (launch_svd_subspace_f32(a32, ca[k + 1] * cb[k + 1], 4 * rcap[k], s)) {
+      bool found = false;
+      if (TCs.p && tc_search_supported(4 * rcap[k], ca[k + 1] * cb[k + 1], rpo)) {
+        // left vectors of T ((r, s) x (a', b')): the subspace is on the row side
+        TcSearch t{};
+        t.X = Tb.p;
+        t.ld = ca[k + 1] * cb[k + 1];
+        t.rows = 4 * rcap[k];
+        t.cols = ca[k + 1] * cb[k + 1];
+        t.small_is_rows = 1;
+        t.sact = DimRef{C->dims + k, 4};
+        t.lact = dref(A->dims + k + 1);
+        t.lact2 = dref(B->dims + k + 1);
+        t.p = rpo;
+        t.iters = tc_search_iters();
+        t.key = 0x2A9000ull + (unsigned long long)k;
+        t.out = Ut.p;
+        t.ldo = rpo;
+        t.outT = 0;
+        t.r_out = rp.p;
+        t.keep = std::min(chi, rpo);
+        t.rho_max = tc_rho_max();
+        t.accept = tca.p;
+        t.stop = tca.p + 1;
+        t.counts = ctx->d_rf_counts + 2;
+        tc_search(t, TCs.p, TCs.n, ctx->d_err, s);
+        // the FP32 cluster SVD overwrites the result unless it was accepted
+        SvdArgs f32 = a32;
+        f32.skip = tca.p;
+        launch_svd_subspace_f32(f32, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+        found = true;
+      }
+      if (!found) found = launch_svd_subspace_f32(a32, ca[k + 1] * cb[k + 1], 4 * rcap[k], s);
+      if (found) {
         QrArgs q{};
         q.A = MatView{Ut.p, rpo, a.VT.rows, axis_prefix(rpo, dref(rp.p))};
         q.Q = MatView{Ut.p, rpo, a.VT.rows, axis_prefix(rpo, dconst(1))};
@@ -1161,7 +1297,7 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
                                ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1]);
         g.tA = 1;
         gemm(g, s);
-        {
+        for (int it = 0; it < mixed_fp64_iters(); it++) {
           GemmF64 gy = gemm_plain(Tb.p, Bt.p, Ut.p, 4 * rcap[k], rpo, ca[k + 1] * cb[k + 1],
                                   ca[k + 1] * cb[k + 1], ca[k + 1] * cb[k + 1], rpo);
           gy.tB = 1;
@@ -1888,7 +2024,7 @@ struct Workers {
   void after(int to, int from) {
     if (serial || to == from) return;
     if (nflow >= qtt_ctx_s::kFlowEvents) throw QttError(QTT_ERR_ARG, "flow event pool exhausted");
-    if (to >= qtt_ctx_s::kStageWorkers || from >= qtt_ctx_s::kStageWorkers)
+    if (to < 0 || from < 0 || to >= qtt_ctx_s::kStageWorkers || from >= qtt_ctx_s::kStageWorkers)
       throw QttError(QTT_ERR_ARG, "worker index");
     cudaEvent_t e = ctx->flow_ev[nflow++];
     QTT_CUDA_CHECK(cudaEventRecord(e, ctx->workers[from]));
@@ -2045,6 +2181,7 @@ void capture_stage(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], qtt_mps b[2], bool 
   QTT_CUDA_CHECK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
   ctx->stream = ctx->gstream;
   t_capturing = true;
+  t_body_launches = 0;
   try {
     qtt_mps gu[2] = {G.in[0], G.in[1]};
     qtt_mps gb[2] = {alias ? G.in[0] : G.in[2], alias ? G.in[1] : G.in[3]};
@@ -2054,6 +2191,7 @@ void capture_stage(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], qtt_mps b[2], bool 
     t_capturing = false;
   } catch (...) {
     t_capturing = false;
+    t_body_launches = 0;
     cudaStreamEndCapture(ctx->gstream, &graph);
     if (graph) cudaGraphDestroy(graph);
     ctx->stream = orig;
@@ -2145,6 +2283,23 @@ void rk4_core(qtt_ctx ctx, qtt_mps u[2], double dt, double nu, MpsPtr out[2], in
   static const bool ser = getenv("QTT_SERIAL") != nullptr;
   const bool side = !ser && ctx->workers[qtt_ctx_s::kWorkers - 1] != nullptr;
   MpsPtr acc[2];
+  // Declared after U and acc, so destroyed before them: on every exit,
+  // including an exception from a later stage, the context stream waits for
+  // the running-sum work on workers 10 and 11 before U and acc are freed
+  // (stream-ordered) on it.
+  struct SideJoin {
+    qtt_ctx ctx;
+    bool on;
+    void join() {
+      if (!on) return;
+      on = false;
+      for (int i = 0; i < 2; i++) {
+        if (cudaEventRecord(ctx->join_ev[10 + i], ctx->workers[10 + i]) == cudaSuccess)
+          cudaStreamWaitEvent(ctx->stream, ctx->join_ev[10 + i], 0);
+      }
+    }
+    ~SideJoin() { join(); }
+  } side_join{ctx, side};
   auto accumulate = [&](int st) {
     if (side) {
       QTT_CUDA_CHECK(cudaEventRecord(ctx->sum_ev, ctx->stream));
@@ -2185,12 +2340,8 @@ void rk4_core(qtt_ctx ctx, qtt_mps u[2], double dt, double nu, MpsPtr out[2], in
     U[st][1] = MpsPtr(v2);
     if (st >= 1) accumulate(st);
   }
-  if (side) {
-    for (int i = 0; i < 2; i++) {
-      QTT_CUDA_CHECK(cudaEventRecord(ctx->join_ev[10 + i], ctx->workers[10 + i]));
-      QTT_CUDA_CHECK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev[10 + i], 0));
-    }
-  }
+  side_join.join();
+  QTT_CUDA_CHECK(cudaGetLastError());
   for (int i = 0; i < 2; i++) {
     acc[i]->stream = ctx->stream;
     out[i] = std::move(acc[i]);
@@ -2243,6 +2394,7 @@ void capture_step(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], double dt, double nu
   } catch (...) {
     t_capturing = false;
     ctx->dev_loops = false;
+    t_body_launches = 0;
     cudaStreamEndCapture(ctx->gstream, &graph);
     if (graph) cudaGraphDestroy(graph);
     ctx->stream = orig;
@@ -2254,7 +2406,10 @@ void capture_step(qtt_ctx ctx, StageGraph& G, qtt_mps u[2], double dt, double nu
   }
   const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
   ctx->stream = orig;
-  G.launches = ctx->launches.n - n0;
+  // kernels outside the loop bodies run once per replay; the bodies count
+  // their passes on the device
+  G.launches = ctx->launches.n - n0 - t_body_launches;
+  t_body_launches = 0;
   ctx->launches.n = n0;
   cudaError_t ei = ec;
   if (ec == cudaSuccess) ei = cudaGraphInstantiate(&G.exec, graph, 0);
@@ -2554,6 +2709,7 @@ qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* 
     for (int e = 0; e < qtt_ctx_s::kFlowEvents; e++)
       QTT_CUDA_CHECK(cudaEventCreateWithFlags(&ctx->flow_ev[e], cudaEventDisableTiming));
     QTT_CUDA_CHECK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    noalloc_prepare_current_device();
     {
       const size_t cells = (size_t)qtt_ctx_s::kSlots * qtt_ctx_s::kBonds;
       for (int t = 0; t < 2; t++) {
@@ -2569,9 +2725,9 @@ qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* 
       QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_mlp, QTT_MLP_PARAMS * sizeof(float)));
       QTT_CUDA_CHECK(cudaMemset(ctx->d_mlp, 0, QTT_MLP_PARAMS * sizeof(float)));
       reg_alloc(ctx->d_mlp, QTT_MLP_PARAMS * sizeof(float));
-      QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_rf_counts, 2 * sizeof(long long)));
-      QTT_CUDA_CHECK(cudaMemset(ctx->d_rf_counts, 0, 2 * sizeof(long long)));
-      reg_alloc(ctx->d_rf_counts, 2 * sizeof(long long));
+      QTT_CUDA_CHECK(cudaMalloc((void**)&ctx->d_rf_counts, 4 * sizeof(long long)));
+      QTT_CUDA_CHECK(cudaMemset(ctx->d_rf_counts, 0, 4 * sizeof(long long)));
+      reg_alloc(ctx->d_rf_counts, 4 * sizeof(long long));
     }
     const int n = params->n;
     const double dx = ctx->dx;
@@ -2913,6 +3069,31 @@ qtt_status qtt_inner(qtt_ctx ctx, qtt_mps a, qtt_mps b, double* out) {
     check_mps(ctx, b);
     *out = inner_impl(ctx, a, b);
     return check_device_errors(ctx);
+  });
+}
+
+qtt_status qtt_tc_stats(qtt_ctx ctx, long long* accepted, long long* fell_back) {
+  if (!ctx || !accepted || !fell_back) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    QTT_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    long long h[2];
+    QTT_CUDA_CHECK(cudaMemcpy(h, ctx->d_rf_counts + 2, sizeof h, cudaMemcpyDeviceToHost));
+    *accepted = h[0];
+    *fell_back = h[1];
+    return check_device_errors(ctx);
+  });
+}
+
+qtt_status qtt_gemm_tf32x3(qtt_ctx ctx, int M, int N, int K, const double* A, int lda, int tA,
+                           const double* B, int ldb, int tB, double* C, int ldc) {
+  if (!ctx || !A || !B || !C || M < 1 || N < 1 || K < 1) return QTT_ERR_ARG;
+  if (lda < (tA ? M : K) || ldb < (tB ? K : N) || ldc < N) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    cudaStream_t s = stream_of(ctx);
+    const int S = tc_gemm_splits(M, N, K);
+    DBuf<float> scr(tc_gemm_scratch_floats(M, N, K, S), s);
+    tc_gemm_f64(s, M, N, K, A, lda, tA, B, ldb, tB, C, ldc, ctx->d_err, scr.p, scr.n);
+    return QTT_OK;
   });
 }
 

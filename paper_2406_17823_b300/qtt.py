@@ -38,7 +38,7 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
            "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
            "qtt_euler_step", "qtt_rk2_step", "qtt_inner", "qtt_graph_stats",
-           "qtt_mps_upload_packed")
+           "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_tc_stats")
 
 
 class QttError(RuntimeError):
@@ -98,6 +98,9 @@ def lib():
             "qtt_profile_begin": (c_int, [vp]),
             "qtt_profile_end": (c_int, [vp, ctypes.c_char_p, c_size_t]),
             "qtt_to_dense_noalloc": (c_int, [vp, ip, c_int, vp, vp]),
+            "qtt_tc_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong)]),
+            "qtt_gemm_tf32x3": (c_int, [vp, c_int, c_int, c_int, vp, c_int, c_int, vp, c_int,
+                                        c_int, vp, c_int]),
             "qtt_learned_set": (c_int, [vp, vp]),
             "qtt_learned_next_step": (c_int, [vp]),
             "qtt_learned_log": (c_int, [vp, vp, vp, c_int, ip]),
@@ -343,6 +346,29 @@ class Context:
     def rk2_step(self, u1: MPS, u2: MPS, dt: float, nu: float):
         """Midpoint RK2 in place (App. B); True if both projections converged."""
         return self._step(lib().qtt_rk2_step, u1, u2, dt, nu)
+
+    def gemm_tf32x3(self, A, B, transA: bool = False, transB: bool = False):
+        """op(A) op(B) of FP64 device matrices on the tensor cores (3xTF32,
+        FP32 accumulation); returns a new FP64 device tensor."""
+        torch = _torch()
+        A = A.contiguous()
+        B = B.contiguous()
+        M, K = (A.shape[1], A.shape[0]) if transA else (A.shape[0], A.shape[1])
+        Kb, N = (B.shape[1], B.shape[0]) if transB else (B.shape[0], B.shape[1])
+        if K != Kb:
+            raise ValueError("inner dimensions differ")
+        C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+        self._check(lib().qtt_gemm_tf32x3(self.h, M, N, K, c_void_p(A.data_ptr()), A.shape[1],
+                                          int(transA), c_void_p(B.data_ptr()), B.shape[1],
+                                          int(transB), c_void_p(C.data_ptr()), N))
+        return C
+
+    def tc_stats(self):
+        """(accepted, fell_back): the mixed form's tensor-core subspace
+        searches, and those recomputed by the FP32 cluster SVD."""
+        a, f = c_longlong(), c_longlong()
+        self._check(lib().qtt_tc_stats(self.h, byref(a), byref(f)))
+        return a.value, f.value
 
     def profile_begin(self):
         self._check(lib().qtt_profile_begin(self.h))

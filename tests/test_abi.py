@@ -101,6 +101,10 @@ def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
         ("qtt_inner", [vp, vp, vp, vp], (None,) * 4),
         ("qtt_graph_stats", [vp, vp, vp], (None,) * 3),
         ("qtt_mps_upload_packed", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 0, None)),
+        ("qtt_tc_stats", [vp, vp, vp], (None,) * 3),
+        ("qtt_gemm_tf32x3", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                             ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int],
+         (None, 4, 4, 4, None, 4, 0, None, 4, 0, None, 4)),
     ]
     for name, argtypes, args in calls:
         f = getattr(lib, name)
@@ -135,3 +139,32 @@ def test_parameter_validation_without_gpu(libpath):
     for kw in bad:
         p = params(**kw)
         assert lib.qtt_create(ctypes.byref(h), 0, None, ctypes.byref(p)) == 1, kw
+
+
+def test_noalloc_size_checks_without_gpu(libpath):
+    """qtt_to_dense_noalloc checks its sizes against the static array before
+    any CUDA call: n outside 1..9 is QTT_ERR_ARG; at n = 9 a partial
+    contraction 4^k D_k one column over 2^18 doubles is QTT_ERR_SHAPE, as are
+    end bonds other than 1.  (The exact 2^18 edge is accepted and run in the
+    GPU test.)"""
+    lib = ctypes.CDLL(libpath)
+    vp = ctypes.c_void_p
+    f = lib.qtt_to_dense_noalloc
+    f.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    f.restype = ctypes.c_int
+    fake = vp(16)  # never dereferenced: every case is rejected on the host
+
+    def call(bonds, n):
+        b = (ctypes.c_int * len(bonds))(*bonds)
+        return f(fake, b, n, fake, None)
+
+    edge = [1, 4, 16, 64, 64, 64, 64, 16, 4, 1]
+    for k in (6, 7, 8):
+        over = list(edge)
+        over[k] += 1
+        assert call(over, 9) == 2, k
+    assert call([1] * 11, 10) == 1
+    assert call([1] * 2, 0) == 1
+    assert call([2, 4, 1], 2) == 2
+    assert call([1, 0, 1], 2) == 2
+    assert f(None, (ctypes.c_int * 3)(1, 4, 1), 2, fake, None) == 1

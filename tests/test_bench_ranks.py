@@ -69,3 +69,33 @@ def test_reference_arm_prints_once_under_torchrun():
     line = lines[0]
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["config"]["n"] == 3 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["steps"] == 1 and line["algorithmic_flops_per_step"] > 0
+    # the timed region really holds steps x ms_per_step of oracle work
+    assert line["ms_per_step"] > 0
+
+
+def test_flop_counter_models():
+    """The oracle's FLOP counter: products 2 x output x contracted size,
+    Householder QR with explicit Q 4mn^2 - 4n^3/3, thin SVD 6mn^2 + 20n^3."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.FlopCounter().install()
+    try:
+        a, b = np.ones((3, 4, 2)), np.ones((4, 2, 5))
+        np.tensordot(a, b, ([1, 2], [0, 1]))
+        assert c.total == 2 * 3 * 5 * 8
+        c.total = 0.0
+        np.einsum("ab,bc->ac", np.ones((3, 4)), np.ones((4, 5)))
+        assert c.total == 2 * 3 * 4 * 5
+        c.total = 0.0
+        np.linalg.qr(np.ones((6, 4)))
+        assert abs(c.total - (4 * 6 * 16 - 4 / 3 * 64)) < 1e-9
+        c.total = 0.0
+        np.linalg.svd(np.eye(4, 7), full_matrices=False)
+        assert c.total == 6 * 7 * 16 + 20 * 64
+    finally:
+        c.uninstall()
+    c.total = 0.0
+    np.tensordot(np.ones((2, 2)), np.ones((2, 2)), 1)
+    assert c.total == 0.0

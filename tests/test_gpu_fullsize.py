@@ -63,23 +63,50 @@ def test_add_full_size(state):
     assert rel(ctx.to_dense(g).cpu().numpy(), Q.to_dense(o)) <= TOL
 
 
-def test_rk4_step_full_size(state):
-    """One RK4 step of the bench workload (paper solver settings, Re = 2e5,
-    dt = 0.1 dx / max|u0|), twice on the GPU so that the second step runs
-    from replayed stage graphs, against two oracle steps."""
-    import paper_2406_17823_b300 as P
+@pytest.fixture(scope="module")
+def oracle_two_steps(state):
+    """Two oracle RK4 steps of the bench workload (paper solver settings,
+    Re = 2e5, dt = 0.1 dx / max|u0|), about a minute of CPU time."""
     _, (u, v), A, B, ops = state
     dx = 2 * np.pi / 2 ** N_BITS
     dt, nu = 0.1 * dx / float(np.abs(u).max()), 1 / 2e5
-    ctx = P.Context(N_BITS, eps=EPS, chi_max=CHI, graphs=1)
-    g = [ctx.from_cores(c) for c in (A, B)]
     o = [A, B]
     prm = Q.Params(eps=EPS, chi_max=CHI)
     for _ in range(2):
-        ctx.rk4_step(g[0], g[1], dt, nu)
         o = Q.rk4_step(o, dt, nu, prm, ops)
+    return dt, nu, [Q.to_dense(x) for x in o]
+
+
+def test_rk4_step_full_size(state, oracle_two_steps):
+    """One RK4 step of the bench workload, twice on the GPU so that the
+    second step runs from replayed stage graphs, against two oracle steps."""
+    import paper_2406_17823_b300 as P
+    _, (u, v), A, B, ops = state
+    dt, nu, want = oracle_two_steps
+    ctx = P.Context(N_BITS, eps=EPS, chi_max=CHI, graphs=1)
+    g = [ctx.from_cores(c) for c in (A, B)]
+    for _ in range(2):
+        ctx.rk4_step(g[0], g[1], dt, nu)
     assert ctx.graph_stats()[1] >= 2
-    for got, ref in zip(g, o):
-        r = rel(ctx.to_dense(got).cpu().numpy(), Q.to_dense(ref))
+    for got, ref in zip(g, want):
+        r = rel(ctx.to_dense(got).cpu().numpy(), ref)
         print(f"full-size RK4, two steps: relative L2 {r:.2e}")
         assert r <= TOL
+
+
+def test_mixed_rk4_two_steps_full_size(state, oracle_two_steps):
+    """The mixed form at the bench configuration, against the oracle itself
+    (not through the FP64 GPU path): two RK4 steps with whole-step graphs
+    (the bench's mode; the second step replays nothing yet, the graph is
+    captured there), within the mixed form's 1e-6 relative L2."""
+    import paper_2406_17823_b300 as P
+    _, (u, v), A, B, ops = state
+    dt, nu, want = oracle_two_steps
+    ctx = P.Context(N_BITS, eps=EPS, chi_max=CHI, graphs=2, precision=P.PREC_MIXED)
+    g = [ctx.from_cores(c) for c in (A, B)]
+    for _ in range(2):
+        ctx.rk4_step(g[0], g[1], dt, nu)
+    for got, ref in zip(g, want):
+        r = rel(ctx.to_dense(got).cpu().numpy(), ref)
+        print(f"full-size mixed RK4, two steps: relative L2 {r:.2e}")
+        assert r <= 1e-6
