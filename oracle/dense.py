@@ -13,37 +13,56 @@ from __future__ import annotations
 import numpy as np
 
 
-def d(F: np.ndarray, axis: int, dx: float) -> np.ndarray:
-    """(F(x+1) - F(x-1)) / (2 dx) along axis 1 (x1) or 2 (x2), periodic."""
+def _weights(order: int):
+    """Central-difference weights c_1..c_m of the given even order (the
+    same conditions as oracle.qtt.central_weights)."""
+    from oracle.qtt import central_weights
+    return central_weights(order)
+
+
+def d(F: np.ndarray, axis: int, dx: float, order: int = 2) -> np.ndarray:
+    """Central difference along axis 1 (x1) or 2 (x2), periodic: order 2 is
+    (F(x+1) - F(x-1)) / (2 dx); order 2m is sum_k c_k (F(x+k) - F(x-k)) / dx."""
     ax = axis - 1
-    return (np.roll(F, -1, axis=ax) - np.roll(F, 1, axis=ax)) / (2.0 * dx)
+    if order == 2:
+        return (np.roll(F, -1, axis=ax) - np.roll(F, 1, axis=ax)) / (2.0 * dx)
+    out = np.zeros_like(F)
+    for k, c in enumerate(_weights(order), start=1):
+        out += c * (np.roll(F, -k, axis=ax) - np.roll(F, k, axis=ax))
+    return out / dx
 
 
-def convection(u, dx):
+def convection(u, dx, order: int = 2):
     """Skew-symmetric convection 1/2 sum_j (u_j D_j u_i + D_j(u_j u_i)) (App. B)."""
     out = []
     for i in range(2):
         acc = np.zeros_like(u[i])
         for j in range(2):
-            acc += 0.5 * (u[j] * d(u[i], j + 1, dx) + d(u[j] * u[i], j + 1, dx))
+            acc += 0.5 * (u[j] * d(u[i], j + 1, dx, order) + d(u[j] * u[i], j + 1, dx, order))
         out.append(acc)
     return out
 
 
-def rhs_B(u, nu, dx):
+def rhs_B(u, nu, dx, order: int = 2):
     """B_i = convection_i - nu sum_j D_j D_j u_i (App. B, Eq. for B_i)."""
-    conv = convection(u, dx)
-    return [conv[i] - nu * sum(d(d(u[i], j, dx), j, dx) for j in (1, 2)) for i in range(2)]
+    conv = convection(u, dx, order)
+    return [conv[i] - nu * sum(d(d(u[i], j, dx, order), j, dx, order) for j in (1, 2))
+            for i in range(2)]
 
 
-def symbols(N: int, dx: float):
-    """Fourier symbols g_j = i sin(2 pi m_j / N) / dx of D_j (axis 0, 1)."""
+def symbols(N: int, dx: float, order: int = 2):
+    """Fourier symbols g_j of D_j (axis 0, 1): i sin(2 pi m_j / N) / dx for
+    order 2, i sum_k 2 c_k sin(2 pi k m_j / N) / dx for order 2m."""
     m = np.fft.fftfreq(N) * N
-    g = 1j * np.sin(2.0 * np.pi * m / N) / dx
+    if order == 2:
+        g = 1j * np.sin(2.0 * np.pi * m / N) / dx
+    else:
+        g = 1j * sum(2.0 * c * np.sin(2.0 * np.pi * k * m / N)
+                     for k, c in enumerate(_weights(order), start=1)) / dx
     return g[:, None] * np.ones((1, N)), np.ones((N, 1)) * g[None, :]
 
 
-def project(w, h: float, mu: float, dx: float):
+def project(w, h: float, mu: float, dx: float, order: int = 2):
     """Exact minimiser of mu |D1 v1 + D2 v2|^2 + |v - w|^2 / h^2.
 
     Per Fourier mode the normal matrix is I + c conj(g) g^T (c = mu h^2;
@@ -51,7 +70,7 @@ def project(w, h: float, mu: float, dx: float):
     v = w - c conj(g) (g^T w) / (1 + c |g|^2).
     """
     N = w[0].shape[0]
-    g1, g2 = symbols(N, dx)
+    g1, g2 = symbols(N, dx, order)
     c = mu * h * h
     W1, W2 = np.fft.fft2(w[0]), np.fft.fft2(w[1])
     gw = g1 * W1 + g2 * W2
@@ -69,7 +88,7 @@ RK4_H = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
 RK4_B = (None, (3.0, 0.25), (1.5, 0.625), (3.0, 0.25))
 
 
-def rk4_step(u, dt, nu, mu, dx):
+def rk4_step(u, dt, nu, mu, dx, order: int = 2):
     """Four projected Euler stages (App. B, Table RK4, Eqs. U1-U4)."""
     U = []
     b = u
@@ -78,9 +97,9 @@ def rk4_step(u, dt, nu, mu, dx):
             c1, c2 = RK4_B[s]
             b = [c1 * U[s - 1][i] + c2 * u[i] for i in range(2)]
         h = RK4_H[s] * dt
-        B = rhs_B(b, nu, dx)
+        B = rhs_B(b, nu, dx, order)
         w = [0.25 * u[i] - h * B[i] for i in range(2)]
-        U.append(project(w, h, mu, dx))
+        U.append(project(w, h, mu, dx, order))
     return [U[0][i] + U[1][i] + U[2][i] + U[3][i] for i in range(2)]
 
 

@@ -220,6 +220,73 @@ def mpo_diff(n: int, axis: int, dx: float) -> list:
     return W
 
 
+def central_weights(order: int) -> np.ndarray:
+    """Weights c_1..c_m (m = order / 2) of the central difference of the
+    given even order, D U(x) = sum_k c_k (U(x + k dx) - U(x - k dx)) / dx
+    (Sec. II.B: finite-difference operators of any order; App. D uses an
+    8th-order stencil).  From the Taylor expansion, the difference
+    U(x + k dx) - U(x - k dx) holds only odd derivatives, so D U = U' + O(dx^order)
+    requires sum_k c_k k = 1/2 and sum_k c_k k^j = 0 for odd j = 3..order-1:
+    m linear equations, solved here."""
+    assert order >= 2 and order % 2 == 0
+    m = order // 2
+    k = np.arange(1, m + 1, dtype=np.float64)
+    A = np.array([k ** (2 * i + 1) for i in range(m)])
+    rhs = np.zeros(m)
+    rhs[0] = 0.5
+    return np.linalg.solve(A, rhs)
+
+
+def mpo_shift(n: int, axis: int, a: int) -> list:
+    """S^a along one axis, (S^a U)(x) = U(x + a e_axis) on the periodic grid,
+    as the binary addition of the integer a to that axis' bits (the carry
+    logic of App. A, Table "diff_mpo", for any constant).  Reading the bits
+    from the least significant site upwards, the bond carries the value p
+    still to be added to the more significant part: at a site with output
+    bit b and incoming p, the input bit is (b + p) mod 2 and the outgoing
+    value floor((b + p) / 2).  The value left over at the most significant
+    site is a multiple of N and is dropped (periodic wrap).  Bond states are
+    the values reachable from a at each bond."""
+    states = [None] * (n + 1)
+    states[n] = [a]
+    for k in range(n - 1, -1, -1):
+        nxt = sorted({(b + p) // 2 for p in states[k + 1] for b in (0, 1)})
+        states[k] = nxt
+    W = []
+    for k in range(n):
+        left, right = states[k], states[k + 1]
+        w = np.zeros((len(left), D_PHYS, D_PHYS, len(right)))
+        for qi, p in enumerate(right):
+            for s_out in range(D_PHYS):
+                x, y = s_out >> 1, s_out & 1
+                b = x if axis == 1 else y
+                nb, carry = (b + p) % 2, (b + p) // 2
+                s_in = (nb << 1 | y) if axis == 1 else (x << 1 | nb)
+                w[left.index(carry), s_out, s_in, qi] = 1.0
+        W.append(w)
+    W[0] = W[0].sum(axis=0)[None]   # drop the final carry
+    return W
+
+
+def mpo_scale(W: list, c: float) -> list:
+    out = [w.copy() for w in W]
+    out[0] = out[0] * c
+    return out
+
+
+def mpo_diff_order(n: int, axis: int, dx: float, order: int) -> list:
+    """Central difference of the given even order along one axis,
+    sum_k c_k (S^k - S^-k) / dx with the weights of central_weights, as a
+    compressed sum of shift MPOs.  Order 2 is the paper's D (App. A)."""
+    c = central_weights(order)
+    W = None
+    for k in range(1, len(c) + 1):
+        for sign in (1, -1):
+            t = mpo_scale(mpo_shift(n, axis, sign * k), sign * c[k - 1] / dx)
+            W = t if W is None else mpo_sum(W, t)
+    return mpo_compress(W)
+
+
 def mpo_transpose(W: list) -> list:
     return [w.transpose(0, 2, 1, 3).copy() for w in W]
 
@@ -312,9 +379,16 @@ class Operators:
     K: dict            # (i, j) -> D_i^T D_j, the blocks of the projection system
 
 
-def build_operators(n: int, dx: float) -> Operators:
-    D1 = mpo_diff(n, 1, dx)
-    D2 = mpo_diff(n, 2, dx)
+def build_operators(n: int, dx: float, order: int = 2) -> Operators:
+    """D_1, D_2 (App. A for order 2; the higher even orders of Sec. II.B by
+    mpo_diff_order), the Laplacian D_1 D_1 + D_2 D_2 and the projection
+    blocks D_i^T D_j."""
+    if order == 2:
+        D1 = mpo_diff(n, 1, dx)
+        D2 = mpo_diff(n, 2, dx)
+    else:
+        D1 = mpo_diff_order(n, 1, dx, order)
+        D2 = mpo_diff_order(n, 2, dx, order)
     lap = mpo_compress(mpo_sum(mpo_compress(mpo_product(D1, D1)),
                                mpo_compress(mpo_product(D2, D2))))
     D = [D1, D2]

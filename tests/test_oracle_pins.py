@@ -394,3 +394,98 @@ def test_euler_rk2_amplification_factors():
         assert abs(amp(v) / g ** steps - 1) < 1e-9, step.__name__
     # the three schemes are told apart at this step size
     assert abs((1 - z) ** steps / (1 - z + z * z / 2) ** steps - 1) > 1e-5
+
+
+# ------------------------------------------------ higher-order stencils (Sec. II.B, App. D)
+# Textbook central-difference weights c_1..c_m of orders 4, 6, 8 (from the
+# Taylor conditions; e.g. Fornberg 1988, Table 1), typed in as the pin of
+# the oracle's linear solve.
+TEXTBOOK_WEIGHTS = {2: [1 / 2], 4: [2 / 3, -1 / 12], 6: [3 / 4, -3 / 20, 1 / 60],
+                    8: [4 / 5, -1 / 5, 4 / 105, -1 / 280]}
+
+
+def test_central_weights_textbook():
+    for order, want in TEXTBOOK_WEIGHTS.items():
+        np.testing.assert_allclose(Q.central_weights(order), want, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("a", [-5, -3, -1, 1, 2, 7])
+@pytest.mark.parametrize("axis", [1, 2])
+def test_shift_mpo_is_a_periodic_translation(a, axis):
+    """S^a: every row of the dense MPO holds one 1 at the translated point."""
+    n = 4
+    N = 2 ** n
+    M = Q.mpo_to_dense(Q.mpo_shift(n, axis, a))
+    S = np.zeros((N * N, N * N))
+    for x1 in range(N):
+        for x2 in range(N):
+            t = ((x1 + a) % N) * N + x2 if axis == 1 else x1 * N + (x2 + a) % N
+            S[x1 * N + x2, t] = 1.0
+    np.testing.assert_array_equal(M, S)
+
+
+def test_order2_machine_equals_paper_carry_table():
+    n = 5
+    dx = 2 * math.pi / 2 ** n
+    for axis in (1, 2):
+        A = Q.mpo_to_dense(Q.mpo_diff_order(n, axis, dx, 2))
+        B = Q.mpo_to_dense(Q.mpo_diff(n, axis, dx))
+        assert np.abs(A - B).max() <= 1e-13 / dx
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("axis", [1, 2])
+def test_high_order_diff_equals_stencil_bruteforce(order, axis):
+    """Dense matrix of the order-p MPO == the periodic stencil with the
+    textbook weights; D^T = -D."""
+    n = 4
+    N = 2 ** n
+    dx = 2 * math.pi / N
+    M = Q.mpo_to_dense(Q.mpo_diff_order(n, axis, dx, order))
+    S = np.zeros((N * N, N * N))
+    for x1 in range(N):
+        for x2 in range(N):
+            r = x1 * N + x2
+            for k, c in enumerate(TEXTBOOK_WEIGHTS[order], start=1):
+                for sgn in (1, -1):
+                    t = (((x1 + sgn * k) % N) * N + x2 if axis == 1
+                         else x1 * N + (x2 + sgn * k) % N)
+                    S[r, t] += sgn * c / dx
+    assert np.abs(M - S).max() <= 1e-12 / dx
+    assert np.abs(M + M.T).max() <= 1e-12 / dx
+    assert max(w.shape[3] for w in Q.mpo_diff_order(n, axis, dx, order)) <= 5
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
+def test_high_order_diff_convergence_rate(order):
+    """D sin(x) -> cos(x) with error ~ dx^order (closed form of the symbol
+    sum_k 2 c_k sin(k dx) / dx), checked through the QTT at n = 5 and 6."""
+    errs = []
+    for n in (5, 6):
+        X1, X2, dx = I.grid(n)
+        D = Q.mpo_diff_order(n, 1, dx, order)
+        q = Q.from_dense(np.sin(X1) * np.cos(X2), 1e-14, 64)
+        out = Q.to_dense(Q.apply_mpo(D, q, 0.0, FULL))
+        sym = sum(2 * c * math.sin(k * dx) for k, c in
+                  enumerate(TEXTBOOK_WEIGHTS[order], start=1)) / dx
+        assert rel(out, sym * np.cos(X1) * np.cos(X2)) < 1e-12
+        errs.append(abs(sym - 1.0))
+    rate = math.log2(errs[0] / errs[1])
+    assert abs(rate - order) < 0.1, rate
+
+
+def test_qtt_rk4_order4_equals_dense_rk4():
+    """Untruncated QTT RK4 step with 4th-order stencils == the dense
+    projected RK4 step with the same stencils (Fourier-space projection
+    with the 4th-order symbols)."""
+    n = 4
+    X1, X2, dx = I.grid(n)
+    ops = Q.build_operators(n, dx, order=4)
+    u0, _ = I.taylor_green(n)
+    u = [u0[0] + 0.1 * I.random_field(n, seed=3), u0[1] + 0.1 * I.random_field(n, seed=4)]
+    uq = [Q.from_dense(f, 0.0, FULL) for f in u]
+    p = Q.Params(eps=0.0, chi_max=FULL, **TIGHT)
+    out = Q.rk4_step(uq, 1e-2, 0.01, p, ops)
+    ref = Dn.rk4_step(u, 1e-2, 0.01, p.mu, dx, order=4)
+    for i in range(2):
+        assert rel(Q.to_dense(out[i]), ref[i]) < 1e-10
