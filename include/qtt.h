@@ -111,6 +111,11 @@ typedef struct {
                          per-stream order are those of the eager run, so
                          results are identical.  Ignored while profiling or
                          with learned truncation. */
+  int fd_order;       /* order of the central differences: 0 or 2 the
+                         paper's (App. A's carry table); 4, 6, 8 the
+                         higher-order stencils of Sec. II.B / App. D.  D_1,
+                         D_2, the Laplacian and the projection blocks are
+                         all built with it.  Fixed at creation. */
 } qtt_params;
 
 /* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,
@@ -157,6 +162,12 @@ qtt_status qtt_mps_to_packed(qtt_ctx ctx, qtt_mps mps, double* cores, int cores_
 qtt_status qtt_mps_info(qtt_mps mps, int* n, int* bonds);
 void qtt_free_mps(qtt_mps mps);
 
+/* A new derivative MPO (App. A; Sec. II.B for higher orders): the central
+ * difference of the context's fd_order along `axis` (1: x1, 2: x2) with
+ * spacing dx, to the power `power` (1: D, 2: D D, the literal square the
+ * paper's diffusion term uses).  The caller owns the handle (qtt_free_mpo).
+ * QTT_ERR_ARG for an axis or power outside 1..2 or dx <= 0. */
+qtt_status qtt_mpo_diff(qtt_ctx ctx, int axis, int power, double dx, qtt_mpo* out);
 /* The context's operators: which = 1 (D_1), 2 (D_2), 3 (Laplacian),
  * 4 + 2i + j (the projection block D_i^T D_j, i, j in {0, 1}).  The handle
  * is a new reference owned by the caller. */

@@ -11,9 +11,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <initializer_list>
 #include <map>
 #include <memory>
+#include <set>
 #include <mutex>
 #include <thread>
 #include <tuple>
@@ -708,6 +710,163 @@ HostMpo mpo_mul(const HostMpo& A, const HostMpo& B) {
 HostMpo mpo_scaled(HostMpo m, double s) {
   for (double& v : m.c[0]) v *= s;
   return m;
+}
+
+// Weights c_1..c_m of the central difference of even order 2m,
+// D U(x) = sum_k c_k (U(x + k dx) - U(x - k dx)) / dx (Sec. II.B, any order;
+// App. D, 8th order): by Taylor expansion the difference holds only odd
+// derivatives, so D U = U' + O(dx^2m) needs sum_k c_k k = 1/2 and
+// sum_k c_k k^j = 0 for odd j = 3..2m-1.  Gaussian elimination with partial
+// pivoting on that m x m system.
+std::vector<double> central_weights(int order) {
+  const int m = order / 2;
+  std::vector<std::vector<double>> A(m, std::vector<double>(m + 1, 0.0));
+  for (int i = 0; i < m; i++) {
+    for (int k = 1; k <= m; k++) A[i][k - 1] = std::pow((double)k, 2 * i + 1);
+    A[i][m] = i == 0 ? 0.5 : 0.0;
+  }
+  for (int c = 0; c < m; c++) {
+    int piv = c;
+    for (int r = c + 1; r < m; r++)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    std::swap(A[c], A[piv]);
+    for (int r = c + 1; r < m; r++) {
+      const double f = A[r][c] / A[c][c];
+      for (int q = c; q <= m; q++) A[r][q] -= f * A[c][q];
+    }
+  }
+  std::vector<double> x(m);
+  for (int r = m - 1; r >= 0; r--) {
+    double v = A[r][m];
+    for (int q = r + 1; q < m; q++) v -= A[r][q] * x[q];
+    x[r] = v / A[r][r];
+  }
+  return x;
+}
+
+// MPO of coef0 I + sum_t coef_t S_{axis_t}^{a_t} for any integer shifts,
+// (S^a U)(x) = U(x + a e_axis) on the periodic grid.  A finite-state
+// machine over the bits read from the least significant site up: the bond
+// carries (axis, p), the integer p still to be added to that axis' more
+// significant part (p = 0 is one idle state shared by both axes).  At a site
+// with output bit b the input bit is (b + p) mod 2 and the state becomes
+// (axis, floor((b + p) / 2)) -- App. A's carry table, generalised from +-1
+// to any constant.  The value left over at the most significant site is a
+// multiple of N and is dropped (periodic wrap: L sums every state).  Bond
+// states are the values reachable from the requested shifts at each bond.
+HostMpo translation_mpo(int n, double coef0, const std::vector<int>& axes,
+                        const std::vector<int>& shifts, const std::vector<double>& coefs) {
+  using St = std::pair<int, long long>;  // (axis, p); (0, 0) idle
+  auto fdiv2 = [](long long x) { return x >= 0 ? x / 2 : -((-x + 1) / 2); };
+  auto next = [&](const St& q, int b) -> St {
+    if (q.first == 0) return St{0, 0};
+    const long long p = fdiv2(b + q.second);
+    return p == 0 ? St{0, 0} : St{q.first, p};
+  };
+  std::map<St, double> start;
+  start[St{0, 0}] += coef0;
+  for (size_t t = 0; t < axes.size(); t++) {
+    const St q = shifts[t] == 0 ? St{0, 0} : St{axes[t], (long long)shifts[t]};
+    start[q] += coefs[t];
+  }
+  std::vector<std::vector<St>> st(n + 1);
+  for (auto& kv : start) st[n].push_back(kv.first);
+  for (int k = n - 1; k >= 0; k--) {
+    std::set<St> nx;
+    for (const St& q : st[k + 1])
+      for (int b = 0; b < 2; b++) nx.insert(next(q, b));
+    st[k].assign(nx.begin(), nx.end());
+  }
+  auto index = [](const std::vector<St>& v, const St& q) {
+    return (int)(std::lower_bound(v.begin(), v.end(), q) - v.begin());
+  };
+  HostMpo m;
+  m.n = n;
+  m.w.resize(n + 1);
+  for (int b = 0; b <= n; b++) m.w[b] = (int)st[b].size();
+  m.w[0] = 1;
+  m.w[n] = 1;
+  m.c.resize(n);
+  for (int k = 0; k < n; k++) {
+    const int wl = m.w[k], wr = m.w[k + 1];
+    m.c[k].assign((size_t)wl * 16 * wr, 0.0);
+    for (size_t qi = 0; qi < st[k + 1].size(); qi++) {
+      const St q = st[k + 1][qi];
+      const double wq = (k == n - 1) ? start[q] : 1.0;  // R: the requested shifts
+      const int qo = (k == n - 1) ? 0 : (int)qi;
+      for (int so = 0; so < 4; so++) {
+        const int x = so >> 1, y = so & 1;
+        int si = so;
+        if (q.first != 0) {
+          const int b = q.first == 1 ? x : y;
+          const int nb = (int)(((b + q.second) % 2 + 2) % 2);
+          si = q.first == 1 ? (nb << 1 | y) : (x << 1 | nb);
+        }
+        const int pl = (k == 0) ? 0 : index(st[k], next(q, q.first == 1 ? x : y));
+        m.c[k][((size_t)(pl * 4 + so) * 4 + si) * wr + qo] += wq;  // L sums at k = 0
+      }
+    }
+  }
+  return m;
+}
+
+// Central difference of order `order` along `axis` raised to `power` (1: D,
+// 2: D D, the literal square of App. B) with spacing dx, as translations.
+HostMpo fd_mpo(int n, int axis, int power, int order, double dx) {
+  const std::vector<double> c = central_weights(order);
+  const int m = (int)c.size();
+  std::map<int, double> d;  // shift -> coefficient of D
+  for (int k = 1; k <= m; k++) {
+    d[k] += c[k - 1] / dx;
+    d[-k] -= c[k - 1] / dx;
+  }
+  std::map<int, double> e = d;
+  if (power == 2) {
+    e.clear();
+    for (auto& a : d)
+      for (auto& b : d) e[a.first + b.first] += a.second * b.second;
+  }
+  double coef0 = 0.0;
+  std::vector<int> axes, shifts;
+  std::vector<double> coefs;
+  for (auto& kv : e) {
+    if (kv.first == 0) {
+      coef0 += kv.second;
+      continue;
+    }
+    axes.push_back(axis);
+    shifts.push_back(kv.first);
+    coefs.push_back(kv.second);
+  }
+  return translation_mpo(n, coef0, axes, shifts, coefs);
+}
+
+// The Laplacian D_1 D_1 + D_2 D_2 of order `order` (the literal squares of
+// App. B) as one translation machine over both axes.
+HostMpo fd_laplacian(int n, int order, double dx) {
+  const std::vector<double> c = central_weights(order);
+  const int m = (int)c.size();
+  std::map<int, double> d, e;
+  for (int k = 1; k <= m; k++) {
+    d[k] += c[k - 1] / dx;
+    d[-k] -= c[k - 1] / dx;
+  }
+  for (auto& x : d)
+    for (auto& y : d) e[x.first + y.first] += x.second * y.second;
+  double coef0 = 0.0;
+  std::vector<int> axes, shifts;
+  std::vector<double> coefs;
+  for (int ax = 1; ax <= 2; ax++)
+    for (auto& kv : e) {
+      if (kv.first == 0) {
+        coef0 += kv.second;
+        continue;
+      }
+      axes.push_back(ax);
+      shifts.push_back(kv.first);
+      coefs.push_back(kv.second);
+    }
+  return translation_mpo(n, coef0, axes, shifts, coefs);
 }
 
 // ------------------------------------------------------------ compression
@@ -2672,7 +2831,9 @@ bool valid_params(const qtt_params* p) {
          p->learned_trunc >= QTT_LEARNED_OFF && p->learned_trunc <= QTT_LEARNED_ON &&
          (p->learned_trunc != QTT_LEARNED_LOG || p->precision == QTT_PREC_FP64) &&
          p->rf_oversample >= 0 && p->rf_oversample <= 256 && p->rf_min_width >= 1 &&
-         p->graphs >= 0 && p->graphs <= 2;
+         p->graphs >= 0 && p->graphs <= 2 &&
+         (p->fd_order == 0 || p->fd_order == 2 || p->fd_order == 4 || p->fd_order == 6 ||
+          p->fd_order == 8);
 }
 
 void check_mps(qtt_ctx ctx, qtt_mps m) {
@@ -2731,24 +2892,40 @@ qtt_status qtt_create(qtt_ctx* out, int device, void* stream, const qtt_params* 
     }
     const int n = params->n;
     const double dx = ctx->dx;
-    HostMpo D1 = diff_mpo(n, 1, dx), D2 = diff_mpo(n, 2, dx);
-    ctx->D[0] = upload_mpo(ctx, D1);
-    ctx->D[1] = upload_mpo(ctx, D2);
-    // Laplacian D1 D1 + D2 D2 = (S1^{+2} + S1^{-2} + S2^{+2} + S2^{-2} - 4) / (4 dx^2)
-    const double c2 = 1.0 / (4.0 * dx * dx);
-    ctx->lap = upload_mpo(ctx, shift_sum_mpo(n, -4.0 * c2, {1, 1, 2, 2}, {2, -2, 2, -2},
-                                             {c2, c2, c2, c2}));
-    // projection blocks D_i^T D_j = -D_i D_j
-    HostMpo Ds[2] = {D1, D2};
-    for (int i = 0; i < 2; i++)
-      for (int j = 0; j < 2; j++) {
-        if (i == j) {
-          ctx->K[i][j] = upload_mpo(ctx, shift_sum_mpo(n, 2.0 * c2, {i + 1, i + 1}, {2, -2},
-                                                       {-c2, -c2}));
-        } else {
-          ctx->K[i][j] = upload_mpo(ctx, mpo_scaled(mpo_mul(Ds[i], Ds[j]), -1.0));
+    const int order = params->fd_order == 0 ? 2 : params->fd_order;
+    if (order == 2) {
+      // the paper's operators: D from App. A's carry table
+      HostMpo D1 = diff_mpo(n, 1, dx), D2 = diff_mpo(n, 2, dx);
+      ctx->D[0] = upload_mpo(ctx, D1);
+      ctx->D[1] = upload_mpo(ctx, D2);
+      // Laplacian D1 D1 + D2 D2 = (S1^{+2} + S1^{-2} + S2^{+2} + S2^{-2} - 4) / (4 dx^2)
+      const double c2 = 1.0 / (4.0 * dx * dx);
+      ctx->lap = upload_mpo(ctx, shift_sum_mpo(n, -4.0 * c2, {1, 1, 2, 2}, {2, -2, 2, -2},
+                                               {c2, c2, c2, c2}));
+      // projection blocks D_i^T D_j = -D_i D_j
+      HostMpo Ds[2] = {D1, D2};
+      for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) {
+          if (i == j) {
+            ctx->K[i][j] = upload_mpo(ctx, shift_sum_mpo(n, 2.0 * c2, {i + 1, i + 1}, {2, -2},
+                                                         {-c2, -c2}));
+          } else {
+            ctx->K[i][j] = upload_mpo(ctx, mpo_scaled(mpo_mul(Ds[i], Ds[j]), -1.0));
+          }
         }
-      }
+    } else {
+      // higher even orders (Sec. II.B): the same operators from central
+      // differences of that order, built as translation machines
+      HostMpo Ds[2] = {fd_mpo(n, 1, 1, order, dx), fd_mpo(n, 2, 1, order, dx)};
+      ctx->D[0] = upload_mpo(ctx, Ds[0]);
+      ctx->D[1] = upload_mpo(ctx, Ds[1]);
+      ctx->lap = upload_mpo(ctx, fd_laplacian(n, order, dx));
+      for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++)
+          ctx->K[i][j] = upload_mpo(
+              ctx, i == j ? mpo_scaled(fd_mpo(n, i + 1, 2, order, dx), -1.0)
+                          : mpo_scaled(mpo_mul(Ds[i], Ds[j]), -1.0));
+    }
     return QTT_OK;
   });
   if (st != QTT_OK) {
@@ -2805,7 +2982,9 @@ qtt_status qtt_destroy(qtt_ctx ctx) {
 }
 
 qtt_status qtt_set_params(qtt_ctx ctx, const qtt_params* p) {
-  if (!ctx || !valid_params(p) || p->n != ctx->p.n || p->L != ctx->p.L) return QTT_ERR_ARG;
+  if (!ctx || !valid_params(p) || p->n != ctx->p.n || p->L != ctx->p.L ||
+      (p->fd_order == 0 ? 2 : p->fd_order) != (ctx->p.fd_order == 0 ? 2 : ctx->p.fd_order))
+    return QTT_ERR_ARG;
   return guarded(ctx, [&]() -> qtt_status {
     graphs_clear(ctx);  // captured with the previous eps / chi / precision
     ctx->p = *p;
@@ -3069,6 +3248,27 @@ qtt_status qtt_inner(qtt_ctx ctx, qtt_mps a, qtt_mps b, double* out) {
     check_mps(ctx, b);
     *out = inner_impl(ctx, a, b);
     return check_device_errors(ctx);
+  });
+}
+
+qtt_status qtt_mpo_diff(qtt_ctx ctx, int axis, int power, double dx, qtt_mpo* out) {
+  if (!ctx || !out || (axis != 1 && axis != 2) || (power != 1 && power != 2) || !(dx > 0.0))
+    return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    cudaSetDevice(ctx->device);
+    const int n = ctx->p.n;
+    const int order = ctx->p.fd_order == 0 ? 2 : ctx->p.fd_order;
+    HostMpo m;
+    if (order == 2 && power == 1) {
+      m = diff_mpo(n, axis, dx);  // App. A's carry table
+    } else if (order == 2) {
+      const double c2 = 1.0 / (4.0 * dx * dx);  // (S^2 - 2 + S^-2) / (4 dx^2)
+      m = shift_sum_mpo(n, -2.0 * c2, {axis, axis}, {2, -2}, {c2, c2});
+    } else {
+      m = fd_mpo(n, axis, power, order, dx);
+    }
+    *out = upload_mpo(ctx, m);
+    return QTT_OK;
   });
 }
 

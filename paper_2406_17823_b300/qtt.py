@@ -38,7 +38,7 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
            "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
            "qtt_euler_step", "qtt_rk2_step", "qtt_inner", "qtt_graph_stats",
-           "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_tc_stats")
+           "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_tc_stats", "qtt_mpo_diff")
 
 
 class QttError(RuntimeError):
@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
                 ("mu", c_double), ("cg_tol", c_double), ("cg_maxit", c_int),
                 ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int),
                 ("learned_trunc", c_int), ("rf_oversample", c_int), ("rf_min_width", c_int),
-                ("graphs", c_int)]
+                ("graphs", c_int), ("fd_order", c_int)]
 
 
 _lib = None
@@ -80,6 +80,7 @@ def lib():
             "qtt_mps_info": (c_int, [vp, ip, ip]),
             "qtt_free_mps": (None, [vp]),
             "qtt_mpo_get": (c_int, [vp, c_int, POINTER(vp)]),
+            "qtt_mpo_diff": (c_int, [vp, c_int, c_int, c_double, POINTER(vp)]),
             "qtt_free_mpo": (None, [vp]),
             "qtt_apply_mpo": (c_int, [vp, vp, vp, c_double, c_int, POINTER(vp)]),
             "qtt_add": (c_int, [vp, c_int, POINTER(c_double), POINTER(vp), c_double, c_int,
@@ -165,7 +166,7 @@ class Context:
                  mu: float = 2.5e5, cg_tol: float = 1e-5, cg_maxit: int = 100,
                  sweep_tol: float = 1e-5, max_sweeps: int = 20, precision: int = PREC_FP64,
                  learned_trunc: int = LEARNED_OFF, rf_oversample: int = 8,
-                 rf_min_width: int = 128, graphs: int = 0,
+                 rf_min_width: int = 128, graphs: int = 0, fd_order: int = 0,
                  device: int = 0, stream=None):
         torch = _torch()
         self.device = device
@@ -173,7 +174,8 @@ class Context:
             stream = torch.cuda.current_stream(device)
         self.stream = stream
         self.params = Params(n, L, eps, chi_max, mu, cg_tol, cg_maxit, sweep_tol, max_sweeps,
-                             precision, learned_trunc, rf_oversample, rf_min_width, graphs)
+                             precision, learned_trunc, rf_oversample, rf_min_width, graphs,
+                             fd_order)
         h = c_void_p()
         st = lib().qtt_create(byref(h), device, c_void_p(stream.cuda_stream), byref(self.params))
         if st != 0:
@@ -266,8 +268,21 @@ class Context:
         self._check(lib().qtt_mpo_get(self.h, which, byref(out)))
         return out
 
-    def apply_mpo(self, which: int, mps: MPS, eps=None, chi_max=None) -> MPS:
-        m = self.mpo(which)
+    def mpo_diff(self, axis: int, power: int = 1, dx: float = None):
+        """A new derivative MPO handle (the context's stencil order); the
+        caller frees it with free_mpo."""
+        out = c_void_p()
+        dx = self.params.L / self.N if dx is None else dx
+        self._check(lib().qtt_mpo_diff(self.h, axis, power, dx, byref(out)))
+        return out
+
+    def free_mpo(self, m):
+        lib().qtt_free_mpo(m)
+
+    def apply_mpo(self, which, mps: MPS, eps=None, chi_max=None) -> MPS:
+        """`which`: an operator index of qtt_mpo_get, or an MPO handle."""
+        own = isinstance(which, int)
+        m = self.mpo(which) if own else which
         out = c_void_p()
         try:
             self._check(lib().qtt_apply_mpo(self.h, m, mps.h,
@@ -275,7 +290,8 @@ class Context:
                                             self.params.chi_max if chi_max is None else chi_max,
                                             byref(out)))
         finally:
-            lib().qtt_free_mpo(m)
+            if own:
+                lib().qtt_free_mpo(m)
         return MPS(self, out.value)
 
     def add(self, coefs, terms, eps=None, chi_max=None) -> MPS:
@@ -476,7 +492,8 @@ class Batch:
                             kw.pop("cg_maxit", 100), kw.pop("sweep_tol", 1e-5),
                             kw.pop("max_sweeps", 20), kw.pop("precision", PREC_FP64),
                             kw.pop("learned_trunc", LEARNED_OFF), kw.pop("rf_oversample", 8),
-                            kw.pop("rf_min_width", 128), kw.pop("graphs", 0))
+                            kw.pop("rf_min_width", 128), kw.pop("graphs", 0),
+                            kw.pop("fd_order", 0))
             if kw:
                 raise TypeError(f"unknown parameters {sorted(kw)}")
         h = c_void_p()
