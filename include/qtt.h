@@ -225,6 +225,16 @@ qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
 qtt_status qtt_gemm_tf32x3(qtt_ctx ctx, int M, int N, int K, const double* A, int lda, int tA,
                            const double* B, int ldb, int tB, double* C, int ldc);
 
+/* Turbulent kinetic energy spectrum of the velocity (u1, u2) (the paper's
+ * TKE spectra, Sec. III.A), computed on the device: the dense fields, their
+ * 2-D DFTs, and E(k) = sum over wavevectors m with round(|m|) = k of
+ * (|u1_hat(m)|^2 + |u2_hat(m)|^2) / (2 N^4) for k = 0..kmax (shells in units
+ * of 2 pi / L; wavevectors beyond kmax are left out; with kmax >=
+ * ceil(N / sqrt 2) the shells sum to the mean kinetic energy
+ * 1/2 mean(u1^2 + u2^2)).  Writes kmax + 1 doubles to h_E (host) and
+ * synchronises.  QTT_ERR_SHAPE for n > 12 or components on different grids. */
+qtt_status qtt_tke_spectrum(qtt_ctx ctx, qtt_mps u1, qtt_mps u2, int kmax, double* h_E);
+
 /* Subspace searches of the mixed form (QTT_PREC_MIXED) served by the
  * tensor cores since creation, and those whose acceptance test failed so
  * that the FP32 cluster SVD recomputed the subspace.  Synchronises. */

@@ -116,3 +116,24 @@ def rk2_step(u, dt, nu, mu, dx):
     B = rhs_B(um, nu, dx)
     return project([u[i] - dt * B[i] for i in range(2)], dt, mu, dx)
 
+
+
+def tke_spectrum(u, kmax: int):
+    """Turbulent kinetic energy spectrum of a velocity field on the periodic
+    N x N grid (Sec. III.A, the TKE spectra of the paper's figures):
+    E(k) = sum over wavevectors (m1, m2) with round(|m|) = k of
+    (|u_hat|^2 + |v_hat|^2) / (2 N^4), u_hat = fft2(u), k = 0..kmax (integer
+    shells in units of the fundamental 2 pi / L; wavevectors beyond kmax
+    are left out).  By Parseval sum_k E(k) = 1/2 mean(u^2 + v^2) when kmax
+    covers every shell.  A shell holds the integers q = m1^2 + m2^2 with
+    (k - 1/2)^2 < q < (k + 1/2)^2, i.e. k^2 - k + 1 <= q <= k^2 + k (q = 0 for
+    k = 0): no wavevector sits on a shell boundary."""
+    N = u[0].shape[0]
+    P = sum(np.abs(np.fft.fft2(c)) ** 2 for c in u)
+    m = (np.fft.fftfreq(N) * N).astype(np.int64)
+    q = m[:, None] ** 2 + m[None, :] ** 2
+    E = np.zeros(kmax + 1)
+    for k in range(kmax + 1):
+        sel = (q == 0) if k == 0 else ((q >= k * k - k + 1) & (q <= k * k + k))
+        E[k] = P[sel].sum() / (2.0 * N ** 4)
+    return E

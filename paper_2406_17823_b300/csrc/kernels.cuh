@@ -152,3 +152,9 @@ void launch_rf_decide(const double* nM, const double* nB, double eps, const int*
 void launch_rf_features(const double* sv, const int* skip_full, const int* w, const int* Dact,
                         const int* Nact4, const int* r, int bond, int n, float* feat, int* rank,
                         int* valid, cudaStream_t s);
+
+// ---------------------------------------------------------------- diagnostics
+// TKE spectrum of two dense N x N components (N = 2^logn <= 4096), see
+// spectrum.cu; C1, C2: N * N double2 scratch, P: N * N, E: kmax + 1.
+void launch_tke_spectrum(const double* u1, const double* u2, int logn, double2* C1, double2* C2,
+                         double* P, double* E, int kmax, cudaStream_t s);

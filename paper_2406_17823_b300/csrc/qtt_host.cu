@@ -3251,6 +3251,27 @@ qtt_status qtt_inner(qtt_ctx ctx, qtt_mps a, qtt_mps b, double* out) {
   });
 }
 
+qtt_status qtt_tke_spectrum(qtt_ctx ctx, qtt_mps u1, qtt_mps u2, int kmax, double* h_E) {
+  if (!ctx || !h_E || kmax < 0) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, u1);
+    check_mps(ctx, u2);
+    const int n = u1->n;
+    if (u2->n != n) throw QttError(QTT_ERR_SHAPE, "components on different grids");
+    if (n > 12) throw QttError(QTT_ERR_SHAPE, "spectrum: n > 12");
+    cudaStream_t s = stream_of(ctx);
+    const size_t NN = (size_t)1 << (2 * n);
+    DBuf<double> F1(NN, s), F2(NN, s), P(NN, s), E(kmax + 1, s);
+    DBuf<double2> C1(NN, s), C2(NN, s);
+    to_dense_impl(ctx, u1, F1.p);
+    to_dense_impl(ctx, u2, F2.p);
+    launch_tke_spectrum(F1.p, F2.p, n, C1.p, C2.p, P.p, E.p, kmax, s);
+    QTT_CUDA_CHECK(cudaMemcpyAsync(h_E, E.p, (kmax + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    QTT_CUDA_CHECK(cudaStreamSynchronize(s));
+    return check_device_errors(ctx);
+  });
+}
+
 qtt_status qtt_mpo_diff(qtt_ctx ctx, int axis, int power, double dx, qtt_mpo* out) {
   if (!ctx || !out || (axis != 1 && axis != 2) || (power != 1 && power != 2) || !(dx > 0.0))
     return QTT_ERR_ARG;

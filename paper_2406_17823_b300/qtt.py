@@ -38,7 +38,8 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
            "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
            "qtt_euler_step", "qtt_rk2_step", "qtt_inner", "qtt_graph_stats",
-           "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_tc_stats", "qtt_mpo_diff")
+           "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_tc_stats", "qtt_mpo_diff",
+           "qtt_tke_spectrum")
 
 
 class QttError(RuntimeError):
@@ -81,6 +82,7 @@ def lib():
             "qtt_free_mps": (None, [vp]),
             "qtt_mpo_get": (c_int, [vp, c_int, POINTER(vp)]),
             "qtt_mpo_diff": (c_int, [vp, c_int, c_int, c_double, POINTER(vp)]),
+            "qtt_tke_spectrum": (c_int, [vp, vp, vp, c_int, POINTER(c_double)]),
             "qtt_free_mpo": (None, [vp]),
             "qtt_apply_mpo": (c_int, [vp, vp, vp, c_double, c_int, POINTER(vp)]),
             "qtt_add": (c_int, [vp, c_int, POINTER(c_double), POINTER(vp), c_double, c_int,
@@ -343,6 +345,15 @@ class Context:
         """|<a|b>|^2 / (<a|a> <b|b>) (Sec. III's fidelity of two states)."""
         ab, aa, bb = self.inner(a, b), self.inner(a, a), self.inner(b, b)
         return ab * ab / (aa * bb) if aa > 0 and bb > 0 else 0.0
+
+    def tke_spectrum(self, u1: MPS, u2: MPS, kmax: int = None) -> np.ndarray:
+        """E(k), k = 0..kmax (default: every shell of the grid), computed on
+        the device (qtt_tke_spectrum)."""
+        if kmax is None:
+            kmax = int(np.ceil(self.N / np.sqrt(2.0))) + 1
+        E = (c_double * (kmax + 1))()
+        self._check(lib().qtt_tke_spectrum(self.h, u1.h, u2.h, kmax, E))
+        return np.array(E[:])
 
     def kinetic_energy(self, u1: MPS, u2: MPS) -> float:
         """1/2 mean(u1^2 + u2^2) over the grid."""

@@ -103,6 +103,7 @@ def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
         ("qtt_graph_stats", [vp, vp, vp], (None,) * 3),
         ("qtt_mps_upload_packed", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 0, None)),
         ("qtt_tc_stats", [vp, vp, vp], (None,) * 3),
+        ("qtt_tke_spectrum", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 4, None)),
         ("qtt_mpo_diff", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp],
          (None, 1, 1, 0.1, None)),
         ("qtt_gemm_tf32x3", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,

@@ -489,3 +489,25 @@ def test_qtt_rk4_order4_equals_dense_rk4():
     ref = Dn.rk4_step(u, 1e-2, 0.01, p.mu, dx, order=4)
     for i in range(2):
         assert rel(Q.to_dense(out[i]), ref[i]) < 1e-10
+
+
+# ------------------------------------------------ TKE spectrum (Sec. III.A)
+def test_tke_spectrum_parseval_and_single_modes():
+    """Parseval: the shells of all wavevectors sum to 1/2 mean(u^2 + v^2);
+    a single Fourier mode puts all its energy in the shell of its
+    wavenumber; Taylor-Green (modes (+-1, +-1)) sits in shell round(sqrt 2) = 1."""
+    n = 5
+    N = 2 ** n
+    X1, X2, dx = I.grid(n)
+    u = [I.white_field(n, seed=1), I.white_field(n, seed=2)]
+    kmax = int(math.ceil(math.sqrt(2) * N / 2)) + 1
+    E = Dn.tke_spectrum(u, kmax)
+    ke = 0.5 * np.mean(u[0] ** 2 + u[1] ** 2)
+    assert abs(E.sum() - ke) <= 1e-13 * ke
+    for (a, b, k) in ((3, 4, 5), (0, 7, 7), (5, 5, 7), (2, 1, 2)):
+        f = np.cos(a * X1 + b * X2)
+        E = Dn.tke_spectrum([f, np.zeros_like(f)], kmax)
+        assert abs(E[k] - 0.25) < 1e-13 and abs(E.sum() - 0.25) < 1e-13, (a, b)
+    tg, _ = I.taylor_green(n)
+    E = Dn.tke_spectrum(tg, kmax)
+    assert abs(E[1] - 0.25) < 1e-13 and abs(E.sum() - 0.25) < 1e-13
