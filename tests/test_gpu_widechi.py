@@ -1,0 +1,65 @@
+"""Bond caps past 64 (the chi = 128 and chi = 256 configurations): factors
+wider than 256 columns, which the cluster SVD serves with its scalar
+tournament (columns homed in distributed shared memory) instead of the
+register-resident systolic kernel, against the oracle.
+
+At n = 9 with chi = 128 the two middle bonds are at the cap: an MPO
+application makes 384-wide factors (3 chi), a sum 256-wide ones (2 chi) and
+the Hadamard zip-up 512-row factors (4 chi rows, chi^2 columns).  With
+chi = 256 the application reaches 768 and the sum 512.  Every result is
+compared with the oracle's on the reconstructed dense field: 1e-10 for the
+FP64 form, 1e-6 for the mixed form (whose searches fall back to the FP32
+cluster SVD at these widths).
+"""
+import numpy as np
+import pytest
+
+import qtt_inputs as I
+from oracle import qtt as Q
+
+pytestmark = pytest.mark.gpu
+N_BITS, EPS = 9, 1e-10
+
+
+@pytest.fixture(scope="module")
+def fields():
+    F = I.random_field(N_BITS, seed=1) + 1e-3 * I.white_field(N_BITS, seed=2)
+    G = I.random_field(N_BITS, seed=3) + 1e-3 * I.white_field(N_BITS, seed=4)
+    X1, X2, dx = I.grid(N_BITS)
+    return F, G, Q.build_operators(N_BITS, dx)
+
+
+def rel(a, b):
+    r = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    print(f"relative L2 {r:.2e}")
+    return r
+
+
+def dense(ctx, m):
+    return ctx.to_dense(m).cpu().numpy()
+
+
+@pytest.mark.parametrize("chi", [128, 256])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_apply_and_add_wide(fields, chi, prec, tol):
+    import paper_2406_17823_b300 as P
+    F, G, ops = fields
+    ctx = P.Context(N_BITS, eps=EPS, chi_max=chi, precision=prec)
+    A, B = Q.from_dense(F, EPS, chi), Q.from_dense(G, EPS, chi)
+    assert max(Q.bond_dims(A)) == chi  # the cap is reached
+    ga, gb = ctx.from_cores(A), ctx.from_cores(B)
+    assert rel(dense(ctx, ctx.apply_mpo(1, ga)), Q.to_dense(Q.apply_mpo(ops.D[0], A, EPS, chi))) <= tol
+    assert rel(dense(ctx, ctx.apply_mpo(3, gb)), Q.to_dense(Q.apply_mpo(ops.lap, B, EPS, chi))) <= tol
+    assert rel(dense(ctx, ctx.add([1.0, -0.7], [ga, gb])),
+               Q.to_dense(Q.add([1.0, -0.7], [A, B], EPS, chi))) <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_hadamard_chi128(fields, prec, tol):
+    import paper_2406_17823_b300 as P
+    F, G, ops = fields
+    chi = 128
+    ctx = P.Context(N_BITS, eps=EPS, chi_max=chi, precision=prec)
+    A, B = Q.from_dense(F, EPS, chi), Q.from_dense(G, EPS, chi)
+    got = dense(ctx, ctx.hadamard(ctx.from_cores(A), ctx.from_cores(B)))
+    assert rel(got, Q.to_dense(Q.hadamard(A, B, EPS, chi))) <= tol
