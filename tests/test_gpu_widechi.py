@@ -63,3 +63,28 @@ def test_hadamard_chi128(fields, prec, tol):
     A, B = Q.from_dense(F, EPS, chi), Q.from_dense(G, EPS, chi)
     got = dense(ctx, ctx.hadamard(ctx.from_cores(A), ctx.from_cores(B)))
     assert rel(got, Q.to_dense(Q.hadamard(A, B, EPS, chi))) <= tol
+
+
+def test_rk4_step_turbulence_chi128():
+    """One RK4 step in the shape of the chi = 128 turbulence configuration
+    (2^11 x 2^11, seeded random-phase vorticity with E(k) ~ k^4
+    exp(-2 (k / 10)^2), unit kinetic energy, eps = 1e-7, chi = 128, Re = 1e6,
+    dt = 0.1 dx / max|u|, the paper's solver settings): the step grows the
+    first middle bond to the cap.  FP64 form against the oracle at 1e-10,
+    mixed form at 1e-6 (about a minute of oracle time)."""
+    import paper_2406_17823_b300 as P
+    n, chi, eps = 11, 128, 1e-7
+    (u, v), dx = I.decaying_turbulence(n, k0=10, seed=0)
+    dt = 0.1 * dx / float(max(np.abs(u).max(), np.abs(v).max()))
+    nu = 1e-6
+    prm = Q.Params(eps=eps, chi_max=chi)
+    uq = [Q.from_dense(f, eps, chi) for f in (u, v)]
+    ref = Q.rk4_step(uq, dt, nu, prm, Q.build_operators(n, dx))
+    assert max(Q.bond_dims(ref[0])) == chi
+    want = [Q.to_dense(r) for r in ref]
+    for prec, tol in ((0, 1e-10), (1, 1e-6)):
+        ctx = P.Context(n, eps=eps, chi_max=chi, precision=prec, graphs=2)
+        g = [ctx.from_cores(c) for c in uq]
+        ctx.rk4_step(g[0], g[1], dt, nu)
+        for got, w in zip(g, want):
+            assert rel(dense(ctx, got), w) <= tol
