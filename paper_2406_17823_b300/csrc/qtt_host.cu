@@ -916,7 +916,7 @@ int tc_search_iters() {
 }
 
 // compress X -> new MPS with caps ocap; X unchanged.
-qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
+qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi, bool left_canonical = false) {
   const int n = X->n;
   cudaStream_t s = stream_of(ctx);
   const auto& cin = X->cap;
@@ -924,6 +924,11 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   for (int b = 1; b < n; b++) qcap[b] = std::min(4 * qcap[b - 1], cin[b]);
   for (int b = n - 1; b >= 1; b--)
     ocap[b] = std::min({qcap[b], 4 * ocap[b + 1], chi, clampi(natural_cap(n, b))});
+  // A left-canonical input (cores 1..n-1 with orthonormal columns, stored at
+  // the capacities the sweep would give them) is its own left-to-right QR
+  // sweep: Q_k = X_k and R = I.  The sweep is skipped.
+  bool lc = left_canonical;
+  for (int b = 0; b <= n && lc; b++) lc = qcap[b] == cin[b];
   MpsPtr Y(new_mps(ctx, n, ocap));
   launch_fill_int(Y->dims, n + 1, 1, s);  // interior bonds are written by the SVDs
   if (n == 1) {
@@ -944,10 +949,13 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   for (int k = 0; k < n; k++) mmax = std::max(mmax, (size_t)qcap[k] * 4 * ocap[k + 1]);
   for (int k = 0; k < n - 1; k++) qrw = std::max(qrw, qr_work_doubles(4 * qcap[k], cin[k + 1]));
   for (int k = 1; k < n; k++) svw = std::max(svw, svd_work_doubles(qcap[k], 4 * ocap[k + 1]));
-  DBuf<double> Qc(qcore_tot, s), Rb(rmax, s), Tb(tmax, s), USb(usmax, s), Mb(mmax, s),
-      W(std::max(qrw, svw), s);
-  DBuf<int> qD(n + 1, s);
-  launch_fill_int(qD.p, n + 1, 1, s);
+  DBuf<double> Qc(lc ? 0 : qcore_tot, s), Rb(lc ? 0 : rmax, s), Tb(lc ? 0 : tmax, s),
+      USb(usmax, s), Mb(mmax, s), W(std::max(qrw, svw), s);
+  DBuf<int> qD(lc ? 0 : n + 1, s);
+  if (!lc) launch_fill_int(qD.p, n + 1, 1, s);
+  // Q cores of the left-to-right sweep, their actual right dims, and the last core R X_{n-1}
+  auto qcore = [&](int k) -> const double* { return lc ? X->core(k) : Qc.p + qoff[k]; };
+  int* const qdims = lc ? X->dims : qD.p;
   const bool mixed = ctx->p.precision == QTT_PREC_MIXED;
   constexpr int kOver = 16;
   size_t vtm = 1, bmm = 1, vbm = 1, rsm = 1;
@@ -994,7 +1002,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       sv(logged ? svm : 0, s), rfd(learn ? 3 : 0, s);
   DBuf<int> rfi(learn ? 3 : 0, s);  // width, use_rf, skip_full
   // left-to-right QR
-  for (int k = 0; k < n - 1; k++) {
+  for (int k = 0; k < n - 1 && !lc; k++) {
     const double* Tp;
     if (k == 0) {
       Tp = X->core(0);
@@ -1018,7 +1026,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
     launch_qr_f64(a, 4 * qcap[k], cin[k + 1], s);
   }
   // last core after the sweep: T = R * X_{n-1}  (qcap[n-1] x 4)
-  {
+  if (!lc) {
     GemmF64 g = gemm_plain(Rb.p, X->core(n - 1), Tb.p, qcap[n - 1], 4, cin[n - 1], cin[n - 1], 4, 4);
     gemm(g, s);
   }
@@ -1026,18 +1034,18 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   for (int k = n - 1; k >= 1; k--) {
     const double* Mp;
     if (k == n - 1) {
-      Mp = Tb.p;
+      Mp = lc ? X->core(n - 1) : Tb.p;
     } else {
       // M = Qcore_k (4 qcap[k] x qcap[k+1]) * US (qcap[k+1] x ocap[k+1])
-      GemmF64 g = gemm_plain(Qc.p + qoff[k], USb.p, Mb.p, 4 * qcap[k], ocap[k + 1], qcap[k + 1],
+      GemmF64 g = gemm_plain(qcore(k), USb.p, Mb.p, 4 * qcap[k], ocap[k + 1], qcap[k + 1],
                              qcap[k + 1], ocap[k + 1], ocap[k + 1]);
       gemm(g, s);
       Mp = Mb.p;
     }
     SvdArgs a{};
-    a.M = MatView{const_cast<double*>(Mp), 4 * ocap[k + 1], axis_prefix(qcap[k], dref(qD.p + k)),
+    a.M = MatView{const_cast<double*>(Mp), 4 * ocap[k + 1], axis_prefix(qcap[k], dref(qdims + k)),
                   axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
-    a.US = MatView{USb.p, ocap[k], axis_prefix(qcap[k], dref(qD.p + k)),
+    a.US = MatView{USb.p, ocap[k], axis_prefix(qcap[k], dref(qdims + k)),
                    axis_prefix(ocap[k], dconst(1))};
     a.VT = MatView{Y->core(k), 4 * ocap[k + 1], axis_prefix(ocap[k], dconst(1)),
                    axis_pair(4, dconst(4), ocap[k + 1], dref(Y->dims + k + 1))};
@@ -1063,14 +1071,14 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       int* use_rf = rfi.p + 1;
       int* skip_full = rfi.p + 2;
       launch_rf_predict(ctx->d_mlp, ctx->d_feat[prev] + cell * QTT_MLP_FEATURES,
-                        ctx->d_valid[prev] + cell, chi, over, Wc, qD.p + k, Y->dims + k + 1, wdev,
+                        ctx->d_valid[prev] + cell, chi, over, Wc, qdims + k, Y->dims + k + 1, wdev,
                         use_rf, s);
       const unsigned long long key = ((unsigned long long)slot << 8) ^ (unsigned long long)k;
       launch_rf_omega(Om.p, ocap[k + 1], Y->dims + k + 1, Wc, wdev, key, s);
       gemm(gemm_plain(Mp, Om.p, Yr.p, qcap[k], Wc, N4, N4, Wc, Wc), s);  // Y = M Omega
       QrArgs q{};
-      q.A = MatView{Yr.p, Wc, axis_prefix(qcap[k], dref(qD.p + k)), axis_prefix(Wc, dref(wdev))};
-      q.Q = MatView{Qy.p, Wc, axis_prefix(qcap[k], dref(qD.p + k)), axis_prefix(Wc, dconst(1))};
+      q.A = MatView{Yr.p, Wc, axis_prefix(qcap[k], dref(qdims + k)), axis_prefix(Wc, dref(wdev))};
+      q.Q = MatView{Qy.p, Wc, axis_prefix(qcap[k], dref(qdims + k)), axis_prefix(Wc, dconst(1))};
       q.R = MatView{Rr.p, Wc, axis_prefix(Wc, dconst(1)), axis_prefix(Wc, dconst(1))};
       q.work = W.p;
       q.work_len = (long long)W.n;
@@ -1095,7 +1103,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       launch_svd_f64(f, qcap[k], N4, s);
       if (logged) {
         const int t = ctx->tab;
-        launch_rf_features(sv.p, skip_full, wdev, qD.p + k, Y->dims + k + 1, Y->dims + k, k, n,
+        launch_rf_features(sv.p, skip_full, wdev, qdims + k, Y->dims + k + 1, Y->dims + k, k, n,
                            ctx->d_feat[t] + cell * QTT_MLP_FEATURES, ctx->d_rank[t] + cell,
                            ctx->d_valid[t] + cell, s);
       }
@@ -1124,7 +1132,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
         t.cols = 4 * ocap[k + 1];
         t.small_is_rows = 0;
         t.sact = DimRef{Y->dims + k + 1, 4};
-        t.lact = dref(qD.p + k);
+        t.lact = dref(qdims + k);
         t.lact2 = dconst(1);
         t.lact2.p = nullptr;
         t.p = rpo;
@@ -1217,7 +1225,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
       if (logged) {
         const size_t cell = (size_t)slot * qtt_ctx_s::kBonds + k;
         const int t = ctx->tab;
-        launch_rf_features(sv.p, nullptr, nullptr, qD.p + k, Y->dims + k + 1, Y->dims + k, k, n,
+        launch_rf_features(sv.p, nullptr, nullptr, qdims + k, Y->dims + k + 1, Y->dims + k, k, n,
                            ctx->d_feat[t] + cell * QTT_MLP_FEATURES, ctx->d_rank[t] + cell,
                            ctx->d_valid[t] + cell, s);
       }
@@ -1225,7 +1233,7 @@ qtt_mps compress_impl(qtt_ctx ctx, qtt_mps X, double eps, int chi) {
   }
   // first core: Y_0 = Qcore_0 (4 x qcap[1]) * US (qcap[1] x ocap[1])
   {
-    GemmF64 g = gemm_plain(Qc.p + qoff[0], USb.p, Y->core(0), 4, ocap[1], qcap[1], qcap[1],
+    GemmF64 g = gemm_plain(qcore(0), USb.p, Y->core(0), 4, ocap[1], qcap[1], qcap[1],
                            ocap[1], ocap[1]);
     gemm(g, s);
   }
@@ -1506,7 +1514,8 @@ qtt_mps hadamard_impl(qtt_ctx ctx, qtt_mps A, qtt_mps B, double eps, int chi) {
     }
     std::swap(Rc, Rn);
   }
-  return compress_impl(ctx, C.get(), eps, chi);
+  // the zip-up leaves C left-canonical (orthonormal cores, centre at site n)
+  return compress_impl(ctx, C.get(), eps, chi, true);
 }
 
 }  // namespace
