@@ -471,6 +471,41 @@ def roofline_of(torch, dev, prof):
             "kernel_shares": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items()}}
 
 
+def tc_gemm_record(torch, ctx, peaks):
+    """Throughput of the tensor-core product (qtt_gemm_tf32x3: 3xTF32 on
+    tcgen05, FP32 accumulation) at 4096^3, CUDA events over 5 calls after
+    3 warm-up calls: the whole call (operand split, product, reduction)
+    and the product kernel alone (from the launch profiler).  Peak: the
+    measured BF16 tensor peak x 1/2 (TF32 runs at half the BF16 rate),
+    counting the three TF32 products of each 3xTF32 step."""
+    n = 4096
+    A = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    B = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.gemm_tf32x3(A, B)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        ctx.gemm_tf32x3(A, B)
+    e1.record()
+    e1.synchronize()
+    call_ms = e0.elapsed_time(e1) / 5
+    ctx.profile_begin()
+    ctx.gemm_tf32x3(A, B)
+    torch.cuda.synchronize()
+    kms = ctx.profile_end()["k_tc_gemm"]["ms"]
+    flops = 2.0 * n ** 3
+    tf32_peak = peaks.get("bf16_tflops") / 2 if peaks.get("bf16_tflops") else None
+    tensor_tflops = 3 * flops / (kms * 1e-3) / 1e12
+    return {"shape": [n, n, n], "call_ms": call_ms, "kernel_ms": kms,
+            "algorithmic_tflops": flops / (kms * 1e-3) / 1e12,
+            "tensor_tflops": tensor_tflops, "tf32_peak_tflops": tf32_peak,
+            "frac": tensor_tflops / tf32_peak if tf32_peak else None,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops x 1/2 (TF32 / BF16 nominal ratio; "
+                           "of measured)"}
+
+
 def rel_l2(fa, fb):
     """sqrt(sum_i |a_i - b_i|^2) / sqrt(sum_i |b_i|^2) over the components."""
     num = sum(float(((a - b) ** 2).sum()) for a, b in zip(fa, fb))
@@ -616,6 +651,9 @@ def main():
                           "(of measured)"}
     clocks = clk.summary()
     peaks = measured_peaks()
+    tcg = None
+    if "mixed" in names:
+        tcg = tc_gemm_record(torch, forms["mixed"]["ctxs"][0], peaks)
     hs = sums[head]
     line = {"metric": METRIC, "value": hs["value"], "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": hs["ms_per_step"],
@@ -638,6 +676,8 @@ def main():
         line["mixed_vs_fp64_rel_l2"] = cmp
         line["mixed_vs_fp64_after_steps"] = steps_taken
         line["mixed_over_fp64"] = hs["value"] / sums["fp64"]["value"]
+    if tcg:
+        line["tc_gemm"] = tcg
     line["peaks_file"] = {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -31,6 +31,7 @@ CASES = [
     (300, 37, 1000, True, True),     # ragged in every dimension
     (129, 257, 33, False, False),
     (1, 1, 1, False, False),
+    (4096, 4096, 4096, False, False),  # many full tiles (throughput shape)
 ]
 
 
