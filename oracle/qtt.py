@@ -652,6 +652,138 @@ def project(w: list, h: float, params: Params, ops: Operators):
     return V, info
 
 
+def hadamard_mpo(Y: list) -> list:
+    """The MPO H_Y of the element-wise product with the MPS Y:
+    H_Y[c, s, t, c'] = Y[c, s, c'] delta(s, t), so that H_Y X = Y (.) X
+    (Sec. II.B: the Hadamard product as a "nonlinear MPO")."""
+    eye = np.eye(D_PHYS)
+    return [np.einsum("asb,st->astb", y, eye) for y in Y]
+
+
+def implicit_terms(u, b, h: float, nu: float, ops: Operators, a_scale: float = 0.25):
+    """The right-hand side a u_i - h B_i(b) of one penalised Euler
+    minimisation as a sum of networks that are never contracted into an MPS
+    (the paper's form of the step, Sec. II.C and App. B, Eq. for B_i inside
+    the cost Theta): for component i a list of (coef, P, X) with P an MPO
+    (None: the identity) applied to the MPS X,
+      a_scale u_i                              (coef a_scale, P = I, X = u_i)
+      - h/2 b_j (.) D_j b_i = -h/2 (H_{b_j} D_j) b_i      (j = 1, 2)
+      - h/2 D_j (b_j (.) b_i) = -h/2 (D_j H_{b_j}) b_i    (j = 1, 2)
+      + h nu (D_1 D_1 + D_2 D_2) b_i           (the literal squares, reading 3).
+    """
+    terms = [[], []]
+    for i in range(2):
+        terms[i].append((a_scale, None, u[i]))
+        for j in range(2):
+            Hj = hadamard_mpo(b[j])
+            terms[i].append((-0.5 * h, mpo_product(Hj, ops.D[j]), b[i]))
+            terms[i].append((-0.5 * h, mpo_product(ops.D[j], Hj), b[i]))
+        terms[i].append((h * nu, ops.lap, b[i]))
+    return terms
+
+
+def project_implicit(terms, guess, h: float, params: Params, ops: Operators):
+    """The projection of `project` with the right-hand side given as the
+    networks of `implicit_terms` instead of an MPS w (the paper's form,
+    Sec. II.C: the nonlinear MPOs are contracted with the velocity states
+    inside the local problem).  The local right-hand side of component i at
+    the centre d is sum_t coef_t <L_t| P_t X_t |R_t>, with environments of
+    V_i against each term (overlaps for P = I, MPO sandwiches otherwise),
+    updated as the centre moves.  Initial guess `guess` (the paper: the
+    previous time step), brought to right-canonical form; its bonds are kept.
+    Same sweeps, CG and stopping rules as `project`."""
+    n = ops.n
+    c = params.mu * h * h
+    V = [right_canonicalize(guess[0]), right_canonicalize(guess[1])]
+    blocks = [(i, j) for i in range(2) for j in range(2)]
+    one3 = np.ones((1, 1, 1))
+    one2 = np.ones((1, 1))
+    LE = {bk: [None] * (n + 1) for bk in blocks}
+    RE = {bk: [None] * (n + 1) for bk in blocks}
+    nt = [len(terms[i]) for i in range(2)]
+    TL = [[[None] * (n + 1) for _ in range(nt[i])] for i in range(2)]
+    TR = [[[None] * (n + 1) for _ in range(nt[i])] for i in range(2)]
+    for bk in blocks:
+        LE[bk][0] = one3
+        RE[bk][n] = one3
+    for i in range(2):
+        for t, (_, P, _) in enumerate(terms[i]):
+            TL[i][t][0] = one2 if P is None else one3
+            TR[i][t][n] = one2 if P is None else one3
+
+    def build_right(k):
+        for (i, j) in blocks:
+            RE[(i, j)][k] = env_right(RE[(i, j)][k + 1], V[i][k], ops.K[(i, j)][k], V[j][k])
+        for i in range(2):
+            for t, (_, P, X) in enumerate(terms[i]):
+                TR[i][t][k] = (ovl_right(TR[i][t][k + 1], V[i][k], X[k]) if P is None else
+                               env_right(TR[i][t][k + 1], V[i][k], P[k], X[k]))
+
+    def build_left(k):
+        for (i, j) in blocks:
+            LE[(i, j)][k] = env_left(LE[(i, j)][k - 1], V[i][k - 1], ops.K[(i, j)][k - 1],
+                                     V[j][k - 1])
+        for i in range(2):
+            for t, (_, P, X) in enumerate(terms[i]):
+                TL[i][t][k] = (ovl_left(TL[i][t][k - 1], V[i][k - 1], X[k - 1]) if P is None else
+                               env_left(TL[i][t][k - 1], V[i][k - 1], P[k - 1], X[k - 1]))
+
+    for k in range(n - 1, 0, -1):
+        build_right(k)
+
+    info = ProjectInfo()
+
+    def matvec(d, Xv):
+        Y = [Xv[0].copy(), Xv[1].copy()]
+        for (i, j) in blocks:
+            Y[i] += c * local_apply(LE[(i, j)][d], ops.K[(i, j)][d], Xv[j], RE[(i, j)][d + 1])
+        return Y
+
+    def rhs_at(d, i):
+        acc = None
+        for t, (coef, P, X) in enumerate(terms[i]):
+            r = (local_rhs(TL[i][t][d], X[d], TR[i][t][d + 1]) if P is None else
+                 local_apply(TL[i][t][d], P[d], X[d], TR[i][t][d + 1]))
+            acc = coef * r if acc is None else acc + coef * r
+        return acc
+
+    def solve(d):
+        rhs = [rhs_at(d, i) for i in range(2)]
+        x = [V[0][d].copy(), V[1][d].copy()]
+        its = conjugate_gradient(lambda X: matvec(d, X), rhs, x, params.cg_tol, params.cg_maxit)
+        info.cg_iters += its
+        V[0][d], V[1][d] = x
+
+    def norm_total():
+        return float(sum(np.sum(V[i][0] ** 2) for i in range(2)))
+
+    n_prev = norm_total()
+    for sweep in range(params.max_sweeps):
+        for d in range(0, n - 1):
+            solve(d)
+            for i in range(2):
+                Dl, dd, Dr = V[i][d].shape
+                Q, R = np.linalg.qr(V[i][d].reshape(Dl * dd, Dr))
+                V[i][d] = Q.reshape(Dl, dd, Q.shape[1])
+                V[i][d + 1] = np.tensordot(R, V[i][d + 1], axes=(1, 0))
+            build_left(d + 1)
+        for d in range(n - 1, 0, -1):
+            solve(d)
+            for i in range(2):
+                Dl, dd, Dr = V[i][d].shape
+                Q, R = np.linalg.qr(V[i][d].reshape(Dl, dd * Dr).T)
+                V[i][d] = Q.T.reshape(Q.shape[1], dd, Dr)
+                V[i][d - 1] = np.tensordot(V[i][d - 1], R.T, axes=(2, 0))
+            build_right(d)
+        info.sweeps = sweep + 1
+        n_new = norm_total()
+        if n_new == 0.0 or abs(n_new - n_prev) <= params.sweep_tol * n_new:
+            info.converged = True
+            break
+        n_prev = n_new
+    return V, info
+
+
 def conjugate_gradient(matvec, b, x, tol, maxit) -> int:
     """Plain CG on a list-of-arrays vector, in place on x (App. B).
 
@@ -737,6 +869,43 @@ def rk4_step(u, dt: float, nu: float, params: Params, ops: Operators, stats=None
         h = RK4_H[s] * dt
         w = stage_w(u, b, h, nu, params, ops)
         v, info = project(w, h, params, ops)
+        if stats is not None:
+            stats.append(info)
+        U.append(v)
+    out = []
+    for i in range(2):
+        acc = add([1.0, 1.0], [U[0][i], U[1][i]], eps, chi)
+        acc = add([1.0, 1.0], [acc, U[2][i]], eps, chi)
+        acc = add([1.0, 1.0], [acc, U[3][i]], eps, chi)
+        out.append(acc)
+    return out
+
+
+def scaled(A: list, c: float) -> list:
+    out = [a.copy() for a in A]
+    out[0] = out[0] * c
+    return out
+
+
+def rk4_step_implicit(u, dt: float, nu: float, params: Params, ops: Operators, stats=None):
+    """One RK4 step in the paper's form (Sec. II.C, App. B): the four
+    penalised Euler minimisations of `rk4_step` (Table RK4, Eqs. U1-U4) with
+    B never formed as an MPS -- each stage's right-hand side a u - h B(b)
+    enters its projection as the networks of `implicit_terms`.  Initial
+    guess of every stage: the previous time step, a u (a = 1/4), so each
+    U_s keeps the bonds of u.  u^{s+1} = ((U1 + U2) + U3) + U4 as in
+    `rk4_step`.  Identical to `rk4_step` when nothing is truncated; they
+    differ by about eps otherwise."""
+    eps, chi = params.eps, params.chi_max
+    U = []
+    b = u
+    for s in range(4):
+        if s > 0:
+            c1, c2 = RK4_B[s]
+            b = [add([c1, c2], [U[s - 1][i], u[i]], eps, chi) for i in range(2)]
+        h = RK4_H[s] * dt
+        terms = implicit_terms(u, b, h, nu, ops, 0.25)
+        v, info = project_implicit(terms, [scaled(u[i], 0.25) for i in range(2)], h, params, ops)
         if stats is not None:
             stats.append(info)
         U.append(v)

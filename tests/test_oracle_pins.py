@@ -511,3 +511,53 @@ def test_tke_spectrum_parseval_and_single_modes():
     tg, _ = I.taylor_green(n)
     E = Dn.tke_spectrum(tg, kmax)
     assert abs(E[1] - 0.25) < 1e-13 and abs(E.sum() - 0.25) < 1e-13
+
+
+# ------------------------------------------------ the paper's implicit right-hand side (f1)
+def test_hadamard_mpo_is_the_elementwise_product():
+    n = 4
+    A = Q.from_dense(I.random_field(n, seed=1), 0.0, FULL)
+    B = Q.from_dense(I.random_field(n, seed=2), 0.0, FULL)
+    out = Q.to_dense(Q.apply_mpo_exact(Q.hadamard_mpo(A), B))
+    assert rel(out, Q.to_dense(A) * Q.to_dense(B)) < 1e-13
+
+
+def test_implicit_projection_equals_fourier_solve():
+    """At full rank the projection of the implicit right-hand side
+    a u - h B(b) (never formed as an MPS) is the exact minimiser: the dense
+    Fourier-space solve of w = a u - h B(b) computed densely (App. B)."""
+    n = 4
+    X1, X2, dx = I.grid(n)
+    ops = Q.build_operators(n, dx)
+    u0, _ = I.taylor_green(n)
+    u = [u0[0] + 0.1 * I.random_field(n, seed=3), u0[1] + 0.1 * I.random_field(n, seed=4)]
+    b = [u[0] + 0.05 * I.random_field(n, seed=5), u[1] - 0.05 * I.random_field(n, seed=6)]
+    h, nu = 2e-2, 0.01
+    p = Q.Params(eps=0.0, chi_max=FULL, **TIGHT)
+    uq = [Q.from_dense(f, 0.0, FULL) for f in u]
+    bq = [Q.from_dense(f, 0.0, FULL) for f in b]
+    terms = Q.implicit_terms(uq, bq, h, nu, ops, 0.25)
+    v, info = Q.project_implicit(terms, [Q.scaled(x, 0.25) for x in uq], h, p, ops)
+    B = Dn.rhs_B(b, nu, dx)
+    want = Dn.project([0.25 * u[i] - h * B[i] for i in range(2)], h, p.mu, dx)
+    for i in range(2):
+        assert rel(Q.to_dense(v[i]), want[i]) < 1e-10
+    assert info.converged
+
+
+def test_implicit_rk4_equals_dense_and_explicit():
+    """Untruncated: the paper's form of the RK4 step equals the dense
+    projected RK4 step and the explicit (B formed) QTT step."""
+    n = 4
+    X1, X2, dx = I.grid(n)
+    ops = Q.build_operators(n, dx)
+    u0, _ = I.taylor_green(n)
+    u = [u0[0] + 0.1 * I.random_field(n, seed=3), u0[1] + 0.1 * I.random_field(n, seed=4)]
+    uq = [Q.from_dense(f, 0.0, FULL) for f in u]
+    p = Q.Params(eps=0.0, chi_max=FULL, **TIGHT)
+    imp = Q.rk4_step_implicit(uq, 1e-2, 0.01, p, ops)
+    ref = Dn.rk4_step(u, 1e-2, 0.01, p.mu, dx)
+    exp_ = Q.rk4_step(uq, 1e-2, 0.01, p, ops)
+    for i in range(2):
+        assert rel(Q.to_dense(imp[i]), ref[i]) < 1e-10
+        assert rel(Q.to_dense(imp[i]), Q.to_dense(exp_[i])) < 1e-10
