@@ -1,7 +1,7 @@
 """Benchmark: QTT RK4 steps per second on a 2^10 x 2^10 shear jet at chi = 64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|mixed|fp64]
-                    [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight]
+                    [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight] [--rhs explicit|implicit]
                     [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
                     [--clocks-file PATH]
 
@@ -346,12 +346,13 @@ def make_form(P, w, prec, graphs, B, local, rank):
     B = max(1, B)
     if B > 1:
         batch = P.Batch([dict(n=w["n"], precision=prec, graphs=graphs,
-                              **solver_kwargs(w)) for _ in range(B)], device=local)
+                              rhs_form=w.get("rhs_form", 0), **solver_kwargs(w))
+                         for _ in range(B)], device=local)
         ctxs = batch.contexts
     else:
         batch = None
         ctxs = [P.Context(w["n"], precision=prec, device=local, graphs=graphs,
-                          **solver_kwargs(w))]
+                          rhs_form=w.get("rhs_form", 0), **solver_kwargs(w))]
     states, dts = [], []
     for i, c in enumerate(ctxs):
         u, dx, dt_i = workload_state(w["n"], w["seed"] + rank * B + i)
@@ -535,6 +536,9 @@ def main():
     ap.add_argument("--clocks-file", default=None,
                     help="where the nvidia-smi clock samples of the timed region go (CSV; "
                          "default: a file in the temporary directory)")
+    ap.add_argument("--rhs", default="explicit", choices=["explicit", "implicit"],
+                    help="the stages' right-hand side: formed as an MPS (explicit) or the "
+                         "paper's form inside the projection (implicit)")
     ap.add_argument("--stage-graphs", action="store_true",
                     help="replay only each stage's right-hand side as a CUDA graph (the "
                          "projection launched from the host)")
@@ -565,6 +569,9 @@ def main():
         w.update(cg_tol=1e-12, sweep_tol=1e-12, cg_maxit=500)
         w["workload"] += "_tight"
     graphs = 0 if args.eager else (1 if args.stage_graphs else 2)
+    if args.rhs == "implicit":
+        w["rhs_form"] = 1
+        w["workload"] += "_implicit_rhs"
     B = max(1, args.batched)
     if B > 1:
         w["workload"] = f"{w['workload']}_x{B}_trajectories"

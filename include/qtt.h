@@ -62,6 +62,18 @@ typedef enum {
                           weights and projection residual                    */
 } qtt_precision;
 
+/* Form of each Euler minimisation's right-hand side (qtt_params.rhs_form). */
+typedef enum {
+  QTT_RHS_EXPLICIT = 0,  /* w = a u - h B(b) formed as a compressed MPS
+                            (Hadamard products, MPO applications, sums),
+                            then projected; initial guess w                  */
+  QTT_RHS_IMPLICIT = 1   /* the paper's form (Sec. II.C, App. B): B(b) never
+                            formed -- its Hadamard and MPO terms enter the
+                            projection's local right-hand sides through their
+                            own environments; initial guess a u (the
+                            previous time step), whose bonds are kept        */
+} qtt_rhs_form;
+
 /* Learned truncation modes (qtt_params.learned_trunc). */
 typedef enum {
   QTT_LEARNED_OFF = 0,
@@ -116,6 +128,7 @@ typedef struct {
                          higher-order stencils of Sec. II.B / App. D.  D_1,
                          D_2, the Laplacian and the projection blocks are
                          all built with it.  Fixed at creation. */
+  int rhs_form;       /* qtt_rhs_form (RK4, Euler and RK2 steps)          */
 } qtt_params;
 
 /* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,

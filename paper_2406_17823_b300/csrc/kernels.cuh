@@ -103,6 +103,11 @@ struct AddTerm {
 };
 void launch_add_assemble(const AddTerm* terms, int K, int first, int last, double* out,
                          int capl_out, int capr_out, cudaStream_t s);
+// Cores of P = H_B W (order 0) or W H_B (order 1), H_B the Hadamard MPO of
+// the MPS core B (cbl x 4 x cbr), W an MPO core (wl x 4 x 4 x wr), in the raw,
+// k2 and kr2 layouts (each cbl wl x 16 x cbr wr doubles).
+void launch_hadamard_mpo(const double* B, int cbl, int cbr, const double* W, int wl, int wr,
+                         int order, double* raw, double* k2, double* kr2, cudaStream_t s);
 // out[b][s][a] = in[a][s][b]   (capacities)
 void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaStream_t s);
 void launch_set_int(int* p, int v, cudaStream_t s);

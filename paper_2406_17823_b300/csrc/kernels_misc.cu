@@ -342,6 +342,47 @@ void launch_add_assemble(const AddTerm* terms, int K, int first, int last, doubl
   launch_add_assemble_args(terms, K, first, last, out, capl_out, capr_out, s);
 }
 
+// Core of the MPO product of a Hadamard MPO and an MPO (the paper's
+// "nonlinear MPOs"): H_B[c][s][t][c'] = B[c][s][c'] delta(s, t), so
+//   order 0: P = H_B W,  P[(c p)][s][t][(c' q)] = B[c][s][c'] W[p][s][t][q]
+//   order 1: P = W H_B,  P[(c p)][s][t][(c' q)] = B[c][t][c'] W[p][s][t][q]
+// written in the three layouts of an MPO: raw [P][s][t][Q], k2 [(s Q)][(P t)]
+// and kr2 [(s P)][(Q t)] with P = c wl + p, Q = c' wr + q (capacities).
+__global__ void k_hadamard_mpo(const double* __restrict__ B, int cbl, int cbr,
+                               const double* __restrict__ W, int wl, int wr, int order,
+                               double* __restrict__ raw, double* __restrict__ k2,
+                               double* __restrict__ kr2) {
+  const int PL = cbl * wl, PR = cbr * wr;
+  const long long tot = (long long)PL * 16 * PR;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long t = e;
+    const int Q = (int)(t % PR); t /= PR;
+    const int si = (int)(t % 4); t /= 4;
+    const int so = (int)(t % 4); t /= 4;
+    const int P = (int)t;
+    const int c = P / wl, p = P % wl, c1 = Q / wr, q = Q % wr;
+    const int x = order == 0 ? so : si;
+    const double v = B[((long long)c * 4 + x) * cbr + c1] * W[((p * 4 + so) * 4 + si) * wr + q];
+    raw[e] = v;
+    k2[(long long)(so * PR + Q) * (PL * 4) + (P * 4 + si)] = v;
+    kr2[(long long)(so * PL + P) * (PR * 4) + (Q * 4 + si)] = v;
+  }
+}
+
+void launch_hadamard_mpo(const double* B, int cbl, int cbr, const double* W, int wl, int wr,
+                         int order, double* raw, double* k2, double* kr2, cudaStream_t s) {
+  const long long tot = (long long)cbl * wl * 16 * cbr * wr;
+  check_range(B, (long long)cbl * 4 * cbr, sizeof(double), "hadamard mpo B");
+  check_range(W, (long long)wl * 16 * wr, sizeof(double), "hadamard mpo W");
+  check_range(raw, tot, sizeof(double), "hadamard mpo raw");
+  check_range(k2, tot, sizeof(double), "hadamard mpo k2");
+  check_range(kr2, tot, sizeof(double), "hadamard mpo kr2");
+  pre_launch(s);
+  k_hadamard_mpo<<<grid_for(tot), 256, 0, s>>>(B, cbl, cbr, W, wl, wr, order, raw, k2, kr2);
+  post_launch("k_hadamard_mpo", s);
+}
+
 void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaStream_t s) {
   check_range(in, (long long)Ca * 4 * Cb, sizeof(double), "transpose in");
   check_range(out, (long long)Ca * 4 * Cb, sizeof(double), "transpose out");

@@ -883,7 +883,6 @@ int tc_search_mode() {
   }();
   return m;
 }
-bool tc_search_enabled() { return tc_search_mode() != 0; }
 bool tc_search_zipup() { return tc_search_mode() & 1; }
 bool tc_search_compress() { return tc_search_mode() & 2; }
 // Largest accepted contraction rho = (sigma_p / sigma_keep)^2 of a
@@ -1600,6 +1599,19 @@ struct Projector {
   DBuf<int> ist;
   size_t maxcore = 0;
   size_t maxout = 1;  // largest product output of the projection (split-K scratch sizing)
+  // Extra right-hand-side terms (the paper's implicit form, App. B): the
+  // right-hand side of component i is wcoef <basis|W_i> + sum over its terms
+  // of coef <basis| P X>, P an MPO applied to the MPS X, each term with its
+  // own environments of V_i against (P, X).
+  struct XTerm {
+    double coef;
+    qtt_mpo P;
+    qtt_mps X;
+    std::vector<DBuf<double>> L, R;
+  };
+  std::vector<XTerm> xt[2];
+  double wcoef = 1.0;
+  DBuf<double> xtT[2];  // transposed core of a term's X (right environments)
 
   const std::vector<int>& cap(int i) const { return V[i]->cap; }
 
@@ -1645,8 +1657,28 @@ struct Projector {
         qrw = std::max(qrw, qr_work_doubles(4 * cap(i)[k], cap(i)[k + 1]));
         qrw = std::max(qrw, qr_work_doubles(4 * cap(i)[k + 1], cap(i)[k]));
       }
+    for (int i = 0; i < 2; i++)
+      for (XTerm& T : xt[i]) {
+        T.L.resize(n + 1);
+        T.R.resize(n + 1);
+        for (int b = 0; b <= n; b++) {
+          const size_t sz = (size_t)cap(i)[b] * T.P->w[b] * T.X->cap[b];
+          T.L[b] = DBuf<double>(sz, s);
+          T.R[b] = DBuf<double>(sz, s);
+        }
+        for (int k = 0; k < n; k++) {
+          const size_t ci = cap(i)[k], ci1 = cap(i)[k + 1], cx = T.X->cap[k], cx1 = T.X->cap[k + 1];
+          const size_t wl = T.P->w[k], wr = T.P->w[k + 1];
+          t1m = std::max({t1m, ci * wl * 4 * cx1, ci1 * wr * 4 * cx});
+          t2m = std::max({t2m, ci * 4 * wr * cx1, ci1 * 4 * wl * cx});
+          cm = std::max(cm, T.X->core_size(k));
+        }
+      }
     maxcore = cm;
     maxout = std::max({t1m, t2m, cm});
+    for (int i = 0; i < 2; i++)
+      for (XTerm& T : xt[i])
+        for (int b = 0; b <= n; b++) maxout = std::max(maxout, T.L[b].n);
     for (int i = 0; i < 2; i++)
       for (int j = 0; j < 2; j++)
         for (int b = 0; b <= n; b++) maxout = std::max(maxout, LE[i][j][b].n);
@@ -1691,7 +1723,51 @@ struct Projector {
     for (int i = 0; i < 2; i++) {
       launch_fill(LW[i][0].p, 1, 1.0, s);
       launch_fill(RW[i][n].p, 1, 1.0, s);
+      for (XTerm& T : xt[i]) {
+        launch_fill(T.L[0].p, 1, 1.0, s);
+        launch_fill(T.R[n].p, 1, 1.0, s);
+      }
+      if (!xt[i].empty()) xtT[i] = DBuf<double>(cm, s);
     }
+  }
+
+  // A term's right environment at bond k from bond k + 1 (MPO sandwich, as
+  // the coupling blocks with V_j replaced by X); ViT the transposed V_i core.
+  void xterm_right(int i, XTerm& T, int k, const double* ViT, double* t1p, double* t2p) {
+    const int wl = T.P->w[k], wr = T.P->w[k + 1];
+    const int ci = cap(i)[k], ci1 = cap(i)[k + 1], cx = T.X->cap[k], cx1 = T.X->cap[k + 1];
+    launch_core_transpose(T.X->core(k), cx, cx1, xtT[i].p, s);
+    gemm(gemm_plain(T.R[k + 1].p, xtT[i].p, t1p, ci1 * wr, 4 * cx, cx1, cx1, 4 * cx, 4 * cx), s);
+    GemmF64 g{};
+    g.A = T.P->kr2(k); g.B = t1p; g.C = t2p;
+    g.M = 4 * wl; g.N = cx; g.K = wr * 4;
+    g.lda = wr * 4; g.ldb = cx; g.ldc = cx;
+    g.nb1 = ci1; g.nb2 = 1;
+    g.sA1 = 0; g.sB1 = (long long)wr * 4 * cx; g.sC1 = (long long)4 * wl * cx;
+    g.alpha = 1.0;
+    gemm(g, s);
+    GemmF64 g3 = gemm_plain(ViT, t2p, T.R[k].p, ci, wl * cx, ci1 * 4, ci, wl * cx, wl * cx);
+    g3.tA = 1;
+    gemm(g3, s);
+  }
+
+  // A term's left environment at bond k + 1 from bond k.
+  void xterm_left(int i, XTerm& T, int k, double* t1p, double* t2p) {
+    const int wl = T.P->w[k], wr = T.P->w[k + 1];
+    const int ci = cap(i)[k], ci1 = cap(i)[k + 1], cx = T.X->cap[k], cx1 = T.X->cap[k + 1];
+    gemm(gemm_plain(T.L[k].p, T.X->core(k), t1p, ci * wl, 4 * cx1, cx, cx, 4 * cx1, 4 * cx1), s);
+    GemmF64 g{};
+    g.A = T.P->k2(k); g.B = t1p; g.C = t2p;
+    g.M = 4 * wr; g.N = cx1; g.K = 4 * wl;
+    g.lda = 4 * wl; g.ldb = cx1; g.ldc = cx1;
+    g.nb1 = ci; g.nb2 = 1;
+    g.sA1 = 0; g.sB1 = (long long)wl * 4 * cx1; g.sC1 = (long long)4 * wr * cx1;
+    g.alpha = 1.0;
+    gemm(g, s);
+    GemmF64 g3 = gemm_plain(V[i]->core(k), t2p, T.L[k + 1].p, ci1, wr * cx1, 4 * ci, ci1,
+                            wr * cx1, wr * cx1);
+    g3.tA = 1;
+    gemm(g3, s);
   }
 
   // RE[b] from RE[b+1] and site b (sites b..n-1), all blocks + overlaps.
@@ -1735,6 +1811,7 @@ struct Projector {
       GemmF64 g = gemm_plain(ViT, t1p, RW[i][k].p, ci, cw, ci1 * 4, ci, cw, cw);
       g.tA = 1;
       gemm(g, s);
+      for (XTerm& T : xt[i]) xterm_right(i, T, k, ViT, t1p, t2p);
     });
   }
 
@@ -1772,6 +1849,7 @@ struct Projector {
       GemmF64 g = gemm_plain(V[i]->core(k), t1p, LW[i][k + 1].p, ci1, cw1, 4 * ci, ci1, cw1, cw1);
       g.tA = 1;
       gemm(g, s);
+      for (XTerm& T : xt[i]) xterm_left(i, T, k, t1p, t2p);
     });
   }
 
@@ -1867,12 +1945,34 @@ struct Projector {
   void local_rhs(int d) {
     by_component([&](int i) {
       double* const t1p = i == 0 ? t1.p : t1b.p;
+      double* const t2p = i == 0 ? t2.p : t2b.p;
       const int ci = cap(i)[d], ci1 = cap(i)[d + 1];
       const int cw = W[i]->cap[d], cw1 = W[i]->cap[d + 1];
       gemm(gemm_plain(LW[i][d].p, W[i]->core(d), t1p, ci, 4 * cw1, cw, cw, 4 * cw1, 4 * cw1), s);
       GemmF64 g = gemm_plain(t1p, RW[i][d + 1].p, rhs[i].p, 4 * ci, ci1, cw1, cw1, cw1, ci1);
       g.tB = 1;
+      g.alpha = wcoef;
       gemm(g, s);
+      // the implicit terms: rhs += coef L P X R (the coupling blocks' pattern)
+      for (XTerm& T : xt[i]) {
+        const int wl = T.P->w[d], wr = T.P->w[d + 1];
+        const int cx = T.X->cap[d], cx1 = T.X->cap[d + 1];
+        gemm(gemm_plain(T.L[d].p, T.X->core(d), t1p, ci * wl, 4 * cx1, cx, cx, 4 * cx1, 4 * cx1), s);
+        GemmF64 g2{};
+        g2.A = T.P->k2(d); g2.B = t1p; g2.C = t2p;
+        g2.M = 4 * wr; g2.N = cx1; g2.K = 4 * wl;
+        g2.lda = 4 * wl; g2.ldb = cx1; g2.ldc = cx1;
+        g2.nb1 = ci; g2.nb2 = 1;
+        g2.sA1 = 0; g2.sB1 = (long long)wl * 4 * cx1; g2.sC1 = (long long)4 * wr * cx1;
+        g2.alpha = 1.0;
+        gemm(g2, s);
+        GemmF64 g3 = gemm_plain(t2p, T.R[d + 1].p, rhs[i].p, 4 * ci, ci1, wr * cx1, wr * cx1,
+                                wr * cx1, ci1);
+        g3.tB = 1;
+        g3.alpha = T.coef;
+        g3.beta = 1.0;
+        gemm(g3, s);
+      }
     });
   }
 
@@ -2050,21 +2150,12 @@ qtt_mps copy_mps(qtt_ctx ctx, qtt_mps A) {
   return X.release();
 }
 
-void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qtt_mps* v2,
-                  int* cg_out, int* sw_out) {
-  const int n = w1->n;
-  Projector P;
-  P.ctx = ctx;
-  P.s = ctx->stream;
-  P.n = n;
-  P.c = ctx->p.mu * h * h;
-  MpsPtr V0(copy_mps(ctx, w1)), V1(copy_mps(ctx, w2));
-  P.V[0] = V0.get();
-  P.V[1] = V1.get();
-  P.W[0] = w1;
-  P.W[1] = w2;
-  for (int i = 0; i < 2; i++)
-    for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
+// The sweeps of a projector whose V, W, K and terms are set (Sec. II.C,
+// App. B): environments allocated here, centre brought to site 1, then
+// single-site sweeps until the norm test or the cap; the results are V0, V1.
+void run_projection(qtt_ctx ctx, Projector& P, MpsPtr& V0, MpsPtr& V1, qtt_mps* v1,
+                    qtt_mps* v2, int* cg_out, int* sw_out) {
+  const int n = P.n;
   P.alloc();
   DBuf<double> arena(ctx->dev_loops ? 4 * 16 * P.maxout : 0, P.s);  // a quarter per matvec chain
   struct ScratchScope {  // split-K scratch of a captured step's loop bodies
@@ -2149,6 +2240,88 @@ void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qt
   if (sw_out) *sw_out = sweeps;
   *v1 = V0.release();
   *v2 = V1.release();
+}
+
+void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qtt_mps* v2,
+                  int* cg_out, int* sw_out) {
+  Projector P;
+  P.ctx = ctx;
+  P.s = ctx->stream;
+  P.n = w1->n;
+  P.c = ctx->p.mu * h * h;
+  MpsPtr V0(copy_mps(ctx, w1)), V1(copy_mps(ctx, w2));
+  P.V[0] = V0.get();
+  P.V[1] = V1.get();
+  P.W[0] = w1;
+  P.W[1] = w2;
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
+  run_projection(ctx, P, V0, V1, v1, v2, cg_out, sw_out);
+}
+
+// The product MPO of the Hadamard MPO of b with W (order 0: H_b W, so that
+// P X = b (.) (W X); order 1: W H_b, P X = W (b (.) X)), built on the device
+// at the capacities of b and W (bond cap_b w); the memory is `buf`.
+std::unique_ptr<qtt_mpo_s> hadamard_mpo_device(qtt_ctx ctx, qtt_mps b, qtt_mpo W, int order,
+                                               DBuf<double>& buf) {
+  const int n = b->n;
+  cudaStream_t s = stream_of(ctx);
+  std::unique_ptr<qtt_mpo_s> m(new qtt_mpo_s);
+  m->n = n;
+  m->w.resize(n + 1);
+  for (int k = 0; k <= n; k++) m->w[k] = b->cap[k] * W->w[k];
+  m->off.resize(n + 1);
+  size_t o = 0;
+  for (int k = 0; k < n; k++) {
+    m->off[k] = o;
+    o += (size_t)m->w[k] * 16 * m->w[k + 1];
+  }
+  m->off[n] = o;
+  buf = DBuf<double>(3 * o, s);
+  m->dev = buf.p;
+  m->dev_k2 = buf.p + o;
+  m->dev_kr2 = buf.p + 2 * o;
+  for (int k = 0; k < n; k++)
+    launch_hadamard_mpo(b->core(k), b->cap[k], b->cap[k + 1], W->raw(k), W->w[k], W->w[k + 1],
+                        order, m->raw(k), m->k2(k), m->kr2(k), s);
+  return m;
+}
+
+// The projection with the paper's implicit right-hand side (Sec. II.C,
+// App. B, Eq. for B_i inside the cost Theta): a u_i - h B_i(b) is never
+// formed; component i's local right-hand side sums a <u_i>, -h/2 <(H_{b_j}
+// D_j) b_i>, -h/2 <(D_j H_{b_j}) b_i> (j = 1, 2) and h nu <Lap b_i>, each
+// through its own environments.  Initial guess a u (the paper: the previous
+// time step), so the result keeps the bonds of u.
+void project_implicit_impl(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu,
+                           double a_scale, qtt_mps* v1, qtt_mps* v2, int* cg_out, int* sw_out) {
+  DBuf<double> mbuf[4];
+  std::unique_ptr<qtt_mpo_s> HD[2], DH[2];
+  for (int j = 0; j < 2; j++) {
+    HD[j] = hadamard_mpo_device(ctx, b[j], ctx->D[j], 0, mbuf[2 * j]);
+    DH[j] = hadamard_mpo_device(ctx, b[j], ctx->D[j], 1, mbuf[2 * j + 1]);
+  }
+  Projector P;
+  P.ctx = ctx;
+  P.s = ctx->stream;
+  P.n = u[0]->n;
+  P.c = ctx->p.mu * h * h;
+  MpsPtr V0(add_exact(ctx, 1, &a_scale, &u[0])), V1(add_exact(ctx, 1, &a_scale, &u[1]));
+  P.V[0] = V0.get();
+  P.V[1] = V1.get();
+  P.W[0] = u[0];
+  P.W[1] = u[1];
+  P.wcoef = a_scale;
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
+  for (int i = 0; i < 2; i++) {
+    for (int j = 0; j < 2; j++) {
+      P.xt[i].push_back(Projector::XTerm{-0.5 * h, HD[j].get(), b[i], {}, {}});
+      P.xt[i].push_back(Projector::XTerm{-0.5 * h, DH[j].get(), b[i], {}, {}});
+    }
+    P.xt[i].push_back(Projector::XTerm{h * nu, ctx->lap, b[i], {}, {}});
+  }
+  run_projection(ctx, P, V0, V1, v1, v2, cg_out, sw_out);
 }
 
 // ===================================================================== RK4
@@ -2498,11 +2671,15 @@ void rk4_core(qtt_ctx ctx, qtt_mps u[2], double dt, double nu, MpsPtr out[2], in
       wk.join({b[0], b[1]});
     }
     const double h = HS[st] * dt;
-    MpsPtr w[2];
-    stage_w_run(ctx, u, b, h, nu, w, 0.25);
     qtt_mps v1, v2;
     int cg = 0, sw = 0;
-    project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+    if (ctx->p.rhs_form == QTT_RHS_IMPLICIT) {
+      project_implicit_impl(ctx, u, b, h, nu, 0.25, &v1, &v2, &cg, &sw);
+    } else {
+      MpsPtr w[2];
+      stage_w_run(ctx, u, b, h, nu, w, 0.25);
+      project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+    }
     *nc |= ctx->last_not_converged;
     U[st][0] = MpsPtr(v1);
     U[st][1] = MpsPtr(v2);
@@ -2640,11 +2817,15 @@ void rk4_impl(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double nu) {
 
 // One penalised minimisation with a = u (scale 1) and the given b, h.
 void euler_min(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr v[2]) {
-  MpsPtr w[2];
-  stage_w_run(ctx, u, b, h, nu, w, 1.0);
   qtt_mps v1, v2;
   int cg = 0, sw = 0;
-  project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+  if (ctx->p.rhs_form == QTT_RHS_IMPLICIT) {
+    project_implicit_impl(ctx, u, b, h, nu, 1.0, &v1, &v2, &cg, &sw);
+  } else {
+    MpsPtr w[2];
+    stage_w_run(ctx, u, b, h, nu, w, 1.0);
+    project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+  }
   v[0] = MpsPtr(v1);
   v[1] = MpsPtr(v2);
 }
@@ -2842,7 +3023,8 @@ bool valid_params(const qtt_params* p) {
          p->rf_oversample >= 0 && p->rf_oversample <= 256 && p->rf_min_width >= 1 &&
          p->graphs >= 0 && p->graphs <= 2 &&
          (p->fd_order == 0 || p->fd_order == 2 || p->fd_order == 4 || p->fd_order == 6 ||
-          p->fd_order == 8);
+          p->fd_order == 8) &&
+         (p->rhs_form == QTT_RHS_EXPLICIT || p->rhs_form == QTT_RHS_IMPLICIT);
 }
 
 void check_mps(qtt_ctx ctx, qtt_mps m) {

@@ -16,6 +16,8 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqtt_b30
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+RHS_EXPLICIT = 0
+RHS_IMPLICIT = 1
 LEARNED_OFF = 0
 LEARNED_LOG = 1
 LEARNED_ON = 2
@@ -53,7 +55,7 @@ class Params(ctypes.Structure):
                 ("mu", c_double), ("cg_tol", c_double), ("cg_maxit", c_int),
                 ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int),
                 ("learned_trunc", c_int), ("rf_oversample", c_int), ("rf_min_width", c_int),
-                ("graphs", c_int), ("fd_order", c_int)]
+                ("graphs", c_int), ("fd_order", c_int), ("rhs_form", c_int)]
 
 
 _lib = None
@@ -169,7 +171,7 @@ class Context:
                  sweep_tol: float = 1e-5, max_sweeps: int = 20, precision: int = PREC_FP64,
                  learned_trunc: int = LEARNED_OFF, rf_oversample: int = 8,
                  rf_min_width: int = 128, graphs: int = 0, fd_order: int = 0,
-                 device: int = 0, stream=None):
+                 rhs_form: int = 0, device: int = 0, stream=None):
         torch = _torch()
         self.device = device
         if stream is None:
@@ -177,7 +179,7 @@ class Context:
         self.stream = stream
         self.params = Params(n, L, eps, chi_max, mu, cg_tol, cg_maxit, sweep_tol, max_sweeps,
                              precision, learned_trunc, rf_oversample, rf_min_width, graphs,
-                             fd_order)
+                             fd_order, rhs_form)
         h = c_void_p()
         st = lib().qtt_create(byref(h), device, c_void_p(stream.cuda_stream), byref(self.params))
         if st != 0:
@@ -504,7 +506,7 @@ class Batch:
                             kw.pop("max_sweeps", 20), kw.pop("precision", PREC_FP64),
                             kw.pop("learned_trunc", LEARNED_OFF), kw.pop("rf_oversample", 8),
                             kw.pop("rf_min_width", 128), kw.pop("graphs", 0),
-                            kw.pop("fd_order", 0))
+                            kw.pop("fd_order", 0), kw.pop("rhs_form", 0))
             if kw:
                 raise TypeError(f"unknown parameters {sorted(kw)}")
         h = c_void_p()
