@@ -75,3 +75,27 @@ def test_implicit_step_graph_replays_bit_for_bit(P):
             assert ctx.graph_stats()[1] >= 2
         out.append([ctx.to_dense(a).cpu().numpy(), ctx.to_dense(b).cpu().numpy()])
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_forms_at_equal_error_full_size(P):
+    """The bench workload (2^10 jet, chi 64, eps 1e-8, paper settings): one
+    RK4 step in each form against the untruncated dense projected RK4 step
+    from the same (truncated) initial state.  Both forms carry the same
+    truncation error (printed); the implicit one may not exceed the explicit
+    one's by more than half."""
+    n = 10
+    (u, v), dx = I.shear_jet(n, seed=0)
+    dt, nu = 0.1 * dx / float(np.abs(u).max()), 1 / 2e5
+    errs = {}
+    for form in (P.RHS_EXPLICIT, P.RHS_IMPLICIT):
+        ctx = P.Context(n, eps=1e-8, chi_max=64, rhs_form=form)
+        g = [ctx.from_dense(f) for f in (u, v)]
+        u0 = [ctx.to_dense(x).cpu().numpy() for x in g]
+        ref = Dn.rk4_step(u0, dt, nu, 2.5e5, dx)
+        ctx.rk4_step(g[0], g[1], dt, nu)
+        got = [ctx.to_dense(x).cpu().numpy() for x in g]
+        num = sum(float(np.sum((a - b) ** 2)) for a, b in zip(got, ref))
+        den = sum(float(np.sum(b ** 2)) for b in ref)
+        errs[form] = math.sqrt(num / den)
+    print(f"one RK4 step vs the dense step: explicit {errs[0]:.3e}, implicit {errs[1]:.3e}")
+    assert errs[1] <= 1.5 * errs[0] + 1e-14
