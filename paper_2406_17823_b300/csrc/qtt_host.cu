@@ -427,6 +427,68 @@ std::map<GemmKey, GemmChoice>& tune_map() {
   return m;
 }
 
+// Optional persistence (QTT_TUNE_CACHE = a file path): the choices are read
+// from that JSON file on first use and the file is rewritten whenever a new
+// shape is tuned, so later processes reuse the same choices (and the same
+// summation orders).  Format: {"version": 1, "entries": [[M, N, K, tA, tB,
+// batch, tile, split], ...]}.  Callers hold g_tune_mu.
+const char* tune_cache_path() {
+  static const char* p = getenv("QTT_TUNE_CACHE");
+  return (p && p[0]) ? p : nullptr;
+}
+void tune_cache_load() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  const char* path = tune_cache_path();
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  std::string txt;
+  char buf[4096];
+  size_t got;
+  while ((got = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, got);
+  fclose(f);
+  const size_t at = txt.find("\"entries\"");
+  if (at == std::string::npos) return;
+  std::vector<long long> v;
+  const char* c = txt.c_str() + at;
+  while (*c) {
+    if ((*c >= '0' && *c <= '9') || *c == '-') {
+      char* end = nullptr;
+      v.push_back(strtoll(c, &end, 10));
+      c = end;
+    } else {
+      c++;
+    }
+  }
+  for (size_t i = 0; i + 8 <= v.size(); i += 8) {
+    const GemmKey k{(int)v[i], (int)v[i + 1], (int)v[i + 2], (int)v[i + 3], (int)v[i + 4],
+                    (int)v[i + 5]};
+    const int tile = (int)v[i + 6], S = (int)v[i + 7];
+    if (tile < 0 || tile > 1 || S < 1 || S > 16 || (S & (S - 1))) continue;  // not ours
+    tune_map().emplace(k, GemmChoice{tile, S});
+  }
+}
+void tune_cache_save() {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "{\"version\": 1, \"entries\": [");
+  bool first = true;
+  for (const auto& kv : tune_map()) {
+    const GemmKey& k = kv.first;
+    fprintf(f, "%s\n  [%d, %d, %d, %d, %d, %d, %d, %d]", first ? "" : ",", k.M, k.N, k.K, k.tA,
+            k.tB, k.nb, kv.second.tile, kv.second.S);
+    first = false;
+  }
+  fprintf(f, "\n]}\n");
+  fclose(f);
+  rename(tmp.c_str(), path);
+}
+
 GemmChoice gemm_tune(const GemmF64& g, cudaStream_t s) {
   const int nb = g.nb1 * g.nb2;
   // scratch output, compact layout (the candidates' results are discarded)
@@ -482,6 +544,7 @@ void gemm(const GemmF64& g, cudaStream_t s) {
   bool found = false;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
     auto it = tune_map().find(key);
     if (it != tune_map().end()) {
       ch = it->second;
@@ -497,6 +560,7 @@ void gemm(const GemmF64& g, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto ins = tune_map().emplace(key, ch);  // another thread may have tuned it first
     ch = ins.first->second;
+    if (ins.second) tune_cache_save();
   }
   gemm_run(g, ch.tile, ch.S, s);
 }
