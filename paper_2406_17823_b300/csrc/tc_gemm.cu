@@ -398,10 +398,11 @@ struct OrthArgs {
 constexpr int kOrthThreads = 512;
 
 __global__ void __launch_bounds__(kOrthThreads, 1) k_tc_orth(OrthArgs a) {
-  extern __shared__ float sq[];  // [p][s]
+  extern __shared__ float sq[];  // [p][s], columns kept unnormalised until the end
   __shared__ float h[128];
+  __shared__ float inv[128];    // 1 / |column|^2 (0: a dropped column)
   __shared__ float cnorm[128];  // column norms after the projections
-  __shared__ float red[kOrthThreads / 32];
+  __shared__ float red[kOrthThreads / 32], red0[kOrthThreads / 32];
   if (a.stop && *a.stop) return;  // uniform over the block
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = kOrthThreads / 32;
   const int s = a.s, p = a.p;
@@ -411,59 +412,78 @@ __global__ void __launch_bounds__(kOrthThreads, 1) k_tc_orth(OrthArgs a) {
     const int r = e / p, j = e % p;
     sq[j * s + r] = a.Y[(long long)r * a.ldy + j];
   }
+  // the update phase: two threads per row, each over half of the earlier
+  // columns (partners are adjacent lanes)
+  const int row = tid >> 1, half = tid & 1;
   __syncthreads();
   for (int j = 0; j < p; j++) {
     float* y = sq + (size_t)j * s;
     if (j >= rank) {
       for (int r = tid; r < s; r += kOrthThreads) y[r] = 0.0f;
-      if (tid == 0) cnorm[j] = 0.0f;
+      inv[j] = 0.0f;  // every thread writes the same value before it reads it
+      cnorm[j] = 0.0f;
       continue;  // uniform over the block
     }
-    float nrm0 = 0.0f;
     for (int pass = 0; pass < 2; pass++) {
+      // h_i = (q_i . y) / |q_i|^2 for the earlier columns i < j
       for (int i = warp; i < j; i += nw) {
         const float* q = sq + (size_t)i * s;
-        float d = 0.0f;
-        for (int r = lane; r < s; r += 32) d = fmaf(q[r], y[r], d);
+        float d0 = 0.0f, d1 = 0.0f;
+        int r = lane;
+        for (; r + 32 < s; r += 64) {
+          d0 = fmaf(q[r], y[r], d0);
+          d1 = fmaf(q[r + 32], y[r + 32], d1);
+        }
+        if (r < s) d0 = fmaf(q[r], y[r], d0);
+        float d = d0 + d1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        if (lane == 0) h[i] = d;
-      }
-      if (pass == 0) {
-        float t = 0.0f;
-        for (int r = tid; r < s; r += kOrthThreads) t = fmaf(y[r], y[r], t);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) red[warp] = t;
+        if (lane == 0) h[i] = d * inv[i];
       }
       __syncthreads();
-      if (pass == 0) {
-        float t = 0.0f;
-        for (int i = 0; i < nw; i++) t += red[i];
-        nrm0 = t;
+      // y -= sum_i q_i h_i (and the squared norms before / after)
+      float t = 0.0f, c = 0.0f;
+      if (row < s) {
+        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, c3 = 0.0f;
+        int i = half;
+        for (; i + 6 < j; i += 8) {
+          c0 = fmaf(sq[(size_t)i * s + row], h[i], c0);
+          c1 = fmaf(sq[(size_t)(i + 2) * s + row], h[i + 2], c1);
+          c2 = fmaf(sq[(size_t)(i + 4) * s + row], h[i + 4], c2);
+          c3 = fmaf(sq[(size_t)(i + 6) * s + row], h[i + 6], c3);
+        }
+        for (; i < j; i += 2) c0 = fmaf(sq[(size_t)i * s + row], h[i], c0);
+        c = (c0 + c1) + (c2 + c3);
       }
-      for (int r = tid; r < s; r += kOrthThreads) {
-        float acc = y[r];
-        for (int i = 0; i < j; i++) acc = fmaf(-sq[(size_t)i * s + r], h[i], acc);
-        y[r] = acc;
+      c += __shfl_xor_sync(0xffffffffu, c, 1);  // the two halves of the row
+      if (row < s && half == 0) {  // the row's owner
+        const float old = y[row];
+        const float nv = old - c;
+        t = pass == 0 ? old * old : nv * nv;
+        y[row] = nv;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) (pass == 0 ? red0 : red)[warp] = t;
       __syncthreads();
     }
-    float t = 0.0f;
-    for (int r = tid; r < s; r += kOrthThreads) t = fmaf(y[r], y[r], t);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[warp] = t;
-    __syncthreads();
-    float nrm2 = 0.0f;
-    for (int i = 0; i < nw; i++) nrm2 += red[i];
-    // nothing left beyond rounding of an (almost) dependent column: keep a
-    // zero column rather than normalising noise of a vanishing vector
-    const float scale = (nrm2 > 1e-36f && nrm2 > 1e-24f * nrm0) ? rsqrtf(nrm2) : 0.0f;
-    if (tid == 0) cnorm[j] = scale > 0.0f ? sqrtf(nrm2) : 0.0f;
-    for (int r = tid; r < s; r += kOrthThreads) y[r] *= scale;
-    __syncthreads();
+    float nrm2 = 0.0f, nrm0 = 0.0f;
+    for (int i = 0; i < nw; i++) {
+      nrm2 += red[i];
+      nrm0 += red0[i];
+    }
+    // nothing left beyond rounding of an (almost) dependent column: drop it
+    // rather than keep noise of a vanishing vector
+    const bool keep = nrm2 > 1e-36f && nrm2 > 1e-24f * nrm0;
+    inv[j] = keep ? 1.0f / nrm2 : 0.0f;  // every thread writes the same value
+    cnorm[j] = keep ? sqrtf(nrm2) : 0.0f;
   }
+  __syncthreads();
+  for (int e = tid; e < s * p; e += kOrthThreads) {
+    const int j = e / s;
+    sq[e] *= sqrtf(inv[j]);
+  }
+  __syncthreads();
   if ((a.accept || a.early) && tid == 0) {
     // cnorm[j] ~ sigma_j^2 (orthogonal iteration orders the columns)
     const int full = min(dval(a.sact), dval(a.lact) * (a.lact2.p ? dval(a.lact2) : 1));
