@@ -1667,15 +1667,26 @@ struct Projector {
   // right-hand side of component i is wcoef <basis|W_i> + sum over its terms
   // of coef <basis| P X>, P an MPO applied to the MPS X, each term with its
   // own environments of V_i against (P, X).
+  //
+  // kind 0: P a general MPO.  The two nonlinear kinds keep the Hadamard's
+  // delta instead of forming the product MPO (P = H_B D or D H_B, bond
+  // cap_B w): kind 1 is B (.) (D X), environments [a][c][p][e]; kind 2 is
+  // D (B (.) X), environments [a][p][c][e] (a: V_i, c: B, p: D, e: X), each
+  // site update four GEMMs (about a quarter of the product MPO's work).
   struct XTerm {
     double coef;
     qtt_mpo P;
     qtt_mps X;
     std::vector<DBuf<double>> L, R;
+    int kind = 0;
+    qtt_mps B = nullptr;
+    qtt_mpo Dm = nullptr;
+    int wbond(int k) const { return kind ? B->cap[k] * Dm->w[k] : P->w[k]; }
   };
   std::vector<XTerm> xt[2];
   double wcoef = 1.0;
   DBuf<double> xtT[2];  // transposed core of a term's X (right environments)
+  DBuf<double> t3, t3b;  // third scratch of the nonlinear kinds (per component)
 
   const std::vector<int>& cap(int i) const { return V[i]->cap; }
 
@@ -1698,7 +1709,7 @@ struct Projector {
         RW[i][b] = DBuf<double>((size_t)cap(i)[b] * W[i]->cap[b], s);
       }
     }
-    size_t t1m = 1, t2m = 1, cm = 1, qrw = 1;
+    size_t t1m = 1, t2m = 1, t3m = 1, cm = 1, qrw = 1;
     int wmax = 1;
     for (int i = 0; i < 2; i++)
       for (int j = 0; j < 2; j++)
@@ -1726,15 +1737,26 @@ struct Projector {
         T.L.resize(n + 1);
         T.R.resize(n + 1);
         for (int b = 0; b <= n; b++) {
-          const size_t sz = (size_t)cap(i)[b] * T.P->w[b] * T.X->cap[b];
+          const size_t sz = (size_t)cap(i)[b] * T.wbond(b) * T.X->cap[b];
           T.L[b] = DBuf<double>(sz, s);
           T.R[b] = DBuf<double>(sz, s);
         }
         for (int k = 0; k < n; k++) {
           const size_t ci = cap(i)[k], ci1 = cap(i)[k + 1], cx = T.X->cap[k], cx1 = T.X->cap[k + 1];
-          const size_t wl = T.P->w[k], wr = T.P->w[k + 1];
+          const size_t wl = T.wbond(k), wr = T.wbond(k + 1);
+          // (wl, wr here count the product bond cap_B w; the nonlinear kinds'
+          // three intermediates have the same sizes as the product MPO's two,
+          // the third one's size taken into t3m)
           t1m = std::max({t1m, ci * wl * 4 * cx1, ci1 * wr * 4 * cx});
           t2m = std::max({t2m, ci * 4 * wr * cx1, ci1 * 4 * wl * cx});
+          if (T.kind) {
+            t3m = std::max({t3m, ci * 4 * wr * cx1, ci1 * 4 * wl * cx});
+            // the middle intermediates take B's and D's bonds separately
+            const size_t cb = T.B->cap[k], cb1 = T.B->cap[k + 1];
+            const size_t dl = T.Dm->w[k], dr = T.Dm->w[k + 1];
+            t2m = std::max({t2m, ci * cb * 4 * dr * cx1, ci * dl * 4 * cb1 * cx1,
+                            ci1 * cb1 * 4 * dl * cx, ci1 * dr * 4 * cb * cx});
+          }
           cm = std::max(cm, T.X->core_size(k));
         }
       }
@@ -1793,6 +1815,143 @@ struct Projector {
       }
       if (!xt[i].empty()) xtT[i] = DBuf<double>(cm, s);
     }
+    bool nl = false;
+    for (int i = 0; i < 2; i++)
+      for (XTerm& T : xt[i]) nl = nl || T.kind != 0;
+    if (nl) {
+      t3 = DBuf<double>(t3m, s);
+      t3b = DBuf<double>(t3m, s);
+      maxout = std::max(maxout, t3m);
+    }
+  }
+
+  // Steps 1-3 of a nonlinear term at site k from its left environment L:
+  //   kind 1 (B (.) (D X)): T3[(a so)][(c' p' e')]
+  //   kind 2 (D (B (.) X)): T3[(a so)][(p' c' e')]
+  // (the left environment of bond k + 1 is V^T T3; the local right-hand side
+  // is T3 R^T).
+  void nl_left3(int i, XTerm& T, int k, const double* L, double* t1p, double* t2p, double* t3p) {
+    const int ci = cap(i)[k];
+    const int cb = T.B->cap[k], cb1 = T.B->cap[k + 1], wl = T.Dm->w[k], wr = T.Dm->w[k + 1];
+    const int ce = T.X->cap[k], ce1 = T.X->cap[k + 1];
+    const double* Bc = T.B->core(k);
+    // T1[(a [c p | p c])][(t e')] = L[..][e] X[e][(t e')]
+    gemm(gemm_plain(L, T.X->core(k), t1p, ci * cb * wl, 4 * ce1, ce, ce, 4 * ce1, 4 * ce1), s);
+    if (T.kind == 1) {
+      // T2[(a c)][(so p')][e'] = D2[(so p')][(p t)] T1[(a c)][(p t)][e']
+      GemmF64 g{};
+      g.A = T.Dm->k2(k); g.B = t1p; g.C = t2p;
+      g.M = 4 * wr; g.N = ce1; g.K = 4 * wl;
+      g.lda = 4 * wl; g.ldb = ce1; g.ldc = ce1;
+      g.nb1 = ci * cb; g.nb2 = 1;
+      g.sB1 = (long long)wl * 4 * ce1; g.sC1 = (long long)4 * wr * ce1;
+      g.alpha = 1.0;
+      gemm(g, s);
+      // T3[(a so)][c'][(p' e')] = B_so[c][c']^T T2[(a c)][so][(p' e')], batch (a, so)
+      GemmF64 h{};
+      h.A = Bc; h.B = t2p; h.C = t3p;
+      h.M = cb1; h.N = wr * ce1; h.K = cb;
+      h.tA = 1; h.lda = 4 * cb1; h.ldb = 4 * wr * ce1; h.ldc = wr * ce1;
+      h.nb1 = ci; h.nb2 = 4;
+      h.sA1 = 0; h.sA2 = cb1;
+      h.sB1 = (long long)cb * 4 * wr * ce1; h.sB2 = (long long)wr * ce1;
+      h.sC1 = (long long)4 * cb1 * wr * ce1; h.sC2 = (long long)cb1 * wr * ce1;
+      h.alpha = 1.0;
+      gemm(h, s);
+    } else {
+      // T2[(a p)][t][c'][e'] = B_t[c][c']^T T1[(a p)][c][t][e'], batch (a p) for each t
+      for (int t = 0; t < 4; t++) {
+        GemmF64 h{};
+        h.A = Bc + t * cb1; h.B = t1p + (long long)t * ce1; h.C = t2p + (long long)t * cb1 * ce1;
+        h.M = cb1; h.N = ce1; h.K = cb;
+        h.tA = 1; h.lda = 4 * cb1; h.ldb = 4 * ce1; h.ldc = ce1;
+        h.nb1 = ci * wl; h.nb2 = 1;
+        h.sA1 = 0; h.sB1 = (long long)cb * 4 * ce1; h.sC1 = (long long)4 * cb1 * ce1;
+        h.alpha = 1.0;
+        gemm(h, s);
+      }
+      // T3[a][(so p')][(c' e')] = D2[(so p')][(p t)] T2[a][(p t)][(c' e')], batch a
+      GemmF64 g{};
+      g.A = T.Dm->k2(k); g.B = t2p; g.C = t3p;
+      g.M = 4 * wr; g.N = cb1 * ce1; g.K = 4 * wl;
+      g.lda = 4 * wl; g.ldb = cb1 * ce1; g.ldc = cb1 * ce1;
+      g.nb1 = ci; g.nb2 = 1;
+      g.sB1 = (long long)wl * 4 * cb1 * ce1; g.sC1 = (long long)4 * wr * cb1 * ce1;
+      g.alpha = 1.0;
+      gemm(g, s);
+    }
+  }
+
+  // Left environment of bond k + 1 of a nonlinear term.
+  void nl_left(int i, XTerm& T, int k, double* t1p, double* t2p, double* t3p) {
+    nl_left3(i, T, k, T.L[k].p, t1p, t2p, t3p);
+    const int ci = cap(i)[k], ci1 = cap(i)[k + 1];
+    const int n1 = T.B->cap[k + 1] * T.Dm->w[k + 1] * T.X->cap[k + 1];
+    GemmF64 g = gemm_plain(V[i]->core(k), t3p, T.L[k + 1].p, ci1, n1, 4 * ci, ci1, n1, n1);
+    g.tA = 1;
+    gemm(g, s);
+  }
+
+  // Right environment of bond k of a nonlinear term from bond k + 1; ViT the
+  // transposed V_i core [a'][so][a].
+  void nl_right(int i, XTerm& T, int k, const double* ViT, double* t1p, double* t2p,
+                double* t3p) {
+    const int ci = cap(i)[k], ci1 = cap(i)[k + 1];
+    const int cb = T.B->cap[k], cb1 = T.B->cap[k + 1], wl = T.Dm->w[k], wr = T.Dm->w[k + 1];
+    const int ce = T.X->cap[k], ce1 = T.X->cap[k + 1];
+    const double* Bc = T.B->core(k);
+    launch_core_transpose(T.X->core(k), ce, ce1, xtT[i].p, s);
+    // T1[(a' [c' p' | p' c'])][(t e)] = R[..][e'] XT[e'][(t e)]
+    gemm(gemm_plain(T.R[k + 1].p, xtT[i].p, t1p, ci1 * cb1 * wr, 4 * ce, ce1, ce1, 4 * ce,
+                    4 * ce), s);
+    if (T.kind == 1) {
+      // T2[(a' c')][(so p)][e] = DR2[(so p)][(p' t)] T1[(a' c')][(p' t)][e]
+      GemmF64 g{};
+      g.A = T.Dm->kr2(k); g.B = t1p; g.C = t2p;
+      g.M = 4 * wl; g.N = ce; g.K = 4 * wr;
+      g.lda = 4 * wr; g.ldb = ce; g.ldc = ce;
+      g.nb1 = ci1 * cb1; g.nb2 = 1;
+      g.sB1 = (long long)wr * 4 * ce; g.sC1 = (long long)4 * wl * ce;
+      g.alpha = 1.0;
+      gemm(g, s);
+      // T3[(a' so)][c][(p e)] = B_so[c][c'] T2[(a' c')][so][(p e)], batch (a', so)
+      GemmF64 h{};
+      h.A = Bc; h.B = t2p; h.C = t3p;
+      h.M = cb; h.N = wl * ce; h.K = cb1;
+      h.lda = 4 * cb1; h.ldb = 4 * wl * ce; h.ldc = wl * ce;
+      h.nb1 = ci1; h.nb2 = 4;
+      h.sA1 = 0; h.sA2 = cb1;
+      h.sB1 = (long long)cb1 * 4 * wl * ce; h.sB2 = (long long)wl * ce;
+      h.sC1 = (long long)4 * cb * wl * ce; h.sC2 = (long long)cb * wl * ce;
+      h.alpha = 1.0;
+      gemm(h, s);
+    } else {
+      // T2[(a' p')][t][c][e] = B_t[c][c'] T1[(a' p')][c'][t][e], batch (a' p') for each t
+      for (int t = 0; t < 4; t++) {
+        GemmF64 h{};
+        h.A = Bc + t * cb1; h.B = t1p + (long long)t * ce; h.C = t2p + (long long)t * cb * ce;
+        h.M = cb; h.N = ce; h.K = cb1;
+        h.lda = 4 * cb1; h.ldb = 4 * ce; h.ldc = ce;
+        h.nb1 = ci1 * wr; h.nb2 = 1;
+        h.sA1 = 0; h.sB1 = (long long)cb1 * 4 * ce; h.sC1 = (long long)4 * cb * ce;
+        h.alpha = 1.0;
+        gemm(h, s);
+      }
+      // T3[a'][(so p)][(c e)] = DR2[(so p)][(p' t)] T2[a'][(p' t)][(c e)], batch a'
+      GemmF64 g{};
+      g.A = T.Dm->kr2(k); g.B = t2p; g.C = t3p;
+      g.M = 4 * wl; g.N = cb * ce; g.K = 4 * wr;
+      g.lda = 4 * wr; g.ldb = cb * ce; g.ldc = cb * ce;
+      g.nb1 = ci1; g.nb2 = 1;
+      g.sB1 = (long long)wr * 4 * cb * ce; g.sC1 = (long long)4 * wl * cb * ce;
+      g.alpha = 1.0;
+      gemm(g, s);
+    }
+    // R[k][a][...] = ViT[(a' so)][a]^T T3[(a' so)][...]
+    const int n0 = cb * wl * ce;
+    GemmF64 g3 = gemm_plain(ViT, t3p, T.R[k].p, ci, n0, ci1 * 4, ci, n0, n0);
+    g3.tA = 1;
+    gemm(g3, s);
   }
 
   // A term's right environment at bond k from bond k + 1 (MPO sandwich, as
@@ -1875,7 +2034,11 @@ struct Projector {
       GemmF64 g = gemm_plain(ViT, t1p, RW[i][k].p, ci, cw, ci1 * 4, ci, cw, cw);
       g.tA = 1;
       gemm(g, s);
-      for (XTerm& T : xt[i]) xterm_right(i, T, k, ViT, t1p, t2p);
+      double* const t3p = i == 0 ? t3.p : t3b.p;
+      for (XTerm& T : xt[i]) {
+        if (T.kind) nl_right(i, T, k, ViT, t1p, t2p, t3p);
+        else xterm_right(i, T, k, ViT, t1p, t2p);
+      }
     });
   }
 
@@ -1913,7 +2076,11 @@ struct Projector {
       GemmF64 g = gemm_plain(V[i]->core(k), t1p, LW[i][k + 1].p, ci1, cw1, 4 * ci, ci1, cw1, cw1);
       g.tA = 1;
       gemm(g, s);
-      for (XTerm& T : xt[i]) xterm_left(i, T, k, t1p, t2p);
+      double* const t3p = i == 0 ? t3.p : t3b.p;
+      for (XTerm& T : xt[i]) {
+        if (T.kind) nl_left(i, T, k, t1p, t2p, t3p);
+        else xterm_left(i, T, k, t1p, t2p);
+      }
     });
   }
 
@@ -2018,7 +2185,18 @@ struct Projector {
       g.alpha = wcoef;
       gemm(g, s);
       // the implicit terms: rhs += coef L P X R (the coupling blocks' pattern)
+      double* const t3p = i == 0 ? t3.p : t3b.p;
       for (XTerm& T : xt[i]) {
+        if (T.kind) {
+          nl_left3(i, T, d, T.L[d].p, t1p, t2p, t3p);
+          const int n1 = T.B->cap[d + 1] * T.Dm->w[d + 1] * T.X->cap[d + 1];
+          GemmF64 g3 = gemm_plain(t3p, T.R[d + 1].p, rhs[i].p, 4 * ci, ci1, n1, n1, n1, ci1);
+          g3.tB = 1;
+          g3.alpha = T.coef;
+          g3.beta = 1.0;
+          gemm(g3, s);
+          continue;
+        }
         const int wl = T.P->w[d], wr = T.P->w[d + 1];
         const int cx = T.X->cap[d], cx1 = T.X->cap[d + 1];
         gemm(gemm_plain(T.L[d].p, T.X->core(d), t1p, ci * wl, 4 * cx1, cx, cx, 4 * cx1, 4 * cx1), s);
@@ -2359,9 +2537,12 @@ std::unique_ptr<qtt_mpo_s> hadamard_mpo_device(qtt_ctx ctx, qtt_mps b, qtt_mpo W
 // time step), so the result keeps the bonds of u.
 void project_implicit_impl(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu,
                            double a_scale, qtt_mps* v1, qtt_mps* v2, int* cg_out, int* sw_out) {
+  // QTT_IMPLICIT_PRODUCT: contract the product MPOs H_b D_j, D_j H_b (built
+  // on the device) instead of the structured nonlinear terms (same sums)
+  static const bool product = getenv("QTT_IMPLICIT_PRODUCT") != nullptr;
   DBuf<double> mbuf[4];
   std::unique_ptr<qtt_mpo_s> HD[2], DH[2];
-  for (int j = 0; j < 2; j++) {
+  for (int j = 0; j < 2 && product; j++) {
     HD[j] = hadamard_mpo_device(ctx, b[j], ctx->D[j], 0, mbuf[2 * j]);
     DH[j] = hadamard_mpo_device(ctx, b[j], ctx->D[j], 1, mbuf[2 * j + 1]);
   }
@@ -2380,8 +2561,13 @@ void project_implicit_impl(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, do
     for (int j = 0; j < 2; j++) P.K[i][j] = ctx->K[i][j];
   for (int i = 0; i < 2; i++) {
     for (int j = 0; j < 2; j++) {
-      P.xt[i].push_back(Projector::XTerm{-0.5 * h, HD[j].get(), b[i], {}, {}});
-      P.xt[i].push_back(Projector::XTerm{-0.5 * h, DH[j].get(), b[i], {}, {}});
+      if (product) {
+        P.xt[i].push_back(Projector::XTerm{-0.5 * h, HD[j].get(), b[i], {}, {}});
+        P.xt[i].push_back(Projector::XTerm{-0.5 * h, DH[j].get(), b[i], {}, {}});
+      } else {
+        P.xt[i].push_back(Projector::XTerm{-0.5 * h, nullptr, b[i], {}, {}, 1, b[j], ctx->D[j]});
+        P.xt[i].push_back(Projector::XTerm{-0.5 * h, nullptr, b[i], {}, {}, 2, b[j], ctx->D[j]});
+      }
     }
     P.xt[i].push_back(Projector::XTerm{h * nu, ctx->lap, b[i], {}, {}});
   }
