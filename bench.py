@@ -1,6 +1,6 @@
 """Benchmark: QTT RK4 steps per second on a 2^10 x 2^10 shear jet at chi = 64.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision both|mixed|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision all|both|mixed|fp64]
                     [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight] [--rhs explicit|implicit]
                     [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
                     [--clocks-file PATH]
@@ -15,13 +15,18 @@ A step is one full RK4 step (four penalised Euler minimisations) of both
 velocity components; the state advances from step to step.
 
 The metric compares the plain FP64 form with the mixed form.  By default
-(--precision both) one run times both on the same initial state: W warm-up
-steps of each, then K timed steps of the mixed form (the line's value,
-ms_per_step, e2e and roofline) and K timed steps of the FP64 form (the
-line's "fp64" object).  Both forms then take the same further steps (the
-profiled step, the e2e steps), after which "mixed_vs_fp64_rel_l2" is the
-relative L2 distance of their dense fields (both components).
---precision mixed | fp64 times one form only.
+(--precision all) one run times three forms on the same initial state: W
+warm-up steps of each, then K timed steps of the mixed form (the line's
+value, ms_per_step, e2e and roofline), K timed steps of the FP64 form (the
+line's "fp64" object) and K timed steps of the paper's implicit form in FP64
+(the line's "fp64_implicit" object: the stages' right-hand sides inside the
+projection's environments, --rhs implicit).  All forms then take the same
+further steps (the profiled step, the e2e steps), after which
+"mixed_vs_fp64_rel_l2" is the relative L2 distance of the mixed and FP64
+dense fields (both components) and "fp64_implicit_vs_fp64_rel_l2" that of the
+two FP64 forms (different truncations of the same scheme, so of the order of
+the truncation error, not of rounding).  --precision both times the first
+two, mixed | fp64 one form only.
 
 One JSON line is printed by rank 0.  With torchrun (N > 1) every rank runs
 its own trajectory on its own GPU (replicas: the method has no exchange
@@ -341,18 +346,19 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ main arm
-def make_form(P, w, prec, graphs, B, local, rank):
-    """Contexts and initial states of one precision (same seeds for every form)."""
+def make_form(P, w, prec, graphs, B, local, rank, rhs_form=None):
+    """Contexts and initial states of one form (same seeds for every form)."""
+    rhs = w.get("rhs_form", 0) if rhs_form is None else rhs_form
     B = max(1, B)
     if B > 1:
         batch = P.Batch([dict(n=w["n"], precision=prec, graphs=graphs,
-                              rhs_form=w.get("rhs_form", 0), **solver_kwargs(w))
+                              rhs_form=rhs, **solver_kwargs(w))
                          for _ in range(B)], device=local)
         ctxs = batch.contexts
     else:
         batch = None
         ctxs = [P.Context(w["n"], precision=prec, device=local, graphs=graphs,
-                          rhs_form=w.get("rhs_form", 0), **solver_kwargs(w))]
+                          rhs_form=rhs, **solver_kwargs(w))]
     states, dts = [], []
     for i, c in enumerate(ctxs):
         u, dx, dt_i = workload_state(w["n"], w["seed"] + rank * B + i)
@@ -588,7 +594,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own")
-    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--precision", default="all", choices=["all", "both", "fp64", "mixed"],
+                    help="all (default): the mixed form (the line's value), the FP64 form and "
+                         "the paper's implicit form in FP64; both: the first two")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     ap.add_argument("--grid-bits", "--n", dest="n", type=int, default=None,
@@ -650,11 +658,14 @@ def main():
     B = max(1, args.batched)
     if B > 1:
         w["workload"] = f"{w['workload']}_x{B}_trajectories"
-    names = {"both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
-    if B > 1:
-        names = names[:1]
-    precs = {"mixed": P.PREC_MIXED, "fp64": P.PREC_FP64}
-    forms = {nm: make_form(P, w, precs[nm], graphs, B, local, rank) for nm in names}
+    names = {"all": ["mixed", "fp64", "fp64_implicit"], "both": ["mixed", "fp64"],
+             "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
+    if B > 1 or args.rhs == "implicit":
+        names = names[:1] if args.precision in ("all", "both") else names
+    precs = {"mixed": P.PREC_MIXED, "fp64": P.PREC_FP64, "fp64_implicit": P.PREC_FP64}
+    rhs_of = {"fp64_implicit": P.RHS_IMPLICIT}
+    forms = {nm: make_form(P, w, precs[nm], graphs, B, local, rank, rhs_of.get(nm))
+             for nm in names}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -685,11 +696,13 @@ def main():
         for _ in range(n_e2e):
             forms[nm]["step"]()
     torch.cuda.synchronize()
-    cmp = None
-    if len(names) == 2:
+    cmp = cmp_imp = None
+    if "mixed" in names and "fp64" in names:
         fields = {nm: [forms[nm]["ctxs"][0].to_dense(x).cpu().numpy()
                        for x in forms[nm]["states"][0]] for nm in names}
         cmp = rel_l2(fields["mixed"], fields["fp64"])
+        if "fp64_implicit" in names:
+            cmp_imp = rel_l2(fields["fp64_implicit"], fields["fp64"])
     steps_taken = args.warmup + args.steps + 1 + n_e2e
 
     if rank != 0:
@@ -740,7 +753,7 @@ def main():
     line = {"metric": METRIC, "value": hs["value"], "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": hs["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head == "fp64" else "f32/f64",
+            "dtype": "f64" if head.startswith("fp64") else "tf32x3/f32/f64",
             "data": "synthetic (seeded shear-jet initial condition)",
             "timing": ("CUDA events on the stepping stream" if B == 1 else
                        "host clock between device-wide synchronisations (library-owned streams)"),
@@ -753,11 +766,17 @@ def main():
             "e2e": e2e, "gpu_launches": hs["gpu_launches"], "roofline": hs["roofline"],
             "tc_subspace_searches_timed": hs["tc_subspace_searches_timed"],
             "cpu_baseline": cpu, "clocks": clocks, "wall_s": hs["wall_s"]}
-    if len(names) == 2:
+    if "mixed" in names and "fp64" in names:
         line["fp64"] = sums["fp64"]
         line["mixed_vs_fp64_rel_l2"] = cmp
         line["mixed_vs_fp64_after_steps"] = steps_taken
         line["mixed_over_fp64"] = hs["value"] / sums["fp64"]["value"]
+    if "fp64_implicit" in names:
+        line["fp64_implicit"] = sums["fp64_implicit"]
+        line["fp64_implicit"]["form"] = ("the paper's implicit right-hand side (nonlinear terms "
+                                         "inside the projection's environments), FP64")
+        line["fp64_implicit_vs_fp64_rel_l2"] = cmp_imp
+        line["fp64_implicit_over_fp64"] = sums["fp64_implicit"]["value"] / sums["fp64"]["value"]
     if tcg:
         line["tc_gemm"] = tcg
     line["peaks_file"] = {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}
