@@ -3,11 +3,20 @@
 // op = optional transpose, batch z = z1 * nb2 + z2 with two stride levels
 // (the site contractions of the zip-up batch over (carry row, omega)).
 //
-// Tiling: 64 x 64 (256 threads) or 32 x 32 (64 threads) output tile per CTA,
+// Tiling: 64 x 64 (256 threads), 32 x 32 (64 threads) or 16 x 128 (128
+// threads, for outputs of a few rows) output tile per CTA, or (tile 3) a
+// small op(A) in shared memory with one output column per thread,
 // K staged 16 at a time in shared memory, 4 x 4 register accumulators per
 // thread; the host picks the tile and a split of K per product shape.  FP64 on this GPU
 // runs on the CUDA-core DFMA pipe (no FP64 tensor-core rate worth using), so
 // the kernel is DFMA-bound once tiles are full.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <mutex>
+#include <set>
+#include <string>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -86,7 +95,55 @@ __global__ void __launch_bounds__((TBM / 4) * (TBN / 4)) k_gemm_f64(GemmF64 g) {
   }
 }
 
+// Small-operand products over a large batch (an MPO core applied to every
+// slice of a tensor, a few rows by a few columns of K): op(A[z]) (M x K,
+// M <= MM, K <= kSmallK) staged in shared memory, one thread per output
+// column n of one batch entry z, the M rows of that column in registers.
+// Each output is the same chain of fused multiply-adds over k = 0..K-1 as in
+// k_gemm_f64, so the two kernels give the same bits.
+constexpr int kSmallK = 48;
+
+template <int MM>
+__global__ void __launch_bounds__(128) k_gemm_f64_small(GemmF64 g) {
+  if (g.skip && *g.skip) return;
+  __shared__ double As[MM * kSmallK];
+  const int M = g.M, K = g.K, N = g.N;
+  const int z = blockIdx.y;
+  const int z1 = z / g.nb2, z2 = z % g.nb2;
+  const double* A = g.A + z1 * g.sA1 + z2 * g.sA2;
+  for (int e = threadIdx.x; e < M * K; e += blockDim.x) {
+    const int i = e / K, k = e % K;
+    As[e] = g.tA ? A[(long long)k * g.lda + i] : A[(long long)i * g.lda + k];
+  }
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double* B = g.B + z1 * g.sB1 + z2 * g.sB2 + n;
+  double* C = g.C + z1 * g.sC1 + z2 * g.sC2 + n;
+  double acc[MM];
+#pragma unroll
+  for (int i = 0; i < MM; i++) acc[i] = 0.0;
+  for (int k = 0; k < K; k++) {
+    const double b = B[(long long)k * g.ldb];
+#pragma unroll
+    for (int i = 0; i < MM; i++)
+      if (i < M) acc[i] = fma(As[i * K + k], b, acc[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < MM; i++) {
+    if (i >= M) break;
+    double* c = C + (long long)i * g.ldc;
+    double v = g.alpha * acc[i];
+    if (g.beta != 0.0) v = fma(g.beta, *c, v);
+    *c = v;
+  }
+}
+
 }  // namespace
+
+bool gemm_small_eligible(const GemmF64& g) {
+  return !g.tB && g.M <= 48 && g.K <= kSmallK && g.nb1 * g.nb2 <= 65535;
+}
 
 void launch_gemm_f64(const GemmF64& g, cudaStream_t s) { launch_gemm_f64_tile(g, 0, s); }
 
@@ -106,13 +163,38 @@ void launch_gemm_f64_tile(const GemmF64& g, int tile, cudaStream_t s) {
     launch_scale(g, s);
     return;
   }
+  if (tile == 3 && !gemm_small_eligible(g)) tile = 0;
   pre_launch(s);
   if (tile == 1) {
     dim3 grid(ceil_div(g.N, 32), ceil_div(g.M, 32), g.nb1 * g.nb2);
     k_gemm_f64<32, 32><<<grid, 64, 0, s>>>(g);
+  } else if (tile == 3) {
+    const int th = g.N >= 128 ? 128 : ((g.N + 31) / 32) * 32;
+    dim3 grid(ceil_div(g.N, th), g.nb1 * g.nb2);
+    if (g.M <= 16)
+      k_gemm_f64_small<16><<<grid, th, 0, s>>>(g);
+    else
+      k_gemm_f64_small<48><<<grid, th, 0, s>>>(g);
+  } else if (tile == 2) {
+    // skinny outputs (a few rows, e.g. an MPO core applied over a batch)
+    dim3 grid(ceil_div(g.N, 128), ceil_div(g.M, 16), g.nb1 * g.nb2);
+    k_gemm_f64<16, 128><<<grid, 128, 0, s>>>(g);
   } else {
     dim3 grid(ceil_div(g.N, 64), ceil_div(g.M, 64), g.nb1 * g.nb2);
     k_gemm_f64<64, 64><<<grid, 256, 0, s>>>(g);
+  }
+  static const bool by_shape = getenv("QTT_PROFILE_SHAPES") != nullptr;
+  if (by_shape) {
+    // profiling aid: one profiler entry per product shape and tile
+    static std::mutex mu;
+    static std::set<std::string> names;
+    char buf[96];
+    snprintf(buf, sizeof buf, "k_gemm_f64[%dx%dx%d b%d t%d %d%d]", g.M, g.N, g.K,
+             g.nb1 * g.nb2, tile, g.tA, g.tB);
+    std::lock_guard<std::mutex> lk(mu);
+    const char* nm = names.insert(buf).first->c_str();
+    post_launch(nm, s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
+    return;
   }
   post_launch("k_gemm_f64", s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
 }

@@ -27,8 +27,11 @@ static inline GemmF64 gemm_plain(const double* A, const double* B, double* C, in
   return g;
 }
 void launch_gemm_f64(const GemmF64& g, cudaStream_t s);
-// tile 0: 64 x 64 per CTA, tile 1: 32 x 32 per CTA
+// tile 0: 64 x 64 per CTA, tile 1: 32 x 32 per CTA, tile 2: 16 x 128 per CTA,
+// tile 3: op(A) in shared memory, one output column per thread (for
+// gemm_small_eligible shapes; others run tile 0).  All tiles give the same bits.
 void launch_gemm_f64_tile(const GemmF64& g, int tile, cudaStream_t s);
+bool gemm_small_eligible(const GemmF64& g);  // M <= 48, K <= 48, B not transposed
 void launch_scale(const GemmF64& g, cudaStream_t s);  // C = beta C
 void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, double alpha,
                        double beta, const int* skip, cudaStream_t s);

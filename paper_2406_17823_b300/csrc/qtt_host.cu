@@ -466,7 +466,7 @@ void tune_cache_load() {
     const GemmKey k{(int)v[i], (int)v[i + 1], (int)v[i + 2], (int)v[i + 3], (int)v[i + 4],
                     (int)v[i + 5]};
     const int tile = (int)v[i + 6], S = (int)v[i + 7];
-    if (tile < 0 || tile > 1 || S < 1 || S > 16 || (S & (S - 1))) continue;  // not ours
+    if (tile < 0 || tile > 3 || S < 1 || S > 16 || (S & (S - 1))) continue;  // not ours
     tune_map().emplace(k, GemmChoice{tile, S});
   }
 }
@@ -506,8 +506,10 @@ GemmChoice gemm_tune(const GemmF64& g, cudaStream_t s) {
   QTT_CUDA_CHECK(cudaEventCreate(&e1));
   GemmChoice best{0, split_rule(g)};
   float tbest = 1e30f;
-  for (int tile = 0; tile < 2; tile++)
+  for (int tile = 0; tile < 4; tile++)
     for (int S = 1; S <= 16; S *= 2) {
+      if (tile == 2 && g.M > 32) break;  // the skinny tile only for outputs of a few rows
+      if (tile == 3 && !gemm_small_eligible(g)) break;
       if (S > 1 && (nb != 1 || g.K / S < 32)) break;
       gemm_run(t, tile, S, s);  // warm
       QTT_CUDA_CHECK(cudaEventRecord(e0, s));
@@ -533,6 +535,16 @@ void gemm(const GemmF64& g, cudaStream_t s) {
   }();
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nb1 * g.nb2 <= 0) {
     launch_gemm_f64(g, s);  // empty product or C = beta C
+    return;
+  }
+  // QTT_GEMM_TILE=t: every product on tile t with the fixed K split (a
+  // check that the tiles give the same bits, and a way to time one tile)
+  static const int forced = [] {
+    const char* e = getenv("QTT_GEMM_TILE");
+    return e && e[0] >= '0' && e[0] <= '3' && e[1] == 0 ? e[0] - '0' : -1;
+  }();
+  if (forced >= 0) {
+    gemm_run(g, forced, split_rule(g), s);
     return;
   }
   if (!tune) {
