@@ -238,6 +238,34 @@ qtt_status qtt_rk2_step(qtt_ctx ctx, qtt_mps* u1, qtt_mps* u2, double dt, double
 qtt_status qtt_gemm_tf32x3(qtt_ctx ctx, int M, int N, int K, const double* A, int lda, int tA,
                            const double* B, int ldb, int tB, double* C, int ldc);
 
+/* The mixed form's FP64 product on the BF16 tensor cores (north-star
+ * precision option; the paper contracts in FP64 through cuTensorNet), by
+ * the Ozaki splitting (Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59,
+ * 2012): for z = 0..batch-1,
+ *   C_z = alpha op(A_z) op(B_z) + beta C_z,
+ * A_z = A + z sA, B_z = B + z sB, C_z = C + z sC (element strides), op as
+ * in qtt_gemm_tf32x3, all FP64 device buffers.  K is taken in chunks of 64;
+ * in each chunk every row of op(A_z) and every column of op(B_z) is scaled
+ * by a power of two 2^e (e the smallest with every |x| < 2^e) and cut into
+ * eight signed 7-bit slices, the slice pairs (p, q) with p + q <= 7 are
+ * multiplied exactly on the tensor cores (tcgen05 kind::f16, BF16
+ * operands, exact FP32 accumulation) and their exact sum is rounded to FP64
+ * once; the chunks' results are summed in order in FP64.  Error below
+ * K 2^-53 2^(eA_i + eB_j) per element plus the FP64 rounding of the chunk
+ * sums.  An unbatched product whose output tiles cannot fill the GPU has
+ * its K chunks dealt over up to 16 slices computed side by side, whose
+ * partial products (scratch from the stream-ordered pool) are summed in
+ * slice order.  Sizes the kernel takes: K >= 16, K <= 1024 when
+ * batch > 1 and K <= 16384 when batch = 1, 1 <= batch <= 65535,
+ * max(M, N) >= 32, M N K batch >= 2^21; other sizes return QTT_ERR_SHAPE
+ * (the library's FP64 GEMM serves them).  Enqueued on the context stream.
+ * QTT_ERR_ARG for null pointers, sizes < 1 or leading dimensions below the
+ * row length. */
+qtt_status qtt_gemm_ozaki(qtt_ctx ctx, int M, int N, int K, const double* A, int lda, int tA,
+                          long long sA, const double* B, int ldb, int tB, long long sB,
+                          double* C, int ldc, long long sC, int batch, double alpha,
+                          double beta);
+
 /* Turbulent kinetic energy spectrum of the velocity (u1, u2) (the paper's
  * TKE spectra, Sec. III.A), computed on the device: the dense fields, their
  * 2-D DFTs, and E(k) = sum over wavevectors m with round(|m|) = k of

@@ -73,6 +73,11 @@ extern thread_local int* g_dev_err;
 // variable QTT_DEBUG_SYNC is set, waits for it and reports a failure by
 // kernel name (a debugging aid that localises device-side faults).
 void post_launch(const char* name, cudaStream_t s, double flops = 0.0);
+// With QTT_PROFILE_SHAPES set in the environment the profiler separates one
+// kernel's launches by problem shape: shape_name returns `base[tag]` as a
+// stable, interned string (callers build the tag only when shape_profiling()).
+bool shape_profiling();
+const char* shape_name(const char* base, const char* tag);
 // Called just before every kernel launch (records a start event when the
 // context is profiling).
 void pre_launch(cudaStream_t s);

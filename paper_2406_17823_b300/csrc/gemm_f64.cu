@@ -11,11 +11,6 @@
 // runs on the CUDA-core DFMA pipe (no FP64 tensor-core rate worth using), so
 // the kernel is DFMA-bound once tiles are full.
 #include <stdio.h>
-#include <stdlib.h>
-
-#include <mutex>
-#include <set>
-#include <string>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -183,18 +178,12 @@ void launch_gemm_f64_tile(const GemmF64& g, int tile, cudaStream_t s) {
     dim3 grid(ceil_div(g.N, 64), ceil_div(g.M, 64), g.nb1 * g.nb2);
     k_gemm_f64<64, 64><<<grid, 256, 0, s>>>(g);
   }
-  static const bool by_shape = getenv("QTT_PROFILE_SHAPES") != nullptr;
-  if (by_shape) {
-    // profiling aid: one profiler entry per product shape and tile
-    static std::mutex mu;
-    static std::set<std::string> names;
-    char buf[96];
-    snprintf(buf, sizeof buf, "k_gemm_f64[%dx%dx%d b%d t%d %d%d]", g.M, g.N, g.K,
-             g.nb1 * g.nb2, tile, g.tA, g.tB);
-    std::lock_guard<std::mutex> lk(mu);
-    const char* nm = names.insert(buf).first->c_str();
-    post_launch(nm, s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
-    return;
+  const char* name = "k_gemm_f64";
+  if (shape_profiling()) {
+    char tag[80];
+    snprintf(tag, sizeof tag, "%dx%dx%d b%d t%d %d%d", g.M, g.N, g.K, g.nb1 * g.nb2, tile, g.tA,
+             g.tB);
+    name = shape_name(name, tag);
   }
-  post_launch("k_gemm_f64", s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
+  post_launch(name, s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
 }

@@ -1,0 +1,599 @@
+// FP64 products on the BF16 tensor cores by the Ozaki splitting scheme
+// (Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012): K is taken
+// in chunks of 64; in each chunk every row of op(A) and every column of
+// op(B) is written as a fixed-point number with a power-of-two scale and
+// cut into eight signed 7-bit slices, the products of slice pairs (p, q)
+// with p + q <= 7 are exact on the tensor cores and summed exactly, and the
+// exact sum is rounded to FP64 once; the chunks' results add up in FP64.
+// This is the mixed form's contraction kernel: FP64-level accuracy (the
+// dropped pairs and the slicing truncation stay below about
+// K 2^-53 2^(eA + eB), eA, eB the operands' scale exponents) at a
+// tensor-core rate, on a GPU whose FP64 pipe retires about two FMAs per
+// clock per SM.
+//
+// One CTA of 512 threads per 128 x BN output tile (BN = 16, 32 or 64) of one
+// batch entry (or one K slice of it); per K chunk:
+//  * Slicing.  Every thread loads its share of the two FP64 operand tiles
+//    in batches of four pairs (any strides, transposes and batch offsets;
+//    a batch's loads issued before use), the rows' largest magnitudes give
+//    the scales, and
+//    the slices go as BF16 integers into shared memory in the layout the
+//    128-byte-swizzled K-major UMMA descriptor expects (rows of 64 BF16,
+//    16-byte chunks XOR-ed with the row index mod 8).  Integer arithmetic
+//    on the FP64 bit patterns only.
+//  * Products.  One thread issues tcgen05.mma kind::f16 (BF16 x BF16, FP32
+//    accumulation, M = 128, N = BN, K = 16) for the 36 slice pairs, pairs
+//    of equal p + q = d into accumulator d of eight in tensor memory
+//    (8 BN columns).  A diagonal sums at most 8 x 64 products of magnitude
+//    below 2^14, so every partial sum is an integer below 2^23 and the FP32
+//    accumulation is exact.
+//  * Epilogue.  The sixteen warps read the accumulators (warps w, w + 4,
+//    w + 8, w + 12 share TMEM lanes 32 (w mod 4) .. and split the 8-column
+//    groups), combine the exact integers as T = sum_d D_d 2^(7 (7 - d)) in
+//    128-bit integer arithmetic and round T 2^(eA + eB - 63) to FP64 by
+//    integer operations (round to nearest even).  The first chunk stores
+//    the result, later chunks add theirs to it in order; the last applies
+//    alpha (and beta, which only a one-chunk CTA takes: an unbatched product
+//    with beta != 0 and several chunks is split over K slices whose partial
+//    products the slice sum combines, in order, with alpha and beta).  The wait for each
+// chunk's MMAs is bounded by one second of global time; a wait that gives
+// up sets QTT_DEVERR_TIMEOUT, skips the output, frees the tensor memory and
+// returns.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int kOzThreads = 512;
+constexpr int kOzM = 128;          // MMA M (rows of the A-operand tile)
+constexpr int kOzSlices = 8;       // slices per operand
+constexpr int kOzChunk = 64;       // K elements per chunk: one 128-byte swizzled row
+constexpr int kOzTileA = kOzM * 128;  // bytes of one A slice tile
+constexpr int kOzBad = 1 << 20;    // scale exponent of a row holding Inf or NaN
+
+// Instruction descriptor of kind::f16 with BF16 operands: D FP32 (bit 4),
+// A and B BF16 (1 at bits 7 and 10), both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// One operand of the kernel: element (r, k) of batch entry (z1, z2) at
+// p[z1 s1 + z2 s2 + r sr + k sk], r < rows, k < K.
+struct OzOperand {
+  const double* p;
+  long long s1, s2, sr, sk;
+  int rows;
+};
+
+struct OzParams {
+  OzOperand a, b;      // a: the 128-row side, b: the BN-row side
+  int K, nch, BN;
+  int kslice;          // > 0: blockIdx.z is a K slice [z kslice, (z + 1) kslice)
+  int nb2;
+  int swap;            // 0: C(r_a, r_b); 1: C(r_b, r_a)
+  double* C;
+  long long ldc, sC1, sC2;
+  double alpha, beta;
+  const int* skip;
+  int* err;
+};
+
+// |x| as the bit pattern of a non-negative double (monotonic in |x|; NaN
+// above +Inf)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Scale exponent e of a row from its largest |x| (bits): |x| < 2^e for every
+// element; kOzBad for a row holding Inf or NaN.
+__device__ __forceinline__ int row_scale(unsigned long long mx) {
+  if (mx >= 0x7FF0000000000000ull) return kOzBad;
+  const int ex = (int)(mx >> 52);
+  return (ex > 1 ? ex : 1) - 1022;
+}
+
+// floor(|x| 2^(56 - e)) (< 2^56) and the sign of x
+__device__ __forceinline__ unsigned long long fixed56(double x, int e, unsigned& sgn) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  sgn = (unsigned)(b >> 63);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const unsigned long long frac = b & 0xFFFFFFFFFFFFFull;
+  const unsigned long long mant = ex ? (frac | 0x10000000000000ull) : frac;
+  const int sh = (ex ? ex : 1) - 1019 - e;
+  if (sh >= 0) return mant << sh;  // sh <= 3 when |x| < 2^e
+  return sh > -64 ? (mant >> -sh) : 0ull;
+}
+
+// Byte offset of element (r, k), k < 64, in a K-major tile of 128-byte rows
+// with the 128-byte swizzle (8-row groups 1024 bytes apart).
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7))) << 4) +
+                    ((k & 7) << 1));
+}
+
+// FP64 value of T 2^scale, T = H 2^28 + L, rounded once to nearest even
+// (integer operations; ldexp only for a subnormal or overflowing result).
+__device__ __forceinline__ double assemble(long long H, long long L, int scale) {
+  const __int128 T = ((__int128)H << 28) + (__int128)L;
+  if (T == 0) return 0.0;
+  const unsigned long long sgn = T < 0 ? 1ull : 0ull;
+  const unsigned __int128 U = (unsigned __int128)(T < 0 ? -T : T);
+  const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
+  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+  int sh = nb - 53;
+  unsigned long long m;
+  if (sh <= 0) {
+    m = lo << (-sh);
+  } else {
+    const unsigned __int128 q = U >> sh;
+    const unsigned __int128 rem = U - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    m = (unsigned long long)q;
+    if (rem > half || (rem == half && (m & 1ull))) {
+      m++;
+      if (m >> 53) {
+        m >>= 1;
+        sh++;
+      }
+    }
+  }
+  // value = m 2^(sh + scale), 2^52 <= m < 2^53
+  const int E = 52 + sh + scale;
+  if (E < -1022 || E > 1023) {
+    const double v = ldexp((double)m, sh + scale);
+    return sgn ? -v : v;
+  }
+  return __longlong_as_double(
+      (long long)((sgn << 63) | ((unsigned long long)(E + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// Digits of a pair (x0, x1) of one row (scale exponent e): eight words, word
+// p holding the p-th 7-bit digits of x0 (low half) and x1 (high half) as
+// signed BF16 integers (a digit v < 128 is exact in FP32 as (2^23 + v) -
+// 2^23, and its BF16 is the upper half of that FP32).
+__device__ __forceinline__ void pair_digits(double x0, double x1, int e, uint32_t (&w)[kOzSlices]) {
+  unsigned s0, s1;
+  const unsigned long long f0 = fixed56(x0, e, s0), f1 = fixed56(x1, e, s1);
+  const uint32_t h0 = (uint32_t)(f0 >> 28), l0 = (uint32_t)f0 & 0xFFFFFFFu;
+  const uint32_t h1 = (uint32_t)(f1 >> 28), l1 = (uint32_t)f1 & 0xFFFFFFFu;
+  const uint32_t sg = (s0 << 15) | (s1 << 31);
+#pragma unroll
+  for (int p = 0; p < kOzSlices; p++) {
+    const int sh = 7 * (3 - (p & 3));
+    const uint32_t v0 = ((p < 4 ? h0 : l0) >> sh) & 127u, v1 = ((p < 4 ? h1 : l1) >> sh) & 127u;
+    const uint32_t b0 = __float_as_uint(__uint_as_float(0x4B000000u | v0) - 8388608.0f);
+    const uint32_t b1 = __float_as_uint(__uint_as_float(0x4B000000u | v1) - 8388608.0f);
+    w[p] = __byte_perm(b0, b1, 0x7632) | sg;  // upper halves: the BF16 values
+  }
+}
+
+// Where thread t's pair i of a tile of R rows lies (R / 16 pairs per thread,
+// kOzThreads = 512): with k contiguous in memory warp w takes rows w,
+// w + 16, ... and lane l the pair (2 l, 2 l + 1); otherwise consecutive
+// threads take consecutive rows and a row's 32 pairs are dealt over
+// kOzThreads / R threads.
+template <int R>
+__device__ __forceinline__ void pair_at(bool kc, int i, int& r, int& k) {
+  const int tid = threadIdx.x;
+  if (kc) {
+    r = (tid >> 5) + 16 * i;
+    k = 2 * (tid & 31);
+  } else {
+    constexpr int tpr = kOzThreads / R;
+    r = tid % R;
+    k = 2 * (tid / R + tpr * i);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void load_pair(const OzOperand& o, const double* base, int r0,
+                                          int klen, int r, int k, double& x0, double& x1) {
+  const bool live = r0 + r < o.rows;
+  const double* row = base + (long long)(r0 + r) * o.sr;
+  x0 = (live && k < klen) ? row[(long long)k * o.sk] : 0.0;
+  x1 = (live && k + 1 < klen) ? row[(long long)(k + 1) * o.sk] : 0.0;
+}
+
+// One K chunk of a tile of R rows (base already at the chunk's first k):
+// the rows' largest magnitudes into mx[] and the eight slices into dst
+// (slice p at dst + p R 128 bytes).  Batches of four pairs per thread, every
+// load of a batch issued before its first use.  With k contiguous a row
+// lives in one warp and its maximum is a warp reduction; otherwise the
+// maxima go through shared memory first (two passes over the loads).
+template <int R>
+__device__ void slice_tile(const OzOperand& o, const double* base, int r0, int klen,
+                           unsigned long long* mx, uint8_t* dst) {
+  constexpr int kPairs = R / 16, kBatch = kPairs < 4 ? kPairs : 4;
+  constexpr uint32_t slice_bytes = (uint32_t)R * 128;
+  const bool kc = o.sk == 1;
+  if (kc) {
+#pragma unroll 1
+    for (int i0 = 0; i0 < kPairs; i0 += kBatch) {
+      double x[2 * kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; i++) {
+        int r, k;
+        pair_at<R>(true, i0 + i, r, k);
+        load_pair<R>(o, base, r0, klen, r, k, x[2 * i], x[2 * i + 1]);
+      }
+#pragma unroll
+      for (int i = 0; i < kBatch; i++) {
+        int r, k;
+        pair_at<R>(true, i0 + i, r, k);
+        unsigned long long m = max(abs_bits(x[2 * i]), abs_bits(x[2 * i + 1]));
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
+        if ((threadIdx.x & 31) == 0) mx[r] = m;
+        const int e = row_scale(m);
+        uint32_t w[kOzSlices];
+        pair_digits(e == kOzBad ? 0.0 : x[2 * i], e == kOzBad ? 0.0 : x[2 * i + 1], e, w);
+        const uint32_t off = sw128_off(r, k);
+#pragma unroll
+        for (int p = 0; p < kOzSlices; p++) *(uint32_t*)(dst + p * slice_bytes + off) = w[p];
+      }
+    }
+  } else {
+    const int r = threadIdx.x % R;
+    unsigned long long m = 0;
+#pragma unroll 1
+    for (int i0 = 0; i0 < kPairs; i0 += kBatch) {
+      double x[2 * kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; i++) {
+        int rr, k;
+        pair_at<R>(false, i0 + i, rr, k);
+        load_pair<R>(o, base, r0, klen, rr, k, x[2 * i], x[2 * i + 1]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2 * kBatch; i++) m = max(m, abs_bits(x[i]));
+    }
+    atomicMax(&mx[r], m);
+    __syncthreads();
+    const int e = row_scale(mx[r]);
+#pragma unroll 1
+    for (int i0 = 0; i0 < kPairs; i0 += kBatch) {
+      double x[2 * kBatch];
+#pragma unroll
+      for (int i = 0; i < kBatch; i++) {
+        int rr, k;
+        pair_at<R>(false, i0 + i, rr, k);
+        load_pair<R>(o, base, r0, klen, rr, k, x[2 * i], x[2 * i + 1]);
+      }
+#pragma unroll
+      for (int i = 0; i < kBatch; i++) {
+        int rr, k;
+        pair_at<R>(false, i0 + i, rr, k);
+        uint32_t w[kOzSlices];
+        pair_digits(e == kOzBad ? 0.0 : x[2 * i], e == kOzBad ? 0.0 : x[2 * i + 1], e, w);
+        const uint32_t off = sw128_off(rr, k);
+#pragma unroll
+        for (int p = 0; p < kOzSlices; p++) *(uint32_t*)(dst + p * slice_bytes + off) = w[p];
+      }
+    }
+  }
+}
+
+// The eight accumulators' columns c0 .. c0 + 7 of this warp's 32 TMEM lanes
+// (accumulator d at column offset d * BN), one wait for all eight loads.
+template <int BN>
+__device__ __forceinline__ void tmem_ld_diagonals(uint32_t taddr, float (&D)[kOzSlices][8]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%65];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%66];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%67];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%68];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40, %41, %42, %43, %44, %45, %46, %47}, [%69];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48, %49, %50, %51, %52, %53, %54, %55}, [%70];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%56, %57, %58, %59, %60, %61, %62, %63}, [%71];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
+        "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+        "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
+        "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
+        "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr), "r"(taddr + BN), "r"(taddr + 2 * BN), "r"(taddr + 3 * BN),
+        "r"(taddr + 4 * BN), "r"(taddr + 5 * BN), "r"(taddr + 6 * BN), "r"(taddr + 7 * BN)
+      : "memory");
+#pragma unroll
+  for (int d = 0; d < kOzSlices; d++)
+#pragma unroll
+    for (int j = 0; j < 8; j++) D[d][j] = __uint_as_float(r[8 * d + j]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
+  static_assert(BN == 16 || BN == 32 || BN == 64, "output tile width");
+  if (g.skip && *g.skip) return;  // uniform over the grid
+  extern __shared__ uint8_t oz_smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sa = base;                          // 8 slices x 128 rows x 128 B
+  uint8_t* sb = base + kOzSlices * kOzTileA;   // 8 slices x BN rows x 128 B
+  __shared__ unsigned long long mxa[kOzM], mxb[BN];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int z = blockIdx.z, z1 = z / g.nb2, z2 = z % g.nb2;
+  const int ra0 = blockIdx.y * kOzM, rb0 = blockIdx.x * BN;
+  // this CTA's K extent (a K slice: the batch strides step along K)
+  const int Kz = g.kslice > 0 ? min(g.kslice, g.K - z * g.kslice) : g.K;
+  const int nch = (Kz + kOzChunk - 1) / kOzChunk;
+  const double* pa = g.a.p + z1 * g.a.s1 + z2 * g.a.s2;
+  const double* pb = g.b.p + z1 * g.b.s1 + z2 * g.b.s2;
+  double* cz = g.C + z1 * g.sC1 + z2 * g.sC2;
+  constexpr uint32_t ncols = 8u * (uint32_t)BN;  // 128, 256 or 512
+  const uint32_t mbar = smem_u32(&bar);
+
+  if (tid == 0) {
+    s_ok = 1;
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // epilogue geometry: warp w reads TMEM lanes 32 (w & 3) .. (tile rows) and
+  // the 8-column groups w >> 2, (w >> 2) + 4, ...
+  const int quarter = warp & 3, part = warp >> 2;
+  const int r = quarter * 32 + lane;
+  const int ga = ra0 + r;
+  const uint32_t idesc = idesc_bf16(kOzM, BN);
+  for (int c = 0; c < nch; c++) {
+    const int k0 = c * kOzChunk, klen = min(kOzChunk, Kz - k0);
+    for (int i = tid; i < kOzM; i += kOzThreads) mxa[i] = 0ull;
+    if (tid < BN) mxb[tid] = 0ull;
+    __syncthreads();  // zeroed row maxima
+    slice_tile<kOzM>(g.a, pa + (long long)k0 * g.a.sk, ra0, klen, mxa, sa);
+    slice_tile<BN>(g.b, pb + (long long)k0 * g.b.sk, rb0, klen, mxb, sb);
+    // the generic-proxy writes become visible to the tensor core's reads
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint64_t da0 = sw128_desc(smem_u32(sa)), db0 = sw128_desc(smem_u32(sb));
+      // the descriptor's address field is the byte address / 16
+      for (int p = 0; p < kOzSlices; p++)
+        for (int q = 0; q + p < kOzSlices; q++) {
+          const uint32_t dcol = tmem + (uint32_t)((p + q) * BN);
+#pragma unroll
+          for (int kk = 0; kk < kOzChunk / 16; kk++)
+            // first write of accumulator p + q: p = 0, kk = 0
+            mma_bf16(dcol, da0 + (uint64_t)(p * (kOzTileA / 16) + kk * 2),
+                     db0 + (uint64_t)(q * (BN * 128 / 16) + kk * 2), idesc,
+                     (p == 0 && kk == 0) ? 0u : 1u);
+        }
+      tc_commit(mbar);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(mbar, (uint32_t)(c & 1));
+    if (!ok) atomicExch(&s_ok, 0);
+    tc_fence_after();
+    __syncthreads();
+    if (!s_ok) break;
+    // this chunk's exact product, rounded once; the first chunk stores it,
+    // later ones add it to what this thread stored (in chunk order); alpha
+    // (and beta, for a one-chunk CTA) with the last
+    const bool last = c == nch - 1;
+    const int ea = row_scale(mxa[r]);
+#pragma unroll 1
+    for (int cg = part * 8; cg < BN; cg += 32) {
+      float D[kOzSlices][8];
+      tmem_ld_diagonals<BN>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cg, D);
+      if (ga >= g.a.rows) continue;
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int gb = rb0 + cg + j;
+        if (gb >= g.b.rows) continue;
+        const int eb = row_scale(mxb[cg + j]);
+        double x;
+        if (ea == kOzBad || eb == kOzBad) {
+          x = __longlong_as_double(0x7FF8000000000000ll);
+        } else {
+          const long long H = (long long)__float2int_rz(D[0][j]) * (1ll << 21) +
+                              (long long)__float2int_rz(D[1][j]) * (1ll << 14) +
+                              (long long)__float2int_rz(D[2][j]) * (1ll << 7) +
+                              (long long)__float2int_rz(D[3][j]);
+          const long long L = (long long)__float2int_rz(D[4][j]) * (1ll << 21) +
+                              (long long)__float2int_rz(D[5][j]) * (1ll << 14) +
+                              (long long)__float2int_rz(D[6][j]) * (1ll << 7) +
+                              (long long)__float2int_rz(D[7][j]);
+          x = assemble(H, L, ea + eb - 63);
+        }
+        double* cp = cz + (g.swap ? (long long)gb * g.ldc + ga : (long long)ga * g.ldc + gb);
+        double v = c == 0 ? x : *cp + x;
+        if (last) {
+          if (g.alpha != 1.0) v = g.alpha * v;
+          if (g.beta != 0.0) v = fma(g.beta, *cp, v);  // one-chunk CTAs only
+        }
+        *cp = v;
+      }
+    }
+    // every thread's TMEM reads and uses of the row maxima are done before
+    // the next chunk overwrites them
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (!s_ok && tid == 0 && g.err) atomicOr(g.err, QTT_DEVERR_TIMEOUT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
+  }
+}
+
+int oz_bn(int rows) { return rows > 32 ? 64 : rows > 16 ? 32 : 16; }
+
+size_t oz_smem(int BN) { return 1024 + (size_t)kOzSlices * kOzTileA + (size_t)kOzSlices * BN * 128; }
+
+void oz_attr_once() {
+  static std::once_flag once;
+  static bool ok = false;
+  std::call_once(once, [] {
+    ok = cudaFuncSetAttribute(k_gemm_oz<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)oz_smem(16)) == cudaSuccess &&
+         cudaFuncSetAttribute(k_gemm_oz<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)oz_smem(32)) == cudaSuccess &&
+         cudaFuncSetAttribute(k_gemm_oz<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)oz_smem(64)) == cudaSuccess;
+    cudaGetLastError();
+  });
+  if (!ok) throw QttError(QTT_ERR_CUDA, "emulated FP64 GEMM: shared-memory opt-in refused");
+}
+
+// Launch shape of a product: the 128-row side (the orientation with less
+// padding; ties: no swap), the output tile width, and for an unbatched
+// product whose tiles cannot fill the GPU a split of K over CTAs (whole
+// chunks per slice, at most 16 slices, at most 16 chunks per slice).
+struct OzPlan {
+  bool swap;
+  int BN, tiles, nch, S, kslice;
+};
+
+OzPlan oz_plan(const GemmF64& g) {
+  auto padded = [](int ra, int rb) {
+    const int bn = oz_bn(rb);
+    return (double)((ra + kOzM - 1) / kOzM) * kOzM * (double)((rb + bn - 1) / bn) * bn;
+  };
+  OzPlan p{};
+  p.swap = padded(g.N, g.M) < padded(g.M, g.N);
+  const int ra = p.swap ? g.N : g.M, rb = p.swap ? g.M : g.N;
+  p.BN = oz_bn(rb);
+  p.tiles = ((ra + kOzM - 1) / kOzM) * ((rb + p.BN - 1) / p.BN);
+  p.nch = (g.K + kOzChunk - 1) / kOzChunk;
+  p.S = 1;
+  if ((long long)g.nb1 * g.nb2 == 1 && p.nch > 1) {
+    // (a CTA over several chunks accumulates in its output, so beta != 0
+    // takes the slice sum)
+    const int want = g.beta != 0.0 ? 16 : p.tiles < 74 ? (148 + p.tiles - 1) / p.tiles : 1;
+    const int lo = (p.nch + 15) / 16, hi = std::min(16, p.nch);
+    int S = std::max(lo, std::min(want, hi));
+    const int cps = (p.nch + S - 1) / S;
+    p.S = (p.nch + cps - 1) / cps;
+    p.kslice = p.S > 1 ? cps * kOzChunk : 0;
+  }
+  return p;
+}
+
+}  // namespace
+
+bool gemm_oz_eligible(const GemmF64& g) {
+  if (g.K < 16 || g.M < 1 || g.N < 1) return false;
+  const long long nb = (long long)g.nb1 * g.nb2;
+  if (nb < 1 || nb > 65535) return false;
+  if (g.K > (nb == 1 ? 16 * 16 * kOzChunk : 16 * kOzChunk)) return false;
+  if (nb > 1 && g.K > kOzChunk && g.beta != 0.0) return false;  // no slice sum for batches
+  return std::max(g.M, g.N) >= 32 && (double)g.M * g.N * g.K * (double)nb >= (double)(1 << 21);
+}
+
+int gemm_oz_splits(const GemmF64& g) { return oz_plan(g).S; }
+
+void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext, double* scratch,
+                    size_t scratch_n) {
+  if (!gemm_oz_eligible(g)) throw QttError(QTT_ERR_SHAPE, "emulated FP64 GEMM shape");
+  {
+    const long long zb1 = g.nb1 - 1, zb2 = g.nb2 - 1;
+    const long long ea = g.tA ? (long long)(g.K - 1) * g.lda + g.M : (long long)(g.M - 1) * g.lda + g.K;
+    const long long eb = g.tB ? (long long)(g.N - 1) * g.ldb + g.K : (long long)(g.K - 1) * g.ldb + g.N;
+    const long long ec = (long long)(g.M - 1) * g.ldc + g.N;
+    check_range(g.A, zb1 * g.sA1 + zb2 * g.sA2 + ea, sizeof(double), ext ? "ext oz gemm A" : "oz gemm A");
+    check_range(g.B, zb1 * g.sB1 + zb2 * g.sB2 + eb, sizeof(double), ext ? "ext oz gemm B" : "oz gemm B");
+    check_range(g.C, zb1 * g.sC1 + zb2 * g.sC2 + ec, sizeof(double), ext ? "ext oz gemm C" : "oz gemm C");
+  }
+  oz_attr_once();
+  const OzPlan pl = oz_plan(g);
+  // op(A) (M x K): element (m, k); op(B)^T (N x K): element (n, k)
+  OzOperand opA{g.A, g.sA1, g.sA2, g.tA ? 1 : (long long)g.lda, g.tA ? (long long)g.lda : 1, g.M};
+  OzOperand opB{g.B, g.sB1, g.sB2, g.tB ? (long long)g.ldb : 1, g.tB ? 1 : (long long)g.ldb, g.N};
+  OzParams p{};
+  p.K = g.K;
+  p.nch = pl.nch;
+  p.BN = pl.BN;
+  p.nb2 = g.nb2;
+  p.swap = pl.swap ? 1 : 0;
+  p.skip = g.skip;
+  p.err = err;
+  int nz = g.nb1 * g.nb2;
+  if (pl.S > 1) {
+    // K slices into S partial products (M x N each), summed in slice order
+    const size_t need = (size_t)pl.S * g.M * g.N;
+    if (!scratch || scratch_n < need) throw QttError(QTT_ERR_SHAPE, "emulated GEMM: split-K scratch");
+    check_range(scratch, (long long)need, sizeof(double), "oz gemm partials");
+    opA.s1 = (long long)pl.kslice * opA.sk;
+    opB.s1 = (long long)pl.kslice * opB.sk;
+    opA.s2 = opB.s2 = 0;
+    p.kslice = pl.kslice;
+    p.nb2 = 1;
+    p.C = scratch;
+    p.ldc = g.N;
+    p.sC1 = (long long)g.M * g.N;
+    p.sC2 = 0;
+    p.alpha = 1.0;
+    p.beta = 0.0;
+    nz = pl.S;
+  } else {
+    p.C = g.C;
+    p.ldc = g.ldc;
+    p.sC1 = g.sC1;
+    p.sC2 = g.sC2;
+    p.alpha = g.alpha;
+    p.beta = g.beta;
+  }
+  p.a = pl.swap ? opB : opA;
+  p.b = pl.swap ? opA : opB;
+  dim3 grid((p.b.rows + p.BN - 1) / p.BN, (p.a.rows + kOzM - 1) / kOzM, nz);
+  pre_launch(s);
+  if (p.BN == 64)
+    k_gemm_oz<64><<<grid, kOzThreads, oz_smem(64), s>>>(p);
+  else if (p.BN == 32)
+    k_gemm_oz<32><<<grid, kOzThreads, oz_smem(32), s>>>(p);
+  else
+    k_gemm_oz<16><<<grid, kOzThreads, oz_smem(16), s>>>(p);
+  const char* name = "k_gemm_oz";
+  if (shape_profiling()) {
+    char tag[80];
+    snprintf(tag, sizeof tag, "%dx%dx%d b%d %d%d%s s%d", g.M, g.N, g.K, g.nb1 * g.nb2, g.tA,
+             g.tB, pl.swap ? " sw" : "", pl.S);
+    name = shape_name(name, tag);
+  }
+  post_launch(name, s, 2.0 * g.M * g.N * (double)g.K * g.nb1 * g.nb2);
+  if (pl.S > 1)
+    launch_sum_slices(scratch, pl.S, g.M, g.N, g.C, g.ldc, g.alpha, g.beta, g.skip, s, ext);
+}

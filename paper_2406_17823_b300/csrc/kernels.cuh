@@ -32,9 +32,21 @@ void launch_gemm_f64(const GemmF64& g, cudaStream_t s);
 // gemm_small_eligible shapes; others run tile 0).  All tiles give the same bits.
 void launch_gemm_f64_tile(const GemmF64& g, int tile, cudaStream_t s);
 bool gemm_small_eligible(const GemmF64& g);  // M <= 48, K <= 48, B not transposed
+// The mixed form's FP64 product on the BF16 tensor cores (Ozaki splitting,
+// gemm_oz.cu): same GemmF64 semantics, FP64-level accuracy, different
+// rounding from launch_gemm_f64.  Eligible shapes: K >= 16, at most 65535
+// batch entries, max(M, N) >= 32, at least 2^21 multiply-adds, and
+// K <= 1024 (batched) or K <= 16384 (unbatched).  An unbatched product
+// whose output tiles cannot fill the GPU is split over gemm_oz_splits(g)
+// K slices: `scratch` must then hold that many M x N partial products
+// (summed in slice order into C).
+bool gemm_oz_eligible(const GemmF64& g);
+int gemm_oz_splits(const GemmF64& g);
+void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext = false,
+                    double* scratch = nullptr, size_t scratch_n = 0);
 void launch_scale(const GemmF64& g, cudaStream_t s);  // C = beta C
 void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, double alpha,
-                       double beta, const int* skip, cudaStream_t s);
+                       double beta, const int* skip, cudaStream_t s, bool c_ext = false);
 
 // ---------------------------------------------------------------- QR
 // Householder QR of F = A (or A^T when inT): F = Q R, Q (m x r) with

@@ -530,10 +530,11 @@ void launch_sweep_final(const int* stop, long long* stats, cudaStream_t s) {
 }
 
 void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, double alpha,
-                       double beta, const int* skip, cudaStream_t s) {
+                       double beta, const int* skip, cudaStream_t s, bool c_ext) {
   if (M <= 0 || N <= 0 || S <= 0) return;
   check_range(P, (long long)S * M * N, sizeof(double), "sum_slices P");
-  check_range(C, (long long)(M - 1) * ldc + N, sizeof(double), "sum_slices C");
+  check_range(C, (long long)(M - 1) * ldc + N, sizeof(double),
+              c_ext ? "ext sum_slices C" : "sum_slices C");
   const long long tot = (long long)M * N;
   pre_launch(s);
   k_sum_slices<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P, S, M, N, C, ldc, alpha, beta,

@@ -12,6 +12,7 @@
 //
 // Matrices are gathered into a column-major work buffer first, so outputs
 // may alias the input storage.
+#include <stdio.h>
 #include <math.h>
 #include <stdlib.h>
 
@@ -443,7 +444,13 @@ void launch_qr_f64(const QrArgs& a, int mcap, int ccap, cudaStream_t s) {
   const double fm = mcap, fc = ccap < mcap ? ccap : mcap;
   const double flops = 4.0 * fm * fc * fc - 4.0 / 3.0 * fc * fc * fc;
   if ((ccap < mcap ? ccap : mcap) >= cluster_threshold() && launch_qr_cluster(a, mcap, s)) {
-    post_launch("k_qr_cluster", s, flops);
+    const char* name = "k_qr_cluster";
+    if (shape_profiling()) {
+      char tag[48];
+      snprintf(tag, sizeof tag, "%dx%d", mcap, ccap);
+      name = shape_name(name, tag);
+    }
+    post_launch(name, s, flops);
     return;
   }
   pre_launch(s);
@@ -472,7 +479,13 @@ bool launch_svd_subspace_f32(const SvdArgs& a, int mcap, int ncap, cudaStream_t 
   SvdArgs b = a;
   b.no_us = 1;
   if (!launch_svd_cluster(b, mcap, ncap, s, true)) return false;
-  post_launch("k_svd_cluster_f32", s, svd_flops(mcap, ncap));
+  const char* name = "k_svd_cluster_f32";
+  if (shape_profiling()) {
+    char tag[48];
+    snprintf(tag, sizeof tag, "%dx%d", mcap, ncap);
+    name = shape_name(name, tag);
+  }
+  post_launch(name, s, svd_flops(mcap, ncap));
   return true;
 }
 
@@ -498,7 +511,13 @@ void launch_svd_f64(const SvdArgs& a, int mcap, int ncap, cudaStream_t s) {
   check_range(a.VT.ptr, view_extent(a.VT), sizeof(double), "svd VT");
   check_range(a.work, (long long)svd_work_doubles(mcap, ncap), sizeof(double), "svd work");
   if ((mcap < ncap ? mcap : ncap) >= cluster_threshold() && launch_svd_cluster(a, mcap, ncap, s, false)) {
-    post_launch("k_svd_cluster", s, svd_flops(mcap, ncap));
+    const char* name = "k_svd_cluster";
+    if (shape_profiling()) {
+      char tag[48];
+      snprintf(tag, sizeof tag, "%dx%d", mcap, ncap);
+      name = shape_name(name, tag);
+    }
+    post_launch(name, s, svd_flops(mcap, ncap));
     return;
   }
   pre_launch(s);

@@ -81,6 +81,19 @@ void pre_launch(cudaStream_t s) {
   QTT_CUDA_CHECK(cudaEventRecord(t_pending, s));
 }
 
+bool shape_profiling() {
+  static const bool on = getenv("QTT_PROFILE_SHAPES") != nullptr;
+  return on;
+}
+
+const char* shape_name(const char* base, const char* tag) {
+  if (!shape_profiling()) return base;
+  static std::mutex mu;
+  static std::set<std::string> names;
+  std::lock_guard<std::mutex> lk(mu);
+  return names.insert(std::string(base) + "[" + tag + "]").first->c_str();
+}
+
 void post_launch(const char* name, cudaStream_t s, double flops) {
   count_launch();
   if (g_prof.on && t_pending) {
@@ -236,14 +249,32 @@ struct qtt_ctx_s {
 
 namespace {
 
+// Set for the duration of a call on a mixed-precision context: the FP64
+// products of eligible shapes run on the tensor cores (gemm_oz.cu) unless
+// QTT_OZAKI=0.
+thread_local bool t_gemm_emulate = false;
+
+bool ozaki_allowed() {
+  static const bool on = [] {
+    const char* e = getenv("QTT_OZAKI");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 struct CtxGuard {
   LaunchCounter* prev;
-  explicit CtxGuard(qtt_ctx c) : prev(g_launch_counter) {
+  bool prev_emulate;
+  explicit CtxGuard(qtt_ctx c) : prev(g_launch_counter), prev_emulate(t_gemm_emulate) {
     g_launch_counter = &c->launches;
     g_dev_err = c->d_err;
+    t_gemm_emulate = c->p.precision == QTT_PREC_MIXED && ozaki_allowed();
     cudaSetDevice(c->device);
   }
-  ~CtxGuard() { g_launch_counter = prev; }
+  ~CtxGuard() {
+    g_launch_counter = prev;
+    t_gemm_emulate = prev_emulate;
+  }
 };
 
 // Stream-ordered device buffer (cudaMallocAsync / cudaFreeAsync).
@@ -535,6 +566,28 @@ void gemm(const GemmF64& g, cudaStream_t s) {
   }();
   if (g.M <= 0 || g.N <= 0 || g.K <= 0 || g.nb1 * g.nb2 <= 0) {
     launch_gemm_f64(g, s);  // empty product or C = beta C
+    return;
+  }
+  if (t_gemm_emulate && gemm_oz_eligible(g)) {
+    const int S = gemm_oz_splits(g);
+    if (S <= 1) {
+      launch_gemm_oz(g, g_dev_err, s);
+      return;
+    }
+    // K slices: partial products in the caller's split-K scratch (inside
+    // captured loop bodies) or a stream-ordered buffer
+    const size_t need = (size_t)S * g.M * g.N;
+    DBuf<double> own;
+    double* P = t_gemm_scratch;
+    size_t cap = t_gemm_scratch_n;
+    if (P) {
+      if (need > cap) throw QttError(QTT_ERR_SHAPE, "split-K scratch too small");
+    } else {
+      own = DBuf<double>(need, s);
+      P = own.p;
+      cap = need;
+    }
+    launch_gemm_oz(g, g_dev_err, s, false, P, cap);
     return;
   }
   // QTT_GEMM_TILE=t: every product on tile t with the fixed K split (a
@@ -3767,6 +3820,30 @@ qtt_status qtt_gemm_tf32x3(qtt_ctx ctx, int M, int N, int K, const double* A, in
     const int S = tc_gemm_splits(M, N, K);
     DBuf<float> scr(tc_gemm_scratch_floats(M, N, K, S), s);
     tc_gemm_f64(s, M, N, K, A, lda, tA, B, ldb, tB, C, ldc, ctx->d_err, scr.p, scr.n);
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_gemm_ozaki(qtt_ctx ctx, int M, int N, int K, const double* A, int lda, int tA,
+                          long long sA, const double* B, int ldb, int tB, long long sB,
+                          double* C, int ldc, long long sC, int batch, double alpha,
+                          double beta) {
+  if (!ctx || !A || !B || !C || M < 1 || N < 1 || K < 1 || batch < 1) return QTT_ERR_ARG;
+  if (lda < (tA ? M : K) || ldb < (tB ? K : N) || ldc < N) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    GemmF64 g = gemm_plain(A, B, C, M, N, K, lda, ldb, ldc);
+    g.tA = tA ? 1 : 0;
+    g.tB = tB ? 1 : 0;
+    g.nb1 = batch;
+    g.sA1 = sA;
+    g.sB1 = sB;
+    g.sC1 = sC;
+    g.alpha = alpha;
+    g.beta = beta;
+    if (!gemm_oz_eligible(g)) return QTT_ERR_SHAPE;
+    const int S = gemm_oz_splits(g);
+    DBuf<double> part(S > 1 ? (size_t)S * M * N : 0, stream_of(ctx));
+    launch_gemm_oz(g, ctx->d_err, stream_of(ctx), true, part.p, part.n);
     return QTT_OK;
   });
 }

@@ -40,7 +40,7 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_rf_omega", "qtt_mlp_forward", "qtt_mlp_loss_grad", "qtt_mlp_train",
            "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
            "qtt_euler_step", "qtt_rk2_step", "qtt_inner", "qtt_graph_stats",
-           "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_tc_stats", "qtt_mpo_diff",
+           "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_gemm_ozaki", "qtt_tc_stats", "qtt_mpo_diff",
            "qtt_tke_spectrum")
 
 
@@ -106,6 +106,9 @@ def lib():
             "qtt_tc_stats": (c_int, [vp, POINTER(c_longlong), POINTER(c_longlong)]),
             "qtt_gemm_tf32x3": (c_int, [vp, c_int, c_int, c_int, vp, c_int, c_int, vp, c_int,
                                         c_int, vp, c_int]),
+            "qtt_gemm_ozaki": (c_int, [vp, c_int, c_int, c_int, vp, c_int, c_int, c_longlong, vp,
+                                       c_int, c_int, c_longlong, vp, c_int, c_longlong, c_int,
+                                       ctypes.c_double, ctypes.c_double]),
             "qtt_learned_set": (c_int, [vp, vp]),
             "qtt_learned_next_step": (c_int, [vp]),
             "qtt_learned_log": (c_int, [vp, vp, vp, c_int, ip]),
@@ -390,6 +393,35 @@ class Context:
         self._check(lib().qtt_gemm_tf32x3(self.h, M, N, K, c_void_p(A.data_ptr()), A.shape[1],
                                           int(transA), c_void_p(B.data_ptr()), B.shape[1],
                                           int(transB), c_void_p(C.data_ptr()), N))
+        return C
+
+    def gemm_ozaki(self, A, B, transA: bool = False, transB: bool = False, C=None,
+                   alpha: float = 1.0, beta: float = 0.0):
+        """alpha op(A) op(B) + beta C of FP64 device matrices (2-D, or 3-D
+        batches along the first axis) on the BF16 tensor cores by the Ozaki
+        splitting; returns C (a new tensor when C is None)."""
+        torch = _torch()
+        A = A.contiguous()
+        B = B.contiguous()
+        batched = A.dim() == 3
+        A3 = A if batched else A.unsqueeze(0)
+        B3 = B if batched else B.unsqueeze(0)
+        nb = A3.shape[0]
+        M, K = (A3.shape[2], A3.shape[1]) if transA else (A3.shape[1], A3.shape[2])
+        Kb, N = (B3.shape[2], B3.shape[1]) if transB else (B3.shape[1], B3.shape[2])
+        if K != Kb or B3.shape[0] != nb:
+            raise ValueError("inner dimensions or batch counts differ")
+        if C is None:
+            C = torch.zeros((nb, M, N) if batched else (M, N), dtype=torch.float64,
+                            device=A.device)
+        C3 = C if batched else C.unsqueeze(0)
+        if not C3.is_contiguous() or tuple(C3.shape) != (nb, M, N):
+            raise ValueError("C must be a contiguous (batch,) M x N tensor")
+        self._check(lib().qtt_gemm_ozaki(
+            self.h, M, N, K, c_void_p(A3.data_ptr()), A3.shape[2], int(transA),
+            A3.shape[1] * A3.shape[2], c_void_p(B3.data_ptr()), B3.shape[2], int(transB),
+            B3.shape[1] * B3.shape[2], c_void_p(C3.data_ptr()), N, M * N, nb, float(alpha),
+            float(beta)))
         return C
 
     def tc_stats(self):

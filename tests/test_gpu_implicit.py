@@ -3,7 +3,8 @@ QTT_RHS_IMPLICIT) on the GPU against the oracle's: each stage's right-hand
 side a u - h B(b) is never formed -- its Hadamard products and MPO terms are
 contracted inside the projection's environments (the nonlinear terms as
 products of a Hadamard MPO and D_j), and the initial guess is a u.  Dense
-fields within 1e-10 (FP64) of the oracle's rk4_step_implicit; at full rank
+fields within 1e-10 (FP64) and 1e-6 (mixed) of the oracle's
+rk4_step_implicit; at full rank
 also equal to the dense projected RK4 step; whole-step graphs replay it bit
 for bit.
 """
@@ -47,27 +48,32 @@ def test_implicit_rk4_full_rank_equals_dense(P):
         assert rel(ctx.to_dense(g[i]).cpu().numpy(), ref[i]) <= TOL
 
 
+@pytest.mark.parametrize("prec,tol", [(0, TOL), (1, 1e-6)])
 @pytest.mark.parametrize("n,chi", [(6, 16), (7, 32)])
-def test_implicit_rk4_matches_oracle(P, n, chi):
-    """Shear jet, paper solver settings, truncated (eps 1e-8, chi cap)."""
+def test_implicit_rk4_matches_oracle(P, n, chi, prec, tol):
+    """Shear jet, paper solver settings, truncated (eps 1e-8, chi cap); the
+    FP64 form at 1e-10, the mixed form (its products on the tensor cores by
+    the Ozaki splitting, its cuts by the tensor-core search) at 1e-6."""
     (u, v), dx = I.shear_jet(n, delta=2 * math.pi / 60, seed=0)
     dt, nu = 0.1 * dx / float(np.abs(u).max()), 1 / 2e5
     pp = dict(eps=1e-8, chi_max=chi)
-    ctx = P.Context(n, rhs_form=P.RHS_IMPLICIT, **pp)
+    ctx = P.Context(n, rhs_form=P.RHS_IMPLICIT, precision=prec, **pp)
     uq = [Q.from_dense(f, pp["eps"], chi) for f in (u, v)]
     g = [ctx.from_cores(c) for c in uq]
     ref = Q.rk4_step_implicit(uq, dt, nu, Q.Params(**pp), Q.build_operators(n, dx))
     ctx.rk4_step(g[0], g[1], dt, nu)
     for i in range(2):
-        assert rel(ctx.to_dense(g[i]).cpu().numpy(), Q.to_dense(ref[i])) <= TOL
+        assert rel(ctx.to_dense(g[i]).cpu().numpy(), Q.to_dense(ref[i])) <= tol
 
 
-def test_implicit_step_graph_replays_bit_for_bit(P):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_implicit_step_graph_replays_bit_for_bit(P, prec):
     (u, v), dx = I.shear_jet(6, seed=2)
     dt, nu = 0.1 * dx / float(np.abs(u).max()), 1e-4
     out = []
     for graphs in (0, 2):
-        ctx = P.Context(6, eps=1e-8, chi_max=16, graphs=graphs, rhs_form=P.RHS_IMPLICIT)
+        ctx = P.Context(6, eps=1e-8, chi_max=16, graphs=graphs, rhs_form=P.RHS_IMPLICIT,
+                        precision=prec)
         a, b = ctx.from_dense(u), ctx.from_dense(v)
         for _ in range(4):
             ctx.rk4_step(a, b, dt, nu)
