@@ -15,18 +15,27 @@ A step is one full RK4 step (four penalised Euler minimisations) of both
 velocity components; the state advances from step to step.
 
 The metric compares the plain FP64 form with the mixed form.  By default
-(--precision all) one run times three forms on the same initial state: W
-warm-up steps of each, then K timed steps of the mixed form (the line's
-value, ms_per_step, e2e and roofline), K timed steps of the FP64 form (the
-line's "fp64" object) and K timed steps of the paper's implicit form in FP64
-(the line's "fp64_implicit" object: the stages' right-hand sides inside the
-projection's environments, --rhs implicit).  All forms then take the same
-further steps (the profiled step, the e2e steps), after which
-"mixed_vs_fp64_rel_l2" is the relative L2 distance of the mixed and FP64
-dense fields (both components) and "fp64_implicit_vs_fp64_rel_l2" that of the
-two FP64 forms (different truncations of the same scheme, so of the order of
-the truncation error, not of rounding).  --precision both times the first
-two, mixed | fp64 one form only.
+(--precision all) one run times four forms on the same initial state: W
+warm-up steps of each, then K timed steps of each of
+  * the mixed form with the paper's implicit right-hand side (the stages'
+    nonlinear terms inside the projection's environments; FP64 products on
+    the BF16 tensor cores by the Ozaki splitting, tensor-core subspace
+    searches, FP64 factorisations): the line's value, ms_per_step, e2e and
+    roofline;
+  * the same scheme in FP64 (the line's "fp64_implicit" object);
+  * the mixed form with the explicit right-hand side (B formed by zip-up
+    Hadamard products; "mixed_explicit");
+  * the explicit scheme in FP64 ("fp64").
+All forms then take the same further steps (the profiled step, the e2e
+steps), after which "mixed_vs_fp64_rel_l2" is the relative L2 distance of
+the mixed and FP64 dense fields of the implicit scheme (both components),
+"mixed_explicit_vs_fp64_rel_l2" that of the explicit scheme, and
+"fp64_implicit_vs_fp64_rel_l2" that of the two FP64 schemes (different
+truncations of the same equations, so of the order of the truncation
+error, not of rounding).  --precision both times the explicit mixed and
+FP64 forms, mixed | fp64 one explicit form only; with --rhs implicit the
+named forms take the implicit right-hand side.  "oz_gemm" and "tc_gemm"
+time the two tensor-core products alone.
 
 One JSON line is printed by rank 0.  With torchrun (N > 1) every rank runs
 its own trajectory on its own GPU (replicas: the method has no exchange
@@ -445,10 +454,41 @@ def e2e_steps(torch, form, n_steps, flush, world):
             "d2h_bytes_per_step": d2h}
 
 
+OZ_PAIRS = 36  # slice products of the Ozaki splitting per FP64 product (8 slices, p + q <= 7)
+
+
 def roofline_of(torch, dev, prof):
     """Roofline of the kernel with the largest share of device time."""
     dom, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
     tot_ms = sum(v["ms"] for v in prof.values())
+    if dom.startswith("k_gemm_oz"):
+        # FP64 products on the BF16 tensor cores: the scheme's BF16 slice
+        # products against the sustained BF16 peak (a kernel inside a long
+        # step); the FP64-equivalent rate against DGEMM beside it
+        peaks = measured_peaks()
+        bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        avg_ms = rec["ms"] / rec["launches"]
+        fpl = rec["flops"] / rec["launches"]
+        f64eq = fpl / (avg_ms * 1e-3) / 1e12
+        achieved = OZ_PAIRS * f64eq
+        dpk = gemm_peak(torch, dev, torch.float64)
+        return {"kernel": dom, "bound": "tensor", "achieved": achieved,
+                "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16 if bf16 else None,
+                "traffic": NCU_TRAFFIC.get(dom),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                  "launch of the projection's 12288 x 256 x 64 product; see "
+                                  "profiles/",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
+                "achieved_source": f"{OZ_PAIRS} BF16 slice products per FP64 product "
+                                   "(algorithmic 2MNK each) / launch time",
+                "fp64_equivalent_tflops": f64eq, "fp64_dgemm_peak": dpk,
+                "fp64_equivalent_over_dgemm": f64eq / dpk if dpk else None,
+                "share_of_device_time": rec["ms"] / tot_ms if tot_ms else None,
+                "launches_timed": rec["launches"], "avg_launch_ms": avg_ms,
+                "flops_per_launch": fpl,
+                "timing_source": "one step after the timed region, launched eagerly under the "
+                                 "library's launch profiler",
+                "kernel_shares": {k: round(v["ms"] / tot_ms, 4) for k, v in prof.items()}}
     # the dominant kernel's arithmetic type decides the pipe it is bound by:
     # the FP32 subspace search of the mixed form runs on the FP32 pipe
     f32_kernel = dom.endswith("_f32")
@@ -511,6 +551,34 @@ def tc_gemm_record(torch, ctx, peaks):
             "frac": tensor_tflops / tf32_peak if tf32_peak else None,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops x 1/2 (TF32 / BF16 nominal ratio; "
                            "of measured)"}
+
+
+def oz_gemm_record(torch, ctx, peaks):
+    """Throughput of the emulated FP64 product (qtt_gemm_ozaki: eight BF16
+    slices per K chunk of 64 on tcgen05, exact FP32 accumulation, one FP64
+    rounding) at the projection's dominant shape and at a large K = 64
+    shape: CUDA events over 10 calls after 3 warm-up calls."""
+    out = []
+    for (M, N, K) in ((12288, 256, 64), (16384, 4096, 64)):
+        A = torch.randn(M, K, dtype=torch.float64, device="cuda")
+        B = torch.randn(K, N, dtype=torch.float64, device="cuda")
+        C = torch.empty(M, N, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            ctx.gemm_ozaki(A, B, C=C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            ctx.gemm_ozaki(A, B, C=C)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        f64eq = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        bf16 = peaks.get("bf16_tflops")
+        out.append({"shape": [M, N, K], "ms": ms, "fp64_equivalent_tflops": f64eq,
+                    "tensor_tflops": OZ_PAIRS * f64eq, "bf16_peak_tflops": bf16,
+                    "frac": OZ_PAIRS * f64eq / bf16 if bf16 else None})
+    return {"shapes": out, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; of measured)"}
 
 
 def rel_l2(fa, fb):
@@ -658,12 +726,13 @@ def main():
     B = max(1, args.batched)
     if B > 1:
         w["workload"] = f"{w['workload']}_x{B}_trajectories"
-    names = {"all": ["mixed", "fp64", "fp64_implicit"], "both": ["mixed", "fp64"],
-             "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
+    names = {"all": ["mixed_implicit", "fp64_implicit", "mixed", "fp64"],
+             "both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
     if B > 1 or args.rhs == "implicit":
-        names = names[:1] if args.precision in ("all", "both") else names
-    precs = {"mixed": P.PREC_MIXED, "fp64": P.PREC_FP64, "fp64_implicit": P.PREC_FP64}
-    rhs_of = {"fp64_implicit": P.RHS_IMPLICIT}
+        names = ["mixed"] if args.precision in ("all", "both") else names
+    precs = {"mixed": P.PREC_MIXED, "fp64": P.PREC_FP64, "fp64_implicit": P.PREC_FP64,
+             "mixed_implicit": P.PREC_MIXED}
+    rhs_of = {"fp64_implicit": P.RHS_IMPLICIT, "mixed_implicit": P.RHS_IMPLICIT}
     forms = {nm: make_form(P, w, precs[nm], graphs, B, local, rank, rhs_of.get(nm))
              for nm in names}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -696,13 +765,16 @@ def main():
         for _ in range(n_e2e):
             forms[nm]["step"]()
     torch.cuda.synchronize()
-    cmp = cmp_imp = None
-    if "mixed" in names and "fp64" in names:
+    cmp = cmp_imp = cmp_mi = None
+    if len(names) > 1:
         fields = {nm: [forms[nm]["ctxs"][0].to_dense(x).cpu().numpy()
                        for x in forms[nm]["states"][0]] for nm in names}
-        cmp = rel_l2(fields["mixed"], fields["fp64"])
-        if "fp64_implicit" in names:
+        if "mixed" in names and "fp64" in names:
+            cmp = rel_l2(fields["mixed"], fields["fp64"])
+        if "fp64_implicit" in names and "fp64" in names:
             cmp_imp = rel_l2(fields["fp64_implicit"], fields["fp64"])
+        if "mixed_implicit" in names and "fp64_implicit" in names:
+            cmp_mi = rel_l2(fields["mixed_implicit"], fields["fp64_implicit"])
     steps_taken = args.warmup + args.steps + 1 + n_e2e
 
     if rank != 0:
@@ -746,14 +818,17 @@ def main():
                           "(of measured)"}
     clocks = clk.summary()
     peaks = measured_peaks()
-    tcg = None
-    if "mixed" in names:
-        tcg = tc_gemm_record(torch, forms["mixed"]["ctxs"][0], peaks)
+    tcg = ozg = None
+    mixed_nm = next((nm for nm in names if nm.startswith("mixed")), None)
+    if mixed_nm:
+        tcg = tc_gemm_record(torch, forms[mixed_nm]["ctxs"][0], peaks)
+        ozg = oz_gemm_record(torch, forms[mixed_nm]["ctxs"][0], peaks)
     hs = sums[head]
     line = {"metric": METRIC, "value": hs["value"], "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": hs["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head.startswith("fp64") else "tf32x3/f32/f64",
+            "dtype": ("f64" if head.startswith("fp64") else
+                      "f64 products as bf16 slices (Ozaki) / tf32x3 search / f64 factorisations"),
             "data": "synthetic (seeded shear-jet initial condition)",
             "timing": ("CUDA events on the stepping stream" if B == 1 else
                        "host clock between device-wide synchronisations (library-owned streams)"),
@@ -766,19 +841,34 @@ def main():
             "e2e": e2e, "gpu_launches": hs["gpu_launches"], "roofline": hs["roofline"],
             "tc_subspace_searches_timed": hs["tc_subspace_searches_timed"],
             "cpu_baseline": cpu, "clocks": clocks, "wall_s": hs["wall_s"]}
-    if "mixed" in names and "fp64" in names:
+    implicit_form = ("the paper's implicit right-hand side (nonlinear terms inside the "
+                     "projection's environments)")
+    if head == "mixed_implicit":
+        line["form"] = implicit_form + ", mixed precision"
+        line["fp64_implicit"] = sums["fp64_implicit"]
+        line["fp64_implicit"]["form"] = implicit_form + ", FP64"
+        line["mixed_vs_fp64_rel_l2"] = cmp_mi
+        line["mixed_vs_fp64_forms"] = ["mixed_implicit", "fp64_implicit"]
+        line["mixed_vs_fp64_after_steps"] = steps_taken
+        line["mixed_over_fp64"] = hs["value"] / sums["fp64_implicit"]["value"]
+        if "mixed" in names:
+            line["mixed_explicit"] = sums["mixed"]
+            line["mixed_explicit"]["form"] = "explicit right-hand side (B formed), mixed precision"
+            line["mixed_explicit_vs_fp64_rel_l2"] = cmp
+        if "fp64" in names:
+            line["fp64"] = sums["fp64"]
+            line["fp64"]["form"] = "explicit right-hand side (B formed), FP64"
+            line["fp64_implicit_vs_fp64_rel_l2"] = cmp_imp
+            line["mixed_over_fp64_explicit"] = hs["value"] / sums["fp64"]["value"]
+    elif "mixed" in names and "fp64" in names:
         line["fp64"] = sums["fp64"]
         line["mixed_vs_fp64_rel_l2"] = cmp
         line["mixed_vs_fp64_after_steps"] = steps_taken
         line["mixed_over_fp64"] = hs["value"] / sums["fp64"]["value"]
-    if "fp64_implicit" in names:
-        line["fp64_implicit"] = sums["fp64_implicit"]
-        line["fp64_implicit"]["form"] = ("the paper's implicit right-hand side (nonlinear terms "
-                                         "inside the projection's environments), FP64")
-        line["fp64_implicit_vs_fp64_rel_l2"] = cmp_imp
-        line["fp64_implicit_over_fp64"] = sums["fp64_implicit"]["value"] / sums["fp64"]["value"]
     if tcg:
         line["tc_gemm"] = tcg
+    if ozg:
+        line["oz_gemm"] = ozg
     line["peaks_file"] = {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")}
     print(json.dumps(line), flush=True)
     if dist is not None:
