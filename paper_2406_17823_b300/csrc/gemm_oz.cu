@@ -22,20 +22,25 @@
 //    16-byte chunks XOR-ed with the row index mod 8).  Integer arithmetic
 //    on the FP64 bit patterns only.
 //  * Products.  One thread issues tcgen05.mma kind::f16 (BF16 x BF16, FP32
-//    accumulation, M = 128, N = BN, K = 16) for the 36 slice pairs, pairs
-//    of equal p + q = d into accumulator d of eight in tensor memory
-//    (8 BN columns).  A diagonal sums at most 8 x 64 products of magnitude
+//    accumulation, M = 128, K = 16) for the 36 slice pairs, pairs of equal
+//    p + q = d into accumulator d of eight in tensor memory (8 BN columns):
+//    A_p against the consecutive B slices q = 0 .. 7 - p as one MMA of
+//    N = (8 - p) BN (two when that exceeds 256) whose output starts at
+//    accumulator p.  A diagonal sums at most 8 x 64 products of magnitude
 //    below 2^14, so every partial sum is an integer below 2^23 and the FP32
 //    accumulation is exact.
 //  * Epilogue.  The sixteen warps read the accumulators (warps w, w + 4,
 //    w + 8, w + 12 share TMEM lanes 32 (w mod 4) .. and split the 8-column
 //    groups), combine the exact integers as T = sum_d D_d 2^(7 (7 - d)) in
-//    128-bit integer arithmetic and round T 2^(eA + eB - 63) to FP64 by
-//    integer operations (round to nearest even).  The first chunk stores
-//    the result, later chunks add theirs to it in order; the last applies
-//    alpha (and beta, which only a one-chunk CTA takes: an unbatched product
-//    with beta != 0 and several chunks is split over K slices whose partial
-//    products the slice sum combines, in order, with alpha and beta).  The wait for each
+//    64-bit integer arithmetic and round T 2^(eA + eB - 63) to FP64 by
+//    integer operations (round to nearest even).  A one-chunk item writes
+//    alpha x + beta C straight from the accumulator rows; with several
+//    chunks the results are staged in shared memory and C is updated in a
+//    coalesced pass: the first chunk stores, later ones add theirs in
+//    order, the last applies alpha (beta is not taken there: an unbatched
+//    product with beta != 0 and several chunks is split over K slices whose
+//    partial products the slice sum combines, in order, with alpha and
+//    beta).  The wait for each
 // chunk's MMAs is bounded by one second of global time; a wait that gives
 // up sets QTT_DEVERR_TIMEOUT, skips the output, frees the tensor memory and
 // returns.
@@ -87,7 +92,8 @@ struct OzOperand {
 struct OzParams {
   OzOperand a, b;      // a: the 128-row side, b: the BN-row side
   int K, nch, BN;
-  int kslice;          // > 0: blockIdx.z is a K slice [z kslice, (z + 1) kslice)
+  int kslice;          // > 0: item z is a K slice [z kslice, (z + 1) kslice)
+  int nz;              // batch entries (or K slices)
   int nb2;
   int swap;            // 0: C(r_a, r_b); 1: C(r_b, r_a)
   double* C;
@@ -130,24 +136,36 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
                     ((k & 7) << 1));
 }
 
-// FP64 value of T 2^scale, T = H 2^28 + L, rounded once to nearest even
-// (integer operations; ldexp only for a subnormal or overflowing result).
+// FP64 value of T 2^scale, T = H 2^28 + L (|H|, |L| < 2^47), rounded once to
+// nearest even, in 64-bit integer operations: T is first brought to sign
+// and magnitude A 2^28 + R with 0 <= R < 2^28; below 2^53 it is exact,
+// otherwise its top 53 bits are A's bits and R's upper bits, rounded by R's
+// remaining bits (ldexp only for a subnormal or overflowing result).
 __device__ __forceinline__ double assemble(long long H, long long L, int scale) {
-  const __int128 T = ((__int128)H << 28) + (__int128)L;
-  if (T == 0) return 0.0;
-  const unsigned long long sgn = T < 0 ? 1ull : 0ull;
-  const unsigned __int128 U = (unsigned __int128)(T < 0 ? -T : T);
-  const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
-  const int nb = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-  int sh = nb - 53;
-  unsigned long long m;
-  if (sh <= 0) {
-    m = lo << (-sh);
+  const long long Hn = H + (L >> 28);  // arithmetic shift: floor(L / 2^28)
+  const unsigned long long R = (unsigned long long)L & 0xFFFFFFFull;
+  unsigned long long A, Rn, sgn;
+  if (Hn < 0) {  // -T = (-Hn - 1) 2^28 + (2^28 - R)  (or -Hn 2^28 when R = 0)
+    sgn = 1ull;
+    A = R ? (unsigned long long)(-Hn - 1) : (unsigned long long)(-Hn);
+    Rn = R ? 0x10000000ull - R : 0ull;
   } else {
-    const unsigned __int128 q = U >> sh;
-    const unsigned __int128 rem = U - (q << sh);
-    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-    m = (unsigned long long)q;
+    sgn = 0ull;
+    A = (unsigned long long)Hn;
+    Rn = R;
+  }
+  if ((A | Rn) == 0ull) return 0.0;
+  unsigned long long m;
+  int sh;
+  if (A < (1ull << 25)) {
+    const unsigned long long U = (A << 28) | Rn;  // < 2^53: exact
+    const int nb = 64 - __clzll((long long)U);
+    m = U << (53 - nb);
+    sh = nb - 53;
+  } else {
+    sh = (64 - __clzll((long long)A)) - 25;  // bits of A + 28 - 53, 1 .. 22
+    m = (A << (28 - sh)) | (Rn >> sh);
+    const unsigned long long rem = Rn & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
     if (rem > half || (rem == half && (m & 1ull))) {
       m++;
       if (m >> 53) {
@@ -187,20 +205,24 @@ __device__ __forceinline__ void pair_digits(double x0, double x1, int e, uint32_
 }
 
 // Where thread t's pair i of a tile of R rows lies (R / 16 pairs per thread,
-// kOzThreads = 512): with k contiguous in memory warp w takes rows w,
-// w + 16, ... and lane l the pair (2 l, 2 l + 1); otherwise consecutive
-// threads take consecutive rows and a row's 32 pairs are dealt over
-// kOzThreads / R threads.
+// kOzThreads = 512).  With k contiguous in memory warp w takes rows w,
+// w + 16, ... and lane l the pair (2 l, 2 l + 1).  Otherwise (rows contiguous)
+// each warp step covers a block of 8 consecutive rows x 4 consecutive pairs
+// (lane l: row l mod 8, pair l / 8): loads are 64-byte row runs and the
+// swizzled shared-memory stores of a warp fall in 32 different banks.  Block
+// W = 16 i + w takes rows 8 (W mod R/8) .. and pairs 4 (W div R/8) ..; for
+// R = 128 a thread keeps one row and its warp holds all of that row's pairs.
 template <int R>
 __device__ __forceinline__ void pair_at(bool kc, int i, int& r, int& k) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   if (kc) {
-    r = (tid >> 5) + 16 * i;
-    k = 2 * (tid & 31);
+    r = w + 16 * i;
+    k = 2 * l;
   } else {
-    constexpr int tpr = kOzThreads / R;
-    r = tid % R;
-    k = 2 * (tid / R + tpr * i);
+    constexpr int kRB = R / 8;
+    const int W = 16 * i + w;
+    r = 8 * (W % kRB) + (l & 7);
+    k = 2 * (4 * (W / kRB) + (l >> 3));
   }
 }
 
@@ -209,86 +231,96 @@ __device__ __forceinline__ void load_pair(const OzOperand& o, const double* base
                                           int klen, int r, int k, double& x0, double& x1) {
   const bool live = r0 + r < o.rows;
   const double* row = base + (long long)(r0 + r) * o.sr;
+  if (live && o.sk == 1 && k + 1 < klen && (((uintptr_t)(row + k)) & 15) == 0) {
+    const double2 v = *(const double2*)(row + k);  // both elements in one 16-byte load
+    x0 = v.x;
+    x1 = v.y;
+    return;
+  }
   x0 = (live && k < klen) ? row[(long long)k * o.sk] : 0.0;
   x1 = (live && k + 1 < klen) ? row[(long long)(k + 1) * o.sk] : 0.0;
 }
 
 // One K chunk of a tile of R rows (base already at the chunk's first k):
 // the rows' largest magnitudes into mx[] and the eight slices into dst
-// (slice p at dst + p R 128 bytes).  Batches of four pairs per thread, every
-// load of a batch issued before its first use.  With k contiguous a row
-// lives in one warp and its maximum is a warp reduction; otherwise the
-// maxima go through shared memory first (two passes over the loads).
+// (slice p at dst + p R 128 bytes).  Every load of the thread's R / 16 pairs
+// is issued before the first use.  With k contiguous a row lives in one warp
+// and its maximum is a warp reduction; otherwise over the 4 lanes of the row
+// in each warp and, when the row spans several warps (R < 128), shared
+// memory.
 template <int R>
 __device__ void slice_tile(const OzOperand& o, const double* base, int r0, int klen,
                            unsigned long long* mx, uint8_t* dst) {
-  constexpr int kPairs = R / 16, kBatch = kPairs < 4 ? kPairs : 4;
+  constexpr int kPairs = R / 16;
   constexpr uint32_t slice_bytes = (uint32_t)R * 128;
   const bool kc = o.sk == 1;
+  const int lane = threadIdx.x & 31;
+  double x[2 * kPairs];
+#pragma unroll
+  for (int i = 0; i < kPairs; i++) {
+    int r, k;
+    pair_at<R>(kc, i, r, k);
+    load_pair<R>(o, base, r0, klen, r, k, x[2 * i], x[2 * i + 1]);
+  }
+  int e[kPairs];
   if (kc) {
-#pragma unroll 1
-    for (int i0 = 0; i0 < kPairs; i0 += kBatch) {
-      double x[2 * kBatch];
 #pragma unroll
-      for (int i = 0; i < kBatch; i++) {
-        int r, k;
-        pair_at<R>(true, i0 + i, r, k);
-        load_pair<R>(o, base, r0, klen, r, k, x[2 * i], x[2 * i + 1]);
-      }
+    for (int i = 0; i < kPairs; i++) {
+      unsigned long long m = max(abs_bits(x[2 * i]), abs_bits(x[2 * i + 1]));
 #pragma unroll
-      for (int i = 0; i < kBatch; i++) {
-        int r, k;
-        pair_at<R>(true, i0 + i, r, k);
-        unsigned long long m = max(abs_bits(x[2 * i]), abs_bits(x[2 * i + 1]));
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
-        if ((threadIdx.x & 31) == 0) mx[r] = m;
-        const int e = row_scale(m);
-        uint32_t w[kOzSlices];
-        pair_digits(e == kOzBad ? 0.0 : x[2 * i], e == kOzBad ? 0.0 : x[2 * i + 1], e, w);
-        const uint32_t off = sw128_off(r, k);
-#pragma unroll
-        for (int p = 0; p < kOzSlices; p++) *(uint32_t*)(dst + p * slice_bytes + off) = w[p];
-      }
+      for (int s = 16; s > 0; s >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, s));
+      int r, k;
+      pair_at<R>(true, i, r, k);
+      if (lane == 0) mx[r] = m;
+      e[i] = row_scale(m);
     }
   } else {
-    const int r = threadIdx.x % R;
-    unsigned long long m = 0;
-#pragma unroll 1
-    for (int i0 = 0; i0 < kPairs; i0 += kBatch) {
-      double x[2 * kBatch];
+    // the pairs i of one thread share a row when R = 128; in general pair i
+    // lies in row block (16 i + w) mod R/8
+    unsigned long long m[kPairs];
 #pragma unroll
-      for (int i = 0; i < kBatch; i++) {
-        int rr, k;
-        pair_at<R>(false, i0 + i, rr, k);
-        load_pair<R>(o, base, r0, klen, rr, k, x[2 * i], x[2 * i + 1]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2 * kBatch; i++) m = max(m, abs_bits(x[i]));
+    for (int i = 0; i < kPairs; i++) {
+      m[i] = max(abs_bits(x[2 * i]), abs_bits(x[2 * i + 1]));
+      m[i] = max(m[i], __shfl_xor_sync(0xffffffffu, m[i], 8));
+      m[i] = max(m[i], __shfl_xor_sync(0xffffffffu, m[i], 16));
     }
-    atomicMax(&mx[r], m);
+    if (R == 128) {
+      unsigned long long mm = 0;
+#pragma unroll
+      for (int i = 0; i < kPairs; i++) mm = max(mm, m[i]);
+      int r, k;
+      pair_at<R>(false, 0, r, k);
+      if (lane < 8) mx[r] = mm;
+#pragma unroll
+      for (int i = 0; i < kPairs; i++) e[i] = row_scale(mm);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPairs; i++) {
+        int r, k;
+        pair_at<R>(false, i, r, k);
+        if (lane < 8) atomicMax(&mx[r], m[i]);
+      }
+    }
+  }
+  if (!kc && R != 128) {
     __syncthreads();
-    const int e = row_scale(mx[r]);
-#pragma unroll 1
-    for (int i0 = 0; i0 < kPairs; i0 += kBatch) {
-      double x[2 * kBatch];
 #pragma unroll
-      for (int i = 0; i < kBatch; i++) {
-        int rr, k;
-        pair_at<R>(false, i0 + i, rr, k);
-        load_pair<R>(o, base, r0, klen, rr, k, x[2 * i], x[2 * i + 1]);
-      }
-#pragma unroll
-      for (int i = 0; i < kBatch; i++) {
-        int rr, k;
-        pair_at<R>(false, i0 + i, rr, k);
-        uint32_t w[kOzSlices];
-        pair_digits(e == kOzBad ? 0.0 : x[2 * i], e == kOzBad ? 0.0 : x[2 * i + 1], e, w);
-        const uint32_t off = sw128_off(rr, k);
-#pragma unroll
-        for (int p = 0; p < kOzSlices; p++) *(uint32_t*)(dst + p * slice_bytes + off) = w[p];
-      }
+    for (int i = 0; i < kPairs; i++) {
+      int r, k;
+      pair_at<R>(false, i, r, k);
+      e[i] = row_scale(mx[r]);
     }
+  }
+#pragma unroll
+  for (int i = 0; i < kPairs; i++) {
+    int r, k;
+    pair_at<R>(kc, i, r, k);
+    uint32_t w[kOzSlices];
+    const bool bad = e[i] == kOzBad;
+    pair_digits(bad ? 0.0 : x[2 * i], bad ? 0.0 : x[2 * i + 1], e[i], w);
+    const uint32_t off = sw128_off(r, k);
+#pragma unroll
+    for (int p = 0; p < kOzSlices; p++) *(uint32_t*)(dst + p * slice_bytes + off) = w[p];
   }
 }
 
@@ -327,6 +359,13 @@ __device__ __forceinline__ void tmem_ld_diagonals(uint32_t taddr, float (&D)[kOz
     for (int j = 0; j < 8; j++) D[d][j] = __uint_as_float(r[8 * d + j]);
 }
 
+// D (an integer-valued FP32 accumulator) as an integer: |D| < 2^22 by the
+// FP32 addition of 1.5 2^23 (exact, the sum's low mantissa bits are D),
+// larger ones by conversion.
+__device__ __forceinline__ int int_small(float D) {
+  return __float_as_int(D + 12582912.0f) - 0x4B400000;
+}
+
 template <int BN>
 __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
   static_assert(BN == 16 || BN == 32 || BN == 64, "output tile width");
@@ -335,19 +374,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
   uint8_t* base = (uint8_t*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sa = base;                          // 8 slices x 128 rows x 128 B
   uint8_t* sb = base + kOzSlices * kOzTileA;   // 8 slices x BN rows x 128 B
+  // a chunk's rounded products, staged for coalesced output once the MMAs
+  // have read the A slices (128 rows of BN + 1 doubles)
+  double* stage = (double*)sa;
+  constexpr int kST = BN + 1;
   __shared__ unsigned long long mxa[kOzM], mxb[BN];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int z = blockIdx.z, z1 = z / g.nb2, z2 = z % g.nb2;
-  const int ra0 = blockIdx.y * kOzM, rb0 = blockIdx.x * BN;
-  // this CTA's K extent (a K slice: the batch strides step along K)
-  const int Kz = g.kslice > 0 ? min(g.kslice, g.K - z * g.kslice) : g.K;
-  const int nch = (Kz + kOzChunk - 1) / kOzChunk;
-  const double* pa = g.a.p + z1 * g.a.s1 + z2 * g.a.s2;
-  const double* pb = g.b.p + z1 * g.b.s1 + z2 * g.b.s2;
-  double* cz = g.C + z1 * g.sC1 + z2 * g.sC2;
   constexpr uint32_t ncols = 8u * (uint32_t)BN;  // 128, 256 or 512
   const uint32_t mbar = smem_u32(&bar);
 
@@ -372,82 +407,137 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
   // the 8-column groups w >> 2, (w >> 2) + 4, ...
   const int quarter = warp & 3, part = warp >> 2;
   const int r = quarter * 32 + lane;
-  const int ga = ra0 + r;
-  const uint32_t idesc = idesc_bf16(kOzM, BN);
-  for (int c = 0; c < nch; c++) {
-    const int k0 = c * kOzChunk, klen = min(kOzChunk, Kz - k0);
-    for (int i = tid; i < kOzM; i += kOzThreads) mxa[i] = 0ull;
-    if (tid < BN) mxb[tid] = 0ull;
-    __syncthreads();  // zeroed row maxima
-    slice_tile<kOzM>(g.a, pa + (long long)k0 * g.a.sk, ra0, klen, mxa, sa);
-    slice_tile<BN>(g.b, pb + (long long)k0 * g.b.sk, rb0, klen, mxb, sb);
-    // the generic-proxy writes become visible to the tensor core's reads
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  const int tiles_b = (g.b.rows + BN - 1) / BN, tiles_a = (g.a.rows + kOzM - 1) / kOzM;
+  const int items = tiles_b * tiles_a * g.nz;
+  uint32_t phase = 0;  // completed waits on the MMA barrier
+  // persistent: work items (B tile, A tile, batch entry or K slice) dealt
+  // over the CTAs
+  for (int item = blockIdx.x; item < items && s_ok; item += gridDim.x) {
+    const int bx = item % tiles_b, rest = item / tiles_b;
+    const int by = rest % tiles_a, z = rest / tiles_a;
+    const int z1 = z / g.nb2, z2 = z % g.nb2;
+    const int ra0 = by * kOzM, rb0 = bx * BN;
+    // this item's K extent (a K slice: the batch strides step along K)
+    const int Kz = g.kslice > 0 ? min(g.kslice, g.K - z * g.kslice) : g.K;
+    const int nch = (Kz + kOzChunk - 1) / kOzChunk;
+    const double* pa = g.a.p + z1 * g.a.s1 + z2 * g.a.s2;
+    const double* pb = g.b.p + z1 * g.b.s1 + z2 * g.b.s2;
+    double* cz = g.C + z1 * g.sC1 + z2 * g.sC2;
+    for (int c = 0; c < nch; c++) {
+      const int k0 = c * kOzChunk, klen = min(kOzChunk, Kz - k0);
+      for (int i = tid; i < kOzM; i += kOzThreads) mxa[i] = 0ull;
+      if (tid < BN) mxb[tid] = 0ull;
+      __syncthreads();  // zeroed row maxima; the previous chunk's output read
+      slice_tile<kOzM>(g.a, pa + (long long)k0 * g.a.sk, ra0, klen, mxa, sa);
+      slice_tile<BN>(g.b, pb + (long long)k0 * g.b.sk, rb0, klen, mxb, sb);
+      // the generic-proxy writes become visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint64_t da0 = sw128_desc(smem_u32(sa)), db0 = sw128_desc(smem_u32(sb));
+        // the descriptor's address field is the byte address / 16.  The B
+        // slices lie one after another, so A_p times B_q0 .. B_q1 is one MMA
+        // of N = (q1 - q0 + 1) BN whose output columns start at accumulator
+        // p + q0: every pair (p, q) lands on its diagonal p + q.  N <= 256.
+        constexpr int kQ = 256 / BN < kOzSlices ? 256 / BN : kOzSlices;  // B slices per MMA
+        for (int p = 0; p < kOzSlices; p++)
+          for (int q0 = 0; q0 + p < kOzSlices; q0 += kQ) {
+            const int nq = min(kQ, kOzSlices - p - q0);
+            const uint32_t id = idesc_bf16(kOzM, nq * BN);
+            const uint32_t dcol = tmem + (uint32_t)((p + q0) * BN);
+#pragma unroll
+            for (int kk = 0; kk < kOzChunk / 16; kk++)
+              // first write of every accumulator: p = 0, kk = 0
+              mma_bf16(dcol, da0 + (uint64_t)(p * (kOzTileA / 16) + kk * 2),
+                       db0 + (uint64_t)(q0 * (BN * 128 / 16) + kk * 2), id,
+                       (p == 0 && kk == 0) ? 0u : 1u);
+          }
+        tc_commit(mbar);
+      }
+      __syncwarp();
+      const bool ok = mbar_wait(mbar, phase & 1u);
+      phase++;
+      if (!ok) atomicExch(&s_ok, 0);
       tc_fence_after();
-      const uint64_t da0 = sw128_desc(smem_u32(sa)), db0 = sw128_desc(smem_u32(sb));
-      // the descriptor's address field is the byte address / 16
-      for (int p = 0; p < kOzSlices; p++)
-        for (int q = 0; q + p < kOzSlices; q++) {
-          const uint32_t dcol = tmem + (uint32_t)((p + q) * BN);
-#pragma unroll
-          for (int kk = 0; kk < kOzChunk / 16; kk++)
-            // first write of accumulator p + q: p = 0, kk = 0
-            mma_bf16(dcol, da0 + (uint64_t)(p * (kOzTileA / 16) + kk * 2),
-                     db0 + (uint64_t)(q * (BN * 128 / 16) + kk * 2), idesc,
-                     (p == 0 && kk == 0) ? 0u : 1u);
-        }
-      tc_commit(mbar);
-    }
-    __syncwarp();
-    const bool ok = mbar_wait(mbar, (uint32_t)(c & 1));
-    if (!ok) atomicExch(&s_ok, 0);
-    tc_fence_after();
-    __syncthreads();
-    if (!s_ok) break;
-    // this chunk's exact product, rounded once; the first chunk stores it,
-    // later ones add it to what this thread stored (in chunk order); alpha
-    // (and beta, for a one-chunk CTA) with the last
-    const bool last = c == nch - 1;
-    const int ea = row_scale(mxa[r]);
+      __syncthreads();
+      if (!s_ok) break;
+      // this chunk's exact product, rounded once: a one-chunk item writes it
+      // (with alpha and beta) straight from the accumulator rows; otherwise
+      // it is staged by row for the coalesced accumulation below
+      const bool direct = nch == 1;
+      const int ea = row_scale(mxa[r]);
+      const int ga = ra0 + r;
 #pragma unroll 1
-    for (int cg = part * 8; cg < BN; cg += 32) {
-      float D[kOzSlices][8];
-      tmem_ld_diagonals<BN>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cg, D);
-      if (ga >= g.a.rows) continue;
+      for (int cg = part * 8; cg < BN; cg += 32) {
+        float D[kOzSlices][8];
+        tmem_ld_diagonals<BN>(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cg, D);
 #pragma unroll
-      for (int j = 0; j < 8; j++) {
-        const int gb = rb0 + cg + j;
-        if (gb >= g.b.rows) continue;
-        const int eb = row_scale(mxb[cg + j]);
-        double x;
-        if (ea == kOzBad || eb == kOzBad) {
-          x = __longlong_as_double(0x7FF8000000000000ll);
-        } else {
-          const long long H = (long long)__float2int_rz(D[0][j]) * (1ll << 21) +
-                              (long long)__float2int_rz(D[1][j]) * (1ll << 14) +
-                              (long long)__float2int_rz(D[2][j]) * (1ll << 7) +
-                              (long long)__float2int_rz(D[3][j]);
-          const long long L = (long long)__float2int_rz(D[4][j]) * (1ll << 21) +
-                              (long long)__float2int_rz(D[5][j]) * (1ll << 14) +
-                              (long long)__float2int_rz(D[6][j]) * (1ll << 7) +
-                              (long long)__float2int_rz(D[7][j]);
-          x = assemble(H, L, ea + eb - 63);
+        for (int j = 0; j < 8; j++) {
+          const int eb = row_scale(mxb[cg + j]);
+          double x;
+          if (ea == kOzBad || eb == kOzBad) {
+            x = __longlong_as_double(0x7FF8000000000000ll);
+          } else {
+            // D_0 .. D_3 sum at most 4 x 64 digit products below 2^14: < 2^22
+            const long long H = (long long)int_small(D[0][j]) * (1ll << 21) +
+                                (long long)int_small(D[1][j]) * (1ll << 14) +
+                                (long long)int_small(D[2][j]) * (1ll << 7) +
+                                (long long)int_small(D[3][j]);
+            const long long L = (long long)__float2int_rz(D[4][j]) * (1ll << 21) +
+                                (long long)__float2int_rz(D[5][j]) * (1ll << 14) +
+                                (long long)__float2int_rz(D[6][j]) * (1ll << 7) +
+                                (long long)__float2int_rz(D[7][j]);
+            x = assemble(H, L, ea + eb - 63);
+          }
+          if (!direct) {
+            stage[r * kST + cg + j] = x;
+          } else {
+            const int gb = rb0 + cg + j;
+            if (ga < g.a.rows && gb < g.b.rows) {
+              double* cp = cz + (g.swap ? (long long)gb * g.ldc + ga : (long long)ga * g.ldc + gb);
+              double v = g.alpha == 1.0 ? x : g.alpha * x;
+              if (g.beta != 0.0) v = fma(g.beta, *cp, v);
+              *cp = v;
+            }
+          }
         }
-        double* cp = cz + (g.swap ? (long long)gb * g.ldc + ga : (long long)ga * g.ldc + gb);
-        double v = c == 0 ? x : *cp + x;
-        if (last) {
-          if (g.alpha != 1.0) v = g.alpha * v;
-          if (g.beta != 0.0) v = fma(g.beta, *cp, v);  // one-chunk CTAs only
-        }
-        *cp = v;
+      }
+      // every thread's TMEM reads are done before the next chunk's MMAs
+      tc_fence_before();
+      __syncthreads();
+      if (direct) continue;
+      // coalesced output: consecutive threads on consecutive addresses of C
+      // (along its rows, or along the A side when the product is swapped);
+      // the first chunk stores, later ones add in chunk order; alpha with
+      // the last
+      const bool last = c == nch - 1;
+      // thread tid takes elements tid + 512 i of the tile: along C's rows a
+      // fixed column and rows 512 / BN apart; swapped, a fixed A-side row
+      // and columns 4 apart
+      constexpr int kPer = kOzM * BN / kOzThreads;  // 4, 8 or 16
+      const int row0 = g.swap ? tid % kOzM : tid / BN, col0 = g.swap ? tid / kOzM : tid % BN;
+      const int drow = g.swap ? 0 : kOzThreads / BN, dcol = g.swap ? kOzThreads / kOzM : 0;
+      const long long at0 = g.swap ? (long long)(rb0 + col0) * g.ldc + ra0 + row0
+                                   : (long long)(ra0 + row0) * g.ldc + rb0 + col0;
+      const long long dat = g.swap ? (long long)dcol * g.ldc : (long long)drow * g.ldc;
+      const int st0 = row0 * kST + col0, dst = drow * kST + dcol;
+      const bool need_old = c > 0;
+      double old[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        const bool live = ra0 + row0 + i * drow < g.a.rows && rb0 + col0 + i * dcol < g.b.rows;
+        old[i] = (live && need_old) ? cz[at0 + i * dat] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < kPer; i++) {
+        if (ra0 + row0 + i * drow >= g.a.rows || rb0 + col0 + i * dcol >= g.b.rows) continue;
+        const double x = stage[st0 + i * dst];
+        double v = c == 0 ? x : old[i] + x;
+        if (last && g.alpha != 1.0) v = g.alpha * v;  // (beta is 0 here)
+        cz[at0 + i * dat] = v;
       }
     }
-    // every thread's TMEM reads and uses of the row maxima are done before
-    // the next chunk overwrites them
-    tc_fence_before();
-    __syncthreads();
   }
   if (!s_ok && tid == 0 && g.err) atomicOr(g.err, QTT_DEVERR_TIMEOUT);
   tc_fence_before();
@@ -578,7 +668,17 @@ void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext, double
   }
   p.a = pl.swap ? opB : opA;
   p.b = pl.swap ? opA : opB;
-  dim3 grid((p.b.rows + p.BN - 1) / p.BN, (p.a.rows + kOzM - 1) / kOzM, nz);
+  p.nz = nz;
+  // persistent CTAs (one per SM: the shared memory allows no second)
+  const long long items =
+      (long long)((p.b.rows + p.BN - 1) / p.BN) * ((p.a.rows + kOzM - 1) / kOzM) * nz;
+  static const int sms = [] {
+    int dev = 0, n = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+  }();
+  dim3 grid((unsigned)std::min<long long>(items, sms));
   pre_launch(s);
   if (p.BN == 64)
     k_gemm_oz<64><<<grid, kOzThreads, oz_smem(64), s>>>(p);
