@@ -186,21 +186,23 @@ __device__ __forceinline__ double assemble(long long H, long long L, int scale) 
 
 // Digits of a pair (x0, x1) of one row (scale exponent e): eight words, word
 // p holding the p-th 7-bit digits of x0 (low half) and x1 (high half) as
-// signed BF16 integers (a digit v < 128 is exact in FP32 as (2^23 + v) -
-// 2^23, and its BF16 is the upper half of that FP32).
+// signed BF16 integers.  A digit v < 128 with sign s is exact in FP32 as
+// (-1)^s (2^23 + v) - (-1)^s 2^23: the bit pattern s | 2^23 exponent | v
+// is one logic operation on the shifted field, and the BF16 is the upper
+// half of that FP32.
 __device__ __forceinline__ void pair_digits(double x0, double x1, int e, uint32_t (&w)[kOzSlices]) {
   unsigned s0, s1;
   const unsigned long long f0 = fixed56(x0, e, s0), f1 = fixed56(x1, e, s1);
   const uint32_t h0 = (uint32_t)(f0 >> 28), l0 = (uint32_t)f0 & 0xFFFFFFFu;
   const uint32_t h1 = (uint32_t)(f1 >> 28), l1 = (uint32_t)f1 & 0xFFFFFFFu;
-  const uint32_t sg = (s0 << 15) | (s1 << 31);
+  const uint32_t m0 = 0x4B000000u | (s0 << 31), m1 = 0x4B000000u | (s1 << 31);
+  const float c0 = s0 ? 8388608.0f : -8388608.0f, c1 = s1 ? 8388608.0f : -8388608.0f;
 #pragma unroll
   for (int p = 0; p < kOzSlices; p++) {
     const int sh = 7 * (3 - (p & 3));
-    const uint32_t v0 = ((p < 4 ? h0 : l0) >> sh) & 127u, v1 = ((p < 4 ? h1 : l1) >> sh) & 127u;
-    const uint32_t b0 = __float_as_uint(__uint_as_float(0x4B000000u | v0) - 8388608.0f);
-    const uint32_t b1 = __float_as_uint(__uint_as_float(0x4B000000u | v1) - 8388608.0f);
-    w[p] = __byte_perm(b0, b1, 0x7632) | sg;  // upper halves: the BF16 values
+    const uint32_t b0 = __float_as_uint(__uint_as_float((((p < 4 ? h0 : l0) >> sh) & 127u) | m0) + c0);
+    const uint32_t b1 = __float_as_uint(__uint_as_float((((p < 4 ? h1 : l1) >> sh) & 127u) | m1) + c1);
+    w[p] = __byte_perm(b0, b1, 0x7632);  // upper halves: the BF16 values
   }
 }
 
@@ -316,8 +318,8 @@ __device__ void slice_tile(const OzOperand& o, const double* base, int r0, int k
     int r, k;
     pair_at<R>(kc, i, r, k);
     uint32_t w[kOzSlices];
-    const bool bad = e[i] == kOzBad;
-    pair_digits(bad ? 0.0 : x[2 * i], bad ? 0.0 : x[2 * i + 1], e[i], w);
+    if (e[i] == kOzBad) x[2 * i] = x[2 * i + 1] = 0.0;  // the row's output is NaN
+    pair_digits(x[2 * i], x[2 * i + 1], e[i], w);
     const uint32_t off = sw128_off(r, k);
 #pragma unroll
     for (int p = 0; p < kOzSlices; p++) *(uint32_t*)(dst + p * slice_bytes + off) = w[p];
@@ -407,6 +409,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
   // the 8-column groups w >> 2, (w >> 2) + 4, ...
   const int quarter = warp & 3, part = warp >> 2;
   const int r = quarter * 32 + lane;
+  const bool plain = g.alpha == 1.0 && g.beta == 0.0;  // C = op(A) op(B)
   const int tiles_b = (g.b.rows + BN - 1) / BN, tiles_a = (g.a.rows + kOzM - 1) / kOzM;
   const int items = tiles_b * tiles_a * g.nz;
   uint32_t phase = 0;  // completed waits on the MMA barrier
@@ -468,6 +471,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
       const bool direct = nch == 1;
       const int ea = row_scale(mxa[r]);
       const int ga = ra0 + r;
+      // this thread's output row (or, swapped, column) of C: element
+      // (ga, rb0 + col) at cbase + col * cstride
+      double* const cbase = cz + (g.swap ? (long long)rb0 * g.ldc + ga : (long long)ga * g.ldc + rb0);
+      const long long cstride = g.swap ? g.ldc : 1;
 #pragma unroll 1
       for (int cg = part * 8; cg < BN; cg += 32) {
         float D[kOzSlices][8];
@@ -479,24 +486,25 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
           if (ea == kOzBad || eb == kOzBad) {
             x = __longlong_as_double(0x7FF8000000000000ll);
           } else {
-            // D_0 .. D_3 sum at most 4 x 64 digit products below 2^14: < 2^22
-            const long long H = (long long)int_small(D[0][j]) * (1ll << 21) +
-                                (long long)int_small(D[1][j]) * (1ll << 14) +
-                                (long long)int_small(D[2][j]) * (1ll << 7) +
-                                (long long)int_small(D[3][j]);
-            const long long L = (long long)__float2int_rz(D[4][j]) * (1ll << 21) +
-                                (long long)__float2int_rz(D[5][j]) * (1ll << 14) +
-                                (long long)__float2int_rz(D[6][j]) * (1ll << 7) +
-                                (long long)__float2int_rz(D[7][j]);
+            // D_d sums at most min(d + 1, 8 - ...) x 64 digit products below
+            // 2^14: |D_0 .. D_3| < 2^22, |D_4 .. D_7| < 2^23, so the pairs
+            // D_d 2^7 + D_(d+1) fit in 32 bits
+            const int d01 = int_small(D[0][j]) * 128 + int_small(D[1][j]);
+            const int d23 = int_small(D[2][j]) * 128 + int_small(D[3][j]);
+            const int d45 = __float2int_rz(D[4][j]) * 128 + __float2int_rz(D[5][j]);
+            const int d67 = __float2int_rz(D[6][j]) * 128 + __float2int_rz(D[7][j]);
+            const long long H = (long long)d01 * (1ll << 14) + d23;
+            const long long L = (long long)d45 * (1ll << 14) + d67;
             x = assemble(H, L, ea + eb - 63);
           }
           if (!direct) {
             stage[r * kST + cg + j] = x;
-          } else {
-            const int gb = rb0 + cg + j;
-            if (ga < g.a.rows && gb < g.b.rows) {
-              double* cp = cz + (g.swap ? (long long)gb * g.ldc + ga : (long long)ga * g.ldc + gb);
-              double v = g.alpha == 1.0 ? x : g.alpha * x;
+          } else if (ga < g.a.rows && rb0 + cg + j < g.b.rows) {
+            double* cp = cbase + (long long)(cg + j) * cstride;
+            if (plain) {
+              *cp = x;
+            } else {
+              double v = g.alpha * x;
               if (g.beta != 0.0) v = fma(g.beta, *cp, v);
               *cp = v;
             }
@@ -534,7 +542,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
         if (ra0 + row0 + i * drow >= g.a.rows || rb0 + col0 + i * dcol >= g.b.rows) continue;
         const double x = stage[st0 + i * dst];
         double v = c == 0 ? x : old[i] + x;
-        if (last && g.alpha != 1.0) v = g.alpha * v;  // (beta is 0 here)
+        if (last && !plain) v = g.alpha * v;  // (beta is 0 here)
         cz[at0 + i * dat] = v;
       }
     }

@@ -197,3 +197,25 @@ def test_ozaki_rejects_other_shapes(ctx):
         ctx.gemm_ozaki(A, B, C=torch.zeros((4, 256, 256), dtype=torch.float64, device="cuda"),
                        beta=1.0)
     assert e.value.status == 2
+
+
+def test_ozaki_projection_shape(ctx):
+    """The projection's dominant product at the bench workload (12288 x 256 x
+    64: one K chunk, 384 output tiles): 48 sampled rows bit for bit against
+    the replica (a row's scale depends on that row only), every element
+    within the error bound."""
+    import torch
+    M, N, K = 12288, 256, 64
+    rng = np.random.default_rng(12288)
+    A = rng.standard_normal((M, K)) * np.logspace(0, -8, K)[None, :]
+    B = rng.standard_normal((K, N)) * np.logspace(-2, 2, N)[None, :]
+    got = ctx.gemm_ozaki(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
+    rows = np.sort(rng.choice(M, 48, replace=False))
+    want, _, _ = replica(A[rows], B.T.copy(), 1.0, 0.0, None, nb=1)
+    assert np.array_equal(got[rows], want)
+    ea, _ = scales(A)
+    eb, _ = scales(B.T.copy())
+    exact = A @ B
+    bound = K * 2.0 ** -53 * (np.ldexp(1.0, ea[:, None] + eb[None, :]) + np.abs(A) @ np.abs(B)) \
+        + 4 * 2.0 ** -53 * np.abs(exact) + 1e-300
+    assert float((np.abs(got - exact) / bound).max()) <= 1.0
