@@ -413,9 +413,13 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
   const int tiles_b = (g.b.rows + BN - 1) / BN, tiles_a = (g.a.rows + kOzM - 1) / kOzM;
   const int items = tiles_b * tiles_a * g.nz;
   uint32_t phase = 0;  // completed waits on the MMA barrier
-  // persistent: work items (B tile, A tile, batch entry or K slice) dealt
-  // over the CTAs
-  for (int item = blockIdx.x; item < items && s_ok; item += gridDim.x) {
+  // persistent: each CTA takes a contiguous range of work items (B tile
+  // fastest, then A tile, then batch entry or K slice), so that consecutive
+  // one-chunk items of one A tile reuse its slices in shared memory
+  const int per = (items + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int item_end = min(items, ((int)blockIdx.x + 1) * per);
+  int held = -1;  // the A tile (by + tiles_a z) whose one-chunk slices are in shared memory
+  for (int item = blockIdx.x * per; item < item_end && s_ok; item++) {
     const int bx = item % tiles_b, rest = item / tiles_b;
     const int by = rest % tiles_a, z = rest / tiles_a;
     const int z1 = z / g.nb2, z2 = z % g.nb2;
@@ -426,12 +430,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gemm_oz(OzParams g) {
     const double* pa = g.a.p + z1 * g.a.s1 + z2 * g.a.s2;
     const double* pb = g.b.p + z1 * g.b.s1 + z2 * g.b.s2;
     double* cz = g.C + z1 * g.sC1 + z2 * g.sC2;
+    // one-chunk items write C directly and leave the A slices intact
+    const bool keep_a = nch == 1 && held == rest;
+    held = nch == 1 ? rest : -1;
     for (int c = 0; c < nch; c++) {
       const int k0 = c * kOzChunk, klen = min(kOzChunk, Kz - k0);
-      for (int i = tid; i < kOzM; i += kOzThreads) mxa[i] = 0ull;
+      if (!keep_a)
+        for (int i = tid; i < kOzM; i += kOzThreads) mxa[i] = 0ull;
       if (tid < BN) mxb[tid] = 0ull;
       __syncthreads();  // zeroed row maxima; the previous chunk's output read
-      slice_tile<kOzM>(g.a, pa + (long long)k0 * g.a.sk, ra0, klen, mxa, sa);
+      if (!keep_a) slice_tile<kOzM>(g.a, pa + (long long)k0 * g.a.sk, ra0, klen, mxa, sa);
       slice_tile<BN>(g.b, pb + (long long)k0 * g.b.sk, rb0, klen, mxb, sb);
       // the generic-proxy writes become visible to the tensor core's reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
