@@ -455,6 +455,9 @@ def e2e_steps(torch, form, n_steps, flush, world):
 
 
 OZ_PAIRS = 36  # slice products of the Ozaki splitting per FP64 product (8 slices, p + q <= 7)
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one 12288 x 256 x 64 launch
+# (profiles/ncu_k_gemm_oz_12288x256x64.md): the operands read once, C stays in L2
+OZ_NCU_TRAFFIC = 6783488 + 272384
 
 
 def roofline_of(torch, dev, prof):
@@ -474,10 +477,10 @@ def roofline_of(torch, dev, prof):
         dpk = gemm_peak(torch, dev, torch.float64)
         return {"kernel": dom, "bound": "tensor", "achieved": achieved,
                 "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16 if bf16 else None,
-                "traffic": NCU_TRAFFIC.get(dom),
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                  "launch of the projection's 12288 x 256 x 64 product; see "
-                                  "profiles/",
+                "traffic": None,
+                "traffic_source": "null: this kernel's launches span many product shapes; the "
+                                  "ncu DRAM bytes of the projection's 12288 x 256 x 64 launch "
+                                  "are in oz_gemm (profiles/ncu_k_gemm_oz_12288x256x64.md)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
                 "achieved_source": f"{OZ_PAIRS} BF16 slice products per FP64 product "
                                    "(algorithmic 2MNK each) / launch time",
@@ -575,9 +578,13 @@ def oz_gemm_record(torch, ctx, peaks):
         ms = e0.elapsed_time(e1) / 10
         f64eq = 2.0 * M * N * K / (ms * 1e-3) / 1e12
         bf16 = peaks.get("bf16_tflops")
-        out.append({"shape": [M, N, K], "ms": ms, "fp64_equivalent_tflops": f64eq,
-                    "tensor_tflops": OZ_PAIRS * f64eq, "bf16_peak_tflops": bf16,
-                    "frac": OZ_PAIRS * f64eq / bf16 if bf16 else None})
+        rec = {"shape": [M, N, K], "ms": ms, "fp64_equivalent_tflops": f64eq,
+               "tensor_tflops": OZ_PAIRS * f64eq, "bf16_peak_tflops": bf16,
+               "frac": OZ_PAIRS * f64eq / bf16 if bf16 else None,
+               "algorithmic_bytes": 8 * (M * K + K * N + M * N)}
+        if (M, N, K) == (12288, 256, 64):
+            rec["ncu_dram_bytes"] = OZ_NCU_TRAFFIC
+        out.append(rec)
     return {"shapes": out, "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; of measured)"}
 
 
