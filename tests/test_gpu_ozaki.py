@@ -128,6 +128,8 @@ CASES = [
     (64, 200, 4000, True, False, 1, 1.0, 0.0),
     # unbatched, enough tiles: one CTA adds up three chunks in its output
     (9600, 40, 130, False, False, 1, 0.5, 0.0),
+    # output tiles 16 wide
+    (300, 12, 40, False, False, 64, 1.0, 1.0),
 ]
 
 
@@ -219,3 +221,4 @@ def test_ozaki_projection_shape(ctx):
     bound = K * 2.0 ** -53 * (np.ldexp(1.0, ea[:, None] + eb[None, :]) + np.abs(A) @ np.abs(B)) \
         + 4 * 2.0 ** -53 * np.abs(exact) + 1e-300
     assert float((np.abs(got - exact) / bound).max()) <= 1.0
+
