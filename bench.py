@@ -53,12 +53,17 @@ instead of the paper's settings; --grid-bits / --chi override n / chi_max
 
 CPU oracle: cpu_baseline times one whole RK4 step of the same workload
 from its initial state with the oracle on one core (a subprocess with one
-BLAS thread), counting the algorithmic FLOPs of that step as it runs
-(matrix products 2MNK, Householder QR with explicit Q 4mn^2 - 4n^3/3, thin
-SVD 6mn^2 + 20n^3 for m >= n); the count is the numerator of the line's
-aggregate roofline.  --impl reference times the oracle as the reference
-arm: one untimed RK4 step, then min(K, 3) consecutive whole steps, timed
-(the line's "steps" is the number timed).
+BLAS thread), in the scheme of the headline form (the paper's implicit step
+by default; with the explicit forms in the run also one explicit step),
+counting the algorithmic FLOPs of that step as it runs (matrix products
+2MNK, Householder QR with explicit Q 4mn^2 - 4n^3/3, thin SVD
+6mn^2 + 20n^3 for m >= n); every form's aggregate roofline uses the
+explicit step's count as the unit of work per RK4 step (the oracle's
+implicit step contracts the product MPOs literally, far more FLOPs than the
+library's structured contraction).  --impl reference times the oracle as the reference arm in
+the headline form's scheme: by default two consecutive whole implicit steps
+(about a minute each), with --precision both | mixed | fp64 one untimed and
+then min(K, 3) explicit steps (the line's "steps" is the number timed).
 
 Timing: 3 warm-up steps by default, the L2 flushed (256 MB write) before
 every timed step, CUDA events on the stepping stream (host clock between
@@ -301,13 +306,16 @@ def _oracle_steps_child(wjson):
     uq = [Q.from_dense(f, p.eps, p.chi_max) for f in u]
     ops = Q.build_operators(w["n"], dx)
     nu = 1.0 / w["Re"]
+    # the scheme of the form it stands beside: the explicit step (B formed)
+    # or the paper's implicit one
+    step = Q.rk4_step_implicit if w.get("rhs_form", 0) == 1 else Q.rk4_step
     for _ in range(w["warm"]):
-        uq = Q.rk4_step(uq, dt, nu, p, ops)
+        uq = step(uq, dt, nu, p, ops)
     times, flops = [], []
     for _ in range(w["timed"]):
         f0 = counter.total
         t = time.perf_counter()
-        uq = Q.rk4_step(uq, dt, nu, p, ops)
+        uq = step(uq, dt, nu, p, ops)
         times.append(time.perf_counter() - t)
         flops.append(counter.total - f0)
     print(json.dumps({"times": times, "flops": flops}))
@@ -334,20 +342,31 @@ def run_reference(args):
     if args.n:
         w["n"] = args.n
         w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
-    timed = max(1, min(args.steps, 3))
-    times, flops = oracle_steps(w, 1, timed)
+    # the scheme of the main arm's headline form: the paper's implicit step
+    # by default (an implicit oracle step takes about a minute on one core,
+    # so two steps and no untimed one), the explicit step for the explicit
+    # precisions
+    implicit = args.precision == "all" or args.rhs == "implicit"
+    if implicit:
+        w["rhs_form"] = 1
+        w["workload"] += "_implicit_rhs"
+    warm = 0 if implicit else 1
+    timed = max(1, min(args.steps, 2 if implicit else 3))
+    times, flops = oracle_steps(w, warm, timed)
     total = sum(times)
     value = timed / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": timed, "steps_requested": args.steps,
-            "warmup": 1, "ms_per_step": 1e3 * total / timed, "higher_is_better": True,
+            "warmup": warm, "ms_per_step": 1e3 * total / timed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {**w, "parallelism": "none (CPU oracle)"},
             "algorithmic_flops_per_step": statistics.mean(flops),
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one untimed RK4 step, then {timed} consecutive whole "
-                                       "RK4 steps of the workload, timed; numpy FP64 oracle on "
-                                       "one BLAS thread"},
+                             "sample": (f"{warm} untimed and {timed} consecutive whole RK4 "
+                                        "steps of the workload ("
+                                        + ("the paper's implicit scheme" if implicit else
+                                           "explicit scheme") + "), timed; numpy FP64 oracle on "
+                                        "one BLAS thread")},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -799,14 +818,30 @@ def main():
                 "roofline": roofline_of(torch, dev, r["prof"])}
 
     sums = {nm: summary(nm) for nm in names}
-    cpu, oracle_flops = None, None
+    cpu, oracle_flops = None, {}
     if not args.no_cpu_baseline:
-        times, flops = oracle_steps(w, 0, 1)
-        oracle_flops = flops[0]
-        cpu = {"value": 1.0 / times[0], "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": "one whole RK4 step of the same workload from its initial state, "
-                         "numpy FP64 oracle on one BLAS thread",
-               "algorithmic_flops_per_step": oracle_flops}
+        # one oracle step of each scheme timed: the headline form's scheme
+        # gives cpu_baseline; both give the algorithmic FLOPs per step of
+        # their forms' aggregate rooflines
+        schemes = sorted({0} | {1 if (nm.endswith("implicit") or w.get("rhs_form", 0) == 1)
+                                else 0 for nm in names})
+        ostep = {}
+        for sch in schemes:
+            times, flops = oracle_steps(dict(w, rhs_form=sch), 0, 1)
+            ostep[sch] = (times[0], flops[0])
+        oracle_flops = {sch: ostep[sch][1] for sch in schemes}
+        hsch = 1 if (head.endswith("implicit") or w.get("rhs_form", 0) == 1) else 0
+        cpu = {"value": 1.0 / ostep[hsch][0], "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": "one whole RK4 step of the same workload from its initial state ("
+                         + ("the paper's implicit scheme, as the headline form" if hsch else
+                            "explicit scheme") + "), numpy FP64 oracle on one BLAS thread",
+               "algorithmic_flops_per_step": ostep[hsch][1]}
+        if hsch:
+            cpu["explicit_scheme"] = {"value": 1.0 / ostep[0][0],
+                                      "algorithmic_flops_per_step": ostep[0][1]}
+            cpu["flops_note"] = ("the oracle's implicit step contracts the product MPOs H_b D_j "
+                                 "literally; the library's structured contraction does about a "
+                                 "quarter of those FLOPs")
     fp64_peak = None
     for nm in names:
         rf = sums[nm]["roofline"]
@@ -815,13 +850,22 @@ def main():
     if oracle_flops:
         if fp64_peak is None:
             fp64_peak = gemm_peak(torch, dev, torch.float64)
+        # one unit of work per RK4 step for every form: the explicit scheme's
+        # count (the oracle's implicit step contracts the 3 chi-bond product
+        # MPOs literally, about 9x the explicit step's FLOPs and about 4x what
+        # the library's structured contraction does, so its count is no
+        # measure of the work the GPU forms do)
+        unit = oracle_flops.get(0)
         for nm in names:
-            ach = oracle_flops * sums[nm]["value"] / world / B / 1e12
+            if unit is None:
+                break
+            ach = unit * sums[nm]["value"] / world / B / 1e12
             sums[nm]["roofline"]["aggregate"] = {
-                "flops_per_step": oracle_flops, "achieved": ach, "unit": "TFLOP/s",
+                "flops_per_step": unit, "achieved": ach, "unit": "TFLOP/s",
                 "peak": fp64_peak, "frac": ach / fp64_peak,
-                "source": "algorithmic FLOPs of one RK4 step counted in the CPU oracle (FP64 "
-                          "algorithm) x steps/s; peak = FP64 cuBLAS DGEMM measured in this run "
+                "source": "algorithmic FLOPs of one RK4 step of the explicit scheme counted in "
+                          "the CPU oracle (FP64 algorithm), a common unit of work per step for "
+                          "every form, x steps/s; peak = FP64 cuBLAS DGEMM measured in this run "
                           "(of measured)"}
     clocks = clk.summary()
     peaks = measured_peaks()

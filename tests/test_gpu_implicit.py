@@ -105,3 +105,30 @@ def test_forms_at_equal_error_full_size(P):
         errs[form] = math.sqrt(num / den)
     print(f"one RK4 step vs the dense step: explicit {errs[0]:.3e}, implicit {errs[1]:.3e}")
     assert errs[1] <= 1.5 * errs[0] + 1e-14
+
+
+@pytest.fixture(scope="module")
+def implicit_full_ref():
+    """The oracle's implicit RK4 step on the bench workload (2^10 shear jet,
+    chi 64, eps 1e-8, the paper's solver settings): about a minute on one
+    core."""
+    n = 10
+    (u, v), dx = I.shear_jet(n, seed=0)
+    dt, nu = 0.1 * dx / float(np.abs(u).max()), 1 / 2e5
+    pp = dict(eps=1e-8, chi_max=64)
+    uq = [Q.from_dense(f, pp["eps"], pp["chi_max"]) for f in (u, v)]
+    ref = Q.rk4_step_implicit(uq, dt, nu, Q.Params(**pp), Q.build_operators(n, dx))
+    return n, uq, dt, nu, [Q.to_dense(r) for r in ref]
+
+
+@pytest.mark.parametrize("prec,tol", [(0, TOL), (1, 1e-6)])
+def test_implicit_full_size_matches_oracle(P, implicit_full_ref, prec, tol):
+    """One RK4 step of the bench's headline scheme at full size, replayed as a
+    whole-step graph where the bench replays it: FP64 within 1e-10, mixed
+    (products on the tensor cores) within 1e-6 of the oracle's step."""
+    n, uq, dt, nu, want = implicit_full_ref
+    ctx = P.Context(n, eps=1e-8, chi_max=64, rhs_form=P.RHS_IMPLICIT, precision=prec, graphs=2)
+    g = [ctx.from_cores(c) for c in uq]
+    ctx.rk4_step(g[0], g[1], dt, nu)
+    for i in range(2):
+        assert rel(ctx.to_dense(g[i]).cpu().numpy(), want[i]) <= tol
