@@ -109,6 +109,11 @@ def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
         ("qtt_gemm_tf32x3", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
                              ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int],
          (None, 4, 4, 4, None, 4, 0, None, 4, 0, None, 4)),
+        ("qtt_gemm_ozaki", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                            ctypes.c_int, ctypes.c_longlong, vp, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_longlong, vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_int,
+                            ctypes.c_double, ctypes.c_double],
+         (None, 64, 64, 64, None, 64, 0, 0, None, 64, 0, 0, None, 64, 0, 1, 1.0, 0.0)),
     ]
     for name, argtypes, args in calls:
         f = getattr(lib, name)
