@@ -80,16 +80,44 @@ def project(w, h: float, mu: float, dx: float, order: int = 2):
     return [np.real(np.fft.ifft2(V1)), np.real(np.fft.ifft2(V2))]
 
 
-def divergence(u, dx):
-    return d(u[0], 1, dx) + d(u[1], 2, dx)
+def project_exact(w, dx: float, order: int = 2):
+    """The exact discrete projection onto the kernel of G = [D_1 D_2]: the
+    limit mu -> infinity of `project`, the alternative to the penalty that
+    the paper's outlook (Sec. IV, periodic boundaries, Fourier transforms)
+    points to.  Per Fourier mode g^T w is removed along conj(g):
+    v = w - conj(g) (g^T w) / |g|^2; with g_j = i sigma_j (sigma_j real,
+    D_j^T = -D_j) this is v = w - sigma (sigma . w) / |sigma|^2.  Modes
+    where both symbols vanish (2 m_j = 0 mod N: the mean and the Nyquist
+    modes, which every central difference annihilates) pass unchanged;
+    there sigma_j is set to exactly zero instead of the rounding residue of
+    sin(pi)."""
+    N = w[0].shape[0]
+    m = (np.fft.fftfreq(N) * N).astype(np.int64)
+    if order == 2:
+        sig = np.sin(2.0 * np.pi * m / N) / dx
+    else:
+        sig = sum(2.0 * c * np.sin(2.0 * np.pi * k * m / N)
+                  for k, c in enumerate(_weights(order), start=1)) / dx
+    sig[(2 * m) % N == 0] = 0.0
+    s1, s2 = sig[:, None] * np.ones((1, N)), np.ones((N, 1)) * sig[None, :]
+    W1, W2 = np.fft.fft2(w[0]), np.fft.fft2(w[1])
+    den = s1 * s1 + s2 * s2
+    t = np.where(den > 0, (s1 * W1 + s2 * W2) / np.where(den > 0, den, 1.0), 0.0)
+    return [np.real(np.fft.ifft2(W1 - s1 * t)), np.real(np.fft.ifft2(W2 - s2 * t))]
+
+
+def divergence(u, dx, order: int = 2):
+    return d(u[0], 1, dx, order) + d(u[1], 2, dx, order)
 
 
 RK4_H = (1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0)
 RK4_B = (None, (3.0, 0.25), (1.5, 0.625), (3.0, 0.25))
 
 
-def rk4_step(u, dt, nu, mu, dx, order: int = 2):
-    """Four projected Euler stages (App. B, Table RK4, Eqs. U1-U4)."""
+def rk4_step(u, dt, nu, mu, dx, order: int = 2, exact: bool = False):
+    """Four projected Euler stages (App. B, Table RK4, Eqs. U1-U4); with
+    exact=True each stage takes the exact projection `project_exact`
+    instead of the penalty solve."""
     U = []
     b = u
     for s in range(4):
@@ -99,7 +127,7 @@ def rk4_step(u, dt, nu, mu, dx, order: int = 2):
         h = RK4_H[s] * dt
         B = rhs_B(b, nu, dx, order)
         w = [0.25 * u[i] - h * B[i] for i in range(2)]
-        U.append(project(w, h, mu, dx, order))
+        U.append(project_exact(w, dx, order) if exact else project(w, h, mu, dx, order))
     return [U[0][i] + U[1][i] + U[2][i] + U[3][i] for i in range(2)]
 
 

@@ -377,6 +377,7 @@ class Operators:
     D: list            # [D_1, D_2]
     lap: list          # D_1 D_1 + D_2 D_2, the literal square of the central difference
     K: dict            # (i, j) -> D_i^T D_j, the blocks of the projection system
+    order: int = 2     # order of the central differences
 
 
 def build_operators(n: int, dx: float, order: int = 2) -> Operators:
@@ -396,7 +397,7 @@ def build_operators(n: int, dx: float, order: int = 2) -> Operators:
     for i in range(2):
         for j in range(2):
             K[(i, j)] = mpo_compress(mpo_product(mpo_transpose(D[i]), D[j]))
-    return Operators(n=n, dx=dx, D=D, lap=lap, K=K)
+    return Operators(n=n, dx=dx, D=D, lap=lap, K=K, order=order)
 
 
 # --------------------------------------------------------------------------
@@ -533,6 +534,7 @@ class Params:
     cg_maxit: int = 100
     sweep_tol: float = 1e-5
     max_sweeps: int = 20
+    projection: str = "penalty"   # or "spectral": project_spectral in every stage
 
 
 def right_canonicalize(A: list) -> list:
@@ -650,6 +652,27 @@ def project(w: list, h: float, params: Params, ops: Operators):
             break
         n_prev = n_new
     return V, info
+
+
+def project_spectral(w: list, params: Params, ops: Operators):
+    """The exact discrete projection of w onto divergence-free fields, the
+    alternative to the penalty that the paper's outlook (Sec. IV) points to
+    for periodic boundaries: both components are read out densely, the
+    divergence is removed exactly per Fourier mode (oracle.dense.project_exact,
+    the mu -> infinity limit of the penalty solve), and each component is
+    encoded again by TT-SVD to (eps, chi_max) (`from_dense`)."""
+    from oracle import dense as Dn
+    v = Dn.project_exact([to_dense(w[0]), to_dense(w[1])], ops.dx, ops.order)
+    return [from_dense(v[i], params.eps, params.chi_max) for i in range(2)], ProjectInfo()
+
+
+def project_stage(w: list, h: float, params: Params, ops: Operators):
+    """The projection of one Euler minimisation: the penalty solve
+    (`project`, the paper's) or, with params.projection == "spectral",
+    `project_spectral`."""
+    if params.projection == "spectral":
+        return project_spectral(w, params, ops)
+    return project(w, h, params, ops)
 
 
 def hadamard_mpo(Y: list) -> list:
@@ -868,7 +891,7 @@ def rk4_step(u, dt: float, nu: float, params: Params, ops: Operators, stats=None
             b = [add([c1, c2], [U[s - 1][i], u[i]], eps, chi) for i in range(2)]
         h = RK4_H[s] * dt
         w = stage_w(u, b, h, nu, params, ops)
-        v, info = project(w, h, params, ops)
+        v, info = project_stage(w, h, params, ops)
         if stats is not None:
             stats.append(info)
         U.append(v)
@@ -922,7 +945,7 @@ def euler_step(u, dt: float, nu: float, params: Params, ops: Operators):
     """One explicit Euler (RK1) step (App. B, Eq. "euler" in the cost
     function): u^{s+1} = argmin Theta(v, a = u^s, b = u^s, h = dt)."""
     w = stage_w(u, u, dt, nu, params, ops, a_scale=1.0)
-    v, _ = project(w, dt, params, ops)
+    v, _ = project_stage(w, dt, params, ops)
     return v
 
 
@@ -931,8 +954,8 @@ def rk2_step(u, dt: float, nu: float, params: Params, ops: Operators):
     u^{s+1/2} = argmin Theta(v, u^s, u^s, dt/2), then
     u^{s+1} = argmin Theta(v, u^s, u^{s+1/2}, dt)."""
     w = stage_w(u, u, 0.5 * dt, nu, params, ops, a_scale=1.0)
-    um, _ = project(w, 0.5 * dt, params, ops)
+    um, _ = project_stage(w, 0.5 * dt, params, ops)
     w = stage_w(u, um, dt, nu, params, ops, a_scale=1.0)
-    v, _ = project(w, dt, params, ops)
+    v, _ = project_stage(w, dt, params, ops)
     return v
 

@@ -561,3 +561,104 @@ def test_implicit_rk4_equals_dense_and_explicit():
     for i in range(2):
         assert rel(Q.to_dense(imp[i]), ref[i]) < 1e-10
         assert rel(Q.to_dense(imp[i]), Q.to_dense(exp_[i])) < 1e-10
+
+
+# ------------------------------------------- exact spectral projection
+@pytest.mark.parametrize("order", [2, 4, 8])
+def test_exact_projection_invariants(order):
+    """The exact projection (the mu -> infinity limit of the penalty solve)
+    is checked in real space, not through its own Fourier formula: the
+    result has zero discrete divergence under the stencil of `Dn.d`, the
+    removed part is orthogonal to it, applying it twice changes nothing,
+    and a discrete gradient (D_1 phi, D_2 phi) is removed entirely."""
+    n = 5
+    _, _, dx = I.grid(n)
+    w = [I.white_field(n, seed=60), I.white_field(n, seed=61)]
+    v = Dn.project_exact(w, dx, order)
+    assert np.linalg.norm(Dn.divergence(v, dx, order)) < 1e-13 * np.linalg.norm(
+        Dn.divergence(w, dx, order))
+    r = [w[i] - v[i] for i in range(2)]
+    assert abs(sum(np.vdot(r[i], v[i]) for i in range(2))) < 1e-13 * sum(
+        np.vdot(x, x) for x in w)
+    vv = Dn.project_exact(v, dx, order)
+    for i in range(2):
+        assert rel(vv[i], v[i]) < 1e-14
+    phi = I.white_field(n, seed=62)
+    grad = [Dn.d(phi, 1, dx, order), Dn.d(phi, 2, dx, order)]
+    pg = Dn.project_exact(grad, dx, order)
+    assert max(np.abs(x).max() for x in pg) < 1e-12 * max(np.abs(x).max() for x in grad)
+
+
+def test_exact_projection_keeps_annihilated_modes():
+    """Fields the central difference annihilates (a constant, and the
+    alternating (-1)^x1 and (-1)^x2 patterns of the Nyquist modes) are
+    divergence-free and pass unchanged; a divergence-free Taylor-Green field
+    too.  A formula that took the rounding residue of sin(pi) as a non-zero
+    symbol would zero the Nyquist mode of u_1."""
+    n = 5
+    N = 2 ** n
+    _, _, dx = I.grid(n)
+    alt = np.where(np.arange(N) % 2 == 0, 1.0, -1.0)
+    w = [np.outer(alt, np.ones(N)) + 0.5, np.outer(np.ones(N), alt) - 0.25]
+    for i, x in enumerate(Dn.project_exact(w, dx)):
+        np.testing.assert_allclose(x, w[i], atol=1e-14)
+    tg, dxt = I.taylor_green(n)
+    for i, x in enumerate(Dn.project_exact(tg, dxt)):
+        assert rel(x, tg[i]) < 1e-14
+
+
+def test_exact_projection_is_the_penalty_limit():
+    """|project(w, h, mu) - project_exact(w)| <= |w| / (1 + mu h^2 lambda_min)
+    with lambda_min the smallest non-zero |g|^2 (the penalty solve damps
+    each mode's divergent part by 1 / (1 + mu h^2 |g|^2))."""
+    n = 5
+    _, _, dx = I.grid(n)
+    w = [I.white_field(n, seed=63), I.white_field(n, seed=64)]
+    ve = Dn.project_exact(w, dx)
+    lam_min = (math.sin(2 * math.pi / 2 ** n) / dx) ** 2
+    nw = math.sqrt(sum(np.vdot(x, x) for x in w))
+    for mu_h2 in (1e2, 1e6):
+        vp = Dn.project(w, 1.0, mu_h2, dx)
+        d = math.sqrt(sum(np.vdot(vp[i] - ve[i], vp[i] - ve[i]) for i in range(2)))
+        assert d <= nw / (1 + mu_h2 * lam_min) * (1 + 1e-9)
+        assert d >= 1e-3 * nw / (1 + mu_h2 * lam_min)  # the bound is not vacuous
+
+
+def test_taylor_green_exact_projection_rk4_amplification():
+    """With the exact projection the Taylor-Green convection term (a
+    discrete gradient) is removed completely, so one RK4 step multiplies the
+    field by the classical RK4 amplification 1 + z + z^2/2 + z^3/6 + z^4/24
+    of the viscous decay, z = -2 nu c^2 dt, c = sin(dx)/dx."""
+    n, nu, dt = 6, 0.01, 1e-3
+    u0, dx = I.taylor_green(n)
+    z = -2 * nu * (math.sin(dx) / dx) ** 2 * dt
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    v = Dn.rk4_step(u0, dt, nu, 0.0, dx, exact=True)
+    for i in range(2):
+        np.testing.assert_allclose(v[i], R * u0[i], atol=1e-14)
+
+
+def test_qtt_spectral_projection_and_rk4_equal_dense():
+    """The QTT oracle's spectral projection and its RK4 step with it
+    (untruncated) reproduce the dense exact projection and the dense RK4
+    step with exact projections; truncated to (eps, chi) the projection's
+    result stays within the TT-SVD bound sqrt(n - 1) eps of the dense one."""
+    n = 5
+    _, _, dx = I.grid(n)
+    ops = Q.build_operators(n, dx)
+    u0, _ = I.taylor_green(n)
+    u = [u0[0] + 0.1 * I.random_field(n, seed=65), u0[1] + 0.1 * I.random_field(n, seed=66)]
+    uq = [Q.from_dense(f, 0.0, FULL) for f in u]
+    p = Q.Params(eps=0.0, chi_max=FULL, projection="spectral")
+    v, _ = Q.project_spectral(uq, p, ops)
+    ve = Dn.project_exact(u, dx)
+    for i in range(2):
+        assert rel(Q.to_dense(v[i]), ve[i]) < 1e-13
+    out = Q.rk4_step(uq, 1e-2, 0.01, p, ops)
+    ref = Dn.rk4_step(u, 1e-2, 0.01, 0.0, dx, exact=True)
+    for i in range(2):
+        assert rel(Q.to_dense(out[i]), ref[i]) < 1e-12
+    eps = 1e-3
+    vt, _ = Q.project_spectral(uq, Q.Params(eps=eps, chi_max=FULL), ops)
+    for i in range(2):
+        assert rel(Q.to_dense(vt[i]), ve[i]) <= math.sqrt(n - 1) * eps
