@@ -2,6 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision all|both|mixed|fp64]
                     [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight] [--rhs explicit|implicit]
+                    [--projection penalty|spectral]
                     [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
                     [--clocks-file PATH]
 
@@ -35,7 +36,10 @@ truncations of the same equations, so of the order of the truncation
 error, not of rounding).  --precision both times the explicit mixed and
 FP64 forms, mixed | fp64 one explicit form only; with --rhs implicit the
 named forms take the implicit right-hand side.  "oz_gemm" and "tc_gemm"
-time the two tensor-core products alone.
+time the two tensor-core products alone.  --projection spectral replaces
+every stage's penalty solve by the exact projection through Fourier space
+(explicit right-hand side; with the default --precision the explicit mixed
+and FP64 forms are timed).
 
 One JSON line is printed by rank 0.  With torchrun (N > 1) every rank runs
 its own trajectory on its own GPU (replicas: the method has no exchange
@@ -114,7 +118,8 @@ def workload_state(n, seed):
 
 def solver_kwargs(w):
     return dict(eps=w["eps"], chi_max=w["chi_max"], mu=w["mu"], cg_tol=w["cg_tol"],
-                cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"])
+                cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"],
+                projection=w.get("projection", 0))
 
 
 # ------------------------------------------------------------------ clocks
@@ -302,7 +307,8 @@ def _oracle_steps_child(wjson):
     from oracle import qtt as Q
     u, dx, dt = workload_state(w["n"], w["seed"])
     p = Q.Params(eps=w["eps"], chi_max=w["chi_max"], mu=w["mu"], cg_tol=w["cg_tol"],
-                 cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"])
+                 cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"],
+                 projection="spectral" if w.get("projection", 0) == 1 else "penalty")
     uq = [Q.from_dense(f, p.eps, p.chi_max) for f in u]
     ops = Q.build_operators(w["n"], dx)
     nu = 1.0 / w["Re"]
@@ -346,7 +352,11 @@ def run_reference(args):
     # by default (an implicit oracle step takes about a minute on one core,
     # so two steps and no untimed one), the explicit step for the explicit
     # precisions
-    implicit = args.precision == "all" or args.rhs == "implicit"
+    implicit = (args.precision == "all" or args.rhs == "implicit") and \
+        args.projection != "spectral"
+    if args.projection == "spectral":
+        w["projection"] = 1
+        w["workload"] += "_spectral_projection"
     if implicit:
         w["rhs_form"] = 1
         w["workload"] += "_implicit_rhs"
@@ -709,6 +719,9 @@ def main():
     ap.add_argument("--rhs", default="explicit", choices=["explicit", "implicit"],
                     help="the stages' right-hand side: formed as an MPS (explicit) or the "
                          "paper's form inside the projection (implicit)")
+    ap.add_argument("--projection", default="penalty", choices=["penalty", "spectral"],
+                    help="each stage's projection: the paper's penalty solve or the exact "
+                         "projection through Fourier space (explicit right-hand side only)")
     ap.add_argument("--stage-graphs", action="store_true",
                     help="replay only each stage's right-hand side as a CUDA graph (the "
                          "projection launched from the host)")
@@ -749,6 +762,11 @@ def main():
     if args.rhs == "implicit":
         w["rhs_form"] = 1
         w["workload"] += "_implicit_rhs"
+    if args.projection == "spectral":
+        if args.rhs == "implicit":
+            ap.error("--projection spectral needs the explicit right-hand side")
+        w["projection"] = 1
+        w["workload"] += "_spectral_projection"
     B = max(1, args.batched)
     if B > 1:
         w["workload"] = f"{w['workload']}_x{B}_trajectories"
@@ -756,6 +774,8 @@ def main():
              "both": ["mixed", "fp64"], "mixed": ["mixed"], "fp64": ["fp64"]}[args.precision]
     if B > 1 or args.rhs == "implicit":
         names = ["mixed"] if args.precision in ("all", "both") else names
+    if args.projection == "spectral" and args.precision == "all":
+        names = ["mixed", "fp64"]  # the implicit forms have no spectral projection
     precs = {"mixed": P.PREC_MIXED, "fp64": P.PREC_FP64, "fp64_implicit": P.PREC_FP64,
              "mixed_implicit": P.PREC_MIXED}
     rhs_of = {"fp64_implicit": P.RHS_IMPLICIT, "mixed_implicit": P.RHS_IMPLICIT}

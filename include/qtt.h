@@ -74,6 +74,17 @@ typedef enum {
                             previous time step), whose bonds are kept        */
 } qtt_rhs_form;
 
+/* How each Euler minimisation projects onto divergence-free fields
+ * (qtt_params.projection). */
+typedef enum {
+  QTT_PROJ_PENALTY = 0,  /* the paper's penalised minimisation (App. B, cost
+                            Theta): DMRG-like sweeps with CG local solves   */
+  QTT_PROJ_SPECTRAL = 1  /* exact projection in Fourier space, the
+                            alternative the paper's outlook (Sec. IV) points
+                            to for periodic boundaries: qtt_project_spectral.
+                            Explicit right-hand side only; n <= 13          */
+} qtt_projection;
+
 /* Learned truncation modes (qtt_params.learned_trunc). */
 typedef enum {
   QTT_LEARNED_OFF = 0,
@@ -129,6 +140,8 @@ typedef struct {
                          D_2, the Laplacian and the projection blocks are
                          all built with it.  Fixed at creation. */
   int rhs_form;       /* qtt_rhs_form (RK4, Euler and RK2 steps)          */
+  int projection;     /* qtt_projection (RK4, Euler and RK2 steps); 0 the
+                         paper's penalty                                    */
 } qtt_params;
 
 /* Create a context on `device`, enqueuing on `cuda_stream` (a cudaStream_t,
@@ -210,6 +223,21 @@ qtt_status qtt_compress(qtt_ctx ctx, qtt_mps inout, double eps, int chi_max);
  * QTT_ERR_NOT_CONVERGED (results still written) when a cap was hit. */
 qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1,
                        qtt_mps* v2, int* cg_iters, int* sweeps);
+/* The exact discrete projection of (w1, w2) onto divergence-free fields:
+ * the limit mu -> infinity of qtt_project, i.e. the orthogonal projection
+ * onto the kernel of G = [D_1 D_2] (the central differences of the
+ * context's fd_order), as the paper's outlook (Sec. IV) suggests for
+ * periodic boundaries: both components are read out densely on the device,
+ * transformed by 2-D FFTs, per wavevector m the part along sigma(m) is
+ * removed (v_hat = w_hat - sigma (sigma . w_hat) / |sigma|^2, where D_j has
+ * the Fourier symbol i sigma_j; wavevectors with sigma = 0, the mean and the
+ * Nyquist modes, are kept), transformed back and encoded again by TT-SVD to
+ * the context's (eps, chi_max).  New handles in *v1, *v2 (caller frees);
+ * the inputs are left as they are.  Device scratch: 6 N^2 doubles
+ * (N = 2^n).  QTT_ERR_SHAPE for n > 13 or inputs of another n.  Enqueued on
+ * the context stream; device errors surface at the next synchronising
+ * call. */
+qtt_status qtt_project_spectral(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, qtt_mps* v1, qtt_mps* v2);
 /* One RK4 step (App. B, Eq. "4euler", Table RK4, Eqs. U1-U4) in place:
  * *u1, *u2 are replaced by new handles (the old ones are released).
  * nu = 1 / Re.  Synchronises (the projections do). */

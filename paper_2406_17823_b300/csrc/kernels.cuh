@@ -178,3 +178,8 @@ void launch_rf_features(const double* sv, const int* skip_full, const int* w, co
 // spectrum.cu; C1, C2: N * N double2 scratch, P: N * N, E: kmax + 1.
 void launch_tke_spectrum(const double* u1, const double* u2, int logn, double2* C1, double2* C2,
                          double* P, double* E, int kmax, cudaStream_t s);
+// Exact spectral projection of the dense pair (F1, F2) in place (N = 2^logn
+// <= 8192), see spectrum.cu; c: nw <= 4 central-difference weights;
+// C1, C2: N * N double2 scratch, sig: N doubles of scratch.
+void launch_spectral_project(double* F1, double* F2, int logn, const double* c, int nw, double dx,
+                             double2* C1, double2* C2, double* sig, cudaStream_t s);

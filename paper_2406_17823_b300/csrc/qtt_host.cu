@@ -2697,6 +2697,56 @@ struct Workers {
   }
 };
 
+// The exact spectral projection (the alternative to the penalty that the
+// paper's outlook, Sec. IV, points to for periodic boundaries): both
+// components read out densely, the divergence removed per Fourier mode on
+// the device (launch_spectral_project: the orthogonal projection onto the
+// kernel of [D_1 D_2], the penalty's mu -> infinity limit), then each
+// component encoded again by TT-SVD to the context's (eps, chi_max), the two
+// encodings on two worker streams.
+qtt_mps from_dense_impl(qtt_ctx ctx, const double* F, double eps, int chi);
+void to_dense_impl(qtt_ctx ctx, qtt_mps A, double* F);
+
+void project_spectral_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, qtt_mps* v1, qtt_mps* v2) {
+  const int n = w1->n;
+  if (w2->n != n) throw QttError(QTT_ERR_SHAPE, "components on different grids");
+  if (n > 13) throw QttError(QTT_ERR_SHAPE, "spectral projection: n > 13");
+  cudaStream_t s = stream_of(ctx);
+  const size_t N = (size_t)1 << n, NN = N * N;
+  DBuf<double> F1(NN, s), F2(NN, s), sig(N, s);
+  {
+    DBuf<double2> C1(NN, s), C2(NN, s);
+    to_dense_impl(ctx, w1, F1.p);
+    to_dense_impl(ctx, w2, F2.p);
+    const std::vector<double> c = central_weights(ctx->p.fd_order == 0 ? 2 : ctx->p.fd_order);
+    launch_spectral_project(F1.p, F2.p, n, c.data(), (int)c.size(), ctx->p.L / (double)N, C1.p,
+                            C2.p, sig.p, s);
+  }
+  Workers wk(ctx);
+  wk.fork();
+  MpsPtr o[2];
+  for (int i = 0; i < 2; i++)
+    o[i] = MpsPtr(wk.run(i, [&] { return from_dense_impl(ctx, i ? F2.p : F1.p, ctx->p.eps,
+                                                          ctx->p.chi_max); }));
+  wk.join({o[0].get(), o[1].get()});
+  *v1 = o[0].release();
+  *v2 = o[1].release();
+}
+
+// The projection of one Euler minimisation with an explicit right-hand side
+// w: the paper's penalty solve or, with QTT_PROJ_SPECTRAL, the exact one.
+void project_stage(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qtt_mps* v2,
+                   int* cg_out, int* sw_out) {
+  if (ctx->p.projection == QTT_PROJ_SPECTRAL) {
+    project_spectral_impl(ctx, w1, w2, v1, v2);
+    ctx->last_not_converged = 0;
+    if (cg_out) *cg_out = 0;
+    if (sw_out) *sw_out = 0;
+    return;
+  }
+  project_impl(ctx, w1, w2, h, v1, v2, cg_out, sw_out);
+}
+
 void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2],
              double a_scale = 0.25) {
   const double eps = ctx->p.eps;
@@ -2993,7 +3043,7 @@ void rk4_core(qtt_ctx ctx, qtt_mps u[2], double dt, double nu, MpsPtr out[2], in
     } else {
       MpsPtr w[2];
       stage_w_run(ctx, u, b, h, nu, w, 0.25);
-      project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+      project_stage(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
     }
     *nc |= ctx->last_not_converged;
     U[st][0] = MpsPtr(v1);
@@ -3139,7 +3189,7 @@ void euler_min(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, Mps
   } else {
     MpsPtr w[2];
     stage_w_run(ctx, u, b, h, nu, w, 1.0);
-    project_impl(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
+    project_stage(ctx, w[0].get(), w[1].get(), h, &v1, &v2, &cg, &sw);
   }
   v[0] = MpsPtr(v1);
   v[1] = MpsPtr(v2);
@@ -3339,7 +3389,9 @@ bool valid_params(const qtt_params* p) {
          p->graphs >= 0 && p->graphs <= 2 &&
          (p->fd_order == 0 || p->fd_order == 2 || p->fd_order == 4 || p->fd_order == 6 ||
           p->fd_order == 8) &&
-         (p->rhs_form == QTT_RHS_EXPLICIT || p->rhs_form == QTT_RHS_IMPLICIT);
+         (p->rhs_form == QTT_RHS_EXPLICIT || p->rhs_form == QTT_RHS_IMPLICIT) &&
+         (p->projection == QTT_PROJ_PENALTY ||
+          (p->projection == QTT_PROJ_SPECTRAL && p->rhs_form == QTT_RHS_EXPLICIT && p->n <= 13));
 }
 
 void check_mps(qtt_ctx ctx, qtt_mps m) {
@@ -3695,6 +3747,16 @@ qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v
       ctx->err = "projection reached its CG or sweep cap";
       return QTT_ERR_NOT_CONVERGED;
     }
+    return QTT_OK;
+  });
+}
+
+qtt_status qtt_project_spectral(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, qtt_mps* v1, qtt_mps* v2) {
+  if (!ctx || !v1 || !v2) return QTT_ERR_ARG;
+  return guarded(ctx, [&]() -> qtt_status {
+    check_mps(ctx, w1);
+    check_mps(ctx, w2);
+    project_spectral_impl(ctx, w1, w2, v1, v2);
     return QTT_OK;
   });
 }

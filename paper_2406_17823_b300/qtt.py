@@ -18,6 +18,8 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 RHS_EXPLICIT = 0
 RHS_IMPLICIT = 1
+PROJ_PENALTY = 0
+PROJ_SPECTRAL = 1
 LEARNED_OFF = 0
 LEARNED_LOG = 1
 LEARNED_ON = 2
@@ -41,7 +43,7 @@ EXPORTS = ("qtt_create", "qtt_destroy", "qtt_set_params", "qtt_sync", "qtt_last_
            "qtt_batch_create", "qtt_batch_destroy", "qtt_batch_context", "qtt_rk4_step_batched",
            "qtt_euler_step", "qtt_rk2_step", "qtt_inner", "qtt_graph_stats",
            "qtt_mps_upload_packed", "qtt_gemm_tf32x3", "qtt_gemm_ozaki", "qtt_tc_stats", "qtt_mpo_diff",
-           "qtt_tke_spectrum")
+           "qtt_tke_spectrum", "qtt_project_spectral")
 
 
 class QttError(RuntimeError):
@@ -55,7 +57,8 @@ class Params(ctypes.Structure):
                 ("mu", c_double), ("cg_tol", c_double), ("cg_maxit", c_int),
                 ("sweep_tol", c_double), ("max_sweeps", c_int), ("precision", c_int),
                 ("learned_trunc", c_int), ("rf_oversample", c_int), ("rf_min_width", c_int),
-                ("graphs", c_int), ("fd_order", c_int), ("rhs_form", c_int)]
+                ("graphs", c_int), ("fd_order", c_int), ("rhs_form", c_int),
+                ("projection", c_int)]
 
 
 _lib = None
@@ -92,6 +95,7 @@ def lib():
             "qtt_hadamard": (c_int, [vp, vp, vp, c_double, c_int, POINTER(vp)]),
             "qtt_compress": (c_int, [vp, vp, c_double, c_int]),
             "qtt_project": (c_int, [vp, vp, vp, c_double, POINTER(vp), POINTER(vp), ip, ip]),
+            "qtt_project_spectral": (c_int, [vp, vp, vp, POINTER(vp), POINTER(vp)]),
             "qtt_rk4_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_euler_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_inner": (c_int, [vp, vp, vp, POINTER(c_double)]),
@@ -174,7 +178,7 @@ class Context:
                  sweep_tol: float = 1e-5, max_sweeps: int = 20, precision: int = PREC_FP64,
                  learned_trunc: int = LEARNED_OFF, rf_oversample: int = 8,
                  rf_min_width: int = 128, graphs: int = 0, fd_order: int = 0,
-                 rhs_form: int = 0, device: int = 0, stream=None):
+                 rhs_form: int = 0, projection: int = 0, device: int = 0, stream=None):
         torch = _torch()
         self.device = device
         if stream is None:
@@ -182,7 +186,7 @@ class Context:
         self.stream = stream
         self.params = Params(n, L, eps, chi_max, mu, cg_tol, cg_maxit, sweep_tol, max_sweeps,
                              precision, learned_trunc, rf_oversample, rf_min_width, graphs,
-                             fd_order, rhs_form)
+                             fd_order, rhs_form, projection)
         h = c_void_p()
         st = lib().qtt_create(byref(h), device, c_void_p(stream.cuda_stream), byref(self.params))
         if st != 0:
@@ -329,6 +333,14 @@ class Context:
         st = lib().qtt_project(self.h, w1.h, w2.h, h, byref(v1), byref(v2), byref(cg), byref(sw))
         self._check(st, allow_not_converged=True)
         return MPS(self, v1.value), MPS(self, v2.value), cg.value, sw.value, st == 0
+
+    def project_spectral(self, w1: MPS, w2: MPS):
+        """The exact projection onto divergence-free fields (the penalty's
+        mu -> infinity limit) through Fourier space, re-encoded to the
+        context's (eps, chi_max): qtt_project_spectral."""
+        v1, v2 = c_void_p(), c_void_p()
+        self._check(lib().qtt_project_spectral(self.h, w1.h, w2.h, byref(v1), byref(v2)))
+        return MPS(self, v1.value), MPS(self, v2.value)
 
     def rk4_step(self, u1: MPS, u2: MPS, dt: float, nu: float):
         """In place: u1, u2 receive the new state.  Returns True if every
@@ -538,7 +550,8 @@ class Batch:
                             kw.pop("max_sweeps", 20), kw.pop("precision", PREC_FP64),
                             kw.pop("learned_trunc", LEARNED_OFF), kw.pop("rf_oversample", 8),
                             kw.pop("rf_min_width", 128), kw.pop("graphs", 0),
-                            kw.pop("fd_order", 0), kw.pop("rhs_form", 0))
+                            kw.pop("fd_order", 0), kw.pop("rhs_form", 0),
+                            kw.pop("projection", 0))
             if kw:
                 raise TypeError(f"unknown parameters {sorted(kw)}")
         h = c_void_p()

@@ -42,14 +42,15 @@ def test_params_layout_matches_header():
 #include <stddef.h>
 #include "qtt.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(qtt_params),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(qtt_params),
          offsetof(qtt_params, n), offsetof(qtt_params, L), offsetof(qtt_params, eps),
          offsetof(qtt_params, chi_max), offsetof(qtt_params, mu), offsetof(qtt_params, cg_tol),
          offsetof(qtt_params, cg_maxit), offsetof(qtt_params, sweep_tol),
          offsetof(qtt_params, max_sweeps), offsetof(qtt_params, precision),
          offsetof(qtt_params, learned_trunc), offsetof(qtt_params, rf_oversample),
          offsetof(qtt_params, rf_min_width), offsetof(qtt_params, graphs),
-         offsetof(qtt_params, fd_order), offsetof(qtt_params, rhs_form), QTT_MLP_PARAMS);
+         offsetof(qtt_params, fd_order), offsetof(qtt_params, rhs_form),
+         offsetof(qtt_params, projection), QTT_MLP_PARAMS);
   return 0;
 }
 """
@@ -104,6 +105,7 @@ def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
         ("qtt_mps_upload_packed", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 0, None)),
         ("qtt_tc_stats", [vp, vp, vp], (None,) * 3),
         ("qtt_tke_spectrum", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 4, None)),
+        ("qtt_project_spectral", [vp, vp, vp, vp, vp], (None,) * 5),
         ("qtt_mpo_diff", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp],
          (None, 1, 1, 0.1, None)),
         ("qtt_gemm_tf32x3", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
@@ -135,7 +137,7 @@ def test_parameter_validation_without_gpu(libpath):
     lib.qtt_create.restype = ctypes.c_int
 
     def params(**kw):
-        p = Params(5, 6.283185307179586, 1e-8, 16, 2.5e5, 1e-5, 100, 1e-5, 20, 0, 0, 8, 128, 0, 0, 0)
+        p = Params(5, 6.283185307179586, 1e-8, 16, 2.5e5, 1e-5, 100, 1e-5, 20, 0, 0, 8, 128, 0, 0, 0, 0)
         for k, v in kw.items():
             setattr(p, k, v)
         return p
@@ -144,7 +146,8 @@ def test_parameter_validation_without_gpu(libpath):
            dict(learned_trunc=1, precision=1), dict(rf_oversample=257), dict(rf_min_width=0),
            dict(n=0), dict(n=16), dict(chi_max=0), dict(cg_maxit=0), dict(max_sweeps=0),
            dict(eps=-1.0), dict(L=0.0), dict(fd_order=3), dict(fd_order=10), dict(fd_order=-2), dict(rhs_form=2),
-           dict(rhs_form=-1)]
+           dict(rhs_form=-1), dict(projection=2), dict(projection=-1),
+           dict(projection=1, rhs_form=1), dict(projection=1, n=14)]
     h = ctypes.c_void_p()
     for kw in bad:
         p = params(**kw)
