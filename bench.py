@@ -2,7 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision all|both|mixed|fp64]
                     [--impl reference] [--batched B] [--eager | --stage-graphs] [--tight] [--rhs explicit|implicit]
-                    [--projection penalty|spectral]
+                    [--projection penalty|spectral] [--workload jet|turbulence|taylor_green]
                     [--grid-bits n] [--chi c] [--no-cpu-baseline] [--no-e2e]
                     [--clocks-file PATH]
 
@@ -39,7 +39,10 @@ named forms take the implicit right-hand side.  "oz_gemm" and "tc_gemm"
 time the two tensor-core products alone.  --projection spectral replaces
 every stage's penalty solve by the exact projection through Fourier space
 (explicit right-hand side; with the default --precision the explicit mixed
-and FP64 forms are timed).
+and FP64 forms are timed).  --workload turbulence runs the decaying
+turbulence configuration instead (2^12 x 2^12, chi 128, eps 1e-7, Re 1e6,
+E(k) ~ k^4 exp(-2 (k/10)^2), unit kinetic energy), --workload taylor_green
+the Taylor-Green vortex (2^6, chi 16, eps 1e-12, nu 0.01, dt 1e-3).
 
 One JSON line is printed by rank 0.  With torchrun (N > 1) every rank runs
 its own trajectory on its own GPU (replicas: the method has no exchange
@@ -109,10 +112,47 @@ L2_FLUSH_BYTES = 256 << 20
 NCU_TRAFFIC = {"k_svd_cluster": 520448 + 118272, "k_svd_cluster_f32": 8479232 + 444672}
 
 
-def workload_state(n, seed):
+# The other configurations of the workload table: the decaying turbulence
+# (n = 12, chi = 128, eps = 1e-7, Re = 1e6, E(k) ~ k^4 exp(-2 (k/10)^2)) and the
+# Taylor-Green vortex (n = 6, chi = 16, eps = 1e-12, nu = 0.01, dt = 1e-3).
+WORKLOADS = {
+    "jet": WORKLOAD,
+    "turbulence": dict(WORKLOAD, workload="turbulence_2^12_chi128", n=12, chi_max=128, eps=1e-7,
+                       Re=1e6, ic="turbulence", k0=10.0),
+    "taylor_green": dict(WORKLOAD, workload="taylor_green_2^6_chi16", n=6, chi_max=16,
+                         eps=1e-12, Re=100.0, ic="taylor_green", dt=1e-3, dt_rule="1e-3"),
+}
+
+
+def metric_of(w):
+    if w["n"] == 10 and w["chi_max"] == 64:
+        return METRIC
+    return f"RK4 steps/s at 2^{w['n']}x2^{w['n']}, chi={w['chi_max']}"
+
+
+def workload_of(args):
+    """The workload of --workload with the --grid-bits / --chi overrides."""
+    w = dict(WORKLOADS[args.workload])
+    if args.n:
+        w["n"] = args.n
+    if args.chi:
+        w["chi_max"] = args.chi
+    if args.n or args.chi:
+        w["workload"] = f"{w['workload'].split('_2^')[0]}_2^{w['n']}_chi{w['chi_max']}"
+    return w
+
+
+def workload_state(w, seed):
+    """Initial velocity, grid spacing and time step of workload w (seeded)."""
     import qtt_inputs as I
-    u, dx = I.shear_jet(n, seed=seed)
-    dt = 0.1 * dx / float(np.abs(u[0]).max())
+    ic, n = w.get("ic", "jet"), w["n"]
+    if ic == "turbulence":
+        u, dx = I.decaying_turbulence(n, w["k0"], seed=seed)
+    elif ic == "taylor_green":
+        u, dx = I.taylor_green(n)
+    else:
+        u, dx = I.shear_jet(n, seed=seed)
+    dt = w["dt"] if "dt" in w else 0.1 * dx / float(np.abs(u[0]).max())
     return u, dx, dt
 
 
@@ -305,7 +345,7 @@ def _oracle_steps_child(wjson):
     w = json.loads(wjson)
     counter = FlopCounter().install()  # before the oracle binds numpy's functions
     from oracle import qtt as Q
-    u, dx, dt = workload_state(w["n"], w["seed"])
+    u, dx, dt = workload_state(w, w["seed"])
     p = Q.Params(eps=w["eps"], chi_max=w["chi_max"], mu=w["mu"], cg_tol=w["cg_tol"],
                  cg_maxit=w["cg_maxit"], sweep_tol=w["sweep_tol"], max_sweeps=w["max_sweeps"],
                  projection="spectral" if w.get("projection", 0) == 1 else "penalty")
@@ -344,10 +384,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    w = dict(WORKLOAD)
-    if args.n:
-        w["n"] = args.n
-        w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
+    w = workload_of(args)
     # the scheme of the main arm's headline form: the paper's implicit step
     # by default (an implicit oracle step takes about a minute on one core,
     # so two steps and no untimed one), the explicit step for the explicit
@@ -365,7 +402,7 @@ def run_reference(args):
     times, flops = oracle_steps(w, warm, timed)
     total = sum(times)
     value = timed / total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+    line = {"impl": "reference", "metric": metric_of(w), "value": value, "unit": "steps/s",
             "n_gpus": args.gpus, "steps": timed, "steps_requested": args.steps,
             "warmup": warm, "ms_per_step": 1e3 * total / timed, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -399,7 +436,7 @@ def make_form(P, w, prec, graphs, B, local, rank, rhs_form=None):
                           rhs_form=rhs, **solver_kwargs(w))]
     states, dts = [], []
     for i, c in enumerate(ctxs):
-        u, dx, dt_i = workload_state(w["n"], w["seed"] + rank * B + i)
+        u, dx, dt_i = workload_state(w, w["seed"] + rank * B + i)
         states.append([c.from_dense(f) for f in u])
         dts.append(dt_i)
     nu = 1.0 / w["Re"]
@@ -703,6 +740,10 @@ def main():
                          "the paper's implicit form in FP64; both: the first two")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
+    ap.add_argument("--workload", default="jet", choices=sorted(WORKLOADS),
+                    help="jet (default): the 2^10 shear jet at chi 64; turbulence: decaying "
+                         "turbulence at 2^12, chi 128, eps 1e-7, Re 1e6; taylor_green: 2^6, "
+                         "chi 16, eps 1e-12, nu 0.01, dt 1e-3")
     ap.add_argument("--grid-bits", "--n", dest="n", type=int, default=None,
                     help="override grid bits (testing only; under torchrun use --grid-bits)")
     ap.add_argument("--tight", action="store_true",
@@ -748,13 +789,7 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
-    w = dict(WORKLOAD)
-    if args.n:
-        w["n"] = args.n
-        w["workload"] = f"shear_jet_2^{args.n}_chi{w['chi_max']}"
-    if args.chi:
-        w["chi_max"] = args.chi
-        w["workload"] = f"shear_jet_2^{w['n']}_chi{args.chi}"
+    w = workload_of(args)
     if args.tight:
         w.update(cg_tol=1e-12, sweep_tol=1e-12, cg_maxit=500)
         w["workload"] += "_tight"
@@ -895,7 +930,7 @@ def main():
         tcg = tc_gemm_record(torch, forms[mixed_nm]["ctxs"][0], peaks)
         ozg = oz_gemm_record(torch, forms[mixed_nm]["ctxs"][0], peaks)
     hs = sums[head]
-    line = {"metric": METRIC, "value": hs["value"], "unit": "steps/s", "n_gpus": world,
+    line = {"metric": metric_of(w), "value": hs["value"], "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": hs["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": ("f64" if head.startswith("fp64") else

@@ -629,11 +629,36 @@ bool gemm_oz_eligible(const GemmF64& g) {
   return std::max(g.M, g.N) >= 32 && (double)g.M * g.N * g.K * (double)nb >= (double)(1 << 21);
 }
 
+// The library's own products: the shapes above, with the smallest K and the
+// smallest multiply-add count that go to the tensor cores settable for
+// measurement (QTT_OZ_MIN_K, default 16; QTT_OZ_MIN_LOG2, default 21).  The
+// kernel zero-fills a partial K chunk, so any K >= 1 is exact.
+bool gemm_oz_dispatch(const GemmF64& g) {
+  static const int min_k = [] {
+    const char* e = getenv("QTT_OZ_MIN_K");
+    const int v = e ? atoi(e) : 16;
+    return v < 1 ? 1 : v;
+  }();
+  static const int min_log2 = [] {
+    const char* e = getenv("QTT_OZ_MIN_LOG2");
+    const int v = e ? atoi(e) : 21;
+    return v < 10 ? 10 : (v > 40 ? 40 : v);
+  }();
+  if (g.K < min_k || g.M < 1 || g.N < 1) return false;
+  const long long nb = (long long)g.nb1 * g.nb2;
+  if (nb < 1 || nb > 65535) return false;
+  if (g.K > (nb == 1 ? 16 * 16 * kOzChunk : 16 * kOzChunk)) return false;
+  if (nb > 1 && g.K > kOzChunk && g.beta != 0.0) return false;
+  return std::max(g.M, g.N) >= 32 &&
+         (double)g.M * g.N * g.K * (double)nb >= ldexp(1.0, min_log2);
+}
+
 int gemm_oz_splits(const GemmF64& g) { return oz_plan(g).S; }
 
 void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext, double* scratch,
                     size_t scratch_n) {
-  if (!gemm_oz_eligible(g)) throw QttError(QTT_ERR_SHAPE, "emulated FP64 GEMM shape");
+  if (ext ? !gemm_oz_eligible(g) : !gemm_oz_dispatch(g))
+    throw QttError(QTT_ERR_SHAPE, "emulated FP64 GEMM shape");
   {
     const long long zb1 = g.nb1 - 1, zb2 = g.nb2 - 1;
     const long long ea = g.tA ? (long long)(g.K - 1) * g.lda + g.M : (long long)(g.M - 1) * g.lda + g.K;

@@ -41,6 +41,7 @@ bool gemm_small_eligible(const GemmF64& g);  // M <= 48, K <= 48, B not transpos
 // K slices: `scratch` must then hold that many M x N partial products
 // (summed in slice order into C).
 bool gemm_oz_eligible(const GemmF64& g);
+bool gemm_oz_dispatch(const GemmF64& g);
 int gemm_oz_splits(const GemmF64& g);
 void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext = false,
                     double* scratch = nullptr, size_t scratch_n = 0);

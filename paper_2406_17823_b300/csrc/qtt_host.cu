@@ -568,7 +568,7 @@ void gemm(const GemmF64& g, cudaStream_t s) {
     launch_gemm_f64(g, s);  // empty product or C = beta C
     return;
   }
-  if (t_gemm_emulate && gemm_oz_eligible(g)) {
+  if (t_gemm_emulate && gemm_oz_dispatch(g)) {
     const int S = gemm_oz_splits(g);
     if (S <= 1) {
       launch_gemm_oz(g, g_dev_err, s);
