@@ -568,6 +568,29 @@ void gemm(const GemmF64& g, cudaStream_t s) {
     launch_gemm_f64(g, s);  // empty product or C = beta C
     return;
   }
+  // A single product whose K exceeds what one emulated launch takes (16384:
+  // the environment contractions at chi >= 128, K = 3 chi^2) runs as K
+  // pieces on the tensor cores, accumulated in order into C (beta of the
+  // first piece, 1 after); QTT_OZ_SPLIT_K=0 leaves it to the FP64 GEMM.
+  static const bool split_long_k = [] {
+    const char* e = getenv("QTT_OZ_SPLIT_K");
+    return !(e && e[0] == '0');
+  }();
+  constexpr int kOzMaxK1 = 16384;
+  if (t_gemm_emulate && split_long_k && g.nb1 * g.nb2 == 1 && g.K > kOzMaxK1) {
+    GemmF64 h = g;
+    h.K = kOzMaxK1;
+    if (gemm_oz_dispatch(h)) {
+      for (int k0 = 0; k0 < g.K; k0 += kOzMaxK1) {
+        h.K = std::min(kOzMaxK1, g.K - k0);
+        h.A = g.A + (g.tA ? (long long)k0 * g.lda : k0);  // A stored K x M (tA) or M x K
+        h.B = g.B + (g.tB ? k0 : (long long)k0 * g.ldb);  // B stored N x K (tB) or K x N
+        h.beta = k0 == 0 ? g.beta : 1.0;
+        gemm(h, s);
+      }
+      return;
+    }
+  }
   if (t_gemm_emulate && gemm_oz_dispatch(g)) {
     const int S = gemm_oz_splits(g);
     if (S <= 1) {

@@ -88,3 +88,27 @@ def test_rk4_step_turbulence_chi128():
         ctx.rk4_step(g[0], g[1], dt, nu)
         for got, w in zip(g, want):
             assert rel(dense(ctx, got), w) <= tol
+
+
+def test_implicit_long_k_products_chi128(fields):
+    """The paper's implicit step at chi = 128 (n = 9, middle bonds at the
+    cap): its environment contractions have K = 3 chi^2 = 49152, past what
+    one emulated launch takes, so the mixed form runs them as K pieces on the
+    tensor cores accumulated in order.  Mixed within 1e-10 of the FP64 form
+    after one RK4 step (the emulated products are FP64-accurate; the FP64
+    implicit form is pinned to the oracle at chi = 16..64)."""
+    import paper_2406_17823_b300 as P
+    F, G, ops = fields
+    chi = 128
+    dx = 2 * np.pi / 2 ** N_BITS
+    dt, nu = 0.1 * dx / float(max(np.abs(F).max(), np.abs(G).max())), 1e-4
+    out = []
+    for prec in (0, 1):
+        ctx = P.Context(N_BITS, eps=1e-8, chi_max=chi, precision=prec,
+                        rhs_form=P.RHS_IMPLICIT)
+        g = [ctx.from_cores(Q.from_dense(f, 1e-8, chi)) for f in (F, G)]
+        assert max(g[0].bonds) == chi
+        ctx.rk4_step(g[0], g[1], dt, nu)
+        out.append([dense(ctx, x) for x in g])
+    for a, b in zip(out[1], out[0]):
+        assert rel(a, b) <= 1e-10
