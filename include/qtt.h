@@ -218,10 +218,11 @@ qtt_status qtt_hadamard(qtt_ctx ctx, qtt_mps a, qtt_mps b, double eps, int chi_m
 qtt_status qtt_compress(qtt_ctx ctx, qtt_mps inout, double eps, int chi_max);
 /* (v1, v2) = argmin mu |D_1 v1 + D_2 v2|^2 + |v - w|^2 / h^2 by DMRG-like
  * single-site sweeps with CG local solves (App. B, Eqs. "first", "second",
- * "big_LS"; Sec. II.C).  Initial guess w; bonds of w are kept.
+ * "big_LS"; Sec. II.C).  mu >= 0 is the penalty of this call (the steps use
+ * qtt_params.mu); h > 0.  Initial guess w; bonds of w are kept.
  * Synchronises; cg_iters / sweeps may be NULL.  Returns
  * QTT_ERR_NOT_CONVERGED (results still written) when a cap was hit. */
-qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1,
+qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, double mu, qtt_mps* v1,
                        qtt_mps* v2, int* cg_iters, int* sweeps);
 /* The exact discrete projection of (w1, w2) onto divergence-free fields:
  * the limit mu -> infinity of qtt_project, i.e. the orthogonal projection

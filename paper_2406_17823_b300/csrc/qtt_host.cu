@@ -2572,13 +2572,13 @@ void run_projection(qtt_ctx ctx, Projector& P, MpsPtr& V0, MpsPtr& V1, qtt_mps* 
   *v2 = V1.release();
 }
 
-void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qtt_mps* v2,
-                  int* cg_out, int* sw_out) {
+void project_impl(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, double mu, qtt_mps* v1,
+                  qtt_mps* v2, int* cg_out, int* sw_out) {
   Projector P;
   P.ctx = ctx;
   P.s = ctx->stream;
   P.n = w1->n;
-  P.c = ctx->p.mu * h * h;
+  P.c = mu * h * h;
   MpsPtr V0(copy_mps(ctx, w1)), V1(copy_mps(ctx, w2));
   P.V[0] = V0.get();
   P.V[1] = V1.get();
@@ -2767,7 +2767,7 @@ void project_stage(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, q
     if (sw_out) *sw_out = 0;
     return;
   }
-  project_impl(ctx, w1, w2, h, v1, v2, cg_out, sw_out);
+  project_impl(ctx, w1, w2, h, ctx->p.mu, v1, v2, cg_out, sw_out);
 }
 
 void stage_w(qtt_ctx ctx, qtt_mps u[2], qtt_mps b[2], double h, double nu, MpsPtr w[2],
@@ -3757,13 +3757,13 @@ qtt_status qtt_compress(qtt_ctx ctx, qtt_mps inout, double eps, int chi_max) {
   });
 }
 
-qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, qtt_mps* v1, qtt_mps* v2,
-                       int* cg_iters, int* sweeps) {
-  if (!v1 || !v2 || !(h > 0)) return QTT_ERR_ARG;
+qtt_status qtt_project(qtt_ctx ctx, qtt_mps w1, qtt_mps w2, double h, double mu, qtt_mps* v1,
+                       qtt_mps* v2, int* cg_iters, int* sweeps) {
+  if (!v1 || !v2 || !(h > 0) || !(mu >= 0)) return QTT_ERR_ARG;
   return guarded(ctx, [&]() -> qtt_status {
     check_mps(ctx, w1);
     check_mps(ctx, w2);
-    project_impl(ctx, w1, w2, h, v1, v2, cg_iters, sweeps);
+    project_impl(ctx, w1, w2, h, mu, v1, v2, cg_iters, sweeps);
     qtt_status st = check_device_errors(ctx);
     if (st != QTT_OK) return st;
     if (ctx->last_not_converged) {

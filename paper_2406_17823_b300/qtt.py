@@ -94,7 +94,8 @@ def lib():
                                 POINTER(vp)]),
             "qtt_hadamard": (c_int, [vp, vp, vp, c_double, c_int, POINTER(vp)]),
             "qtt_compress": (c_int, [vp, vp, c_double, c_int]),
-            "qtt_project": (c_int, [vp, vp, vp, c_double, POINTER(vp), POINTER(vp), ip, ip]),
+            "qtt_project": (c_int, [vp, vp, vp, c_double, c_double, POINTER(vp), POINTER(vp), ip,
+                                    ip]),
             "qtt_project_spectral": (c_int, [vp, vp, vp, POINTER(vp), POINTER(vp)]),
             "qtt_rk4_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
             "qtt_euler_step": (c_int, [vp, POINTER(vp), POINTER(vp), c_double, c_double]),
@@ -327,10 +328,13 @@ class Context:
                                        self.params.chi_max if chi_max is None else chi_max))
         return mps
 
-    def project(self, w1: MPS, w2: MPS, h: float):
+    def project(self, w1: MPS, w2: MPS, h: float, mu: float = None):
+        """The penalty projection (qtt_project) with penalty mu (default: the
+        context's)."""
         v1, v2 = c_void_p(), c_void_p()
         cg, sw = c_int(), c_int()
-        st = lib().qtt_project(self.h, w1.h, w2.h, h, byref(v1), byref(v2), byref(cg), byref(sw))
+        st = lib().qtt_project(self.h, w1.h, w2.h, h, self.params.mu if mu is None else mu,
+                               byref(v1), byref(v2), byref(cg), byref(sw))
         self._check(st, allow_not_converged=True)
         return MPS(self, v1.value), MPS(self, v2.value), cg.value, sw.value, st == 0
 

@@ -106,6 +106,8 @@ def test_newer_entry_points_reject_null_arguments_without_gpu(libpath):
         ("qtt_tc_stats", [vp, vp, vp], (None,) * 3),
         ("qtt_tke_spectrum", [vp, vp, vp, ctypes.c_int, vp], (None, None, None, 4, None)),
         ("qtt_project_spectral", [vp, vp, vp, vp, vp], (None,) * 5),
+        ("qtt_project", [vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp, vp],
+         (None, None, None, 1e-3, 2.5e5, None, None, None, None)),
         ("qtt_mpo_diff", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp],
          (None, 1, 1, 0.1, None)),
         ("qtt_gemm_tf32x3", [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,

@@ -182,6 +182,25 @@ def test_projection_parity(Q3, h, full):
         assert rel(gpu_dense(ctx, v1), vd[0]) < 1e-9
 
 
+def test_projection_mu_argument(Q3):
+    """qtt_project's own penalty (mu = 1e3 on a context made with the
+    paper's 2.5e5) against the oracle's projection with that mu."""
+    n, h = 5, 1e-2
+    ctx = ctx_for(Q3, n, cg_tol=1e-12, cg_maxit=500, sweep_tol=1e-12, max_sweeps=30)
+    X1, X2, dx = I.grid(n)
+    ops = Q.build_operators(n, dx)
+    w = [I.white_field(n, seed=55), I.white_field(n, seed=56)]
+    wq = [Q.from_dense(f, 0.0, FULL) for f in w]
+    p = Q.Params(eps=0.0, chi_max=FULL, mu=1e3, cg_tol=1e-12, cg_maxit=500, sweep_tol=1e-12,
+                 max_sweeps=30)
+    vo, info = Q.project(wq, h, p, ops)
+    v1, v2, cg, sw, ok = ctx.project(ctx.from_cores(wq[0]), ctx.from_cores(wq[1]), h, mu=1e3)
+    for g, o in zip((v1, v2), vo):
+        assert rel(gpu_dense(ctx, g), Q.to_dense(o)) < 1e-10
+    vd = Dn.project(w, h, 1e3, dx)
+    assert rel(gpu_dense(ctx, v1), vd[0]) < 1e-9
+
+
 # ------------------------------------------------------------ RK4 step
 def _rk4_case(Q3, n, u, dt, nu, steps, **pp):
     ctx = ctx_for(Q3, n, **pp)
