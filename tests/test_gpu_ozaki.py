@@ -222,3 +222,25 @@ def test_ozaki_projection_shape(ctx):
         + 4 * 2.0 ** -53 * np.abs(exact) + 1e-300
     assert float((np.abs(got - exact) / bound).max()) <= 1.0
 
+
+
+def test_ozaki_long_k_piece(ctx):
+    """The largest single product one launch takes (K = 16384, here 512 x 128:
+    the pieces of the chi = 128 environment contractions, K = 3 chi^2 split
+    in 16384s): 256 K chunks over 16 K slices summed in order; 6 sampled rows
+    bit for bit against the replica, every element within the error bound."""
+    import torch
+    M, N, K = 512, 128, 16384
+    rng = np.random.default_rng(16384)
+    A = rng.standard_normal((M, K)) * np.logspace(0, -6, K)[None, :]
+    B = rng.standard_normal((K, N))
+    got = ctx.gemm_ozaki(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
+    rows = np.sort(rng.choice(M, 6, replace=False))
+    want, _, _ = replica(A[rows], B.T.copy(), 1.0, 0.0, None, nb=1)
+    assert np.array_equal(got[rows], want)
+    ea, _ = scales(A)
+    eb, _ = scales(B.T.copy())
+    exact = A @ B
+    bound = K * 2.0 ** -53 * (np.ldexp(1.0, ea[:, None] + eb[None, :]) + np.abs(A) @ np.abs(B)) \
+        + 4 * 2.0 ** -53 * np.abs(exact) + 1e-300
+    assert float((np.abs(got - exact) / bound).max()) <= 1.0
