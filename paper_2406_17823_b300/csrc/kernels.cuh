@@ -126,6 +126,23 @@ void launch_hadamard_mpo(const double* B, int cbl, int cbr, const double* W, int
                          int order, double* raw, double* k2, double* kr2, cudaStream_t s);
 // out[b][s][a] = in[a][s][b]   (capacities)
 void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaStream_t s);
+
+// A small constant matrix with few non-zeros (an MPO core reshaped as
+// [(s q)][(p t)] or [(s p)][(q t)]), rows in compressed form; host-built.
+constexpr int kSparseMaxRows = 64;
+constexpr int kSparseMaxNnz = 96;
+struct SparseRows {
+  int rows = 0, cols = 0, nnz = -1;  // nnz < 0: not stored (too many entries)
+  int ptr[kSparseMaxRows + 1];
+  int col[kSparseMaxNnz];
+  double val[kSparseMaxNnz];
+};
+// C_z = A B_z for z < nb (A rows x cols as `sp`; B_z cols x N with row
+// stride ldb, batch stride sB; C_z rows x N, ldc, sC): each output element
+// the FMA chain over A's non-zeros of its row in column order, which is
+// the dense product's chain without its exact zero terms.
+void launch_sparse_rows(const SparseRows& sp, const double* B, int ldb, long long sB, double* C,
+                        int ldc, long long sC, int N, int nb, cudaStream_t s);
 void launch_set_int(int* p, int v, cudaStream_t s);
 void launch_fill_int(int* p, int n, int v, cudaStream_t s);
 // out[b] = sum_t src[t][b] * mul[t][b] for 0 < b < nb-1, out[0] = out[nb-1] = 1

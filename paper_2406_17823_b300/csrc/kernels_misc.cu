@@ -391,6 +391,38 @@ void launch_core_transpose(const double* in, int Ca, int Cb, double* out, cudaSt
   post_launch("k_core_transpose", s);
 }
 
+__global__ void k_sparse_rows(const double* __restrict__ B, int ldb, long long sB,
+                              double* __restrict__ C, int ldc, long long sC, int N,
+                              long long total, const __grid_constant__ SparseRows sp) {
+  const long long per = (long long)sp.rows * N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long z = e / per;
+    const int rem = (int)(e - z * per);
+    const int r = rem / N, j = rem - r * N;
+    const double* Bz = B + z * sB + j;
+    double acc = 0.0;
+    for (int q = sp.ptr[r]; q < sp.ptr[r + 1]; q++) acc = fma(sp.val[q], Bz[(long long)sp.col[q] * ldb], acc);
+    C[z * sC + (long long)r * ldc + j] = acc;
+  }
+}
+
+void launch_sparse_rows(const SparseRows& sp, const double* B, int ldb, long long sB, double* C,
+                        int ldc, long long sC, int N, int nb, cudaStream_t s) {
+  if (sp.nnz < 0 || sp.rows < 1 || sp.rows > kSparseMaxRows || sp.cols < 1 || N < 1 || nb < 1 ||
+      ldb < N || ldc < N)
+    throw QttError(QTT_ERR_SHAPE, "sparse-row product shape");
+  check_range(B, (long long)(nb - 1) * sB + (long long)(sp.cols - 1) * ldb + N, sizeof(double),
+              "sparse rows B");
+  check_range(C, (long long)(nb - 1) * sC + (long long)(sp.rows - 1) * ldc + N, sizeof(double),
+              "sparse rows C");
+  const long long total = (long long)nb * sp.rows * N;
+  const int blocks = grid_for(total);
+  pre_launch(s);
+  k_sparse_rows<<<blocks, 256, 0, s>>>(B, ldb, sB, C, ldc, sC, N, total, sp);
+  post_launch("k_sparse_rows", s, 2.0 * (double)nb * N * (sp.nnz > 0 ? sp.nnz : 0));
+}
+
 void launch_set_int(int* p, int v, cudaStream_t s) {
   pre_launch(s);
   k_set_int<<<1, 1, 0, s>>>(p, v);

@@ -173,6 +173,10 @@ struct qtt_mpo_s {
   double* raw(int k) const { return dev + off[k]; }
   double* k2(int k) const { return dev_k2 + off[k]; }
   double* kr2(int k) const { return dev_kr2 + off[k]; }
+  // the non-zeros of k2 / kr2 per core (host-built MPOs only)
+  std::vector<SparseRows> sk2, skr2;
+  const SparseRows* sp_k2(int k) const { return k < (int)sk2.size() ? &sk2[k] : nullptr; }
+  const SparseRows* sp_kr2(int k) const { return k < (int)skr2.size() ? &skr2[k] : nullptr; }
 };
 
 // A stage's right-hand side captured as a CUDA graph: graph-owned input
@@ -653,6 +657,24 @@ void gemm(const GemmF64& g, cudaStream_t s) {
   gemm_run(g, ch.tile, ch.S, s);
 }
 
+// C_z = A B_z with A one MPO core reshaped as k2 or kr2 and shared by the
+// batch: the sparse-row kernel over the core's non-zeros when they were
+// stored (the dense product's FMA chain without its zero terms: the same
+// values); QTT_MPO_SPARSE=0 keeps every such product on the GEMM.
+void mpo_gemm(const GemmF64& g, const SparseRows* sp, cudaStream_t s) {
+  static const bool on = [] {
+    const char* e = getenv("QTT_MPO_SPARSE");
+    return !(e && e[0] == '0');
+  }();
+  if (on && sp && sp->nnz >= 0 && sp->rows == g.M && sp->cols == g.K && g.tA == 0 &&
+      g.tB == 0 && g.nb2 == 1 && g.sA1 == 0 && g.alpha == 1.0 && g.beta == 0.0 && !g.skip &&
+      g.M > 0 && g.N > 0 && g.nb1 > 0) {
+    launch_sparse_rows(*sp, g.B, g.ldb, g.sB1, g.C, g.ldc, g.sC1, g.N, g.nb1, s);
+    return;
+  }
+  gemm(g, s);
+}
+
 // Split-K product with the fixed rule (Gram matrices of long factors).
 void gemm_splitk(const GemmF64& g, cudaStream_t s) { gemm(g, s); }
 
@@ -781,6 +803,35 @@ qtt_mpo upload_mpo(qtt_ctx ctx, const HostMpo& hm) {
             // kr2[(s p)][(q t)]
             kr2[m->off[k] + (size_t)(s * wl + p) * (wr * 4) + (q * 4 + t)] = v;
           }
+  }
+  // compressed rows of k2 ((s q) x (p t)) and kr2 ((s p) x (q t)) for the
+  // sparse-row product; a core with too many non-zeros keeps nnz = -1
+  auto compress_rows = [](const double* M, int rows, int cols) {
+    SparseRows sp;
+    sp.rows = rows;
+    sp.cols = cols;
+    if (rows > kSparseMaxRows) return sp;
+    int nnz = 0;
+    sp.ptr[0] = 0;
+    for (int r = 0; r < rows; r++) {
+      for (int c = 0; c < cols; c++) {
+        const double v = M[(size_t)r * cols + c];
+        if (v == 0.0) continue;
+        if (nnz == kSparseMaxNnz) return sp;
+        sp.col[nnz] = c;
+        sp.val[nnz++] = v;
+      }
+      sp.ptr[r + 1] = nnz;
+    }
+    sp.nnz = nnz;
+    return sp;
+  };
+  m->sk2.resize(hm.n);
+  m->skr2.resize(hm.n);
+  for (int k = 0; k < hm.n; k++) {
+    const int wl = hm.w[k], wr = hm.w[k + 1];
+    m->sk2[k] = compress_rows(k2.data() + m->off[k], 4 * wr, 4 * wl);
+    m->skr2[k] = compress_rows(kr2.data() + m->off[k], 4 * wl, 4 * wr);
   }
   cudaSetDevice(ctx->device);
   if (cudaMalloc((void**)&m->dev, 3 * o * sizeof(double)) != cudaSuccess) {
@@ -1934,7 +1985,7 @@ struct Projector {
       g.nb1 = ci * cb; g.nb2 = 1;
       g.sB1 = (long long)wl * 4 * ce1; g.sC1 = (long long)4 * wr * ce1;
       g.alpha = 1.0;
-      gemm(g, s);
+      mpo_gemm(g, T.Dm->sp_k2(k), s);
       // T3[(a so)][c'][(p' e')] = B_so[c][c']^T T2[(a c)][so][(p' e')], batch (a, so)
       GemmF64 h{};
       h.A = Bc; h.B = t2p; h.C = t3p;
@@ -1966,7 +2017,7 @@ struct Projector {
       g.nb1 = ci; g.nb2 = 1;
       g.sB1 = (long long)wl * 4 * cb1 * ce1; g.sC1 = (long long)4 * wr * cb1 * ce1;
       g.alpha = 1.0;
-      gemm(g, s);
+      mpo_gemm(g, T.Dm->sp_k2(k), s);
     }
   }
 
@@ -2001,7 +2052,7 @@ struct Projector {
       g.nb1 = ci1 * cb1; g.nb2 = 1;
       g.sB1 = (long long)wr * 4 * ce; g.sC1 = (long long)4 * wl * ce;
       g.alpha = 1.0;
-      gemm(g, s);
+      mpo_gemm(g, T.Dm->sp_kr2(k), s);
       // T3[(a' so)][c][(p e)] = B_so[c][c'] T2[(a' c')][so][(p e)], batch (a', so)
       GemmF64 h{};
       h.A = Bc; h.B = t2p; h.C = t3p;
@@ -2033,7 +2084,7 @@ struct Projector {
       g.nb1 = ci1; g.nb2 = 1;
       g.sB1 = (long long)wr * 4 * cb * ce; g.sC1 = (long long)4 * wl * cb * ce;
       g.alpha = 1.0;
-      gemm(g, s);
+      mpo_gemm(g, T.Dm->sp_kr2(k), s);
     }
     // R[k][a][...] = ViT[(a' so)][a]^T T3[(a' so)][...]
     const int n0 = cb * wl * ce;
@@ -2056,7 +2107,7 @@ struct Projector {
     g.nb1 = ci1; g.nb2 = 1;
     g.sA1 = 0; g.sB1 = (long long)wr * 4 * cx; g.sC1 = (long long)4 * wl * cx;
     g.alpha = 1.0;
-    gemm(g, s);
+    mpo_gemm(g, T.P->sp_kr2(k), s);
     GemmF64 g3 = gemm_plain(ViT, t2p, T.R[k].p, ci, wl * cx, ci1 * 4, ci, wl * cx, wl * cx);
     g3.tA = 1;
     gemm(g3, s);
@@ -2074,7 +2125,7 @@ struct Projector {
     g.nb1 = ci; g.nb2 = 1;
     g.sA1 = 0; g.sB1 = (long long)wl * 4 * cx1; g.sC1 = (long long)4 * wr * cx1;
     g.alpha = 1.0;
-    gemm(g, s);
+    mpo_gemm(g, T.P->sp_k2(k), s);
     GemmF64 g3 = gemm_plain(V[i]->core(k), t2p, T.L[k + 1].p, ci1, wr * cx1, 4 * ci, ci1,
                             wr * cx1, wr * cx1);
     g3.tA = 1;
@@ -2106,7 +2157,7 @@ struct Projector {
         g.nb1 = ci1; g.nb2 = 1;
         g.sA1 = 0; g.sB1 = (long long)wr * 4 * cj; g.sC1 = (long long)4 * wl * cj;
         g.alpha = 1.0;
-        gemm(g, s);
+        mpo_gemm(g, Kij->sp_kr2(k), s);
         // RE[k][a][(p x)] = ViT[(b s)][a]^T * T2[(b s)][(p x)]
         GemmF64 g3 = gemm_plain(ViT, t2p, RE[i][j][k].p, ci, wl * cj, ci1 * 4, ci, wl * cj, wl * cj);
         g3.tA = 1;
@@ -2149,7 +2200,7 @@ struct Projector {
         g.nb1 = ci; g.nb2 = 1;
         g.sA1 = 0; g.sB1 = (long long)wl * 4 * cj1; g.sC1 = (long long)4 * wr * cj1;
         g.alpha = 1.0;
-        gemm(g, s);
+        mpo_gemm(g, Kij->sp_k2(k), s);
         // LE[k+1][b][(q z)] = Vi[(a s)][b]^T * T2[(a s)][(q z)]
         GemmF64 g3 = gemm_plain(V[i]->core(k), t2p, LE[i][j][k + 1].p, ci1, wr * cj1, 4 * ci, ci1,
                                 wr * cj1, wr * cj1);
