@@ -10,7 +10,7 @@ and Tropp, SIAM Review 53 (2011), Algorithm 4.1: Y = M Omega, Q = orth(Y),
 B = Q^T M, SVD of the small B) of width w = predicted rank + oversampling.
 The weight of M outside span(Q), |M|_F^2 - |B|_F^2 = |M - Q Q^T M|_F^2, is
 the error estimate: when it exceeds ACCEPT eps^2 |M|_F^2 (ACCEPT = 0.1: the
-sketch may miss at most 1% of the bond's truncation budget) the bond falls
+sketch may miss at most a tenth of the bond's truncation budget) the bond falls
 back to the full SVD; otherwise the eps rule runs on the singular values of
 B with that outside weight counted as discarded, and chi_max caps the rank.  The
 estimate is a difference of two sums of squares, so its rounding floor is
