@@ -662,3 +662,25 @@ def test_qtt_spectral_projection_and_rk4_equal_dense():
     vt, _ = Q.project_spectral(uq, Q.Params(eps=eps, chi_max=FULL), ops)
     for i in range(2):
         assert rel(Q.to_dense(vt[i]), ve[i]) <= math.sqrt(n - 1) * eps
+
+
+def test_qtt_euler_and_rk2_spectral_equal_dense():
+    """Untruncated QTT Euler and midpoint RK2 steps with the spectral
+    projection equal the dense steps built from the exact projection:
+    P(u - dt B(u)) and P(u - dt B(P(u - dt/2 B(u))))."""
+    n, dt, nu = 4, 1e-2, 0.02
+    _, _, dx = I.grid(n)
+    ops = Q.build_operators(n, dx)
+    u = [I.random_field(n, seed=70), I.random_field(n, seed=71)]
+    uq = [Q.from_dense(f, 0.0, FULL) for f in u]
+    p = Q.Params(eps=0.0, chi_max=FULL, projection="spectral")
+    B = Dn.rhs_B(u, nu, dx)
+    e_ref = Dn.project_exact([u[i] - dt * B[i] for i in range(2)], dx)
+    um = Dn.project_exact([u[i] - 0.5 * dt * B[i] for i in range(2)], dx)
+    Bm = Dn.rhs_B(um, nu, dx)
+    r_ref = Dn.project_exact([u[i] - dt * Bm[i] for i in range(2)], dx)
+    e = Q.euler_step(uq, dt, nu, p, ops)
+    r = Q.rk2_step(uq, dt, nu, p, ops)
+    for i in range(2):
+        assert rel(Q.to_dense(e[i]), e_ref[i]) < 1e-12
+        assert rel(Q.to_dense(r[i]), r_ref[i]) < 1e-12
