@@ -593,7 +593,7 @@ struct OzPlan {
   int BN, tiles, nch, S, kslice;
 };
 
-OzPlan oz_plan(const GemmF64& g) {
+OzPlan oz_plan(const GemmF64& g, int max_s) {
   auto padded = [](int ra, int rb) {
     const int bn = oz_bn(rb);
     return (double)((ra + kOzM - 1) / kOzM) * kOzM * (double)((rb + bn - 1) / bn) * bn;
@@ -608,8 +608,14 @@ OzPlan oz_plan(const GemmF64& g) {
   if ((long long)g.nb1 * g.nb2 == 1 && p.nch > 1) {
     // (a CTA over several chunks accumulates in its output, so beta != 0
     // takes the slice sum)
-    const int want = g.beta != 0.0 ? 16 : p.tiles < 74 ? (148 + p.tiles - 1) / p.tiles : 1;
-    const int lo = (p.nch + 15) / 16, hi = std::min(16, p.nch);
+    // max_s > 16 (the library's own products, when their scratch allows):
+    // as many slices as keep every item on its own SM
+    int want;
+    if (max_s > 16)
+      want = p.tiles < 74 ? std::max(2, 148 / p.tiles) : g.beta != 0.0 ? 16 : 1;
+    else
+      want = g.beta != 0.0 ? 16 : p.tiles < 74 ? (148 + p.tiles - 1) / p.tiles : 1;
+    const int lo = (p.nch + 15) / 16, hi = std::min(std::max(16, max_s), p.nch);
     int S = std::max(lo, std::min(want, hi));
     const int cps = (p.nch + S - 1) / S;
     p.S = (p.nch + cps - 1) / cps;
@@ -653,10 +659,10 @@ bool gemm_oz_dispatch(const GemmF64& g) {
          (double)g.M * g.N * g.K * (double)nb >= ldexp(1.0, min_log2);
 }
 
-int gemm_oz_splits(const GemmF64& g) { return oz_plan(g).S; }
+int gemm_oz_splits(const GemmF64& g, int max_s) { return oz_plan(g, max_s).S; }
 
 void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext, double* scratch,
-                    size_t scratch_n) {
+                    size_t scratch_n, int max_s) {
   if (ext ? !gemm_oz_eligible(g) : !gemm_oz_dispatch(g))
     throw QttError(QTT_ERR_SHAPE, "emulated FP64 GEMM shape");
   {
@@ -669,7 +675,7 @@ void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext, double
     check_range(g.C, zb1 * g.sC1 + zb2 * g.sC2 + ec, sizeof(double), ext ? "ext oz gemm C" : "oz gemm C");
   }
   oz_attr_once();
-  const OzPlan pl = oz_plan(g);
+  const OzPlan pl = oz_plan(g, ext ? 16 : max_s);
   // op(A) (M x K): element (m, k); op(B)^T (N x K): element (n, k)
   OzOperand opA{g.A, g.sA1, g.sA2, g.tA ? 1 : (long long)g.lda, g.tA ? (long long)g.lda : 1, g.M};
   OzOperand opB{g.B, g.sB1, g.sB2, g.tB ? (long long)g.ldb : 1, g.tB ? 1 : (long long)g.ldb, g.N};

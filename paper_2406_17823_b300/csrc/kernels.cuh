@@ -42,9 +42,13 @@ bool gemm_small_eligible(const GemmF64& g);  // M <= 48, K <= 48, B not transpos
 // (summed in slice order into C).
 bool gemm_oz_eligible(const GemmF64& g);
 bool gemm_oz_dispatch(const GemmF64& g);
-int gemm_oz_splits(const GemmF64& g);
+// max_s: the most K slices the plan may take (16, and always 16 for the
+// public entry point; the library's own products up to 64 when their
+// scratch holds that many partial products).
+int gemm_oz_splits(const GemmF64& g, int max_s = 16);
+constexpr long long kOzWideSplitMN = 1 << 16;  // outputs that may take up to 64 slices
 void launch_gemm_oz(const GemmF64& g, int* err, cudaStream_t s, bool ext = false,
-                    double* scratch = nullptr, size_t scratch_n = 0);
+                    double* scratch = nullptr, size_t scratch_n = 0, int max_s = 16);
 void launch_scale(const GemmF64& g, cudaStream_t s);  // C = beta C
 void launch_sum_slices(const double* P, int S, int M, int N, double* C, int ldc, double alpha,
                        double beta, const int* skip, cudaStream_t s, bool c_ext = false);

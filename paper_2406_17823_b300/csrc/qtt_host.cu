@@ -596,9 +596,20 @@ void gemm(const GemmF64& g, cudaStream_t s) {
     }
   }
   if (t_gemm_emulate && gemm_oz_dispatch(g)) {
-    const int S = gemm_oz_splits(g);
+    // an unbatched product with a small output (M N <= kOzWideSplitMN) and
+    // few output tiles may deal its K chunks over up to 64 slices (the
+    // public entry point's plan stops at 16): a rule of the shape alone, so
+    // eager and captured runs take the same plan, and the projection's
+    // captured scratch is sized for it; QTT_OZ_MAX_SPLITS=16 keeps 16
+    static const int env_max = [] {
+      const char* e = getenv("QTT_OZ_MAX_SPLITS");
+      const int v = e ? atoi(e) : 64;
+      return v < 16 ? 16 : (v > 64 ? 64 : v);
+    }();
+    const int max_s = (long long)g.M * g.N <= kOzWideSplitMN ? env_max : 16;
+    const int S = gemm_oz_splits(g, max_s);
     if (S <= 1) {
-      launch_gemm_oz(g, g_dev_err, s);
+      launch_gemm_oz(g, g_dev_err, s, false, nullptr, 0, max_s);
       return;
     }
     // K slices: partial products in the caller's split-K scratch (inside
@@ -614,7 +625,7 @@ void gemm(const GemmF64& g, cudaStream_t s) {
       P = own.p;
       cap = need;
     }
-    launch_gemm_oz(g, g_dev_err, s, false, P, cap);
+    launch_gemm_oz(g, g_dev_err, s, false, P, cap, max_s);
     return;
   }
   // QTT_GEMM_TILE=t: every product on tile t with the fixed K split (a
@@ -2538,7 +2549,12 @@ void run_projection(qtt_ctx ctx, Projector& P, MpsPtr& V0, MpsPtr& V1, qtt_mps* 
                     qtt_mps* v2, int* cg_out, int* sw_out) {
   const int n = P.n;
   P.alloc();
-  DBuf<double> arena(ctx->dev_loops ? 4 * 16 * P.maxout : 0, P.s);  // a quarter per matvec chain
+  // a quarter per matvec chain; a quarter holds 16 split-K slices of the
+  // largest output, or 64 of an output up to kOzWideSplitMN (the emulated
+  // GEMM's wide split)
+  const size_t quarter = std::max<size_t>(16 * P.maxout,
+                                          64 * std::min<size_t>(P.maxout, kOzWideSplitMN));
+  DBuf<double> arena(ctx->dev_loops ? 4 * quarter : 0, P.s);
   struct ScratchScope {  // split-K scratch of a captured step's loop bodies
     explicit ScratchScope(DBuf<double>& a) {
       t_gemm_scratch = a.p;
